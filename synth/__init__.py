@@ -1,0 +1,361 @@
+"""Seeded synthetic inputs for the uncertain-signed-triangle path.
+
+This module is shared by the CUDA path's tests and benchmark and by the
+CPU oracle's tests.  It only draws graphs and edge-sign probabilities; it
+contains none of the method's arithmetic (no balance probabilities, no
+thresholds, no triangle listing).
+
+The paper's datasets (SNAP/Konect graphs with synthetic sign probabilities,
+Sec. 7.1, Table 2) are not available, so these generators stand in for them:
+
+* ``er_graph``     -- Erdos-Renyi G(n, m): m distinct unordered pairs.
+* ``chung_lu``     -- power-law expected-degree graph (Chung-Lu).
+* ``rmat``         -- R-MAT / Kronecker edge draws, symmetrised, deduplicated.
+* ``k_uniform``    -- 16-bit fixed-point probabilities k ~ U{0..65536}.
+* ``quantise``     -- real p in [0,1] -> k = round-half-even(p * 65536).
+* ``p_beta`` / ``p_beta_mixture`` / ``p_uniform_f32`` -- the P+ distributions
+  the paper uses (uniform, Beta(0.5,0.5), sign-biased Betas; Sec. 7.1).
+* ``ego_nets``     -- batches of induced ego-net subgraphs of a parent graph.
+* ``bfs_induced``  -- induced subgraph grown in BFS order to a target size.
+
+Every graph is returned as ``(src, dst)`` uint32 arrays of an undirected
+simple graph (no self-loops, no duplicate pairs); the edge index in these
+arrays is the edge id ``eid`` used everywhere else.
+"""
+from __future__ import annotations
+
+import numpy as np
+
+__all__ = [
+    "rng", "er_graph", "chung_lu", "rmat", "k_uniform", "quantise",
+    "p_beta", "p_beta_mixture", "p_uniform_f32", "ego_nets", "bfs_induced",
+    "csr_undirected", "random_orientation", "Graph", "config_graph",
+]
+
+K_ONE = 65536  # fixed-point denominator: p = k / 65536, k in [0, 65536]
+
+
+def rng(seed: int) -> np.random.Generator:
+    return np.random.Generator(np.random.PCG64(seed))
+
+
+def _sorted_unique(keys: np.ndarray) -> np.ndarray:
+    """Sorted distinct values (sort + adjacent compare; faster than np.unique here)."""
+    keys = np.sort(keys, kind="stable")
+    if keys.size == 0:
+        return keys
+    keep = np.empty(keys.size, dtype=bool)
+    keep[0] = True
+    np.not_equal(keys[1:], keys[:-1], out=keep[1:])
+    return keys[keep]
+
+
+def _dedup_pairs(a: np.ndarray, b: np.ndarray, n: int):
+    """Canonicalise to (min, max), drop self-loops and duplicate pairs.
+
+    Keeps the first draw of each pair and returns pairs sorted by (min, max).
+    """
+    a = a.astype(np.int64)
+    b = b.astype(np.int64)
+    keep = a != b
+    a, b = a[keep], b[keep]
+    lo = np.minimum(a, b)
+    hi = np.maximum(a, b)
+    key = _sorted_unique(lo * np.int64(n) + hi)
+    return (key // n).astype(np.uint32), (key % n).astype(np.uint32)
+
+
+def er_graph(n: int, m: int, seed: int, shuffle_endpoints: bool = True):
+    """G(n, m): m distinct unordered pairs drawn uniformly, no self-loops.
+
+    The edges come out in a random order and, with ``shuffle_endpoints``,
+    with a random endpoint first, so consumers must canonicalise.
+    """
+    if m > n * (n - 1) // 2:
+        raise ValueError("m exceeds the number of vertex pairs")
+    g = rng(seed)
+    keys = np.empty(0, dtype=np.int64)
+    while keys.size < m:
+        need = int((m - keys.size) * 1.3) + 16
+        a = g.integers(0, n, size=need, dtype=np.int64)
+        b = g.integers(0, n, size=need, dtype=np.int64)
+        ok = a != b
+        lo = np.minimum(a[ok], b[ok])
+        hi = np.maximum(a[ok], b[ok])
+        new = lo * n + hi
+        allk = np.concatenate([keys, new])
+        _, first = np.unique(allk, return_index=True)
+        keys = allk[np.sort(first)]
+    keys = keys[:m]
+    src = (keys // n).astype(np.uint32)
+    dst = (keys % n).astype(np.uint32)
+    if shuffle_endpoints:
+        flip = g.random(m) < 0.5
+        src, dst = np.where(flip, dst, src), np.where(flip, src, dst)
+    return src, dst
+
+
+def chung_lu(n: int, gamma: float, mean_deg: float, max_deg: float, seed: int):
+    """Chung-Lu power-law graph.
+
+    Expected-degree weights w_i = c * (i + 1)^(-1/(gamma-1)), scaled so the
+    mean is ``mean_deg`` after capping every weight at ``max_deg`` (the scale
+    is solved by bisection).  n * mean_deg / 2 endpoint pairs are drawn with
+    probability proportional to w (inverse-CDF sampling); self-loops and
+    repeated pairs are dropped, so the realised edge count is a little below
+    the nominal one and is whatever the returned arrays hold.
+    """
+    g = rng(seed)
+    base = (np.arange(n, dtype=np.float64) + 1.0) ** (-1.0 / (gamma - 1.0))
+    lo, hi = 0.0, mean_deg * n / base.sum() * 1e4
+    for _ in range(200):
+        mid = 0.5 * (lo + hi)
+        if np.minimum(base * mid, max_deg).mean() < mean_deg:
+            lo = mid
+        else:
+            hi = mid
+    w = np.minimum(base * hi, max_deg)
+    cdf = np.cumsum(w)
+    cdf /= cdf[-1]
+    draws = int(round(n * mean_deg / 2.0))
+    a = np.searchsorted(cdf, g.random(draws), side="right")
+    b = np.searchsorted(cdf, g.random(draws), side="right")
+    a = np.minimum(a, n - 1)
+    b = np.minimum(b, n - 1)
+    return _dedup_pairs(a, b, n)
+
+
+def rmat(scale: int, edge_factor: int, a: float, b: float, c: float, seed: int,
+         chunk: int = 1 << 24):
+    """R-MAT edge draws on 2^scale vertices, symmetrised and deduplicated.
+
+    Each of the 2^scale * edge_factor draws picks one quadrant per level
+    with probabilities (a, b, c, 1-a-b-c).  Vertex labels are not permuted.
+    """
+    g = rng(seed)
+    n = 1 << scale
+    total = n * edge_factor
+    keys = []
+    ab, abc = a + b, a + b + c
+    for start in range(0, total, chunk):
+        cnt = min(chunk, total - start)
+        u = np.zeros(cnt, dtype=np.int64)
+        v = np.zeros(cnt, dtype=np.int64)
+        for _ in range(scale):
+            r = g.random(cnt, dtype=np.float32)
+            ubit = r >= ab                      # quadrants c, d
+            vbit = ((r >= a) & (r < ab)) | (r >= abc)  # quadrants b, d
+            u = (u << 1) | ubit
+            v = (v << 1) | vbit
+        keep = u != v
+        u, v = u[keep], v[keep]
+        lo = np.minimum(u, v)
+        hi = np.maximum(u, v)
+        keys.append(_sorted_unique(lo * n + hi))
+    key = _sorted_unique(np.concatenate(keys))
+    return (key // n).astype(np.uint32), (key % n).astype(np.uint32)
+
+
+def k_uniform(m: int, seed: int) -> np.ndarray:
+    """k ~ Uniform{0, ..., 65536} (all 65,537 fixed-point values)."""
+    return rng(seed).integers(0, K_ONE + 1, size=m, dtype=np.int64).astype(np.uint32)
+
+
+def quantise(p: np.ndarray) -> np.ndarray:
+    """k = round-half-even(p * 65536), clamped to [0, 65536]."""
+    k = np.rint(np.asarray(p, dtype=np.float64) * K_ONE)
+    return np.clip(k, 0, K_ONE).astype(np.uint32)
+
+
+def p_beta(m: int, alpha: float, beta: float, seed: int) -> np.ndarray:
+    return rng(seed).beta(alpha, beta, size=m)
+
+
+def p_beta_mixture(m: int, seed: int, w: float = 0.5,
+                   ab1=(8.0, 2.0), ab2=(2.0, 8.0)) -> np.ndarray:
+    """w * Beta(ab1) + (1 - w) * Beta(ab2): sign-confident bimodal P+."""
+    g = rng(seed)
+    pick = g.random(m) < w
+    x1 = g.beta(ab1[0], ab1[1], size=m)
+    x2 = g.beta(ab2[0], ab2[1], size=m)
+    return np.where(pick, x1, x2)
+
+
+def p_uniform_f32(m: int, seed: int) -> np.ndarray:
+    return rng(seed).random(m, dtype=np.float32)
+
+
+def random_orientation(src, dst, seed: int):
+    """Swap the endpoints of a random half of the edges (same graph)."""
+    flip = rng(seed).random(len(src)) < 0.5
+    return np.where(flip, dst, src).astype(np.uint32), np.where(flip, src, dst).astype(np.uint32)
+
+
+def csr_undirected(n: int, src, dst):
+    """Undirected adjacency (both directions) as (offsets int64, nbr uint32, eid int64)."""
+    m = len(src)
+    a = np.concatenate([src, dst]).astype(np.int64)
+    b = np.concatenate([dst, src]).astype(np.int64)
+    e = np.concatenate([np.arange(m), np.arange(m)]).astype(np.int64)
+    order = np.lexsort((b, a))
+    a, b, e = a[order], b[order], e[order]
+    off = np.zeros(n + 1, dtype=np.int64)
+    np.add.at(off, a + 1, 1)
+    off = np.cumsum(off)
+    return off, b.astype(np.uint32), e
+
+
+def ego_nets(n: int, src, dst, count: int, smin: int, smax: int, seed: int):
+    """Seeded batch of induced ego-net subgraphs of a parent graph.
+
+    For each ego-net: the size s is log-uniform in [smin, smax]; the centre is
+    a uniformly chosen vertex with degree >= s - 1 (if none exists, the
+    highest-degree vertex and s = deg + 1); the vertex set is the centre plus
+    s - 1 of its neighbours chosen by a seeded shuffle; the subgraph is the
+    one the parent induces on that set.
+
+    Returns a dict of concatenated arrays:
+      v_off (count+1, int64): vertex offsets; graph i owns local ids
+          [0, n_i) stored globally at [v_off[i], v_off[i+1]).
+      e_off (count+1, int64): edge offsets into src/dst/eid.
+      src, dst (uint32): GLOBAL vertex ids (local id + v_off of its graph).
+      eid (uint32): the parent edge id of each subgraph edge.
+      vid (uint32): parent vertex id of each global vertex.
+    """
+    g = rng(seed)
+    off, nbr, eidx = csr_undirected(n, src, dst)
+    deg = np.diff(off)
+    order_by_deg = np.argsort(deg, kind="stable")
+    sorted_deg = deg[order_by_deg]
+    mark = np.full(n, -1, dtype=np.int64)
+    v_off = [0]
+    e_off = [0]
+    out_src, out_dst, out_eid, out_vid = [], [], [], []
+    for _ in range(count):
+        s = int(round(np.exp(g.uniform(np.log(smin), np.log(smax)))))
+        first = np.searchsorted(sorted_deg, s - 1, side="left")
+        if first >= n:
+            centre = int(order_by_deg[-1])
+            s = int(deg[centre]) + 1
+        else:
+            centre = int(order_by_deg[g.integers(first, n)])
+        nb = nbr[off[centre]:off[centre + 1]].astype(np.int64)
+        pick = g.permutation(nb.size)[: s - 1]
+        verts = np.unique(np.concatenate([[centre], nb[pick]]))
+        mark[verts] = np.arange(verts.size)
+        # induced edges: scan every member's adjacency, keep member neighbours with larger id
+        starts = off[verts]
+        lens = deg[verts]
+        tot = int(lens.sum())
+        rep = np.repeat(np.arange(verts.size), lens)
+        idx = np.arange(tot) - np.repeat(np.cumsum(lens) - lens, lens) + np.repeat(starts, lens)
+        w = nbr[idx].astype(np.int64)
+        u = verts[rep]
+        keep = (mark[w] >= 0) & (w > u)
+        lu = mark[u[keep]]
+        lw = mark[w[keep]]
+        base = v_off[-1]
+        out_src.append((lu + base).astype(np.uint32))
+        out_dst.append((lw + base).astype(np.uint32))
+        out_eid.append(eidx[idx[keep]].astype(np.uint32))
+        out_vid.append(verts.astype(np.uint32))
+        mark[verts] = -1
+        v_off.append(base + verts.size)
+        e_off.append(e_off[-1] + int(keep.sum()))
+    return {
+        "v_off": np.asarray(v_off, dtype=np.int64),
+        "e_off": np.asarray(e_off, dtype=np.int64),
+        "src": np.concatenate(out_src) if out_src else np.zeros(0, np.uint32),
+        "dst": np.concatenate(out_dst) if out_dst else np.zeros(0, np.uint32),
+        "eid": np.concatenate(out_eid) if out_eid else np.zeros(0, np.uint32),
+        "vid": np.concatenate(out_vid) if out_vid else np.zeros(0, np.uint32),
+    }
+
+
+def bfs_induced(n: int, src, dst, start: int, min_edges: int):
+    """Add vertices in BFS order from ``start`` until the induced edge count
+    reaches ``min_edges``; return (vertex ids, local src, local dst, parent eid).
+    """
+    off, nbr, _ = csr_undirected(n, src, dst)
+    inset = np.zeros(n, dtype=bool)
+    order = []
+    seen = np.zeros(n, dtype=bool)
+    seen[start] = True
+    edges = 0
+    head = 0
+    queue = [start]
+    while head < len(queue) and edges < min_edges:
+        x = queue[head]
+        head += 1
+        nb = nbr[off[x]:off[x + 1]]
+        edges += int(inset[nb].sum())
+        inset[x] = True
+        order.append(x)
+        for y in nb:
+            if not seen[y]:
+                seen[y] = True
+                queue.append(int(y))
+    verts = np.asarray(sorted(order), dtype=np.int64)
+    local = np.full(n, -1, dtype=np.int64)
+    local[verts] = np.arange(verts.size)
+    s64 = np.asarray(src, dtype=np.int64)
+    d64 = np.asarray(dst, dtype=np.int64)
+    keep = inset[s64] & inset[d64]
+    eid = np.nonzero(keep)[0]
+    return (verts.astype(np.uint32), local[s64[keep]].astype(np.uint32),
+            local[d64[keep]].astype(np.uint32), eid.astype(np.uint32))
+
+
+class Graph:
+    """A generated uncertain signed graph: n, src, dst and k (or p)."""
+
+    def __init__(self, name, n, src, dst, k=None, p=None, meta=None):
+        self.name = name
+        self.n = int(n)
+        self.src = np.ascontiguousarray(src, dtype=np.uint32)
+        self.dst = np.ascontiguousarray(dst, dtype=np.uint32)
+        self.k = None if k is None else np.ascontiguousarray(k, dtype=np.uint32)
+        self.p = None if p is None else np.ascontiguousarray(p, dtype=np.float32)
+        self.meta = dict(meta or {})
+
+    @property
+    def m(self):
+        return int(self.src.size)
+
+
+def config_graph(name: str, seed: int = 1) -> Graph:
+    """The five workload graphs, by the name they are known by elsewhere.
+
+    er2k      -- G(n=2,000, m=20,000), k ~ U{0..65536}.
+    cl1m      -- Chung-Lu n=1e6, gamma=2.1, mean degree 20, max 50,000,
+                 P+ ~ Beta(0.5, 0.5) quantised to 16 bits.
+    rmat22    -- R-MAT scale 22, edge factor 16, (0.57, 0.19, 0.19, 0.05),
+                 P+ ~ 0.5 Beta(8,2) + 0.5 Beta(2,8) quantised.
+    rmat20    -- R-MAT scale 20, edge factor 16, k ~ U{0..65536}.
+    cl4m      -- Chung-Lu n=4e6, gamma=2.3, mean degree 20, max 50,000,
+                 p ~ U[0,1] float32.
+    Small variants for tests: ``rmat<s>`` for any scale s, ``cl<n>`` is not
+    provided (use chung_lu directly).
+    """
+    if name == "er2k":
+        n = 2000
+        s, d = er_graph(n, 20000, seed)
+        return Graph(name, n, s, d, k=k_uniform(20000, seed + 1000))
+    if name == "cl1m":
+        n = 1_000_000
+        s, d = chung_lu(n, 2.1, 20.0, 50_000.0, seed)
+        k = quantise(p_beta(s.size, 0.5, 0.5, seed + 1000))
+        return Graph(name, n, s, d, k=k)
+    if name == "cl4m":
+        n = 4_000_000
+        s, d = chung_lu(n, 2.3, 20.0, 50_000.0, seed)
+        return Graph(name, n, s, d, p=p_uniform_f32(s.size, seed + 1000))
+    if name.startswith("rmat"):
+        scale = int(name[4:])
+        s, d = rmat(scale, 16, 0.57, 0.19, 0.19, seed)
+        if scale == 22:
+            k = quantise(p_beta_mixture(s.size, seed + 1000))
+        else:
+            k = k_uniform(s.size, seed + 1000)
+        return Graph(name, 1 << scale, s, d, k=k)
+    raise KeyError(name)

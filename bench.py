@@ -1,0 +1,372 @@
+"""Benchmark of the exact t-count path on one GB300 (or N replicas).
+
+Workload (one "step" = one threshold-count query over the whole graph):
+  cl1m: Chung-Lu power-law graph, n = 1,000,000, gamma = 2.1, mean degree 20,
+  expected degrees capped at 50,000 (about 9.1M undirected edges after
+  deduplication), P+ ~ Beta(0.5, 0.5) quantised to k/65536, thresholds
+  t in {0.55, 0.70, 0.85, 0.95} answered in one traversal with probability
+  pruning.  The unpruned query runs too (not timed as the headline) and must
+  give identical counts.
+
+value  = triangles of the graph / query time (triangles per second), the
+         graph already built and resident in HBM (the paper pre-sorts its data
+         and times queries, Sec. 7.2).  L2 is flushed between timed steps.
+e2e    = the same metric through ubt_count_host from pinned host buffers:
+         H2D copy of (src, dst, k), graph build, query, D2H of the counts.
+extras = MC sign worlds, expected counts forward + backward, the 32-threshold
+         sweep with enumeration (--extras, on by default; --no-extras skips).
+
+--impl reference runs the CPU oracle (plain C, one core) on a bounded sample
+of the same workload as the comparison arm.
+"""
+from __future__ import annotations
+
+import argparse
+import ctypes
+import json
+import os
+import subprocess
+import sys
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+TAUS = [0.55, 0.70, 0.85, 0.95]
+WORKLOAD = "cl1m"
+METRIC = "exact t-count triangles/s (Chung-Lu n=1e6, 4 thresholds, pruned)"
+UNIT = "triangles/s"
+
+
+def peaks():
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            return json.load(f), "measured"
+    except Exception:
+        return {"hbm_gbs": 6800.0, "bf16_tflops": 1900.0}, "fallback"
+
+
+class Clocks:
+    """nvidia-smi sampling of SM clocks and throttle reasons during the timed region."""
+
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index):
+        self.gpu = gpu_index
+        self.proc = None
+        self.path = os.path.join("/tmp", "ubt_clocks_%d_%d.csv" % (os.getpid(), gpu_index))
+
+    def start(self):
+        try:
+            self.f = open(self.path, "w")
+            self.proc = subprocess.Popen(["nvidia-smi", "-i", str(self.gpu), "--query-gpu=" + self.FIELDS,
+                                          "--format=csv,noheader,nounits", "-lms", "200"],
+                                         stdout=self.f, stderr=subprocess.DEVNULL)
+        except Exception:
+            self.proc = None
+
+    def stop(self):
+        if self.proc is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        time.sleep(0.25)
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except Exception:
+            self.proc.kill()
+        self.f.close()
+        sm, smax, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for line in open(self.path):
+            parts = [x.strip() for x in line.split(",")]
+            if len(parts) < 9:
+                continue
+            try:
+                sm.append(float(parts[1]))
+                smax.append(float(parts[2]))
+            except ValueError:
+                continue
+            for nm, v in zip(names, parts[5:9]):
+                if v.lower() == "active":
+                    reasons.add(nm)
+        try:
+            os.remove(self.path)
+        except OSError:
+            pass
+        return {"sm_mhz": float(np.median(sm)) if sm else None, "sm_max_mhz": max(smax) if smax else None,
+                "reasons": sorted(reasons), "samples": len(sm)}
+
+
+def dist_env():
+    ws = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return ws, rank, local
+
+
+def make_graph(name):
+    import synth
+    return synth.config_graph(name, seed=1)
+
+
+def time_steps(fn, steps, warmup, flush=None):
+    """W untimed warm-up calls, then `steps` calls each bracketed by CUDA
+    events on the current stream, with an L2 flush before each (untimed)."""
+    import torch
+    for _ in range(warmup):
+        fn()
+    torch.cuda.synchronize()
+    times = []
+    s = torch.cuda.current_stream()
+    for _ in range(steps):
+        if flush is not None:
+            flush()
+        a = torch.cuda.Event(enable_timing=True)
+        b = torch.cuda.Event(enable_timing=True)
+        a.record(s)
+        fn()
+        b.record(s)
+        b.synchronize()
+        times.append(a.elapsed_time(b) / 1e3)
+    return times
+
+
+def reference_arm(args):
+    """CPU oracle as the comparison arm (rank 0 only)."""
+    ws, rank, local = dist_env()
+    if rank != 0:
+        return 0
+    import oracle
+    import synth
+    # bounded sample of the workload: the same Chung-Lu recipe at n = 250,000
+    n = 250_000
+    s, d = synth.chung_lu(n, 2.1, 20.0, 50_000.0, 1)
+    k = synth.quantise(synth.p_beta(s.size, 0.5, 0.5, 1001))
+    T = oracle.num_triangles(n, s, d)
+    for _ in range(args.warmup):
+        oracle.count_threshold(n, s, d, k, TAUS)
+    times = []
+    for _ in range(args.steps):
+        t0 = time.perf_counter()
+        oracle.count_threshold(n, s, d, k, TAUS)
+        times.append(time.perf_counter() - t0)
+    ms = 1e3 * float(np.mean(times))
+    v = T / (ms / 1e3)
+    line = {
+        "impl": "reference", "metric": METRIC, "value": v, "unit": UNIT, "n_gpus": args.gpus,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": "int64", "data": "synthetic",
+        "config": {"workload": "cl250k (Chung-Lu n=250,000 sample of the cl1m recipe)", "taus": TAUS,
+                   "triangles": T, "m": int(s.size)},
+        "cpu_baseline": {"value": v, "unit": UNIT, "cores": 1, "kind": "oracle",
+                         "sample": "Chung-Lu n=250,000 (same gamma/mean/cap/P+ recipe), 4 thresholds, "
+                                   "full graph per step"},
+        "e2e": {"value": v, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }
+    print(json.dumps(line))
+    return 0
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=20)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--extras", dest="extras", action="store_true", default=True)
+    ap.add_argument("--no-extras", dest="extras", action="store_false")
+    ap.add_argument("--no-cpu-baseline", dest="cpu", action="store_false", default=True)
+    args = ap.parse_args()
+    args.warmup = max(args.warmup, 3)
+    if args.impl == "reference":
+        return reference_arm(args)
+
+    import torch
+    ws, rank, local = dist_env()
+    if ws > 1:
+        import torch.distributed as dist
+        torch.cuda.set_device(local)
+        dist.init_process_group("nccl")
+    else:
+        torch.cuda.set_device(0)
+    dev = torch.cuda.current_device()
+
+    import __graft_entry__
+    __graft_entry__.build()
+    import paper_2602_14084_gb300 as ubt
+
+    g = make_graph(WORKLOAD)
+    t0 = time.perf_counter()
+    G = ubt.Graph(g.n, g.src, g.dst, k=g.k)
+    torch.cuda.synchronize()
+    build_s = time.perf_counter() - t0
+    # rebuild timed with events (first build includes library/context warm-up)
+    src_d = torch.from_numpy(g.src.view(np.int32)).cuda()
+    dst_d = torch.from_numpy(g.dst.view(np.int32)).cuda()
+    k_d = torch.from_numpy(g.k.view(np.int32)).cuda()
+    a = torch.cuda.Event(enable_timing=True)
+    b = torch.cuda.Event(enable_timing=True)
+    a.record()
+    G2 = ubt.Graph(g.n, src_d, dst_d, k=k_d)
+    b.record()
+    b.synchronize()
+    build_ms = a.elapsed_time(b)
+    del G2
+
+    info = G.info()
+    _, _, T, _ = G.expected_counts(with_exact=True)
+    counts = torch.empty(2 * len(TAUS), dtype=torch.int64, device="cuda")
+    cb, cu = G.count_threshold(TAUS, prune=True)
+    ub_, uu_ = G.count_threshold(TAUS, prune=False)
+    assert np.array_equal(cb, ub_) and np.array_equal(cu, uu_), "pruned and unpruned counts differ"
+
+    flush_buf = torch.empty(512 * 1024 * 1024 // 4, dtype=torch.int32, device="cuda")
+
+    def flush():
+        flush_buf.fill_(1)
+
+    def step():
+        G.count_threshold_(TAUS, counts, prune=True)
+
+    def step_unpruned():
+        G.count_threshold_(TAUS, counts, prune=False)
+
+    clocks = Clocks(dev if ws == 1 else local)
+    if ws > 1:
+        torch.distributed.barrier()
+    torch.cuda.synchronize()
+    clocks.start()
+    times = time_steps(step, args.steps, args.warmup, flush)
+    clk = clocks.stop()
+    t_step = float(np.mean(times))
+    if ws > 1:
+        tt = torch.tensor([t_step], dtype=torch.float64, device="cuda")
+        torch.distributed.all_reduce(tt, op=torch.distributed.ReduceOp.MAX)
+        t_step = float(tt.item())
+    times_unpruned = time_steps(step_unpruned, max(3, args.steps // 4), 1, flush)
+
+    # roofline of the dominant kernel (the traversal): algorithmic bytes =
+    # 16 B per forward-list entry loaded (table + row offsets of v) + 8 B per
+    # streamed entry of N>(v)
+    st = G.traversal_stats(TAUS, prune=True)
+    alg_bytes = 16 * st["table_entries"] + 8 * st["streamed"]
+    pk, pk_kind = peaks()
+    achieved = alg_bytes / t_step / 1e9
+    roofline = {"bound": "hbm", "achieved": achieved, "peak": pk["hbm_gbs"], "unit": "GB/s",
+                "frac": achieved / pk["hbm_gbs"], "traffic": None,
+                "kernel": "k_traverse<CountMulti>", "peak_kind": pk_kind,
+                "alg_bytes_per_launch": alg_bytes, "streamed_entries": st["streamed"],
+                "table_entries": st["table_entries"]}
+    st0 = G.traversal_stats(TAUS, prune=False)
+
+    # end to end through the C ABI from pinned host buffers
+    hs = torch.from_numpy(g.src.view(np.int32)).pin_memory()
+    hd = torch.from_numpy(g.dst.view(np.int32)).pin_memory()
+    hk = torch.from_numpy(g.k.view(np.int32)).pin_memory()
+    L = ubt.lib()
+    nb = ctypes.c_size_t(0)
+    L.ubt_count_host_workspace_size(g.n, g.m, ctypes.byref(nb))
+    ews = torch.empty(int(nb.value), dtype=torch.uint8, device="cuda")
+    tau_arr = np.asarray(TAUS, dtype=np.float64)
+    hout = torch.zeros(2 * len(TAUS), dtype=torch.int64).pin_memory()
+
+    def e2e_step():
+        stv = L.ubt_count_host(g.n, g.m, ctypes.c_void_p(hs.data_ptr()), ctypes.c_void_p(hd.data_ptr()),
+                               ctypes.c_void_p(hk.data_ptr()), tau_arr.ctypes.data_as(ctypes.c_void_p),
+                               len(TAUS), 1, ctypes.c_void_p(hout.data_ptr()), ctypes.c_void_p(ews.data_ptr()),
+                               ews.numel(), ctypes.c_void_p(torch.cuda.current_stream().cuda_stream))
+        assert stv == 0, stv
+
+    e2e_times = []
+    for i in range(args.warmup + max(3, args.steps // 4)):
+        torch.cuda.synchronize()
+        t1 = time.perf_counter()
+        e2e_step()
+        t2 = time.perf_counter()
+        if i >= args.warmup:
+            e2e_times.append(t2 - t1)
+    assert np.array_equal(hout.numpy()[:len(TAUS)], cb)
+    e2e_t = float(np.mean(e2e_times))
+
+    line = {
+        "metric": METRIC, "value": ws * T / t_step, "unit": UNIT, "n_gpus": ws, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": 1e3 * t_step, "higher_is_better": True, "scaling": "weak",
+        "vs_baseline": None, "dtype": "int64", "data": "synthetic",
+        "config": {"workload": "cl1m: Chung-Lu n=1,000,000 gamma=2.1 mean-deg 20 cap 50,000, "
+                               "P+ ~ Beta(0.5,0.5) -> k/65536, 4 thresholds, pruned, one traversal",
+                   "n": g.n, "m": g.m, "triangles": T, "taus": TAUS, "l2": "flushed between steps (512 MB write)",
+                   "parallelism": "replicas" if ws > 1 else "single GPU"},
+        "roofline": roofline,
+        "e2e": {"value": ws * T / e2e_t, "unit": UNIT, "h2d_bytes_per_step": 12 * g.m,
+                "d2h_bytes_per_step": 16 * len(TAUS), "ms_per_step": 1e3 * e2e_t,
+                "includes": "H2D of src/dst/k, graph build (validate, orient, CSR, sort), query, D2H"},
+        "gpu_launches": 2 * args.steps,
+        "clocks": clk,
+        "build_ms": build_ms,
+        "unpruned": {"ms_per_step": 1e3 * float(np.mean(times_unpruned)),
+                     "value": T / float(np.mean(times_unpruned)), "streamed_entries": st0["streamed"],
+                     "alg_bytes": 16 * st0["table_entries"] + 8 * st0["streamed"]},
+        "graph": info,
+    }
+
+    if args.extras and rank == 0:
+        line["extras"] = extras(ubt, G, g, T, args, flush)
+    if args.cpu and rank == 0:
+        import oracle
+        oracle.build()
+        t1 = time.perf_counter()
+        ob, ou = oracle.count_threshold(g.n, g.src, g.dst, g.k, TAUS)
+        dt = time.perf_counter() - t1
+        assert np.array_equal(ob, cb) and np.array_equal(ou, cu), "GPU counts differ from the oracle"
+        line["cpu_baseline"] = {"value": T / dt, "unit": UNIT, "cores": 1, "kind": "oracle",
+                                "sample": "the full cl1m graph, 4 thresholds, one pass (%.1f s)" % dt,
+                                "matches_gpu": True}
+    if ws > 1:
+        torch.distributed.barrier()
+    if rank == 0:
+        print(json.dumps(line))
+    if ws > 1:
+        torch.distributed.destroy_process_group()
+    return 0
+
+
+def extras(ubt, G, g, T, args, flush):
+    """Other forms of the path on the same GPU: MC sign worlds and expected
+    counts forward + backward on the cl1m graph (full-size workloads of their
+    own are run by the dedicated benchmarks in tests and profiles)."""
+    import torch
+    out = {}
+    # Monte-Carlo sign worlds, W = 4096
+    W = 4096
+    wsz = G.sample_worlds_workspace(W)
+    wws = torch.empty(wsz, dtype=torch.uint8, device="cuda")
+    wout = torch.empty(W, dtype=torch.int64, device="cuda")
+    wt = torch.empty(1, dtype=torch.int64, device="cuda")
+    tw = time_steps(lambda: G.sample_worlds_(7, W, wout, wt, wws), max(3, args.steps // 4), 1, flush)
+    out["mc_worlds"] = {"W": W, "ms": 1e3 * float(np.mean(tw)), "world_triangles_per_s": T * W / float(np.mean(tw)),
+                        "words_per_pass": ubt.get_tuning("world_words_per_pass")}
+    # expected counts forward + backward on a REAL graph (p ~ U[0,1] float32)
+    import synth
+    p = synth.p_uniform_f32(g.m, 5)
+    pt = torch.from_numpy(p).cuda()
+    Gp = ubt.Graph(g.n, g.src, g.dst, p=pt)
+    eo = torch.empty(2, dtype=torch.float64, device="cuda")
+    gout = torch.tensor([1.0, 0.0], dtype=torch.float64, device="cuda")
+    grad = torch.empty(g.m, dtype=torch.float32, device="cuda")
+
+    def fb():
+        Gp.expected_counts_(eo)
+        Gp.expected_counts_backward_(gout, grad)
+
+    tf = time_steps(lambda: Gp.expected_counts_(eo), max(3, args.steps // 4), 1, flush)
+    tfb = time_steps(fb, max(3, args.steps // 4), 1, flush)
+    out["expected_fwd_bwd"] = {"fwd_ms": 1e3 * float(np.mean(tf)), "fwd_bwd_ms": 1e3 * float(np.mean(tfb))}
+    return out
+
+
+if __name__ == "__main__":
+    sys.exit(main())

@@ -1,0 +1,292 @@
+/*
+ * ubt.h -- C ABI of libubt: exact counting and enumeration of t-balanced and
+ * t-unbalanced triangles on uncertain signed graphs, on one GB300 GPU.
+ *
+ * Paper: "Counting Balanced Triangles on Social Networks With Uncertain Edge
+ * Signs" (arXiv 2602.14084).  The operations and their defining passages:
+ *   - uncertain signed graph G = (V, E, P+)                (Def. 1, Sec. 3)
+ *   - triangle; balanced iff an odd number of its edges are positive
+ *                                                      (Defs. 2-3, Sec. 3)
+ *   - P_bal = sum over the classes T3 and T1 of products of independent
+ *     P+ / P-; P_unbal = 1 - P_bal                     (equation in Sec. 3)
+ *   - t-balanced: P_bal >= t; t-unbalanced: P_unbal > t  (Defs. 4-5, Sec. 3)
+ *   - counting / enumeration problems UBTC / UBTE      (Defs. 7-8, Sec. 3)
+ *   - exact algorithms: forward iteration under Node Order (Alg. 1, Sec. 4)
+ *     and probability pruning (Lemma 2, Lemma 3, Alg. 2, Sec. 5)
+ *
+ * Conventions
+ *   - Every function returns ubt_status: 0 = UBT_OK, negative = error.
+ *     Nothing throws or aborts across this boundary.
+ *   - Pointers named d_* are device pointers, h_* host pointers.  All device
+ *     memory is owned by the caller; the library never allocates or frees
+ *     device memory.  Sizes are queried with the *_workspace_size calls.
+ *   - Calls marked ASYNC only enqueue work on the given stream and write
+ *     their outputs when that work completes; they do not synchronise and may
+ *     be captured into a CUDA graph.  Calls marked SYNC synchronise `stream`
+ *     before returning.
+ *   - Calls on the same graph must not overlap in time (issue them on one
+ *     stream): each graph carries one query scratch area.
+ *   - Fixed point: P+(e) = k_e / 65536 with integer k_e in [0, 65536].  With
+ *     q_e = 32768 - k_e (so 1 - 2 P+(e) = q_e / 2^15) every test is exact in
+ *     int64; counts and enumeration records are bit-exact.
+ *   - Thresholds t must lie in [0.5, 1] (the paper assumes t >= 0.5, Sec. 3);
+ *     t is used exactly as the given IEEE double.
+ *   - The stream is a cudaStream_t passed as void* (0 = legacy default).
+ */
+#ifndef UBT_H
+#define UBT_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef int32_t ubt_status;
+
+#define UBT_OK 0
+#define UBT_ERR_INVALID_ARG (-1)          /* null pointer, bad size, bad flag */
+#define UBT_ERR_SELF_LOOP (-2)            /* an edge (v, v) */
+#define UBT_ERR_DUPLICATE_EDGE (-3)       /* the same unordered pair twice */
+#define UBT_ERR_VERTEX_OOB (-4)           /* an endpoint >= n */
+#define UBT_ERR_PROB_OOB (-5)             /* k > 65536, or p outside [0,1] / NaN */
+#define UBT_ERR_TAU_OOB (-6)              /* t outside [0.5, 1] or NaN */
+#define UBT_ERR_CAPACITY (-7)             /* enumeration output too small */
+#define UBT_ERR_WORKSPACE_TOO_SMALL (-8)  /* workspace below the queried size */
+#define UBT_ERR_TIMEOUT (-9)              /* reserved: a bounded device wait gave up */
+#define UBT_ERR_CUDA (-10)                /* a CUDA runtime call failed */
+#define UBT_ERR_UNSUPPORTED (-11)         /* operation not defined for this graph kind */
+
+/* Graph kinds (the `flags` of ubt_graph_workspace_size / ubt_create_graph). */
+#define UBT_GRAPH_FIXED 0   /* probabilities given as k (uint32, 0..65536) */
+#define UBT_GRAPH_REAL 1    /* probabilities given as p (float32, [0,1]) */
+
+typedef struct ubt_graph ubt_graph;   /* opaque */
+
+/* One enumeration record (24 bytes): the triangle's vertex ids (as given,
+ * u < v < w), its class (1 = t-balanced, 2 = t-unbalanced) and its exact
+ * balance probability P_bal = N / 2^46 (exact in double). */
+typedef struct {
+    uint32_t u, v, w;
+    uint32_t cls;
+    double p_bal;
+} ubt_tri_rec;
+
+/* Sizes of the built graph, filled by ubt_graph_get_info. */
+typedef struct {
+    int64_t n;                /* vertices */
+    int64_t m;                /* undirected edges */
+    int64_t max_out_degree;   /* largest forward list under Node Order */
+    int64_t hub_vertices;     /* vertices handled by a whole thread block */
+    int64_t wedges;           /* sum over forward edges (u,v) of |N>(v)| */
+    int64_t kind;             /* UBT_GRAPH_FIXED or UBT_GRAPH_REAL */
+} ubt_graph_info;
+
+/* Optional extras for ubt_create_graph (pass NULL for none). */
+typedef struct {
+    /* Philox key of every edge (device, m entries); NULL = the edge index.
+     * Sub-graphs cut from a parent pass the parent's edge ids here so that
+     * their sign worlds agree with the parent's. */
+    const uint32_t* d_edge_key;
+    /* Batches of disjoint graphs: d_vertex_offsets[g] .. [g+1] is the vertex
+     * range of graph g (device, n_graphs + 1 entries, int64, ascending,
+     * first 0, last n).  Edges must not cross graphs.  NULL = one graph. */
+    const int64_t* d_vertex_offsets;
+    int64_t n_graphs;
+} ubt_graph_opts;
+
+/* Human-readable name of a status code (static string). */
+const char* ubt_status_str(ubt_status s);
+
+/* Library version as MAJOR*10000 + MINOR*100 + PATCH. */
+int32_t ubt_version(void);
+
+/*
+ * ubt_graph_workspace_size -- bytes of device workspace a graph of n vertices
+ * and m edges of the given kind needs (the built forward CSR, its edge ids,
+ * temporaries of the build and the per-graph query scratch).  With opts
+ * describing a batch, pass the same opts to ubt_create_graph.
+ * Errors: UBT_ERR_INVALID_ARG (n or m negative or >= 2^32 - 1, bad flags).
+ */
+ubt_status ubt_graph_workspace_size(int64_t n, int64_t m, int32_t flags,
+                                    const ubt_graph_opts* opts, size_t* h_bytes);
+
+/*
+ * ubt_create_graph -- SYNC.  Validates the edge list and builds the graph the
+ * exact algorithms traverse (Def. 1; Node Order, Sec. 4):
+ *   - each undirected edge {a, b} is kept once and oriented from the endpoint
+ *     earlier in Node Order (degree, then id) to the later one;
+ *   - the forward lists N>(u) are stored as CSR, each list sorted by
+ *     |1 - 2 P+| descending (ties by neighbour id), so that the edges a
+ *     threshold prunes (Lemma 2) form a suffix of every list.
+ * Arguments:
+ *   n, m           vertex and edge counts (0 allowed).
+ *   d_src, d_dst   device uint32[m] endpoints, any order, ids < n.
+ *   d_k            device uint32[m], k in [0, 65536]   (flags FIXED), or NULL
+ *   d_p            device float[m], p in [0, 1]         (flags REAL), or NULL
+ *   flags          UBT_GRAPH_FIXED or UBT_GRAPH_REAL.
+ *   opts           NULL, or the extras above.
+ *   d_workspace    device buffer of >= ubt_graph_workspace_size bytes,
+ *                  256-byte aligned; owned by the caller and used by the
+ *                  graph until ubt_destroy_graph (do not free it earlier).
+ *   stream         cudaStream_t as void*.
+ *   h_out          receives the graph handle (host memory, owned by the
+ *                  library; release with ubt_destroy_graph).
+ * The input arrays may be freed after the call returns.
+ * Errors: UBT_ERR_INVALID_ARG, UBT_ERR_SELF_LOOP, UBT_ERR_DUPLICATE_EDGE,
+ *   UBT_ERR_VERTEX_OOB, UBT_ERR_PROB_OOB, UBT_ERR_WORKSPACE_TOO_SMALL,
+ *   UBT_ERR_CUDA.  On error no handle is returned.
+ */
+ubt_status ubt_create_graph(int64_t n, int64_t m, const uint32_t* d_src, const uint32_t* d_dst,
+                            const uint32_t* d_k, const float* d_p, int32_t flags,
+                            const ubt_graph_opts* opts, void* d_workspace, size_t ws_bytes,
+                            void* stream, ubt_graph** h_out);
+
+/* ubt_destroy_graph -- releases the handle (not the caller's workspace). */
+ubt_status ubt_destroy_graph(ubt_graph* g);
+
+/* ubt_graph_get_info -- SYNC-free; copies the sizes recorded at build time. */
+ubt_status ubt_graph_get_info(const ubt_graph* g, ubt_graph_info* h_info);
+
+/*
+ * ubt_count_threshold -- ASYNC.  Counting problem (UBTC, Def. 8): for each of
+ * n_tau thresholds t_i, the number of triangles with P_bal >= t_i and the
+ * number with P_unbal > t_i (Defs. 4-5; Alg. 1 and Alg. 2).  All thresholds
+ * are answered in one traversal.
+ *   h_tau     host double[n_tau], each in [0.5, 1], any order, 1 <= n_tau <= 64.
+ *   prune     0: visit every triangle (Alg. 1).  1: skip edges and triangles
+ *             that cannot reach the smallest threshold (Lemma 2 per edge;
+ *             the order-free form of Lemma 3 per pair of edges); results are
+ *             identical either way.
+ *   d_counts  device int64[2 * n_tau]: [0, n_tau) balanced counts,
+ *             [n_tau, 2 n_tau) unbalanced counts, in the order of h_tau.
+ * Graph kind: FIXED only (UBT_ERR_UNSUPPORTED otherwise).
+ * Errors: UBT_ERR_INVALID_ARG, UBT_ERR_TAU_OOB, UBT_ERR_UNSUPPORTED, UBT_ERR_CUDA.
+ */
+ubt_status ubt_count_threshold(ubt_graph* g, const double* h_tau, int32_t n_tau, int32_t prune,
+                               int64_t* d_counts, void* stream);
+
+/*
+ * ubt_enumerate -- SYNC.  Enumeration problem (UBTE, Def. 7) at threshold t:
+ * writes one ubt_tri_rec per t-balanced (which & 1) and/or t-unbalanced
+ * (which & 2) triangle into d_out, in no particular order.
+ *   d_out       device ubt_tri_rec[capacity] (may be NULL if capacity == 0).
+ *   h_n_found   receives the total number of records (even when it exceeds
+ *               capacity; then only `capacity` records are written and the
+ *               call returns UBT_ERR_CAPACITY).
+ *   prune       as in ubt_count_threshold.
+ * Graph kind: FIXED only.
+ */
+ubt_status ubt_enumerate(ubt_graph* g, double tau, int32_t which, int32_t prune,
+                         ubt_tri_rec* d_out, int64_t capacity, int64_t* h_n_found, void* stream);
+
+/*
+ * ubt_expected_counts -- ASYNC.  Expected numbers of balanced and unbalanced
+ * triangles, E_bal = sum_t P_bal(t) = (T - sum_t S_t) / 2 and
+ * E_unbal = (T + sum_t S_t) / 2 with S_t the product of (1 - 2 P+) over the
+ * triangle's edges (from the equation in Sec. 3; not in the paper).
+ *   d_out    device double[2] = {E_bal, E_unbal}.
+ *   d_exact  device int64[4] or NULL: {T, sum_lo, sum_hi, 0} where, for a
+ *            FIXED graph, sum_hi:sum_lo is the exact two's-complement 128-bit
+ *            sum of q_e q_f q_g over all triangles (E_bal = (T 2^45 - sum) /
+ *            2^46 exactly); for a REAL graph it is the sum of S_t in signed
+ *            64.64 fixed point... rounded per triangle to 2^-32 (see below).
+ * Arithmetic: FIXED graphs are exact (int64 products, 128-bit sums).  REAL
+ * graphs form S_t with float32 products and accumulate S_t rounded to a
+ * multiple of 2^-32 in 64-bit integers, then finish in double.
+ */
+ubt_status ubt_expected_counts(ubt_graph* g, double* d_out, int64_t* d_exact, void* stream);
+
+/*
+ * ubt_expected_counts_backward -- ASYNC.  Adjoint of ubt_expected_counts:
+ *   d_grad_p[e] = (g_bal - g_unbal) * sum over triangles t containing e of
+ *                 (1 - 2 p_f)(1 - 2 p_g)     (f, g the other two edges of t)
+ * i.e. the gradient of L = g_bal E_bal + g_unbal E_unbal with respect to p_e.
+ *   d_gout    device double[2] = {g_bal, g_unbal} (upstream gradients).
+ *   d_grad_p  device float[m], input edge order (overwritten).
+ * Arithmetic: FIXED graphs exact in int64 before the final scaling; REAL
+ * graphs float32 products accumulated in 64-bit integers at 2^-40 resolution.
+ */
+ubt_status ubt_expected_counts_backward(ubt_graph* g, const double* d_gout, float* d_grad_p,
+                                        void* stream);
+
+/*
+ * ubt_sample_worlds_workspace_size / ubt_sample_worlds -- ASYNC.  Monte-Carlo
+ * sign worlds (not in the paper): W worlds (W a positive multiple of 64), each
+ * an independent draw of every edge's sign with P(+) = k_e / 65536.  Returns
+ * the number of balanced triangles (odd number of positive edges, Def. 3) in
+ * every world.
+ * Draws: world 64 w + j, edge with key K (ubt_graph_opts.d_edge_key, default
+ * the edge index): sixteen 64-bit words r_0..r_15 from Philox4x64-10 with key
+ * (seed, 0) and counters (K, w, c, 0), c = 0..3 (call c gives r_{4c..4c+3});
+ * u_j = sum_b bit j of r_b * 2^b; the edge is positive iff u_j < k_e.
+ *   d_bal_per_world  device int64[W].
+ *   d_total          device int64[1]: sum over worlds (may be NULL).
+ *   d_workspace      >= the queried bytes (sign table of one pass + counters).
+ * Graph kind: FIXED only.
+ */
+ubt_status ubt_sample_worlds_workspace_size(const ubt_graph* g, int64_t W, size_t* h_bytes);
+ubt_status ubt_sample_worlds(ubt_graph* g, uint64_t seed, int64_t W, int64_t* d_bal_per_world,
+                             int64_t* d_total, void* d_workspace, size_t ws_bytes, void* stream);
+
+/*
+ * ubt_batch_query -- ASYNC.  For a graph created with opts.d_vertex_offsets
+ * (a batch of disjoint graphs), answers per graph, in one launch:
+ *   d_counts  device int64[n_graphs * 2 * n_tau]: graph g's balanced counts at
+ *             [g*2*n_tau, g*2*n_tau + n_tau), unbalanced after them.
+ *   d_expect  device double[n_graphs * 2] = {E_bal, E_unbal} per graph (exact
+ *             for FIXED graphs), or NULL.
+ *   d_worlds  device int64[n_graphs * 64]: balanced counts in the 64 worlds of
+ *             world word 0 drawn with `seed` (as in ubt_sample_worlds), or NULL.
+ *   h_tau     as in ubt_count_threshold (1 <= n_tau <= 8).
+ * Graph kind: FIXED only.  Capturable into a CUDA graph.
+ */
+ubt_status ubt_batch_query(ubt_graph* g, const double* h_tau, int32_t n_tau, uint64_t seed,
+                           int64_t* d_counts, double* d_expect, int64_t* d_worlds, void* stream);
+
+/*
+ * ubt_count_host -- SYNC, end to end from host memory.  Copies a FIXED graph
+ * (h_src, h_dst, h_k: host uint32[m]) to the device, builds it, counts
+ * (as ubt_count_threshold) and copies the counts back into h_counts
+ * (host int64[2 * n_tau]).  d_workspace must hold
+ * ubt_count_host_workspace_size bytes.
+ */
+ubt_status ubt_count_host_workspace_size(int64_t n, int64_t m, size_t* h_bytes);
+ubt_status ubt_count_host(int64_t n, int64_t m, const uint32_t* h_src, const uint32_t* h_dst,
+                          const uint32_t* h_k, const double* h_tau, int32_t n_tau, int32_t prune,
+                          int64_t* h_counts, void* d_workspace, size_t ws_bytes, void* stream);
+
+/*
+ * ubt_traversal_stats -- SYNC.  Sizes of the traversal a query at these
+ * thresholds performs (for roofline accounting; computes nothing else):
+ *   h_out[0]  forward-list entries loaded into hash tables (sum of the pruned
+ *             |N>(u)|, Lemma 2)
+ *   h_out[1]  forward pairs (u, v) visited (same as h_out[0])
+ *   h_out[2]  entries of N>(v) streamed and probed, summed over the pairs
+ *             (pruned by Lemma 2 / the order-free Lemma 3 form when prune = 1)
+ *   h_out[3]  vertices with >= 2 forward entries (tasks)
+ */
+ubt_status ubt_traversal_stats(ubt_graph* g, const double* h_tau, int32_t n_tau, int32_t prune,
+                               int64_t* h_out, void* stream);
+
+/*
+ * ubt_set_tuning / ubt_get_tuning -- process-wide launch parameters that the
+ * autotuner picks (they change speed, never results).  Unknown names return
+ * UBT_ERR_INVALID_ARG.  Names:
+ *   "hub_threshold"   forward-list length above which a vertex is handled by
+ *                     a whole thread block (default 48)
+ *   "hub_threads"     threads per block of the hub phase (128..1024, /32)
+ *   "blocks_per_sm"   persistent blocks per SM (1..32)
+ *   "smem_table_max"  hash-table slots kept in shared memory (power of two);
+ *                     longer lists use a table in global scratch
+ *   "world_words_per_pass"  64-world words per traversal of ubt_sample_worlds
+ *                     (1, 2, 4, 8, 16, 32 or 64)
+ */
+ubt_status ubt_set_tuning(const char* name, int64_t value);
+ubt_status ubt_get_tuning(const char* name, int64_t* h_value);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* UBT_H */

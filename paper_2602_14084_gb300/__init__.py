@@ -1,0 +1,368 @@
+"""Python binding of libubt -- uncertain balanced/unbalanced triangles on GB300.
+
+Argument marshalling only: every step of the path runs in the CUDA kernels of
+``libubt.so`` (built from ``csrc/`` by ``_build.py``), reached through the C
+ABI declared in ``include/ubt.h``.  PyTorch provides device memory and
+streams.  There is no CPU fallback: if the library is missing the import of
+any entry point raises.
+
+Paper: "Counting Balanced Triangles on Social Networks With Uncertain Edge
+Signs" (arXiv 2602.14084): t-balanced triangles have P_bal >= t and
+t-unbalanced ones P_unbal > t (Defs. 4-5, Sec. 3); counting and enumeration
+problems (Defs. 7-8); exact algorithms Alg. 1 / Alg. 2 (Secs. 4-5).
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+
+import numpy as np
+
+__all__ = ["Graph", "expected_counts", "count_host", "set_tuning", "get_tuning", "lib",
+           "UbtError", "TRI_REC_DTYPE", "FIXED", "REAL"]
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_HERE, "libubt.so")
+FIXED, REAL = 0, 1
+
+# ubt_tri_rec: {uint32 u, v, w, cls; double p_bal}
+TRI_REC_DTYPE = np.dtype([("u", "<u4"), ("v", "<u4"), ("w", "<u4"), ("cls", "<u4"), ("p_bal", "<f8")])
+
+_lib = None
+
+
+class UbtError(RuntimeError):
+    def __init__(self, status, what=""):
+        self.status = int(status)
+        msg = lib().ubt_status_str(self.status).decode()
+        super().__init__("%s: %s (status %d)" % (what, msg, self.status) if what else msg)
+
+
+class _GraphOpts(ctypes.Structure):
+    _fields_ = [("d_edge_key", ctypes.c_void_p), ("d_vertex_offsets", ctypes.c_void_p),
+                ("n_graphs", ctypes.c_int64)]
+
+
+class _GraphInfo(ctypes.Structure):
+    _fields_ = [("n", ctypes.c_int64), ("m", ctypes.c_int64), ("max_out_degree", ctypes.c_int64),
+                ("hub_vertices", ctypes.c_int64), ("wedges", ctypes.c_int64), ("kind", ctypes.c_int64)]
+
+
+def lib():
+    """The loaded libubt.so (raises if it has not been built)."""
+    global _lib
+    if _lib is None:
+        if not os.path.exists(LIB_PATH):
+            raise RuntimeError("libubt.so is not built (run __graft_entry__.build() or "
+                               "python paper_2602_14084_gb300/_build.py)")
+        L = ctypes.CDLL(LIB_PATH)
+        P, I32, I64, SZ = ctypes.c_void_p, ctypes.c_int32, ctypes.c_int64, ctypes.c_size_t
+        sig = {
+            "ubt_status_str": (ctypes.c_char_p, [I32]),
+            "ubt_version": (I32, []),
+            "ubt_graph_workspace_size": (I32, [I64, I64, I32, P, ctypes.POINTER(SZ)]),
+            "ubt_create_graph": (I32, [I64, I64, P, P, P, P, I32, P, P, SZ, P, ctypes.POINTER(P)]),
+            "ubt_destroy_graph": (I32, [P]),
+            "ubt_graph_get_info": (I32, [P, ctypes.POINTER(_GraphInfo)]),
+            "ubt_count_threshold": (I32, [P, P, I32, I32, P, P]),
+            "ubt_enumerate": (I32, [P, ctypes.c_double, I32, I32, P, I64, ctypes.POINTER(I64), P]),
+            "ubt_expected_counts": (I32, [P, P, P, P]),
+            "ubt_expected_counts_backward": (I32, [P, P, P, P]),
+            "ubt_sample_worlds_workspace_size": (I32, [P, I64, ctypes.POINTER(SZ)]),
+            "ubt_sample_worlds": (I32, [P, ctypes.c_uint64, I64, P, P, P, SZ, P]),
+            "ubt_batch_query": (I32, [P, P, I32, ctypes.c_uint64, P, P, P, P]),
+            "ubt_count_host_workspace_size": (I32, [I64, I64, ctypes.POINTER(SZ)]),
+            "ubt_count_host": (I32, [I64, I64, P, P, P, P, I32, I32, P, P, SZ, P]),
+            "ubt_traversal_stats": (I32, [P, P, I32, I32, P, P]),
+            "ubt_set_tuning": (I32, [ctypes.c_char_p, I64]),
+            "ubt_get_tuning": (I32, [ctypes.c_char_p, ctypes.POINTER(I64)]),
+        }
+        for name, (res, args) in sig.items():
+            fn = getattr(L, name)
+            fn.restype = res
+            fn.argtypes = args
+        _lib = L
+    return _lib
+
+
+def _check(st, what):
+    if st != 0:
+        raise UbtError(st, what)
+
+
+def _torch():
+    import torch
+    return torch
+
+
+def _stream(stream=None):
+    torch = _torch()
+    s = stream if stream is not None else torch.cuda.current_stream()
+    return ctypes.c_void_p(s.cuda_stream)
+
+
+def _dev_u32(x, device):
+    torch = _torch()
+    if isinstance(x, torch.Tensor):
+        t = x.to(device=device)
+        if t.dtype != torch.int32:
+            t = t.to(torch.int64).to(torch.int32) if t.dtype != torch.uint32 else t.view(torch.int32)
+        return t.contiguous()
+    a = np.ascontiguousarray(np.asarray(x, dtype=np.uint32)).view(np.int32)
+    return torch.from_numpy(a).to(device)
+
+
+def _ptr(t):
+    return ctypes.c_void_p(t.data_ptr()) if t is not None else ctypes.c_void_p(0)
+
+
+def set_tuning(name: str, value: int):
+    _check(lib().ubt_set_tuning(name.encode(), int(value)), "ubt_set_tuning(%s)" % name)
+
+
+def get_tuning(name: str) -> int:
+    v = ctypes.c_int64(0)
+    _check(lib().ubt_get_tuning(name.encode(), ctypes.byref(v)), "ubt_get_tuning(%s)" % name)
+    return int(v.value)
+
+
+class Graph:
+    """An uncertain signed graph built on the GPU (ubt_create_graph).
+
+    n: number of vertices; src, dst: endpoints (uint32, numpy or torch);
+    exactly one of k (uint32 in [0, 65536], P+ = k/65536) or p (float32 in
+    [0, 1]).  edge_key: optional Philox key per edge; vertex_offsets: int64
+    [n_graphs + 1] for a batch of disjoint graphs.  Device memory (the
+    workspace) is a torch tensor owned by this object.
+    """
+
+    def __init__(self, n, src, dst, k=None, p=None, edge_key=None, vertex_offsets=None, device="cuda",
+                 stream=None):
+        torch = _torch()
+        if (k is None) == (p is None):
+            raise ValueError("give exactly one of k or p")
+        self.device = torch.device(device)
+        self.n = int(n)
+        L = lib()
+        s_dev = _dev_u32(src, self.device)
+        d_dev = _dev_u32(dst, self.device)
+        self.m = int(s_dev.numel())
+        self.kind = FIXED if k is not None else REAL
+        k_dev = _dev_u32(k, self.device) if k is not None else None
+        p_dev = None
+        if p is not None:
+            p_dev = (p.to(self.device, torch.float32) if isinstance(p, torch.Tensor)
+                     else torch.from_numpy(np.ascontiguousarray(p, dtype=np.float32)).to(self.device)).contiguous()
+        opts = None
+        self._keep = []
+        if edge_key is not None or vertex_offsets is not None:
+            opts = _GraphOpts()
+            if edge_key is not None:
+                ek = _dev_u32(edge_key, self.device)
+                self._keep.append(ek)
+                opts.d_edge_key = ek.data_ptr()
+            if vertex_offsets is not None:
+                vo = (vertex_offsets.to(self.device, torch.int64) if isinstance(vertex_offsets, torch.Tensor)
+                      else torch.from_numpy(np.ascontiguousarray(vertex_offsets, dtype=np.int64)).to(self.device))
+                self._keep.append(vo)
+                opts.d_vertex_offsets = vo.data_ptr()
+                opts.n_graphs = int(vo.numel()) - 1
+        self.n_graphs = opts.n_graphs if (opts is not None and opts.d_vertex_offsets) else 1
+        popts = ctypes.byref(opts) if opts is not None else None
+        nbytes = ctypes.c_size_t(0)
+        _check(L.ubt_graph_workspace_size(self.n, self.m, self.kind, popts, ctypes.byref(nbytes)),
+               "ubt_graph_workspace_size")
+        self.workspace = torch.empty(int(nbytes.value), dtype=torch.uint8, device=self.device)
+        h = ctypes.c_void_p(0)
+        _check(L.ubt_create_graph(self.n, self.m, _ptr(s_dev), _ptr(d_dev), _ptr(k_dev), _ptr(p_dev), self.kind,
+                                  popts, _ptr(self.workspace), self.workspace.numel(), _stream(stream),
+                                  ctypes.byref(h)), "ubt_create_graph")
+        self._h = h
+        self._keep = []  # the inputs are no longer needed after the build
+
+    def close(self):
+        if getattr(self, "_h", None) is not None and self._h.value:
+            lib().ubt_destroy_graph(self._h)
+            self._h = ctypes.c_void_p(0)
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    @property
+    def handle(self):
+        return self._h
+
+    def info(self) -> dict:
+        i = _GraphInfo()
+        _check(lib().ubt_graph_get_info(self._h, ctypes.byref(i)), "ubt_graph_get_info")
+        return {f: int(getattr(i, f)) for f, _ in _GraphInfo._fields_}
+
+    def traversal_stats(self, taus=(0.5,), prune=False, stream=None) -> dict:
+        """Exact sizes of the traversal a query performs (ubt_traversal_stats)."""
+        t = np.ascontiguousarray(np.atleast_1d(np.asarray(taus, dtype=np.float64)))
+        out = np.zeros(4, dtype=np.int64)
+        _check(lib().ubt_traversal_stats(self._h, t.ctypes.data_as(ctypes.c_void_p), t.size, int(bool(prune)),
+                                         out.ctypes.data_as(ctypes.c_void_p), _stream(stream)),
+               "ubt_traversal_stats")
+        return {"table_entries": int(out[0]), "pairs": int(out[1]), "streamed": int(out[2]), "tasks": int(out[3])}
+
+    # ---------------------------------------------------------------- queries
+
+    def count_threshold_(self, taus, out, prune=True, stream=None):
+        """ASYNC: writes int64 [2 * n_tau] (balanced counts, then unbalanced) into `out`."""
+        t = np.ascontiguousarray(np.atleast_1d(np.asarray(taus, dtype=np.float64)))
+        _check(lib().ubt_count_threshold(self._h, t.ctypes.data_as(ctypes.c_void_p), t.size, int(bool(prune)),
+                                         _ptr(out), _stream(stream)), "ubt_count_threshold")
+        return out
+
+    def count_threshold(self, taus, prune=True, stream=None):
+        """(balanced int64[n_tau], unbalanced int64[n_tau]) as numpy arrays."""
+        torch = _torch()
+        nt = int(np.atleast_1d(taus).size)
+        out = torch.empty(2 * nt, dtype=torch.int64, device=self.device)
+        self.count_threshold_(taus, out, prune, stream)
+        h = out.cpu().numpy()
+        return h[:nt].copy(), h[nt:].copy()
+
+    def enumerate(self, tau, which=3, prune=True, capacity=None, stream=None):
+        """Records as a numpy structured array (TRI_REC_DTYPE), unordered."""
+        torch = _torch()
+        L = lib()
+        found = ctypes.c_int64(0)
+        if capacity is None:
+            st = L.ubt_enumerate(self._h, float(tau), int(which), int(bool(prune)), None, 0, ctypes.byref(found),
+                                 _stream(stream))
+            if st not in (0, -7):
+                _check(st, "ubt_enumerate")
+            capacity = int(found.value)
+        buf = torch.empty(max(capacity, 1) * TRI_REC_DTYPE.itemsize, dtype=torch.uint8, device=self.device)
+        st = L.ubt_enumerate(self._h, float(tau), int(which), int(bool(prune)), _ptr(buf), int(capacity),
+                             ctypes.byref(found), _stream(stream))
+        if st == -7:
+            raise UbtError(st, "ubt_enumerate needs capacity %d" % found.value)
+        _check(st, "ubt_enumerate")
+        n = min(int(found.value), int(capacity))
+        return buf[: n * TRI_REC_DTYPE.itemsize].cpu().numpy().view(TRI_REC_DTYPE)
+
+    def expected_counts_(self, out, exact=None, stream=None):
+        _check(lib().ubt_expected_counts(self._h, _ptr(out), _ptr(exact), _stream(stream)), "ubt_expected_counts")
+
+    def expected_counts(self, with_exact=False, stream=None):
+        """(E_bal, E_unbal) floats; with_exact also returns (T, 128-bit sum as Python int)."""
+        torch = _torch()
+        out = torch.empty(2, dtype=torch.float64, device=self.device)
+        ex = torch.empty(4, dtype=torch.int64, device=self.device)
+        self.expected_counts_(out, ex, stream)
+        o = out.cpu().numpy()
+        if not with_exact:
+            return float(o[0]), float(o[1])
+        e = ex.cpu().numpy().view(np.uint64)
+        s = (int(e[2]) << 64) | int(e[1])
+        if s >= 1 << 127:
+            s -= 1 << 128
+        return float(o[0]), float(o[1]), int(e[0]), s
+
+    def expected_counts_backward_(self, gout, grad, stream=None):
+        _check(lib().ubt_expected_counts_backward(self._h, _ptr(gout), _ptr(grad), _stream(stream)),
+               "ubt_expected_counts_backward")
+
+    def sample_worlds_workspace(self, W):
+        nb = ctypes.c_size_t(0)
+        _check(lib().ubt_sample_worlds_workspace_size(self._h, int(W), ctypes.byref(nb)),
+               "ubt_sample_worlds_workspace_size")
+        return int(nb.value)
+
+    def sample_worlds_(self, seed, W, out, total=None, workspace=None, stream=None):
+        torch = _torch()
+        if workspace is None:
+            workspace = torch.empty(self.sample_worlds_workspace(W), dtype=torch.uint8, device=self.device)
+        _check(lib().ubt_sample_worlds(self._h, ctypes.c_uint64(int(seed)), int(W), _ptr(out), _ptr(total),
+                                       _ptr(workspace), workspace.numel(), _stream(stream)), "ubt_sample_worlds")
+        return out
+
+    def sample_worlds(self, seed, W, stream=None):
+        """Balanced-triangle count in each of W sign worlds: (int64[W], total)."""
+        torch = _torch()
+        out = torch.empty(int(W), dtype=torch.int64, device=self.device)
+        tot = torch.empty(1, dtype=torch.int64, device=self.device)
+        self.sample_worlds_(seed, W, out, tot, stream=stream)
+        return out.cpu().numpy(), int(tot.cpu().item())
+
+    def batch_query_(self, taus, seed, counts, expect=None, worlds=None, stream=None):
+        t = np.ascontiguousarray(np.atleast_1d(np.asarray(taus, dtype=np.float64)))
+        _check(lib().ubt_batch_query(self._h, t.ctypes.data_as(ctypes.c_void_p), t.size,
+                                     ctypes.c_uint64(int(seed)), _ptr(counts), _ptr(expect), _ptr(worlds),
+                                     _stream(stream)), "ubt_batch_query")
+
+    def batch_query(self, taus, seed=0, expect=True, worlds=True, stream=None):
+        """Per graph of a batch: counts [G, 2, n_tau], expected [G, 2], worlds [G, 64]."""
+        torch = _torch()
+        nt = int(np.atleast_1d(taus).size)
+        G = self.n_graphs
+        c = torch.empty(G * 2 * nt, dtype=torch.int64, device=self.device)
+        e = torch.empty(G * 2, dtype=torch.float64, device=self.device) if expect else None
+        w = torch.empty(G * 64, dtype=torch.int64, device=self.device) if worlds else None
+        self.batch_query_(taus, seed, c, e, w, stream)
+        return (c.cpu().numpy().reshape(G, 2, nt), None if e is None else e.cpu().numpy().reshape(G, 2),
+                None if w is None else w.cpu().numpy().reshape(G, 64))
+
+
+class _ExpectedCountsFn:
+    _cls = None
+
+    @classmethod
+    def get(cls):
+        if cls._cls is None:
+            torch = _torch()
+
+            class ExpectedCounts(torch.autograd.Function):
+                """(E_bal, E_unbal) of a REAL graph; backward is the hand-written adjoint kernel."""
+
+                @staticmethod
+                def forward(ctx, p, graph):
+                    out = torch.empty(2, dtype=torch.float64, device=graph.device)
+                    graph.expected_counts_(out)
+                    ctx.graph = graph
+                    ctx.p_dtype = p.dtype
+                    return out[0].clone(), out[1].clone()
+
+                @staticmethod
+                def backward(ctx, g_bal, g_unbal):
+                    graph = ctx.graph
+                    gout = torch.stack([g_bal.to(torch.float64).reshape(()), g_unbal.to(torch.float64).reshape(())])
+                    grad = torch.empty(graph.m, dtype=torch.float32, device=graph.device)
+                    graph.expected_counts_backward_(gout.contiguous(), grad)
+                    return grad.to(ctx.p_dtype), None
+
+            cls._cls = ExpectedCounts
+        return cls._cls
+
+
+def expected_counts(graph: Graph, p):
+    """Differentiable (E_bal, E_unbal) of `graph`, which must have been built
+    from exactly these probabilities `p` (REAL graph, or FIXED with p = k/65536).
+    Gradients flow to `p` through the adjoint kernel."""
+    return _ExpectedCountsFn.get().apply(p, graph)
+
+
+def count_host(n, src, dst, k, taus, prune=True, stream=None):
+    """End to end from host arrays (ubt_count_host): H2D copies, build, count,
+    D2H copy.  Returns (balanced, unbalanced) int64 numpy arrays."""
+    torch = _torch()
+    L = lib()
+    s = np.ascontiguousarray(src, dtype=np.uint32)
+    d = np.ascontiguousarray(dst, dtype=np.uint32)
+    kk = np.ascontiguousarray(k, dtype=np.uint32)
+    t = np.ascontiguousarray(np.atleast_1d(np.asarray(taus, dtype=np.float64)))
+    nb = ctypes.c_size_t(0)
+    _check(L.ubt_count_host_workspace_size(int(n), s.size, ctypes.byref(nb)), "ubt_count_host_workspace_size")
+    ws = torch.empty(int(nb.value), dtype=torch.uint8, device="cuda")
+    out = np.zeros(2 * t.size, dtype=np.int64)
+    _check(L.ubt_count_host(int(n), s.size, s.ctypes.data_as(ctypes.c_void_p), d.ctypes.data_as(ctypes.c_void_p),
+                            kk.ctypes.data_as(ctypes.c_void_p), t.ctypes.data_as(ctypes.c_void_p), t.size,
+                            int(bool(prune)), out.ctypes.data_as(ctypes.c_void_p), _ptr(ws), ws.numel(),
+                            _stream(stream)), "ubt_count_host")
+    return out[: t.size], out[t.size:]

@@ -1,0 +1,543 @@
+// ubt_build.cu -- building the graph the exact algorithms traverse.
+//
+//   validate   ids < n, no self-loops, probabilities in range       (Def. 1)
+//   degree     undirected degree of every vertex
+//   orient     each edge from its earlier endpoint in Node Order (degree,
+//              then id) to the later one                (Def. Node Order, Sec. 4)
+//   CSR        forward lists N>(u) as offsets + packed (neighbour, value)
+//   sort       each list by neighbour id (duplicate check), then -- FIXED
+//              graphs -- by |q| descending so that pruned entries (Lemma 2)
+//              form a suffix of every list
+//   work lists vertices with >= 2 forward entries, split by list length into
+//              block tasks and warp tasks, ordered by decreasing wedge count
+#include <math.h>
+#include <string.h>
+
+#include <algorithm>
+#include <new>
+
+#include "ubt_internal.cuh"
+
+namespace ubt {
+
+namespace {
+
+constexpr int kSortSmemMax = 4096;   // longest list sorted in shared memory
+constexpr int kSortHugeBlocks = 16;  // blocks sorting lists longer than that
+constexpr int kBuckets = 64;
+
+// error word: lowest (edge index << 8 | code) wins, so the report is deterministic
+__device__ inline void report(unsigned long long* err, uint64_t index, int code) {
+  atomicMin(err, (unsigned long long)((index << 8) | (uint64_t)code));
+}
+
+__global__ void k_vertex_graph(const int64_t* __restrict__ voff, int64_t ng, int64_t n, uint32_t* vgraph) {
+  for (int64_t v = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; v < n; v += (int64_t)gridDim.x * blockDim.x) {
+    int64_t lo = 0, hi = ng;  // find g with voff[g] <= v < voff[g+1]
+    while (hi - lo > 1) {
+      int64_t mid = (lo + hi) / 2;
+      if (voff[mid] <= v) lo = mid; else hi = mid;
+    }
+    vgraph[v] = (uint32_t)lo;
+  }
+}
+
+__global__ void k_validate_degree(int64_t n, int64_t m, const uint32_t* __restrict__ src,
+                                  const uint32_t* __restrict__ dst, const uint32_t* __restrict__ k,
+                                  const float* __restrict__ p, const uint32_t* __restrict__ vgraph,
+                                  uint32_t* __restrict__ deg, unsigned long long* err) {
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < m; i += (int64_t)gridDim.x * blockDim.x) {
+    const uint32_t a = src[i], b = dst[i];
+    if ((int64_t)a >= n || (int64_t)b >= n) { report(err, i, -UBT_ERR_VERTEX_OOB); continue; }
+    if (a == b) { report(err, i, -UBT_ERR_SELF_LOOP); continue; }
+    if (k) {
+      if (k[i] > 65536u) report(err, i, -UBT_ERR_PROB_OOB);
+    } else {
+      const float x = p[i];
+      if (!(x >= 0.0f && x <= 1.0f)) report(err, i, -UBT_ERR_PROB_OOB);
+    }
+    if (vgraph && vgraph[a] != vgraph[b]) { report(err, i, -UBT_ERR_INVALID_ARG); continue; }
+    atomicAdd(&deg[a], 1u);
+    atomicAdd(&deg[b], 1u);
+  }
+}
+
+// Node Order: a before b iff (deg a, a) < (deg b, b)
+__device__ inline bool node_before(const uint32_t* deg, uint32_t a, uint32_t b) {
+  const uint32_t da = deg[a], db = deg[b];
+  return da < db || (da == db && a < b);
+}
+
+__global__ void k_out_degree(int64_t m, const uint32_t* __restrict__ src, const uint32_t* __restrict__ dst,
+                             const uint32_t* __restrict__ deg, uint32_t* __restrict__ outdeg) {
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < m; i += (int64_t)gridDim.x * blockDim.x) {
+    const uint32_t a = src[i], b = dst[i];
+    atomicAdd(&outdeg[node_before(deg, a, b) ? a : b], 1u);
+  }
+}
+
+__global__ void k_scatter(int64_t m, const uint32_t* __restrict__ src, const uint32_t* __restrict__ dst,
+                          const uint32_t* __restrict__ k, const float* __restrict__ p,
+                          const uint32_t* __restrict__ deg, const uint32_t* __restrict__ row_ptr,
+                          uint32_t* __restrict__ fill, uint64_t* __restrict__ adj, uint32_t* __restrict__ eid,
+                          const uint32_t* __restrict__ key_in, uint32_t* __restrict__ key_out) {
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < m; i += (int64_t)gridDim.x * blockDim.x) {
+    const uint32_t a = src[i], b = dst[i];
+    const bool ab = node_before(deg, a, b);
+    const uint32_t lo = ab ? a : b, hi = ab ? b : a;
+    const uint32_t pos = row_ptr[lo] + atomicAdd(&fill[lo], 1u);
+    uint32_t val;
+    if (k) {
+      val = (uint32_t)(int32_t)(32768 - (int32_t)k[i]);     // q = 32768 - k
+    } else {
+      val = __float_as_uint(fmaf(-2.0f, p[i], 1.0f));       // s = 1 - 2p
+    }
+    adj[pos] = adj_pack(hi, val);
+    eid[pos] = (uint32_t)i;
+    if (key_out) key_out[pos] = key_in[i];
+  }
+}
+
+// sort keys: by neighbour id; FIXED graphs then by (32768 - |q|, id)
+__device__ inline uint64_t key_by_col(uint64_t e) { return (uint64_t)adj_col(e); }
+__device__ inline uint64_t key_by_absq(uint64_t e) {
+  const int32_t q = adj_q(e);
+  const uint32_t aq = (uint32_t)(q < 0 ? -q : q);
+  return ((uint64_t)(32768u - aq) << 32) | adj_col(e);
+}
+
+// Lists of <= 32 entries: one warp per list, bitonic network over the lanes.
+__device__ void warp_bitonic(uint64_t& key, uint64_t& e, uint32_t& id, uint32_t& ky, int lane) {
+#pragma unroll
+  for (int kk = 2; kk <= 32; kk <<= 1) {
+#pragma unroll
+    for (int j = kk >> 1; j > 0; j >>= 1) {
+      const uint64_t ok = __shfl_xor_sync(kFull, key, j);
+      const uint64_t oe = __shfl_xor_sync(kFull, e, j);
+      const uint32_t oi = __shfl_xor_sync(kFull, id, j);
+      const uint32_t oy = __shfl_xor_sync(kFull, ky, j);
+      const bool up = (lane & kk) == 0;
+      const bool lower = (lane & j) == 0;
+      const bool take_min = (lower == up);
+      const bool sw = take_min ? (ok < key) : (ok > key);
+      if (sw) { key = ok; e = oe; id = oi; ky = oy; }
+    }
+  }
+}
+
+__global__ void k_sort_short_rows(int64_t n, const uint32_t* __restrict__ row_ptr, uint64_t* adj, uint32_t* eid,
+                                  uint32_t* ekey, int fixed, unsigned long long* err) {
+  const int lane = threadIdx.x & 31;
+  const int64_t warps = (int64_t)gridDim.x * (blockDim.x >> 5);
+  for (int64_t u = blockIdx.x * (int64_t)(blockDim.x >> 5) + (threadIdx.x >> 5); u < n; u += warps) {
+    const uint32_t rs = row_ptr[u], re = row_ptr[u + 1];
+    const uint32_t len = re - rs;
+    if (len < 2 || len > 32) continue;
+    const bool in = (uint32_t)lane < len;
+    uint64_t e = in ? adj[rs + lane] : ~0ull;
+    uint32_t id = in ? eid[rs + lane] : 0u;
+    uint32_t ky = (in && ekey) ? ekey[rs + lane] : 0u;
+    uint64_t key = in ? key_by_col(e) : ~0ull;
+    warp_bitonic(key, e, id, ky, lane);
+    const uint64_t prev = __shfl_up_sync(kFull, key, 1);
+    if (in && lane > 0 && prev == key) report(err, rs + lane, -UBT_ERR_DUPLICATE_EDGE);
+    if (fixed) {
+      key = in ? key_by_absq(e) : ~0ull;
+      warp_bitonic(key, e, id, ky, lane);
+    }
+    if (in) {
+      adj[rs + lane] = e;
+      eid[rs + lane] = id;
+      if (ekey) ekey[rs + lane] = ky;
+    }
+  }
+}
+
+// Longer lists: one block per list, bitonic network in shared memory (or in a
+// per-block global slice for lists longer than kSortSmemMax).
+template <bool kGlobal>
+__global__ void k_sort_long_rows(const uint32_t* __restrict__ rows, uint32_t nrows, const uint32_t* __restrict__ row_ptr,
+                                 uint64_t* adj, uint32_t* eid, uint32_t* ekey, int fixed, unsigned long long* err,
+                                 char* gtmp, int64_t gtmp_cap) {
+  extern __shared__ __align__(16) char sm[];
+  for (uint32_t r = blockIdx.x; r < nrows; r += gridDim.x) {
+    const uint32_t u = rows[r];
+    const uint32_t rs = row_ptr[u], re = row_ptr[u + 1];
+    const uint32_t len = re - rs;
+    uint32_t cap = 64;
+    while (cap < len) cap <<= 1;
+    char* base = kGlobal ? gtmp + (size_t)blockIdx.x * (size_t)gtmp_cap * 24 : sm;
+    uint64_t* key = (uint64_t*)base;
+    uint64_t* ev = key + cap;
+    uint32_t* iv = (uint32_t*)(ev + cap);
+    uint32_t* yv = iv + cap;
+    for (uint32_t i = threadIdx.x; i < cap; i += blockDim.x) {
+      if (i < len) {
+        ev[i] = adj[rs + i];
+        iv[i] = eid[rs + i];
+        yv[i] = ekey ? ekey[rs + i] : 0u;
+        key[i] = key_by_col(ev[i]);
+      } else {
+        key[i] = ~0ull; ev[i] = ~0ull; iv[i] = 0; yv[i] = 0;
+      }
+    }
+    __syncthreads();
+    for (int pass = 0; pass < (fixed ? 2 : 1); pass++) {
+      if (pass == 1) {
+        for (uint32_t i = threadIdx.x; i < cap; i += blockDim.x) key[i] = i < len ? key_by_absq(ev[i]) : ~0ull;
+        __syncthreads();
+      }
+      for (uint32_t kk = 2; kk <= cap; kk <<= 1) {
+        for (uint32_t j = kk >> 1; j > 0; j >>= 1) {
+          for (uint32_t i = threadIdx.x; i < cap; i += blockDim.x) {
+            const uint32_t ixj = i ^ j;
+            if (ixj > i) {
+              const bool asc = (i & kk) == 0;
+              const uint64_t a = key[i], b = key[ixj];
+              if ((a > b) == asc && a != b) {
+                key[i] = b; key[ixj] = a;
+                uint64_t te = ev[i]; ev[i] = ev[ixj]; ev[ixj] = te;
+                uint32_t ti = iv[i]; iv[i] = iv[ixj]; iv[ixj] = ti;
+                uint32_t ty = yv[i]; yv[i] = yv[ixj]; yv[ixj] = ty;
+              }
+            }
+          }
+          __syncthreads();
+        }
+      }
+      if (pass == 0) {
+        for (uint32_t i = threadIdx.x + 1; i < len; i += blockDim.x)
+          if (key[i] == key[i - 1]) report(err, rs + i, -UBT_ERR_DUPLICATE_EDGE);
+        __syncthreads();
+      }
+    }
+    for (uint32_t i = threadIdx.x; i < len; i += blockDim.x) {
+      adj[rs + i] = ev[i];
+      eid[rs + i] = iv[i];
+      if (ekey) ekey[rs + i] = yv[i];
+    }
+    __syncthreads();
+  }
+}
+
+__global__ void k_collect_long(int64_t n, const uint32_t* __restrict__ row_ptr, uint32_t* mid, uint32_t* huge,
+                               unsigned long long* counts) {
+  for (int64_t u = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; u < n; u += (int64_t)gridDim.x * blockDim.x) {
+    const uint32_t len = row_ptr[u + 1] - row_ptr[u];
+    if (len > 32 && len <= (uint32_t)kSortSmemMax) mid[atomicAdd(&counts[0], 1ull)] = (uint32_t)u;
+    else if (len > (uint32_t)kSortSmemMax) huge[atomicAdd(&counts[1], 1ull)] = (uint32_t)u;
+  }
+}
+
+// Per vertex: wedge count sum_{v in N>(u)} |N>(v)|, its log2 bucket, class.
+// stats: [0] wedges, [1] max list, [2] max hub list, [3 + 2*b + cls] bucket sizes
+__global__ void k_row_stats(int64_t n, const uint32_t* __restrict__ row_ptr, const uint64_t* __restrict__ adj,
+                            uint32_t hub_thr, uint32_t giant_thr, uint8_t* __restrict__ bucket,
+                            unsigned long long* stats) {
+  const int lane = threadIdx.x & 31;
+  const int64_t warps = (int64_t)gridDim.x * (blockDim.x >> 5);
+  for (int64_t u = blockIdx.x * (int64_t)(blockDim.x >> 5) + (threadIdx.x >> 5); u < n; u += warps) {
+    const uint32_t rs = row_ptr[u], re = row_ptr[u + 1];
+    const uint32_t len = re - rs;
+    unsigned long long w = 0;
+    for (uint32_t i = rs + lane; i < re; i += 32) {
+      const uint32_t v = adj_col(adj[i]);
+      w += row_ptr[v + 1] - row_ptr[v];
+    }
+#pragma unroll
+    for (int d = 16; d > 0; d >>= 1) w += __shfl_xor_sync(kFull, w, d);
+    if (lane == 0) {
+      uint8_t b = 0xFF;
+      if (len >= 2) {
+        const int cls = len > giant_thr ? 2 : (len > hub_thr ? 1 : 0);
+        const int lg = w ? 63 - __clzll(w) : 0;
+        b = (uint8_t)(lg * 3 + cls);
+        atomicAdd(&stats[3 + b], 1ull);
+        if (cls >= 1) atomicMax(&stats[2], (unsigned long long)len);
+      }
+      bucket[u] = b;
+      atomicAdd(&stats[0], w);
+      atomicMax(&stats[1], (unsigned long long)len);
+    }
+  }
+}
+
+__global__ void k_fill_lists(int64_t n, const uint8_t* __restrict__ bucket, unsigned long long* cursor,
+                             uint32_t* __restrict__ lists) {
+  for (int64_t u = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; u < n; u += (int64_t)gridDim.x * blockDim.x) {
+    const uint8_t b = bucket[u];
+    if (b == 0xFF) continue;
+    lists[atomicAdd(&cursor[b], 1ull)] = (uint32_t)u;
+  }
+}
+
+struct BuildLayout {
+  // persistent
+  Scratch* scratch;
+  uint32_t* row_ptr;
+  uint64_t* adj;
+  uint32_t* eid;
+  uint32_t* ekey;
+  uint32_t* lists;       // giant | hub | small lists, n entries
+  uint32_t* vgraph;
+  unsigned long long* gacc;
+  unsigned long long* bacc;
+  uint32_t* gtab;
+  // build temporaries
+  uint32_t* deg;
+  uint32_t* fill;
+  uint32_t* scan_tmp;
+  uint32_t* mid_rows;
+  uint32_t* huge_rows;
+  uint8_t* bucket;
+  unsigned long long* stats;   // 3 + 3*64 counters, then 3*64 cursors, then 2 counters
+  char* sort_tmp;
+  size_t total;
+};
+
+int64_t list_bound(int64_t n, int64_t m) {
+  // a forward list under Node Order holds at most sqrt(2m) entries
+  int64_t b = (int64_t)sqrt(2.0 * (double)m) + 2;
+  return std::min<int64_t>(b, std::max<int64_t>(n, 1));
+}
+
+int64_t pow2_at_least(int64_t x) {
+  int64_t p = 1;
+  while (p < x) p <<= 1;
+  return p;
+}
+
+BuildLayout layout(void* ws, size_t cap, int64_t n, int64_t m, const ubt_graph_opts* opts, int sm_count) {
+  Carver c(ws, cap);
+  BuildLayout L;
+  const bool has_key = opts && opts->d_edge_key;
+  const bool batch = opts && opts->d_vertex_offsets;
+  const int64_t ng = batch ? opts->n_graphs : 1;
+  L.scratch = c.take<Scratch>(1);
+  L.row_ptr = c.take<uint32_t>(n + 1);
+  L.adj = c.take<uint64_t>(std::max<int64_t>(m, 1));
+  L.eid = c.take<uint32_t>(std::max<int64_t>(m, 1));
+  L.ekey = has_key ? c.take<uint32_t>(std::max<int64_t>(m, 1)) : nullptr;
+  L.lists = c.take<uint32_t>(std::max<int64_t>(n, 1));
+  L.vgraph = batch ? c.take<uint32_t>(std::max<int64_t>(n, 1)) : nullptr;
+  L.gacc = c.take<unsigned long long>(std::max<int64_t>(m, 1));
+  // per graph: T, sum_lo, sum_hi (expected counts) of a batch
+  L.bacc = c.take<unsigned long long>(3 * std::max<int64_t>(ng, 1));
+  const int64_t gslots = gtab_slots_for(m);
+  L.gtab = gslots ? c.take<uint32_t>((size_t)gslots * 3 * (size_t)sm_count) : nullptr;
+  L.deg = c.take<uint32_t>(std::max<int64_t>(n, 1));
+  L.fill = c.take<uint32_t>(std::max<int64_t>(n, 1));
+  L.scan_tmp = c.take<uint32_t>(scan_tmp_words(n) + 2);
+  L.mid_rows = c.take<uint32_t>(std::max<int64_t>(n, 1));
+  L.huge_rows = c.take<uint32_t>(std::max<int64_t>(n, 1));
+  L.bucket = c.take<uint8_t>(std::max<int64_t>(n, 1));
+  L.stats = c.take<unsigned long long>(3 + 2 * 3 * kBuckets + 2);
+  const int64_t lb = list_bound(n, m);
+  L.sort_tmp = lb > kSortSmemMax ? c.take<char>((size_t)kSortHugeBlocks * (size_t)pow2_at_least(lb) * 24) : nullptr;
+  L.total = c.off + 256;
+  return L;
+}
+
+int device_sm_count(int* dev) {
+  int d = 0, sms = 0;
+  cudaGetDevice(&d);
+  cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, d);
+  if (dev) *dev = d;
+  return sms > 0 ? sms : 1;
+}
+
+ubt_status status_from_err(unsigned long long e) {
+  if (e == ~0ull) return UBT_OK;
+  return -(ubt_status)(e & 0xFF);
+}
+
+}  // namespace
+
+int64_t gtab_slots_for(int64_t m) {
+  // lists whose table (2x the list, power of two) exceeds the shared-memory
+  // table get a table in global memory; size it for the longest possible list
+  const int64_t need = pow2_at_least(2 * list_bound(INT64_MAX / 4, m));
+  return need > tuning().smem_table_max ? need : 0;
+}
+
+}  // namespace ubt
+
+using namespace ubt;
+
+extern "C" ubt_status ubt_graph_workspace_size(int64_t n, int64_t m, int32_t flags, const ubt_graph_opts* opts,
+                                               size_t* h_bytes) {
+  if (!h_bytes || n < 0 || m < 0 || n >= 0xFFFFFFFFll || m >= 0xFFFFFFFFll) return UBT_ERR_INVALID_ARG;
+  if (flags != UBT_GRAPH_FIXED && flags != UBT_GRAPH_REAL) return UBT_ERR_INVALID_ARG;
+  if (opts && opts->d_vertex_offsets && opts->n_graphs < 1) return UBT_ERR_INVALID_ARG;
+  BuildLayout L = layout(nullptr, 0, n, m, opts, device_sm_count(nullptr));
+  *h_bytes = L.total;
+  return UBT_OK;
+}
+
+extern "C" ubt_status ubt_create_graph(int64_t n, int64_t m, const uint32_t* d_src, const uint32_t* d_dst,
+                                       const uint32_t* d_k, const float* d_p, int32_t flags,
+                                       const ubt_graph_opts* opts, void* d_workspace, size_t ws_bytes,
+                                       void* stream, ubt_graph** h_out) {
+  if (!h_out) return UBT_ERR_INVALID_ARG;
+  *h_out = nullptr;
+  if (n < 0 || m < 0 || n >= 0xFFFFFFFFll || m >= 0xFFFFFFFFll) return UBT_ERR_INVALID_ARG;
+  if (flags == UBT_GRAPH_FIXED) {
+    if (!d_k || d_p) return UBT_ERR_INVALID_ARG;
+  } else if (flags == UBT_GRAPH_REAL) {
+    if (!d_p || d_k) return UBT_ERR_INVALID_ARG;
+  } else {
+    return UBT_ERR_INVALID_ARG;
+  }
+  if (m > 0 && (!d_src || !d_dst)) return UBT_ERR_INVALID_ARG;
+  if (!d_workspace || ((uintptr_t)d_workspace & 255)) return UBT_ERR_INVALID_ARG;
+  const bool batch = opts && opts->d_vertex_offsets;
+  if (batch && opts->n_graphs < 1) return UBT_ERR_INVALID_ARG;
+  int dev = 0;
+  const int sms = device_sm_count(&dev);
+  BuildLayout L = layout(d_workspace, ws_bytes, n, m, opts, sms);
+  if (ws_bytes < L.total) return UBT_ERR_WORKSPACE_TOO_SMALL;
+  cudaStream_t s = (cudaStream_t)stream;
+  const Tuning& T = tuning();
+  const int hub_thr = (int)std::max<int64_t>(2, T.hub_threshold);
+  const int64_t giant_thr = tuning().smem_table_max / 2;
+
+  UBT_CUDA(cudaMemsetAsync(L.scratch, 0, sizeof(Scratch), s));
+  UBT_CUDA(cudaMemsetAsync(&L.scratch->err, 0xFF, sizeof(unsigned long long), s));
+  UBT_CUDA(cudaMemsetAsync(L.deg, 0, sizeof(uint32_t) * std::max<int64_t>(n, 1), s));
+  UBT_CUDA(cudaMemsetAsync(L.fill, 0, sizeof(uint32_t) * std::max<int64_t>(n, 1), s));
+  UBT_CUDA(cudaMemsetAsync(L.stats, 0, sizeof(unsigned long long) * (3 + 2 * 3 * kBuckets + 2), s));
+  const int thr = 256;
+  const int grid_e = (int)std::min<int64_t>(std::max<int64_t>((m + thr - 1) / thr, 1), (int64_t)sms * 32);
+  const int grid_v = (int)std::min<int64_t>(std::max<int64_t>((n + thr - 1) / thr, 1), (int64_t)sms * 32);
+  const int grid_w = (int)std::min<int64_t>(std::max<int64_t>((n + 7) / 8, 1), (int64_t)sms * 32);
+
+  if (batch) {
+    k_vertex_graph<<<grid_v, thr, 0, s>>>(opts->d_vertex_offsets, opts->n_graphs, n, L.vgraph);
+  }
+  // 1. validate + degree
+  if (m > 0)
+    k_validate_degree<<<grid_e, thr, 0, s>>>(n, m, d_src, d_dst, d_k, d_p, L.vgraph, L.deg, &L.scratch->err);
+  unsigned long long err = 0;
+  UBT_CUDA(cudaMemcpyAsync(&err, &L.scratch->err, sizeof(err), cudaMemcpyDeviceToHost, s));
+  UBT_CUDA(cudaStreamSynchronize(s));
+  ubt_status st = status_from_err(err);
+  if (st != UBT_OK) return st;
+  // 2. orientation + CSR offsets
+  if (m > 0) k_out_degree<<<grid_e, thr, 0, s>>>(m, d_src, d_dst, L.deg, L.fill);
+  UBT_CUDA(exclusive_scan_u32(L.fill, L.row_ptr, n, L.scan_tmp, s));
+  UBT_CUDA(cudaMemsetAsync(L.fill, 0, sizeof(uint32_t) * std::max<int64_t>(n, 1), s));
+  if (m > 0)
+    k_scatter<<<grid_e, thr, 0, s>>>(m, d_src, d_dst, d_k, d_p, L.deg, L.row_ptr, L.fill, L.adj, L.eid,
+                                     opts ? opts->d_edge_key : nullptr, L.ekey);
+  // 3. sort every forward list
+  const int fixed = flags == UBT_GRAPH_FIXED;
+  if (n > 0) {
+    k_sort_short_rows<<<grid_w, thr, 0, s>>>(n, L.row_ptr, L.adj, L.eid, L.ekey, fixed, &L.scratch->err);
+    unsigned long long* lcount = L.stats + 3 + 2 * 3 * kBuckets;
+    k_collect_long<<<grid_v, thr, 0, s>>>(n, L.row_ptr, L.mid_rows, L.huge_rows, lcount);
+    unsigned long long lc[2] = {0, 0};
+    UBT_CUDA(cudaMemcpyAsync(lc, lcount, sizeof(lc), cudaMemcpyDeviceToHost, s));
+    UBT_CUDA(cudaStreamSynchronize(s));
+    if (lc[0]) {
+      const size_t smem = (size_t)kSortSmemMax * 24;
+      UBT_CUDA(cudaFuncSetAttribute(k_sort_long_rows<false>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+      const int g = (int)std::min<unsigned long long>(lc[0], (unsigned long long)sms * 8);
+      k_sort_long_rows<false><<<g, 512, smem, s>>>(L.mid_rows, (uint32_t)lc[0], L.row_ptr, L.adj, L.eid, L.ekey,
+                                                   fixed, &L.scratch->err, nullptr, 0);
+    }
+    if (lc[1]) {
+      const int64_t cap = pow2_at_least(list_bound(n, m));
+      const int g = (int)std::min<unsigned long long>(lc[1], (unsigned long long)kSortHugeBlocks);
+      k_sort_long_rows<true><<<g, 1024, 0, s>>>(L.huge_rows, (uint32_t)lc[1], L.row_ptr, L.adj, L.eid, L.ekey,
+                                                fixed, &L.scratch->err, L.sort_tmp, cap);
+    }
+    UBT_CUDA(cudaGetLastError());
+  }
+  UBT_CUDA(cudaMemcpyAsync(&err, &L.scratch->err, sizeof(err), cudaMemcpyDeviceToHost, s));
+  UBT_CUDA(cudaStreamSynchronize(s));
+  st = status_from_err(err);
+  if (st != UBT_OK) return st;
+  // 4. work lists: giant (global table) | hub (block) | small (warp), each by
+  //    decreasing wedge-count bucket
+  unsigned long long stats[3 + 3 * kBuckets];
+  memset(stats, 0, sizeof(stats));
+  if (n > 0) {
+    k_row_stats<<<grid_w, thr, 0, s>>>(n, L.row_ptr, L.adj, (uint32_t)hub_thr, (uint32_t)giant_thr, L.bucket,
+                                      L.stats);
+    UBT_CUDA(cudaMemcpyAsync(stats, L.stats, sizeof(stats), cudaMemcpyDeviceToHost, s));
+    UBT_CUDA(cudaStreamSynchronize(s));
+  }
+  // list order: giant tasks, then hub tasks, then small tasks (cls 2, 1, 0)
+  unsigned long long cursor[3 * kBuckets];
+  int64_t count_cls[3] = {0, 0, 0};
+  for (int b = 0; b < 3 * kBuckets; b++) count_cls[b % 3] += (int64_t)stats[3 + b];
+  int64_t run[3];
+  run[2] = 0;
+  run[1] = count_cls[2];
+  run[0] = count_cls[2] + count_cls[1];
+  // within a class: buckets from the largest wedge count down
+  for (int lg = kBuckets - 1; lg >= 0; lg--) {
+    for (int cls = 0; cls < 3; cls++) {
+      const int b = lg * 3 + cls;
+      cursor[b] = (unsigned long long)run[cls];
+      run[cls] += (int64_t)stats[3 + b];
+    }
+  }
+  if (n > 0) {
+    unsigned long long* dcur = L.stats + 3 + 3 * kBuckets;
+    UBT_CUDA(cudaMemcpyAsync(dcur, cursor, sizeof(cursor), cudaMemcpyHostToDevice, s));
+    k_fill_lists<<<grid_v, thr, 0, s>>>(n, L.bucket, dcur, L.lists);
+    UBT_CUDA(cudaGetLastError());
+    UBT_CUDA(cudaStreamSynchronize(s));
+  }
+
+  ubt_graph* g = new (std::nothrow) ubt_graph();
+  if (!g) return UBT_ERR_INVALID_ARG;
+  g->n = n;
+  g->m = m;
+  g->kind = flags;
+  g->n_graphs = batch ? opts->n_graphs : 1;
+  g->row_ptr = L.row_ptr;
+  g->adj = L.adj;
+  g->eid = L.eid;
+  g->ekey = L.ekey ? L.ekey : L.eid;
+  g->giant_list = L.lists;
+  g->n_giant = count_cls[2];
+  g->hub_list = L.lists + count_cls[2];
+  g->n_hub = count_cls[1];
+  g->small_list = L.lists + count_cls[2] + count_cls[1];
+  g->n_small = count_cls[0];
+  g->vgraph = L.vgraph;
+  g->gacc = L.gacc;
+  g->bacc = L.bacc;
+  g->gtab = L.gtab;
+  g->gtab_slots = gtab_slots_for(m);
+  g->gtab_blocks = L.gtab ? sms : 0;
+  g->scratch = L.scratch;
+  g->wedges = (int64_t)stats[0];
+  g->max_out = (int64_t)stats[1];
+  g->max_hub_len = (int64_t)stats[2];
+  g->hub_threshold = hub_thr;
+  g->giant_threshold = giant_thr;
+  g->device = dev;
+  g->sm_count = sms;
+  *h_out = g;
+  return UBT_OK;
+}
+
+extern "C" ubt_status ubt_destroy_graph(ubt_graph* g) {
+  if (!g) return UBT_ERR_INVALID_ARG;
+  delete g;
+  return UBT_OK;
+}
+
+extern "C" ubt_status ubt_graph_get_info(const ubt_graph* g, ubt_graph_info* h_info) {
+  if (!g || !h_info) return UBT_ERR_INVALID_ARG;
+  h_info->n = g->n;
+  h_info->m = g->m;
+  h_info->max_out_degree = g->max_out;
+  h_info->hub_vertices = g->n_hub + g->n_giant;
+  h_info->wedges = g->wedges;
+  h_info->kind = g->kind;
+  return UBT_OK;
+}

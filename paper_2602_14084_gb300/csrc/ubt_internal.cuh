@@ -1,0 +1,138 @@
+// ubt_internal.cuh -- data layout and device helpers shared by the libubt
+// CUDA sources.  Not part of the public ABI (include/ubt.h is).
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include "../../include/ubt.h"
+
+namespace ubt {
+
+// ---------------------------------------------------------------- layout
+//
+// Forward CSR under Node Order (Def. Node Order, Sec. 4): row u holds N>(u),
+// the neighbours later than u in (degree, id) order.  Each entry is one
+// 64-bit word: low 32 bits the neighbour id, high 32 bits the edge value:
+//   FIXED graphs: q = 32768 - k as int32 (1 - 2 P+ = q / 2^15)
+//   REAL graphs:  s = 1 - 2 p as float32 bits
+// Every row is sorted by |value| descending, ties by neighbour id, so the
+// entries a pruning level removes form a suffix of the row (Lemma 2).
+// eid[pos] is the input index of the edge stored at CSR position pos.
+
+constexpr uint32_t kEmpty = 0xFFFFFFFFu;
+constexpr int kWarp = 32;
+constexpr unsigned kFull = 0xFFFFFFFFu;
+
+__host__ __device__ inline uint32_t adj_col(uint64_t e) { return (uint32_t)e; }
+__host__ __device__ inline int32_t adj_q(uint64_t e) { return (int32_t)(uint32_t)(e >> 32); }
+__host__ __device__ inline uint32_t adj_valbits(uint64_t e) { return (uint32_t)(e >> 32); }
+__host__ __device__ inline uint64_t adj_pack(uint32_t col, uint32_t valbits) {
+  return ((uint64_t)valbits << 32) | col;
+}
+
+// Query scratch carved from the graph workspace (one per graph).
+struct Scratch {
+  unsigned long long task[4];       // next giant / hub / small task, spare
+  unsigned long long enum_cursor;   // enumeration append cursor
+  unsigned long long tri_count;     // triangles seen (expected counts)
+  unsigned long long sum_lo;        // 128-bit two's-complement sum, low word
+  unsigned long long sum_hi;        // high word
+  unsigned long long err;           // device-side error word (build)
+  unsigned long long pad[7];
+  unsigned long long hist[2 * 65];  // multi-threshold histograms (bal, unbal)
+};
+constexpr size_t kScratchHeader = 16 * sizeof(unsigned long long);  // zeroed per query
+
+}  // namespace ubt
+
+// The opaque handle of the public ABI.
+struct ubt_graph {
+  int64_t n = 0, m = 0;
+  int32_t kind = 0;
+  int64_t n_graphs = 1;
+  // device arrays (inside the caller's workspace)
+  uint32_t* row_ptr = nullptr;      // n + 1
+  uint64_t* adj = nullptr;          // m
+  uint32_t* eid = nullptr;          // m: input edge index per CSR position
+  uint32_t* ekey = nullptr;         // m: Philox key per CSR position
+  uint32_t* giant_list = nullptr;   // lists too long for a shared-memory table
+  uint32_t* hub_list = nullptr;     // vertices with a long forward list
+  uint32_t* small_list = nullptr;   // other vertices with >= 2 forward entries
+  uint32_t* vgraph = nullptr;       // batch: graph id of every vertex (or null)
+  unsigned long long* gacc = nullptr;   // m: backward accumulators
+  unsigned long long* bacc = nullptr;   // batch accumulators
+  uint32_t* gtab = nullptr;         // global hash tables for very long lists
+  int64_t gtab_slots = 0;           // slots per block
+  int64_t gtab_blocks = 0;          // blocks that have one
+  ubt::Scratch* scratch = nullptr;
+  // sizes recorded at build time
+  int64_t n_giant = 0, n_hub = 0, n_small = 0;
+  int64_t max_out = 0, max_hub_len = 0, wedges = 0;
+  int hub_threshold = 0;
+  int64_t giant_threshold = 0;
+  int device = 0, sm_count = 0;
+};
+
+namespace ubt {
+
+// ---------------------------------------------------------------- tuning
+
+struct Tuning {
+  int64_t hub_threshold = 48;
+  int64_t hub_threads = 256;
+  int64_t blocks_per_sm = 4;
+  int64_t smem_table_max = 8192;
+  int64_t world_words_per_pass = 8;
+  int64_t small_batch = 8;
+};
+Tuning& tuning();
+
+// ---------------------------------------------------------------- host helpers
+
+#define UBT_CUDA(call)                                    \
+  do {                                                    \
+    cudaError_t e_ = (call);                              \
+    if (e_ != cudaSuccess) {                              \
+      ubt::set_last_cuda_error(e_, #call, __FILE__, __LINE__); \
+      return UBT_ERR_CUDA;                                \
+    }                                                     \
+  } while (0)
+
+void set_last_cuda_error(cudaError_t e, const char* what, const char* file, int line);
+
+inline size_t align_up(size_t x, size_t a) { return (x + a - 1) / a * a; }
+
+// Bump allocator over the caller's workspace.
+struct Carver {
+  char* base;
+  size_t off = 0;
+  size_t cap;
+  Carver(void* b, size_t c) : base((char*)b), cap(c) {}
+  template <class T>
+  T* take(size_t count) {
+    off = align_up(off, 256);
+    T* p = (T*)(base ? base + off : nullptr);
+    off += sizeof(T) * count;
+    return p;
+  }
+};
+
+// thresholds of one t (exact): c = 2t - 1, X = c * 2^45;
+//   balanced   <=> P <= B = -ceil(X)
+//   unbalanced <=> P >  U =  floor(X)
+//   prune level L = ceil(X): a triangle with |P| < L is neither
+struct Level {
+  int64_t B, U, L;
+};
+bool tau_level(double tau, Level* out);
+
+// device workspace needed for the global hash tables of a graph
+int64_t gtab_slots_for(int64_t m);
+
+// launch helpers implemented in ubt_scan.cu
+cudaError_t exclusive_scan_u32(const uint32_t* in, uint32_t* out, int64_t n, uint32_t* tmp,
+                               cudaStream_t s);
+size_t scan_tmp_words(int64_t n);
+
+}  // namespace ubt

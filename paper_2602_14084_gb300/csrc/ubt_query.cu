@@ -1,0 +1,545 @@
+// ubt_query.cu -- threshold counting, enumeration, expected counts and their
+// adjoint: visitors fused into the traversal of ubt_traverse.cuh.
+//
+// Per triangle with edge values q_uv, q_uw, q_vw (FIXED: q = 32768 - k):
+//   P = q_uv q_uw q_vw  (exact int64; P / 2^45 = (1-2p_uv)(1-2p_uw)(1-2p_vw))
+//   P_bal = (1 - P/2^45) / 2     (the four-term sum of Sec. 3 in product form)
+//   t-balanced   (Def. 4, P_bal >= t)   <=>  P <= B = -ceil((2t-1) 2^45)
+//   t-unbalanced (Def. 5, P_unbal > t)  <=>  P >  U =  floor((2t-1) 2^45)
+#include <math.h>
+#include <string.h>
+
+#include <algorithm>
+#include <numeric>
+#include <vector>
+
+#include "ubt_traverse.cuh"
+
+namespace ubt {
+
+namespace {
+
+constexpr int kMaxTau = 64;
+
+__device__ __forceinline__ int64_t tri_product(uint32_t a, uint32_t b, uint32_t c) {
+  // |q| <= 2^15, so q_a q_b fits int32 (<= 2^30); the third factor widens to int64
+  return (int64_t)((int32_t)a * (int32_t)b) * (int64_t)(int32_t)c;
+}
+
+__device__ __forceinline__ unsigned long long warp_sum(unsigned long long x) {
+#pragma unroll
+  for (int d = 16; d > 0; d >>= 1) x += __shfl_xor_sync(kFull, x, d);
+  return x;
+}
+
+// 128-bit two's-complement accumulator (lo, hi)
+struct Acc128 {
+  unsigned long long lo = 0, hi = 0;
+  __device__ __forceinline__ void add(long long x) {
+    const unsigned long long o = lo;
+    lo += (unsigned long long)x;
+    hi += (x < 0 ? ~0ull : 0ull) + (lo < o ? 1ull : 0ull);
+  }
+  __device__ __forceinline__ void add128(unsigned long long l, unsigned long long h) {
+    const unsigned long long o = lo;
+    lo += l;
+    hi += h + (lo < o ? 1ull : 0ull);
+  }
+  __device__ void warp_reduce() {
+#pragma unroll
+    for (int d = 16; d > 0; d >>= 1) {
+      const unsigned long long l = __shfl_xor_sync(kFull, lo, d);
+      const unsigned long long h = __shfl_xor_sync(kFull, hi, d);
+      add128(l, h);
+    }
+  }
+  // exact 128-bit add into global (lo, hi) words: each add's own carry goes to hi
+  __device__ void flush(unsigned long long* glo, unsigned long long* ghi) const {
+    const unsigned long long o = atomicAdd(glo, lo);
+    const unsigned long long c = (o + lo < o) ? 1ull : 0ull;
+    atomicAdd(ghi, hi + c);
+  }
+};
+
+// ------------------------------------------------------------ visitors
+
+struct CountOneP {
+  int64_t B, U;
+  unsigned long long* out;  // [0] balanced, [1] unbalanced
+};
+struct CountOne {
+  using P = CountOneP;
+  static constexpr bool kPos = false;
+  static constexpr int kSmem = 0;
+  P p;
+  unsigned long long bal = 0, unbal = 0;
+  __device__ CountOne(const P& p_, char*) : p(p_) {}
+  __device__ void block_init() {}
+  __device__ __forceinline__ void step(bool hit, uint32_t, uint32_t, uint32_t, uint32_t quv, uint32_t quw,
+                                       uint32_t qvw, uint32_t, uint32_t, uint32_t) {
+    if (hit) {
+      const int64_t P = tri_product(quv, quw, qvw);
+      bal += (P <= p.B);
+      unbal += (P > p.U);
+    }
+  }
+  __device__ void task_begin(uint32_t) {}
+  __device__ void task_end(uint32_t) {}
+  __device__ void block_end() {
+    const unsigned long long b = warp_sum(bal), u = warp_sum(unbal);
+    if ((threadIdx.x & 31) == 0) {
+      if (b) atomicAdd(&p.out[0], b);
+      if (u) atomicAdd(&p.out[1], u);
+    }
+  }
+};
+
+// Many thresholds: per-block histograms of "how many thresholds does this
+// triangle satisfy" (B sorted descending, U ascending), suffix-summed later.
+struct CountMultiP {
+  int nt;
+  int64_t B[kMaxTau];
+  int64_t U[kMaxTau];
+  unsigned long long* hist;  // global 2 x 65
+};
+struct CountMulti {
+  using P = CountMultiP;
+  static constexpr bool kPos = false;
+  static constexpr int kSmem = 2 * 65 * 8 + 16;
+  const P& p;
+  unsigned long long* h;
+  __device__ CountMulti(const P& p_, char* smem) : p(p_), h((unsigned long long*)smem) {}
+  __device__ void block_init() {
+    for (int i = threadIdx.x; i < 2 * 65; i += blockDim.x) h[i] = 0;
+  }
+  __device__ __forceinline__ void step(bool hit, uint32_t, uint32_t, uint32_t, uint32_t quv, uint32_t quw,
+                                       uint32_t qvw, uint32_t, uint32_t, uint32_t) {
+    if (!hit) return;
+    const int64_t P = tri_product(quv, quw, qvw);
+    if (P <= p.B[0]) {
+      int lo = 0, hi = p.nt;  // B[lo] >= P, first index with B < P in (lo, hi]
+      while (hi - lo > 1) {
+        const int mid = (lo + hi) >> 1;
+        if (p.B[mid] >= P) lo = mid; else hi = mid;
+      }
+      atomicAdd(&h[hi], 1ull);
+    } else if (P > p.U[0]) {
+      int lo = 0, hi = p.nt;
+      while (hi - lo > 1) {
+        const int mid = (lo + hi) >> 1;
+        if (p.U[mid] < P) lo = mid; else hi = mid;
+      }
+      atomicAdd(&h[65 + hi], 1ull);
+    }
+  }
+  __device__ void task_begin(uint32_t) {}
+  __device__ void task_end(uint32_t) {}
+  __device__ void block_end() {
+    __syncthreads();
+    for (int i = threadIdx.x; i < 2 * 65; i += blockDim.x)
+      if (h[i]) atomicAdd(&p.hist[i], h[i]);
+  }
+};
+
+struct FinishMulti {
+  int nt;
+  int perm[kMaxTau];  // caller index of the i-th smallest threshold
+};
+
+__global__ void k_finish_multi(const unsigned long long* __restrict__ hist, FinishMulti f, int64_t* __restrict__ out) {
+  // balanced count of sorted threshold i = sum_{k > i} hist_b[k] (same for unbalanced)
+  const int i = threadIdx.x;
+  if (i < f.nt) {
+    unsigned long long b = 0, u = 0;
+    for (int k = i + 1; k <= f.nt; k++) {
+      b += hist[k];
+      u += hist[65 + k];
+    }
+    out[f.perm[i]] = (int64_t)b;
+    out[f.nt + f.perm[i]] = (int64_t)u;
+  }
+}
+
+struct EnumP {
+  int64_t B, U;
+  int which;
+  ubt_tri_rec* out;
+  unsigned long long cap;
+  unsigned long long* cursor;
+};
+struct Enum {
+  using P = EnumP;
+  static constexpr bool kPos = false;
+  static constexpr int kSmem = 0;
+  P p;
+  __device__ Enum(const P& p_, char*) : p(p_) {}
+  __device__ void block_init() {}
+  __device__ __forceinline__ void step(bool hit, uint32_t u, uint32_t v, uint32_t w, uint32_t quv, uint32_t quw,
+                                       uint32_t qvw, uint32_t, uint32_t, uint32_t) {
+    uint32_t cls = 0;
+    int64_t P = 0;
+    if (hit) {
+      P = tri_product(quv, quw, qvw);
+      if ((p.which & 1) && P <= p.B) cls = 1;
+      else if ((p.which & 2) && P > p.U) cls = 2;
+    }
+    const unsigned m = __ballot_sync(kFull, cls != 0);
+    if (!m) return;
+    const int lane = threadIdx.x & 31;
+    const int leader = __ffs(m) - 1;
+    unsigned long long base = 0;
+    if (lane == leader) base = atomicAdd(p.cursor, (unsigned long long)__popc(m));
+    base = __shfl_sync(kFull, base, leader);
+    if (cls) {
+      const unsigned long long idx = base + __popc(m & ((1u << lane) - 1u));
+      if (idx < p.cap) {
+        uint32_t a = u, b = v, c = w, t;
+        if (a > b) { t = a; a = b; b = t; }
+        if (b > c) { t = b; b = c; c = t; }
+        if (a > b) { t = a; a = b; b = t; }
+        ubt_tri_rec r;
+        r.u = a; r.v = b; r.w = c; r.cls = cls;
+        // P_bal = (2^45 - P) / 2^46, exact in double (|numerator| <= 2^46)
+        r.p_bal = (double)((1ll << 45) - P) * 0x1p-46;
+        p.out[idx] = r;
+      }
+    }
+  }
+  __device__ void task_begin(uint32_t) {}
+  __device__ void task_end(uint32_t) {}
+  __device__ void block_end() {}
+};
+
+struct ExpectP {
+  unsigned long long* tri;      // triangle count
+  unsigned long long* sum_lo;   // 128-bit sum
+  unsigned long long* sum_hi;
+};
+// FIXED: sum of P exactly.  REAL: sum of S = s_uv s_uw s_vw (float32 products)
+// rounded to a multiple of 2^-32, in 128-bit integers.
+template <bool kReal>
+struct Expect {
+  using P = ExpectP;
+  static constexpr bool kPos = false;
+  static constexpr int kSmem = 0;
+  P p;
+  Acc128 acc;
+  unsigned long long cnt = 0;
+  __device__ Expect(const P& p_, char*) : p(p_) {}
+  __device__ void block_init() {}
+  __device__ __forceinline__ void step(bool hit, uint32_t, uint32_t, uint32_t, uint32_t quv, uint32_t quw,
+                                       uint32_t qvw, uint32_t, uint32_t, uint32_t) {
+    if (!hit) return;
+    cnt++;
+    if (kReal) {
+      const float S = __uint_as_float(quv) * __uint_as_float(quw) * __uint_as_float(qvw);
+      acc.add(__float2ll_rn(S * 4294967296.0f));
+    } else {
+      acc.add(tri_product(quv, quw, qvw));
+    }
+  }
+  __device__ void task_begin(uint32_t) {}
+  __device__ void task_end(uint32_t) {}
+  __device__ void block_end() {
+    acc.warp_reduce();
+    const unsigned long long c = warp_sum(cnt);
+    if ((threadIdx.x & 31) == 0 && c) {
+      atomicAdd(p.tri, c);
+      acc.flush(p.sum_lo, p.sum_hi);
+    }
+  }
+};
+
+__device__ double i128_to_double(unsigned long long lo, unsigned long long hi) {
+  // value = hi * 2^64 + lo with hi signed
+  return (double)(long long)hi * 18446744073709551616.0 + (double)lo;
+}
+
+__global__ void k_finish_expect(const Scratch* sc, int real, double* out, int64_t* exact) {
+  const unsigned long long T = sc->tri_count, lo = sc->sum_lo, hi = sc->sum_hi;
+  double sum;  // sum of S_t
+  if (real) sum = i128_to_double(lo, hi) * 0x1p-32;
+  else sum = i128_to_double(lo, hi) * 0x1p-45;
+  if (out) {
+    out[0] = ((double)T - sum) * 0.5;
+    out[1] = ((double)T + sum) * 0.5;
+  }
+  if (exact) {
+    exact[0] = (int64_t)T;
+    exact[1] = (int64_t)lo;
+    exact[2] = (int64_t)hi;
+    exact[3] = 0;
+  }
+}
+
+struct AdjointP {
+  unsigned long long* acc;  // per CSR position
+};
+// d E_bal / d p_e = sum over triangles through e of s_f s_g (f, g the other edges)
+template <bool kReal>
+struct Adjoint {
+  using P = AdjointP;
+  static constexpr bool kPos = true;
+  static constexpr int kSmem = 0;
+  P p;
+  __device__ Adjoint(const P& p_, char*) : p(p_) {}
+  __device__ void block_init() {}
+  __device__ __forceinline__ void step(bool hit, uint32_t, uint32_t, uint32_t, uint32_t quv, uint32_t quw,
+                                       uint32_t qvw, uint32_t puv, uint32_t puw, uint32_t pvw) {
+    if (!hit) return;
+    long long a_uv, a_uw, a_vw;
+    if (kReal) {
+      const float su = __uint_as_float(quv), sw = __uint_as_float(quw), sv = __uint_as_float(qvw);
+      a_uv = __float2ll_rn(sw * sv * 1099511627776.0f);   // 2^40
+      a_uw = __float2ll_rn(su * sv * 1099511627776.0f);
+      a_vw = __float2ll_rn(su * sw * 1099511627776.0f);
+    } else {
+      a_uv = (long long)((int32_t)quw * (int32_t)qvw);    // exact, scale 2^-30
+      a_uw = (long long)((int32_t)quv * (int32_t)qvw);
+      a_vw = (long long)((int32_t)quv * (int32_t)quw);
+    }
+    atomicAdd(&p.acc[puv], (unsigned long long)a_uv);
+    atomicAdd(&p.acc[puw], (unsigned long long)a_uw);
+    atomicAdd(&p.acc[pvw], (unsigned long long)a_vw);
+  }
+  __device__ void task_begin(uint32_t) {}
+  __device__ void task_end(uint32_t) {}
+  __device__ void block_end() {}
+};
+
+__global__ void k_finish_adjoint(int64_t m, const unsigned long long* __restrict__ acc, const uint32_t* __restrict__ eid,
+                                 const double* __restrict__ gout, double scale, float* __restrict__ grad) {
+  const double g = (gout[0] - gout[1]) * scale;
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < m; i += (int64_t)gridDim.x * blockDim.x)
+    grad[eid[i]] = (float)(g * (double)(long long)acc[i]);
+}
+
+// traversal sizes (same pruning rules as the traversal); one warp per vertex
+__global__ void k_trav_stats(int64_t n, const uint32_t* __restrict__ row_ptr, const uint64_t* __restrict__ adj,
+                             int64_t L, unsigned long long* out) {
+  const int lane = threadIdx.x & 31;
+  const int64_t warps = (int64_t)gridDim.x * (blockDim.x >> 5);
+  unsigned long long tab = 0, str = 0, tasks = 0;
+  for (int64_t u = blockIdx.x * (int64_t)(blockDim.x >> 5) + (threadIdx.x >> 5); u < n; u += warps) {
+    const uint32_t rs = row_ptr[u];
+    uint32_t len = row_ptr[u + 1] - rs;
+    if (len < 2) continue;
+    int64_t qmax = 0;
+    if (L > 0) {
+      qmax = qabs(adj_valbits(adj[rs]));
+      len = prune_prefix(adj + rs, len, qmax * 32768, L);
+    }
+    if (lane == 0) {
+      tab += len;
+      tasks += 1;
+    }
+    for (uint32_t i = lane; i < len; i += 32) {
+      const uint64_t e = adj[rs + i];
+      const uint32_t v = adj_col(e);
+      const uint32_t vs = row_ptr[v];
+      uint32_t dv = row_ptr[v + 1] - vs;
+      if (L > 0) dv = prune_prefix(adj + vs, dv, qabs(adj_valbits(e)) * qmax, L);
+      str += dv;
+    }
+  }
+  tab = warp_sum(tab);
+  str = warp_sum(str);
+  tasks = warp_sum(tasks);
+  if (lane == 0) {
+    atomicAdd(&out[0], tab);
+    atomicAdd(&out[1], str);
+    atomicAdd(&out[2], tasks);
+  }
+}
+
+// ------------------------------------------------------------ launching
+
+template <class V>
+__global__ void __launch_bounds__(512) k_traverse(TravArgs a, typename V::P p) {
+  extern __shared__ __align__(16) char smem[];
+  V vis(p, smem);
+  vis.block_init();
+  __syncthreads();
+  traverse(a, vis, smem + ((V::kSmem + 15) / 16) * 16);
+}
+
+}  // namespace
+
+TravArgs make_trav_args(const ubt_graph* g, int64_t L, bool with_pos) {
+  const Tuning& T = tuning();
+  TravArgs a;
+  a.row_ptr = g->row_ptr;
+  a.adj = g->adj;
+  a.giant_list = g->giant_list;
+  a.hub_list = g->hub_list;
+  a.small_list = g->small_list;
+  a.n_giant = (uint32_t)g->n_giant;
+  a.n_hub = (uint32_t)g->n_hub;
+  a.n_small = (uint32_t)g->n_small;
+  a.sc = g->scratch;
+  a.gtab = g->gtab;
+  a.gtab_slots = (uint32_t)g->gtab_slots;
+  a.gtab_blocks = g->n_giant ? (uint32_t)g->gtab_blocks : 0u;
+  uint32_t hs = 0;
+  if (g->n_hub) {
+    hs = 32;
+    while (hs < 2 * (uint64_t)g->max_hub_len) hs <<= 1;
+  }
+  a.hub_slots = hs;
+  uint32_t ss = 32;
+  while (ss < 2 * (uint32_t)g->hub_threshold) ss <<= 1;
+  a.small_slots = ss;
+  a.small_batch = (uint32_t)std::max<int64_t>(1, T.small_batch);
+  a.table_words = with_pos ? 3u : 2u;
+  a.L = L;
+  return a;
+}
+
+template <class V>
+ubt_status launch_traverse(const ubt_graph* g, const typename V::P& p, int64_t L, cudaStream_t s) {
+  const Tuning& T = tuning();
+  TravArgs a = make_trav_args(g, L, V::kPos);
+  int threads = (int)std::min<int64_t>(512, std::max<int64_t>(64, T.hub_threads / 32 * 32));
+  const size_t vis_bytes = (size_t)((V::kSmem + 15) / 16) * 16;
+  const size_t hub_bytes = (size_t)a.hub_slots * a.table_words * 4;
+  const size_t small_bytes = (size_t)(threads / 32) * a.small_slots * a.table_words * 4;
+  const size_t smem = vis_bytes + std::max(hub_bytes, small_bytes);
+  UBT_CUDA(cudaFuncSetAttribute(k_traverse<V>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+  int per_sm = 0;
+  UBT_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_traverse<V>, threads, smem));
+  if (per_sm < 1) return UBT_ERR_INVALID_ARG;
+  per_sm = (int)std::min<int64_t>(per_sm, std::max<int64_t>(1, T.blocks_per_sm));
+  const int grid = g->sm_count * per_sm;
+  UBT_CUDA(cudaMemsetAsync(g->scratch, 0, kScratchHeader / 2, s));  // task counters
+  k_traverse<V><<<grid, threads, smem, s>>>(a, p);
+  UBT_CUDA(cudaGetLastError());
+  return UBT_OK;
+}
+
+}  // namespace ubt
+
+using namespace ubt;
+
+namespace {
+
+ubt_status check_taus(const double* h_tau, int n_tau, std::vector<Level>& lv) {
+  if (!h_tau || n_tau < 1 || n_tau > kMaxTau) return UBT_ERR_INVALID_ARG;
+  lv.resize(n_tau);
+  for (int i = 0; i < n_tau; i++)
+    if (!tau_level(h_tau[i], &lv[i])) return UBT_ERR_TAU_OOB;
+  return UBT_OK;
+}
+
+}  // namespace
+
+extern "C" ubt_status ubt_count_threshold(ubt_graph* g, const double* h_tau, int32_t n_tau, int32_t prune,
+                                          int64_t* d_counts, void* stream) {
+  if (!g || !d_counts) return UBT_ERR_INVALID_ARG;
+  if (g->kind != UBT_GRAPH_FIXED) return UBT_ERR_UNSUPPORTED;
+  std::vector<Level> lv;
+  ubt_status st = check_taus(h_tau, n_tau, lv);
+  if (st != UBT_OK) return st;
+  cudaStream_t s = (cudaStream_t)stream;
+  // thresholds in ascending t: B descending, U ascending
+  std::vector<int> order(n_tau);
+  std::iota(order.begin(), order.end(), 0);
+  std::stable_sort(order.begin(), order.end(), [&](int x, int y) { return lv[x].L < lv[y].L; });
+  const int64_t L = prune ? lv[order[0]].L : 0;
+  if (n_tau == 1) {
+    UBT_CUDA(cudaMemsetAsync(d_counts, 0, 2 * sizeof(int64_t), s));
+    CountOneP p{lv[0].B, lv[0].U, (unsigned long long*)d_counts};
+    return launch_traverse<CountOne>(g, p, L, s);
+  }
+  CountMultiP p;
+  p.nt = n_tau;
+  for (int i = 0; i < n_tau; i++) {
+    p.B[i] = lv[order[i]].B;
+    p.U[i] = lv[order[i]].U;
+  }
+  p.hist = g->scratch->hist;
+  UBT_CUDA(cudaMemsetAsync(g->scratch->hist, 0, sizeof(g->scratch->hist), s));
+  st = launch_traverse<CountMulti>(g, p, L, s);
+  if (st != UBT_OK) return st;
+  FinishMulti f;
+  f.nt = n_tau;
+  for (int i = 0; i < n_tau; i++) f.perm[i] = order[i];
+  k_finish_multi<<<1, kMaxTau, 0, s>>>(g->scratch->hist, f, d_counts);
+  UBT_CUDA(cudaGetLastError());
+  return UBT_OK;
+}
+
+extern "C" ubt_status ubt_enumerate(ubt_graph* g, double tau, int32_t which, int32_t prune, ubt_tri_rec* d_out,
+                                    int64_t capacity, int64_t* h_n_found, void* stream) {
+  if (!g || !h_n_found || capacity < 0 || (capacity > 0 && !d_out)) return UBT_ERR_INVALID_ARG;
+  if (which < 1 || which > 3) return UBT_ERR_INVALID_ARG;
+  if (g->kind != UBT_GRAPH_FIXED) return UBT_ERR_UNSUPPORTED;
+  Level lv;
+  if (!tau_level(tau, &lv)) return UBT_ERR_TAU_OOB;
+  cudaStream_t s = (cudaStream_t)stream;
+  EnumP p{lv.B, lv.U, which, d_out, (unsigned long long)capacity, &g->scratch->enum_cursor};
+  ubt_status st = launch_traverse<Enum>(g, p, prune ? lv.L : 0, s);
+  if (st != UBT_OK) return st;
+  unsigned long long found = 0;
+  UBT_CUDA(cudaMemcpyAsync(&found, &g->scratch->enum_cursor, sizeof(found), cudaMemcpyDeviceToHost, s));
+  UBT_CUDA(cudaStreamSynchronize(s));
+  *h_n_found = (int64_t)found;
+  return found > (unsigned long long)capacity ? UBT_ERR_CAPACITY : UBT_OK;
+}
+
+extern "C" ubt_status ubt_expected_counts(ubt_graph* g, double* d_out, int64_t* d_exact, void* stream) {
+  if (!g || (!d_out && !d_exact)) return UBT_ERR_INVALID_ARG;
+  cudaStream_t s = (cudaStream_t)stream;
+  ExpectP p{&g->scratch->tri_count, &g->scratch->sum_lo, &g->scratch->sum_hi};
+  ubt_status st = g->kind == UBT_GRAPH_REAL ? launch_traverse<Expect<true>>(g, p, 0, s)
+                                            : launch_traverse<Expect<false>>(g, p, 0, s);
+  if (st != UBT_OK) return st;
+  k_finish_expect<<<1, 1, 0, s>>>(g->scratch, g->kind == UBT_GRAPH_REAL, d_out, d_exact);
+  UBT_CUDA(cudaGetLastError());
+  return UBT_OK;
+}
+
+extern "C" ubt_status ubt_expected_counts_backward(ubt_graph* g, const double* d_gout, float* d_grad_p,
+                                                   void* stream) {
+  if (!g || !d_gout || (!d_grad_p && g->m > 0)) return UBT_ERR_INVALID_ARG;
+  cudaStream_t s = (cudaStream_t)stream;
+  if (g->m == 0) return UBT_OK;
+  UBT_CUDA(cudaMemsetAsync(g->gacc, 0, sizeof(unsigned long long) * g->m, s));
+  AdjointP p{g->gacc};
+  const bool real = g->kind == UBT_GRAPH_REAL;
+  ubt_status st = real ? launch_traverse<Adjoint<true>>(g, p, 0, s) : launch_traverse<Adjoint<false>>(g, p, 0, s);
+  if (st != UBT_OK) return st;
+  const int grid = (int)std::min<int64_t>((g->m + 255) / 256, (int64_t)g->sm_count * 16);
+  k_finish_adjoint<<<grid, 256, 0, s>>>(g->m, g->gacc, g->eid, d_gout, real ? 0x1p-40 : 0x1p-30, d_grad_p);
+  UBT_CUDA(cudaGetLastError());
+  return UBT_OK;
+}
+
+extern "C" ubt_status ubt_traversal_stats(ubt_graph* g, const double* h_tau, int32_t n_tau, int32_t prune,
+                                          int64_t* h_out, void* stream) {
+  if (!g || !h_out) return UBT_ERR_INVALID_ARG;
+  int64_t L = 0;
+  if (prune) {
+    if (g->kind != UBT_GRAPH_FIXED) return UBT_ERR_UNSUPPORTED;
+    std::vector<Level> lv;
+    ubt_status st = check_taus(h_tau, n_tau, lv);
+    if (st != UBT_OK) return st;
+    L = lv[0].L;
+    for (const Level& x : lv) L = std::min(L, x.L);
+  }
+  cudaStream_t s = (cudaStream_t)stream;
+  unsigned long long* d = &g->scratch->hist[0];
+  UBT_CUDA(cudaMemsetAsync(d, 0, 3 * sizeof(unsigned long long), s));
+  if (g->n > 0) {
+    const int grid = (int)std::min<int64_t>((g->n + 7) / 8, (int64_t)g->sm_count * 16);
+    k_trav_stats<<<grid, 256, 0, s>>>(g->n, g->row_ptr, g->adj, L, d);
+    UBT_CUDA(cudaGetLastError());
+  }
+  unsigned long long h[3];
+  UBT_CUDA(cudaMemcpyAsync(h, d, sizeof(h), cudaMemcpyDeviceToHost, s));
+  UBT_CUDA(cudaStreamSynchronize(s));
+  h_out[0] = (int64_t)h[0];
+  h_out[1] = (int64_t)h[0];
+  h_out[2] = (int64_t)h[1];
+  h_out[3] = (int64_t)h[2];
+  return UBT_OK;
+}

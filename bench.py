@@ -180,6 +180,9 @@ def main():
     ap.add_argument("--extras", dest="extras", action="store_true", default=True)
     ap.add_argument("--no-extras", dest="extras", action="store_false")
     ap.add_argument("--no-cpu-baseline", dest="cpu", action="store_false", default=True)
+    ap.add_argument("--only", default=None, choices=["count", "count-unpruned", "worlds", "expected", "backward"],
+                    help="profiling driver: build the workload graph, run one form of the query "
+                         "--warmup + --steps times, print its mean time and exit")
     args = ap.parse_args()
     args.warmup = max(args.warmup, 3)
     if args.impl == "reference":
@@ -200,6 +203,8 @@ def main():
     import paper_2602_14084_gb300 as ubt
 
     g = make_graph(WORKLOAD)
+    if args.only:
+        return profile_driver(ubt, g, args)
     t0 = time.perf_counter()
     G = ubt.Graph(g.n, g.src, g.dst, k=g.k)
     torch.cuda.synchronize()
@@ -331,6 +336,35 @@ def main():
         print(json.dumps(line))
     if ws > 1:
         torch.distributed.destroy_process_group()
+    return 0
+
+
+def profile_driver(ubt, g, args):
+    """One form of the query on the workload graph, for ncu captures."""
+    import torch
+    import synth
+    if args.only in ("expected", "backward"):
+        p = synth.p_uniform_f32(g.m, 5)
+        G = ubt.Graph(g.n, g.src, g.dst, p=torch.from_numpy(p).cuda())
+    else:
+        G = ubt.Graph(g.n, g.src, g.dst, k=g.k)
+    counts = torch.empty(2 * len(TAUS), dtype=torch.int64, device="cuda")
+    eo = torch.empty(2, dtype=torch.float64, device="cuda")
+    gout = torch.tensor([1.0, 0.0], dtype=torch.float64, device="cuda")
+    grad = torch.empty(g.m, dtype=torch.float32, device="cuda")
+    W = 4096
+    if args.only == "worlds":
+        wws = torch.empty(G.sample_worlds_workspace(W), dtype=torch.uint8, device="cuda")
+        wout = torch.empty(W, dtype=torch.int64, device="cuda")
+    fn = {
+        "count": lambda: G.count_threshold_(TAUS, counts, prune=True),
+        "count-unpruned": lambda: G.count_threshold_(TAUS, counts, prune=False),
+        "worlds": lambda: G.sample_worlds_(7, W, wout, None, wws) if args.only == "worlds" else None,
+        "expected": lambda: G.expected_counts_(eo),
+        "backward": lambda: G.expected_counts_backward_(gout, grad),
+    }[args.only]
+    times = time_steps(fn, args.steps, args.warmup)
+    print(json.dumps({"only": args.only, "ms": 1e3 * float(np.mean(times)), "guard": G.guard()}))
     return 0
 
 

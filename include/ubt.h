@@ -187,14 +187,16 @@ ubt_status ubt_enumerate(ubt_graph* g, double tau, int32_t which, int32_t prune,
  * E_unbal = (T + sum_t S_t) / 2 with S_t the product of (1 - 2 P+) over the
  * triangle's edges (from the equation in Sec. 3; not in the paper).
  *   d_out    device double[2] = {E_bal, E_unbal}.
- *   d_exact  device int64[4] or NULL: {T, sum_lo, sum_hi, 0} where, for a
- *            FIXED graph, sum_hi:sum_lo is the exact two's-complement 128-bit
- *            sum of q_e q_f q_g over all triangles (E_bal = (T 2^45 - sum) /
- *            2^46 exactly); for a REAL graph it is the sum of S_t in signed
- *            64.64 fixed point... rounded per triangle to 2^-32 (see below).
+ *   d_exact  device int64[4] or NULL: {T, sum_lo, sum_hi, 0}: T triangles
+ *            and sum_hi:sum_lo a two's-complement 128-bit integer.  FIXED
+ *            graph: the exact sum of q_e q_f q_g over all triangles, so
+ *            E_bal = (T 2^45 - sum) / 2^46 exactly.  REAL graph: the sum of
+ *            S_t * 2^32, each term rounded to an integer.
  * Arithmetic: FIXED graphs are exact (int64 products, 128-bit sums).  REAL
- * graphs form S_t with float32 products and accumulate S_t rounded to a
- * multiple of 2^-32 in 64-bit integers, then finish in double.
+ * graphs hold s = 1 - 2p as s * 2^30 rounded to an int32 (exact for
+ * p >= 2^-7, within 2^-31 otherwise); the products are exact int64 products
+ * of these, rounded once to 2^-30 and once to 2^-32 per triangle; the sum is
+ * exact in 128 bits and converted to double at the end.
  */
 ubt_status ubt_expected_counts(ubt_graph* g, double* d_out, int64_t* d_exact, void* stream);
 
@@ -206,7 +208,8 @@ ubt_status ubt_expected_counts(ubt_graph* g, double* d_out, int64_t* d_exact, vo
  *   d_gout    device double[2] = {g_bal, g_unbal} (upstream gradients).
  *   d_grad_p  device float[m], input edge order (overwritten).
  * Arithmetic: FIXED graphs exact in int64 before the final scaling; REAL
- * graphs float32 products accumulated in 64-bit integers at 2^-40 resolution.
+ * graphs exact int64 products of the 2^-30 fixed-point s values, rounded to
+ * 2^-40 and accumulated in 64-bit integers, scaled to float at the end.
  */
 ubt_status ubt_expected_counts_backward(ubt_graph* g, const double* d_gout, float* d_grad_p,
                                         void* stream);
@@ -271,17 +274,52 @@ ubt_status ubt_traversal_stats(ubt_graph* g, const double* h_tau, int32_t n_tau,
                                int64_t* h_out, void* stream);
 
 /*
+ * ubt_query_guard -- SYNC.  Reads and clears the self-check word of the
+ * graph's traversals: 0 when every check since the last call passed, else
+ * (code << 56 | detail) of the first failure (1/2 hash-table probe limit in
+ * find/insert, 3 neighbour id >= n, 4 list offsets out of range, 5 table
+ * larger than its region).  A failed check skips the access it guards.
+ */
+ubt_status ubt_query_guard(ubt_graph* g, int64_t* h_word, void* stream);
+
+/*
+ * ubt_graph_export -- SYNC.  Copies the built graph to host memory for
+ * inspection (any pointer may be NULL):
+ *   h_row_ptr  uint32[n + 1] forward-list offsets
+ *   h_adj      uint64[m] entries (low 32 bits neighbour id, high 32 bits the
+ *              value: q = 32768 - k as int32 for FIXED graphs, round(s 2^30)
+ *              as int32 for REAL graphs)
+ *   h_eid      uint32[m] input edge index of every entry
+ *   h_lists    uint32[tasks] the work lists: giant, hub and medium tasks,
+ *              then the short lists in vertex order
+ *   h_list_sizes int64[4] the four sizes
+ */
+ubt_status ubt_graph_export(const ubt_graph* g, uint32_t* h_row_ptr, uint64_t* h_adj, uint32_t* h_eid,
+                            uint32_t* h_lists, int64_t* h_list_sizes, void* stream);
+
+/*
  * ubt_set_tuning / ubt_get_tuning -- process-wide launch parameters that the
  * autotuner picks (they change speed, never results).  Unknown names return
  * UBT_ERR_INVALID_ARG.  Names:
- *   "hub_threshold"   forward-list length above which a vertex is handled by
- *                     a whole thread block (default 48)
- *   "hub_threads"     threads per block of the hub phase (128..1024, /32)
- *   "blocks_per_sm"   persistent blocks per SM (1..32)
+ *   "short_max"       forward lists of 2..short_max entries are concatenated
+ *                     and processed in 32-pair segments, one warp each
+ *                     (2..32, default 16)
+ *   "hub_threshold"   longer lists than this are whole-block tasks; lists
+ *                     between short_max and it are one-warp tasks (default 64)
+ *   "hub_threads"     threads per block of the traversal (64..512, /32)
+ *   "blocks_per_sm"   cap on resident blocks per SM (1..32; occupancy decides
+ *                     below it)
  *   "smem_table_max"  hash-table slots kept in shared memory (power of two);
  *                     longer lists use a table in global scratch
+ *   "block_unit"      pairs a warp takes at a time inside a block task (1..32)
  *   "world_words_per_pass"  64-world words per traversal of ubt_sample_worlds
  *                     (1, 2, 4, 8, 16, 32 or 64)
+ *   "small_batch"     warp tasks / segments taken per grab of a task counter
+ *   "sort_smem_max"   longest forward list sorted in shared memory during the
+ *                     build (power of two, 64..4096); longer lists are sorted
+ *                     in a global-memory slice
+ * Build-time knobs (short_max, hub_threshold, smem_table_max, sort_smem_max)
+ * apply to * graphs created afterwards; query the workspace size after setting them.
  */
 ubt_status ubt_set_tuning(const char* name, int64_t value);
 ubt_status ubt_get_tuning(const char* name, int64_t* h_value);

@@ -74,6 +74,8 @@ def lib():
             "ubt_count_host_workspace_size": (I32, [I64, I64, ctypes.POINTER(SZ)]),
             "ubt_count_host": (I32, [I64, I64, P, P, P, P, I32, I32, P, P, SZ, P]),
             "ubt_traversal_stats": (I32, [P, P, I32, I32, P, P]),
+            "ubt_query_guard": (I32, [P, ctypes.POINTER(I64), P]),
+            "ubt_graph_export": (I32, [P, P, P, P, P, P, P]),
             "ubt_set_tuning": (I32, [ctypes.c_char_p, I64]),
             "ubt_get_tuning": (I32, [ctypes.c_char_p, ctypes.POINTER(I64)]),
         }
@@ -208,6 +210,28 @@ class Graph:
                                          out.ctypes.data_as(ctypes.c_void_p), _stream(stream)),
                "ubt_traversal_stats")
         return {"table_entries": int(out[0]), "pairs": int(out[1]), "streamed": int(out[2]), "tasks": int(out[3])}
+
+    def guard(self, stream=None) -> int:
+        """Reads and clears the traversal self-check word (0 = all checks passed)."""
+        w = ctypes.c_int64(0)
+        _check(lib().ubt_query_guard(self._h, ctypes.byref(w), _stream(stream)), "ubt_query_guard")
+        return int(w.value)
+
+    def export(self, stream=None) -> dict:
+        """The built forward CSR and work lists, copied to host numpy arrays."""
+        sizes = np.zeros(4, dtype=np.int64)
+        _check(lib().ubt_graph_export(self._h, None, None, None, None, sizes.ctypes.data_as(ctypes.c_void_p),
+                                      _stream(stream)), "ubt_graph_export")
+        rp = np.zeros(self.n + 1, dtype=np.uint32)
+        adj = np.zeros(max(self.m, 1), dtype=np.uint64)
+        eid = np.zeros(max(self.m, 1), dtype=np.uint32)
+        lists = np.zeros(max(int(sizes.sum()), 1), dtype=np.uint32)
+        c = lambda a: a.ctypes.data_as(ctypes.c_void_p)
+        _check(lib().ubt_graph_export(self._h, c(rp), c(adj), c(eid), c(lists), None, _stream(stream)),
+               "ubt_graph_export")
+        return {"row_ptr": rp, "col": (adj[: self.m] & 0xFFFFFFFF).astype(np.uint32),
+                "val": (adj[: self.m] >> 32).astype(np.uint32).view(np.int32), "eid": eid[: self.m],
+                "lists": lists[: int(sizes.sum())], "list_sizes": sizes}
 
     # ---------------------------------------------------------------- queries
 

@@ -9,7 +9,9 @@
 //              graphs -- by |q| descending so that pruned entries (Lemma 2)
 //              form a suffix of every list
 //   work lists vertices with >= 2 forward entries, split by list length into
-//              block tasks and warp tasks, ordered by decreasing wedge count
+//              block tasks and warp tasks (ordered by decreasing wedge count)
+//              and short lists (concatenated in vertex order, cut into
+//              32-pair segments that never cross a batch graph)
 #include <math.h>
 #include <string.h>
 
@@ -22,7 +24,6 @@ namespace ubt {
 
 namespace {
 
-constexpr int kSortSmemMax = 4096;   // longest list sorted in shared memory
 constexpr int kSortHugeBlocks = 16;  // blocks sorting lists longer than that
 constexpr int kBuckets = 64;
 
@@ -90,7 +91,9 @@ __global__ void k_scatter(int64_t m, const uint32_t* __restrict__ src, const uin
     if (k) {
       val = (uint32_t)(int32_t)(32768 - (int32_t)k[i]);     // q = 32768 - k
     } else {
-      val = __float_as_uint(fmaf(-2.0f, p[i], 1.0f));       // s = 1 - 2p
+      // s = 1 - 2p as a 2^-30 fixed-point integer: 1 - 2p is exact in double for
+      // float32 p >= 2^-29, and the rounding to the 2^-30 grid is exact for p >= 2^-7
+      val = (uint32_t)(int32_t)__double2ll_rn((1.0 - 2.0 * (double)p[i]) * 1073741824.0);
     }
     adj[pos] = adj_pack(hi, val);
     eid[pos] = (uint32_t)i;
@@ -154,7 +157,7 @@ __global__ void k_sort_short_rows(int64_t n, const uint32_t* __restrict__ row_pt
 }
 
 // Longer lists: one block per list, bitonic network in shared memory (or in a
-// per-block global slice for lists longer than kSortSmemMax).
+// per-block global slice for lists longer than the "sort_smem_max" tuning).
 template <bool kGlobal>
 __global__ void k_sort_long_rows(const uint32_t* __restrict__ rows, uint32_t nrows, const uint32_t* __restrict__ row_ptr,
                                  uint64_t* adj, uint32_t* eid, uint32_t* ekey, int fixed, unsigned long long* err,
@@ -220,20 +223,28 @@ __global__ void k_sort_long_rows(const uint32_t* __restrict__ rows, uint32_t nro
   }
 }
 
-__global__ void k_collect_long(int64_t n, const uint32_t* __restrict__ row_ptr, uint32_t* mid, uint32_t* huge,
-                               unsigned long long* counts) {
+__global__ void k_collect_long(int64_t n, const uint32_t* __restrict__ row_ptr, uint32_t smem_max, uint32_t* mid,
+                               uint32_t* huge, unsigned long long* counts) {
   for (int64_t u = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; u < n; u += (int64_t)gridDim.x * blockDim.x) {
     const uint32_t len = row_ptr[u + 1] - row_ptr[u];
-    if (len > 32 && len <= (uint32_t)kSortSmemMax) mid[atomicAdd(&counts[0], 1ull)] = (uint32_t)u;
-    else if (len > (uint32_t)kSortSmemMax) huge[atomicAdd(&counts[1], 1ull)] = (uint32_t)u;
+    if (len > 32 && len <= smem_max) mid[atomicAdd(&counts[0], 1ull)] = (uint32_t)u;
+    else if (len > smem_max && len > 32) huge[atomicAdd(&counts[1], 1ull)] = (uint32_t)u;
   }
 }
 
-// Per vertex: wedge count sum_{v in N>(u)} |N>(v)|, its log2 bucket, class.
-// stats: [0] wedges, [1] max list, [2] max hub list, [3 + 2*b + cls] bucket sizes
+// Task classes by forward-list length (0 = none: fewer than 2 entries)
+enum : uint8_t { kClsShort = 0, kClsMedium = 1, kClsHub = 2, kClsGiant = 3 };
+constexpr uint8_t kNoTask = 0xFF, kShortTask = 0xFE;
+constexpr int kLgMax = 47;  // wedge-count buckets 2^0 .. 2^47
+
+// Per vertex: wedge count sum_{v in N>(u)} |N>(v)|, its log2 bucket and class.
+//   bucket[u] = lg * 4 + cls for medium / hub / giant lists, kShortTask for
+//   short lists, kNoTask for lists of fewer than 2 entries.
+// stats: [0] wedges, [1] longest list, [2] longest hub list, [3] short lists,
+//        [4 + lg * 4 + cls] bucket sizes
 __global__ void k_row_stats(int64_t n, const uint32_t* __restrict__ row_ptr, const uint64_t* __restrict__ adj,
-                            uint32_t hub_thr, uint32_t giant_thr, uint8_t* __restrict__ bucket,
-                            unsigned long long* stats) {
+                            uint32_t short_max, uint32_t hub_thr, uint32_t giant_thr, uint8_t* __restrict__ bucket,
+                            uint32_t* __restrict__ short_flag, unsigned long long* stats) {
   const int lane = threadIdx.x & 31;
   const int64_t warps = (int64_t)gridDim.x * (blockDim.x >> 5);
   for (int64_t u = blockIdx.x * (int64_t)(blockDim.x >> 5) + (threadIdx.x >> 5); u < n; u += warps) {
@@ -247,15 +258,22 @@ __global__ void k_row_stats(int64_t n, const uint32_t* __restrict__ row_ptr, con
 #pragma unroll
     for (int d = 16; d > 0; d >>= 1) w += __shfl_xor_sync(kFull, w, d);
     if (lane == 0) {
-      uint8_t b = 0xFF;
-      if (len >= 2) {
-        const int cls = len > giant_thr ? 2 : (len > hub_thr ? 1 : 0);
-        const int lg = w ? 63 - __clzll(w) : 0;
-        b = (uint8_t)(lg * 3 + cls);
-        atomicAdd(&stats[3 + b], 1ull);
-        if (cls >= 1) atomicMax(&stats[2], (unsigned long long)len);
+      uint8_t b = kNoTask;
+      uint32_t sf = 0;
+      if (len >= 2 && len <= short_max) {
+        b = kShortTask;
+        sf = 1;
+        atomicAdd(&stats[3], 1ull);
+      } else if (len >= 2) {
+        const int cls = len > giant_thr ? kClsGiant : (len > hub_thr ? kClsHub : kClsMedium);
+        int lg = w ? 63 - __clzll(w) : 0;
+        lg = lg > kLgMax ? kLgMax : lg;
+        b = (uint8_t)(lg * 4 + cls);
+        atomicAdd(&stats[4 + b], 1ull);
+        if (cls == kClsHub) atomicMax(&stats[2], (unsigned long long)len);
       }
       bucket[u] = b;
+      short_flag[u] = sf;
       atomicAdd(&stats[0], w);
       atomicMax(&stats[1], (unsigned long long)len);
     }
@@ -266,8 +284,44 @@ __global__ void k_fill_lists(int64_t n, const uint8_t* __restrict__ bucket, unsi
                              uint32_t* __restrict__ lists) {
   for (int64_t u = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; u < n; u += (int64_t)gridDim.x * blockDim.x) {
     const uint8_t b = bucket[u];
-    if (b == 0xFF) continue;
+    if (b == kNoTask || b == kShortTask) continue;
     lists[atomicAdd(&cursor[b], 1ull)] = (uint32_t)u;
+  }
+}
+
+// short lists in vertex order (stable compaction by the scanned flags) and
+// their lengths; per batch graph, the sum of its short-list lengths
+__global__ void k_short_rows(int64_t n, const uint32_t* __restrict__ flag, const uint32_t* __restrict__ idx,
+                             const uint32_t* __restrict__ row_ptr, const uint32_t* __restrict__ vgraph,
+                             uint32_t* __restrict__ seg_row, uint32_t* __restrict__ slen, uint32_t* __restrict__ gsum) {
+  for (int64_t u = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; u < n; u += (int64_t)gridDim.x * blockDim.x) {
+    if (!flag[u]) continue;
+    const uint32_t r = idx[u];
+    const uint32_t len = row_ptr[u + 1] - row_ptr[u];
+    seg_row[r] = (uint32_t)u;
+    slen[r] = len;
+    if (vgraph) atomicAdd(&gsum[vgraph[u]], len);
+  }
+}
+
+// padding that starts every batch graph's short lists on a multiple of 32
+__global__ void k_graph_pad(int64_t ng, uint32_t* gsum) {
+  for (int64_t g = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; g < ng; g += (int64_t)gridDim.x * blockDim.x)
+    gsum[g] = ((gsum[g] + 31u) & ~31u) - gsum[g];
+}
+
+__global__ void k_seg_first(int64_t nr, const uint32_t* __restrict__ seg_row, uint32_t* __restrict__ seg_start,
+                            const uint32_t* __restrict__ slen, const uint32_t* __restrict__ vgraph,
+                            const uint32_t* __restrict__ gpad, uint32_t* __restrict__ seg_first) {
+  for (int64_t r = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; r < nr; r += (int64_t)gridDim.x * blockDim.x) {
+    uint32_t st = seg_start[r];
+    if (vgraph) {
+      st += gpad[vgraph[seg_row[r]]];
+      seg_start[r] = st;
+    }
+    const uint32_t k0 = st / 32, k1 = (st + slen[r] - 1) / 32;
+    atomicMin(&seg_first[k0], (uint32_t)r);
+    if (k1 != k0) atomicMin(&seg_first[k1], (uint32_t)r);
   }
 }
 
@@ -278,7 +332,11 @@ struct BuildLayout {
   uint64_t* adj;
   uint32_t* eid;
   uint32_t* ekey;
-  uint32_t* lists;       // giant | hub | small lists, n entries
+  uint32_t* lists;       // giant | hub | medium lists
+  uint32_t* seg_row;     // short lists, vertex order
+  uint32_t* seg_start;   // their starts in the concatenation (+ total)
+  uint32_t* seg_first;   // first short list touching each segment
+  int64_t seg_cap;
   uint32_t* vgraph;
   unsigned long long* gacc;
   unsigned long long* bacc;
@@ -289,11 +347,13 @@ struct BuildLayout {
   uint32_t* scan_tmp;
   uint32_t* mid_rows;
   uint32_t* huge_rows;
+  uint32_t* gsum;
   uint8_t* bucket;
-  unsigned long long* stats;   // 3 + 3*64 counters, then 3*64 cursors, then 2 counters
+  unsigned long long* stats;   // 4 + 4*48 counters, 4*48 cursors, 2 counters
   char* sort_tmp;
   size_t total;
 };
+constexpr int kStats = 4 + 4 * (kLgMax + 1);
 
 int64_t list_bound(int64_t n, int64_t m) {
   // a forward list under Node Order holds at most sqrt(2m) entries
@@ -313,27 +373,34 @@ BuildLayout layout(void* ws, size_t cap, int64_t n, int64_t m, const ubt_graph_o
   const bool has_key = opts && opts->d_edge_key;
   const bool batch = opts && opts->d_vertex_offsets;
   const int64_t ng = batch ? opts->n_graphs : 1;
+  const int64_t n1 = std::max<int64_t>(n, 1);
   L.scratch = c.take<Scratch>(1);
   L.row_ptr = c.take<uint32_t>(n + 1);
   L.adj = c.take<uint64_t>(std::max<int64_t>(m, 1));
   L.eid = c.take<uint32_t>(std::max<int64_t>(m, 1));
   L.ekey = has_key ? c.take<uint32_t>(std::max<int64_t>(m, 1)) : nullptr;
-  L.lists = c.take<uint32_t>(std::max<int64_t>(n, 1));
-  L.vgraph = batch ? c.take<uint32_t>(std::max<int64_t>(n, 1)) : nullptr;
+  L.lists = c.take<uint32_t>(n1);
+  L.seg_row = c.take<uint32_t>(n1);
+  L.seg_start = c.take<uint32_t>(n + 1);
+  L.seg_cap = (m + 32 * (ng + 1)) / 32 + 2;
+  L.seg_first = c.take<uint32_t>(L.seg_cap);
+  L.vgraph = batch ? c.take<uint32_t>(n1) : nullptr;
   L.gacc = c.take<unsigned long long>(std::max<int64_t>(m, 1));
   // per graph: T, sum_lo, sum_hi (expected counts) of a batch
   L.bacc = c.take<unsigned long long>(3 * std::max<int64_t>(ng, 1));
   const int64_t gslots = gtab_slots_for(m);
   L.gtab = gslots ? c.take<uint32_t>((size_t)gslots * 3 * (size_t)sm_count) : nullptr;
-  L.deg = c.take<uint32_t>(std::max<int64_t>(n, 1));
-  L.fill = c.take<uint32_t>(std::max<int64_t>(n, 1));
-  L.scan_tmp = c.take<uint32_t>(scan_tmp_words(n) + 2);
-  L.mid_rows = c.take<uint32_t>(std::max<int64_t>(n, 1));
-  L.huge_rows = c.take<uint32_t>(std::max<int64_t>(n, 1));
-  L.bucket = c.take<uint8_t>(std::max<int64_t>(n, 1));
-  L.stats = c.take<unsigned long long>(3 + 2 * 3 * kBuckets + 2);
+  L.deg = c.take<uint32_t>(n + 1);
+  L.fill = c.take<uint32_t>(n + 1);
+  L.scan_tmp = c.take<uint32_t>(scan_tmp_words(std::max(n, ng)) + 2);
+  L.mid_rows = c.take<uint32_t>(n1);
+  L.huge_rows = c.take<uint32_t>(n1);
+  L.gsum = batch ? c.take<uint32_t>(ng + 1) : nullptr;
+  L.bucket = c.take<uint8_t>(n1);
+  L.stats = c.take<unsigned long long>(2 * kStats + 2);
   const int64_t lb = list_bound(n, m);
-  L.sort_tmp = lb > kSortSmemMax ? c.take<char>((size_t)kSortHugeBlocks * (size_t)pow2_at_least(lb) * 24) : nullptr;
+  L.sort_tmp = lb > tuning().sort_smem_max
+                   ? c.take<char>((size_t)kSortHugeBlocks * (size_t)pow2_at_least(lb) * 24) : nullptr;
   L.total = c.off + 256;
   return L;
 }
@@ -354,9 +421,10 @@ ubt_status status_from_err(unsigned long long e) {
 }  // namespace
 
 int64_t gtab_slots_for(int64_t m) {
-  // lists whose table (2x the list, power of two) exceeds the shared-memory
-  // table get a table in global memory; size it for the longest possible list
-  const int64_t need = pow2_at_least(2 * list_bound(INT64_MAX / 4, m));
+  // a list's table holds 4x its entries (power of two); lists whose table
+  // exceeds the shared-memory limit get one in global memory, sized for the
+  // longest possible list
+  const int64_t need = pow2_at_least(4 * list_bound(INT64_MAX / 4, m));
   return need > tuning().smem_table_max ? need : 0;
 }
 
@@ -382,9 +450,9 @@ extern "C" ubt_status ubt_create_graph(int64_t n, int64_t m, const uint32_t* d_s
   *h_out = nullptr;
   if (n < 0 || m < 0 || n >= 0xFFFFFFFFll || m >= 0xFFFFFFFFll) return UBT_ERR_INVALID_ARG;
   if (flags == UBT_GRAPH_FIXED) {
-    if (!d_k || d_p) return UBT_ERR_INVALID_ARG;
+    if ((m > 0 && !d_k) || d_p) return UBT_ERR_INVALID_ARG;
   } else if (flags == UBT_GRAPH_REAL) {
-    if (!d_p || d_k) return UBT_ERR_INVALID_ARG;
+    if ((m > 0 && !d_p) || d_k) return UBT_ERR_INVALID_ARG;
   } else {
     return UBT_ERR_INVALID_ARG;
   }
@@ -392,20 +460,22 @@ extern "C" ubt_status ubt_create_graph(int64_t n, int64_t m, const uint32_t* d_s
   if (!d_workspace || ((uintptr_t)d_workspace & 255)) return UBT_ERR_INVALID_ARG;
   const bool batch = opts && opts->d_vertex_offsets;
   if (batch && opts->n_graphs < 1) return UBT_ERR_INVALID_ARG;
+  const int64_t ng = batch ? opts->n_graphs : 1;
   int dev = 0;
   const int sms = device_sm_count(&dev);
   BuildLayout L = layout(d_workspace, ws_bytes, n, m, opts, sms);
   if (ws_bytes < L.total) return UBT_ERR_WORKSPACE_TOO_SMALL;
   cudaStream_t s = (cudaStream_t)stream;
   const Tuning& T = tuning();
-  const int hub_thr = (int)std::max<int64_t>(2, T.hub_threshold);
-  const int64_t giant_thr = tuning().smem_table_max / 2;
+  const int64_t short_max = std::min<int64_t>(std::max<int64_t>(2, T.short_max), 32);
+  const int64_t hub_thr = std::max<int64_t>(short_max, T.hub_threshold);
+  const int64_t giant_thr = std::max<int64_t>(hub_thr, T.smem_table_max / 4);
 
   UBT_CUDA(cudaMemsetAsync(L.scratch, 0, sizeof(Scratch), s));
   UBT_CUDA(cudaMemsetAsync(&L.scratch->err, 0xFF, sizeof(unsigned long long), s));
-  UBT_CUDA(cudaMemsetAsync(L.deg, 0, sizeof(uint32_t) * std::max<int64_t>(n, 1), s));
-  UBT_CUDA(cudaMemsetAsync(L.fill, 0, sizeof(uint32_t) * std::max<int64_t>(n, 1), s));
-  UBT_CUDA(cudaMemsetAsync(L.stats, 0, sizeof(unsigned long long) * (3 + 2 * 3 * kBuckets + 2), s));
+  UBT_CUDA(cudaMemsetAsync(L.deg, 0, sizeof(uint32_t) * (n + 1), s));
+  UBT_CUDA(cudaMemsetAsync(L.fill, 0, sizeof(uint32_t) * (n + 1), s));
+  UBT_CUDA(cudaMemsetAsync(L.stats, 0, sizeof(unsigned long long) * (2 * kStats + 2), s));
   const int thr = 256;
   const int grid_e = (int)std::min<int64_t>(std::max<int64_t>((m + thr - 1) / thr, 1), (int64_t)sms * 32);
   const int grid_v = (int)std::min<int64_t>(std::max<int64_t>((n + thr - 1) / thr, 1), (int64_t)sms * 32);
@@ -425,21 +495,22 @@ extern "C" ubt_status ubt_create_graph(int64_t n, int64_t m, const uint32_t* d_s
   // 2. orientation + CSR offsets
   if (m > 0) k_out_degree<<<grid_e, thr, 0, s>>>(m, d_src, d_dst, L.deg, L.fill);
   UBT_CUDA(exclusive_scan_u32(L.fill, L.row_ptr, n, L.scan_tmp, s));
-  UBT_CUDA(cudaMemsetAsync(L.fill, 0, sizeof(uint32_t) * std::max<int64_t>(n, 1), s));
+  UBT_CUDA(cudaMemsetAsync(L.fill, 0, sizeof(uint32_t) * (n + 1), s));
   if (m > 0)
     k_scatter<<<grid_e, thr, 0, s>>>(m, d_src, d_dst, d_k, d_p, L.deg, L.row_ptr, L.fill, L.adj, L.eid,
                                      opts ? opts->d_edge_key : nullptr, L.ekey);
   // 3. sort every forward list
   const int fixed = flags == UBT_GRAPH_FIXED;
+  unsigned long long* lcount = L.stats + 2 * kStats;
   if (n > 0) {
     k_sort_short_rows<<<grid_w, thr, 0, s>>>(n, L.row_ptr, L.adj, L.eid, L.ekey, fixed, &L.scratch->err);
-    unsigned long long* lcount = L.stats + 3 + 2 * 3 * kBuckets;
-    k_collect_long<<<grid_v, thr, 0, s>>>(n, L.row_ptr, L.mid_rows, L.huge_rows, lcount);
+    const uint32_t sort_smem = (uint32_t)tuning().sort_smem_max;
+    k_collect_long<<<grid_v, thr, 0, s>>>(n, L.row_ptr, sort_smem, L.mid_rows, L.huge_rows, lcount);
     unsigned long long lc[2] = {0, 0};
     UBT_CUDA(cudaMemcpyAsync(lc, lcount, sizeof(lc), cudaMemcpyDeviceToHost, s));
     UBT_CUDA(cudaStreamSynchronize(s));
     if (lc[0]) {
-      const size_t smem = (size_t)kSortSmemMax * 24;
+      const size_t smem = (size_t)std::max<uint32_t>(sort_smem, 64) * 24;
       UBT_CUDA(cudaFuncSetAttribute(k_sort_long_rows<false>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
       const int g = (int)std::min<unsigned long long>(lc[0], (unsigned long long)sms * 8);
       k_sort_long_rows<false><<<g, 512, smem, s>>>(L.mid_rows, (uint32_t)lc[0], L.row_ptr, L.adj, L.eid, L.ekey,
@@ -457,56 +528,84 @@ extern "C" ubt_status ubt_create_graph(int64_t n, int64_t m, const uint32_t* d_s
   UBT_CUDA(cudaStreamSynchronize(s));
   st = status_from_err(err);
   if (st != UBT_OK) return st;
-  // 4. work lists: giant (global table) | hub (block) | small (warp), each by
-  //    decreasing wedge-count bucket
-  unsigned long long stats[3 + 3 * kBuckets];
+  // 4. work lists: giant | hub | medium tasks, each by decreasing wedge-count
+  //    bucket; short lists concatenated in vertex order and cut into segments
+  unsigned long long stats[kStats];
   memset(stats, 0, sizeof(stats));
   if (n > 0) {
-    k_row_stats<<<grid_w, thr, 0, s>>>(n, L.row_ptr, L.adj, (uint32_t)hub_thr, (uint32_t)giant_thr, L.bucket,
-                                      L.stats);
+    k_row_stats<<<grid_w, thr, 0, s>>>(n, L.row_ptr, L.adj, (uint32_t)short_max, (uint32_t)hub_thr,
+                                      (uint32_t)giant_thr, L.bucket, L.fill, L.stats);
     UBT_CUDA(cudaMemcpyAsync(stats, L.stats, sizeof(stats), cudaMemcpyDeviceToHost, s));
     UBT_CUDA(cudaStreamSynchronize(s));
   }
-  // list order: giant tasks, then hub tasks, then small tasks (cls 2, 1, 0)
-  unsigned long long cursor[3 * kBuckets];
-  int64_t count_cls[3] = {0, 0, 0};
-  for (int b = 0; b < 3 * kBuckets; b++) count_cls[b % 3] += (int64_t)stats[3 + b];
-  int64_t run[3];
-  run[2] = 0;
-  run[1] = count_cls[2];
-  run[0] = count_cls[2] + count_cls[1];
-  // within a class: buckets from the largest wedge count down
-  for (int lg = kBuckets - 1; lg >= 0; lg--) {
-    for (int cls = 0; cls < 3; cls++) {
-      const int b = lg * 3 + cls;
+  unsigned long long cursor[4 * (kLgMax + 1)];
+  int64_t count_cls[4] = {0, 0, 0, 0};
+  for (int b = 0; b < 4 * (kLgMax + 1); b++) count_cls[b % 4] += (int64_t)stats[4 + b];
+  int64_t run[4];
+  run[kClsGiant] = 0;
+  run[kClsHub] = count_cls[kClsGiant];
+  run[kClsMedium] = count_cls[kClsGiant] + count_cls[kClsHub];
+  run[kClsShort] = 0;
+  for (int lg = kLgMax; lg >= 0; lg--) {
+    for (int cls = 1; cls < 4; cls++) {
+      const int b = lg * 4 + cls;
       cursor[b] = (unsigned long long)run[cls];
-      run[cls] += (int64_t)stats[3 + b];
+      run[cls] += (int64_t)stats[4 + b];
     }
   }
+  const int64_t n_srows = (int64_t)stats[3];
+  uint32_t seg_total = 0;
   if (n > 0) {
-    unsigned long long* dcur = L.stats + 3 + 3 * kBuckets;
+    unsigned long long* dcur = L.stats + kStats;
     UBT_CUDA(cudaMemcpyAsync(dcur, cursor, sizeof(cursor), cudaMemcpyHostToDevice, s));
     k_fill_lists<<<grid_v, thr, 0, s>>>(n, L.bucket, dcur, L.lists);
+    // short lists: compaction in vertex order, then their starts
+    UBT_CUDA(exclusive_scan_u32(L.fill, L.deg, n, L.scan_tmp, s));
+    if (batch) UBT_CUDA(cudaMemsetAsync(L.gsum, 0, sizeof(uint32_t) * (ng + 1), s));
+    k_short_rows<<<grid_v, thr, 0, s>>>(n, L.fill, L.deg, L.row_ptr, L.vgraph, L.seg_row, L.mid_rows, L.gsum);
+    UBT_CUDA(exclusive_scan_u32(L.mid_rows, L.seg_start, n_srows, L.scan_tmp, s));
+    if (batch) {
+      const int grid_g = (int)std::min<int64_t>(std::max<int64_t>((ng + thr - 1) / thr, 1), (int64_t)sms * 32);
+      k_graph_pad<<<grid_g, thr, 0, s>>>(ng, L.gsum);
+      UBT_CUDA(exclusive_scan_u32(L.gsum, L.gsum, ng, L.scan_tmp, s));
+    }
+    uint32_t tot[2] = {0, 0};
+    UBT_CUDA(cudaMemcpyAsync(&tot[0], L.seg_start + n_srows, sizeof(uint32_t), cudaMemcpyDeviceToHost, s));
+    if (batch) UBT_CUDA(cudaMemcpyAsync(&tot[1], L.gsum + ng, sizeof(uint32_t), cudaMemcpyDeviceToHost, s));
+    UBT_CUDA(cudaMemsetAsync(L.seg_first, 0xFF, sizeof(uint32_t) * L.seg_cap, s));
+    if (n_srows > 0) {
+      const int grid_r = (int)std::min<int64_t>((n_srows + thr - 1) / thr, (int64_t)sms * 32);
+      k_seg_first<<<grid_r, thr, 0, s>>>(n_srows, L.seg_row, L.seg_start, L.mid_rows, L.vgraph, L.gsum,
+                                        L.seg_first);
+    }
     UBT_CUDA(cudaGetLastError());
     UBT_CUDA(cudaStreamSynchronize(s));
+    seg_total = tot[0] + tot[1];
   }
+  const int64_t n_segs = ((int64_t)seg_total + 31) / 32;
+  if (n_segs > L.seg_cap) return UBT_ERR_INVALID_ARG;
 
   ubt_graph* g = new (std::nothrow) ubt_graph();
   if (!g) return UBT_ERR_INVALID_ARG;
   g->n = n;
   g->m = m;
   g->kind = flags;
-  g->n_graphs = batch ? opts->n_graphs : 1;
+  g->n_graphs = ng;
   g->row_ptr = L.row_ptr;
   g->adj = L.adj;
   g->eid = L.eid;
   g->ekey = L.ekey ? L.ekey : L.eid;
   g->giant_list = L.lists;
-  g->n_giant = count_cls[2];
-  g->hub_list = L.lists + count_cls[2];
-  g->n_hub = count_cls[1];
-  g->small_list = L.lists + count_cls[2] + count_cls[1];
-  g->n_small = count_cls[0];
+  g->n_giant = count_cls[kClsGiant];
+  g->hub_list = L.lists + count_cls[kClsGiant];
+  g->n_hub = count_cls[kClsHub];
+  g->med_list = L.lists + count_cls[kClsGiant] + count_cls[kClsHub];
+  g->n_med = count_cls[kClsMedium];
+  g->seg_row = L.seg_row;
+  g->seg_start = L.seg_start;
+  g->seg_first = L.seg_first;
+  g->n_srows = n_srows;
+  g->n_segs = n_segs;
   g->vgraph = L.vgraph;
   g->gacc = L.gacc;
   g->bacc = L.bacc;
@@ -517,6 +616,7 @@ extern "C" ubt_status ubt_create_graph(int64_t n, int64_t m, const uint32_t* d_s
   g->wedges = (int64_t)stats[0];
   g->max_out = (int64_t)stats[1];
   g->max_hub_len = (int64_t)stats[2];
+  g->short_max = short_max;
   g->hub_threshold = hub_thr;
   g->giant_threshold = giant_thr;
   g->device = dev;

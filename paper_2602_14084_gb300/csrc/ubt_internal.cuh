@@ -15,9 +15,10 @@ namespace ubt {
 // the neighbours later than u in (degree, id) order.  Each entry is one
 // 64-bit word: low 32 bits the neighbour id, high 32 bits the edge value:
 //   FIXED graphs: q = 32768 - k as int32 (1 - 2 P+ = q / 2^15)
-//   REAL graphs:  s = 1 - 2 p as float32 bits
-// Every row is sorted by |value| descending, ties by neighbour id, so the
-// entries a pruning level removes form a suffix of the row (Lemma 2).
+//   REAL graphs:  s = 1 - 2 p as int32 fixed point, s * 2^30 rounded
+// FIXED rows are sorted by |q| descending, ties by neighbour id, so the
+// entries a pruning level removes form a suffix of the row (Lemma 2); REAL
+// rows by neighbour id.
 // eid[pos] is the input index of the edge stored at CSR position pos.
 
 constexpr uint32_t kEmpty = 0xFFFFFFFFu;
@@ -39,7 +40,8 @@ struct Scratch {
   unsigned long long sum_lo;        // 128-bit two's-complement sum, low word
   unsigned long long sum_hi;        // high word
   unsigned long long err;           // device-side error word (build)
-  unsigned long long pad[7];
+  unsigned long long guard;         // first failed self-check of a query (0 = none)
+  unsigned long long pad[6];
   unsigned long long hist[2 * 65];  // multi-threshold histograms (bal, unbal)
 };
 constexpr size_t kScratchHeader = 16 * sizeof(unsigned long long);  // zeroed per query
@@ -57,8 +59,11 @@ struct ubt_graph {
   uint32_t* eid = nullptr;          // m: input edge index per CSR position
   uint32_t* ekey = nullptr;         // m: Philox key per CSR position
   uint32_t* giant_list = nullptr;   // lists too long for a shared-memory table
-  uint32_t* hub_list = nullptr;     // vertices with a long forward list
-  uint32_t* small_list = nullptr;   // other vertices with >= 2 forward entries
+  uint32_t* hub_list = nullptr;     // long lists: whole-block tasks
+  uint32_t* med_list = nullptr;     // medium lists: one-warp tasks
+  uint32_t* seg_row = nullptr;      // short lists (vertex order)
+  uint32_t* seg_start = nullptr;    // their starts in the concatenation
+  uint32_t* seg_first = nullptr;    // first short list of every 32-pair segment
   uint32_t* vgraph = nullptr;       // batch: graph id of every vertex (or null)
   unsigned long long* gacc = nullptr;   // m: backward accumulators
   unsigned long long* bacc = nullptr;   // batch accumulators
@@ -67,10 +72,9 @@ struct ubt_graph {
   int64_t gtab_blocks = 0;          // blocks that have one
   ubt::Scratch* scratch = nullptr;
   // sizes recorded at build time
-  int64_t n_giant = 0, n_hub = 0, n_small = 0;
+  int64_t n_giant = 0, n_hub = 0, n_med = 0, n_srows = 0, n_segs = 0;
   int64_t max_out = 0, max_hub_len = 0, wedges = 0;
-  int hub_threshold = 0;
-  int64_t giant_threshold = 0;
+  int64_t short_max = 0, hub_threshold = 0, giant_threshold = 0;
   int device = 0, sm_count = 0;
 };
 
@@ -79,12 +83,15 @@ namespace ubt {
 // ---------------------------------------------------------------- tuning
 
 struct Tuning {
-  int64_t hub_threshold = 48;
+  int64_t short_max = 16;         // lists up to this length go to segments
+  int64_t hub_threshold = 64;     // longer lists are whole-block tasks
   int64_t hub_threads = 256;
-  int64_t blocks_per_sm = 4;
-  int64_t smem_table_max = 8192;
+  int64_t blocks_per_sm = 32;     // cap on resident blocks (occupancy decides below it)
+  int64_t smem_table_max = 8192;  // hash slots of a shared-memory table
   int64_t world_words_per_pass = 8;
-  int64_t small_batch = 8;
+  int64_t small_batch = 4;        // warp tasks taken per grab
+  int64_t block_unit = 8;         // pairs per warp step in block tasks
+  int64_t sort_smem_max = 4096;
 };
 Tuning& tuning();
 
@@ -129,6 +136,13 @@ bool tau_level(double tau, Level* out);
 
 // device workspace needed for the global hash tables of a graph
 int64_t gtab_slots_for(int64_t m);
+
+// hash-table slots for a list of `entries` entries: a power of two >= 4x (min 32)
+inline int64_t table_slots(int64_t entries) {
+  int64_t s = 32;
+  while (s < 4 * entries) s <<= 1;
+  return s;
+}
 
 // launch helpers implemented in ubt_scan.cu
 cudaError_t exclusive_scan_u32(const uint32_t* in, uint32_t* out, int64_t n, uint32_t* tmp,

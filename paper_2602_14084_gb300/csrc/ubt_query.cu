@@ -215,8 +215,9 @@ struct ExpectP {
   unsigned long long* sum_lo;   // 128-bit sum
   unsigned long long* sum_hi;
 };
-// FIXED: sum of P exactly.  REAL: sum of S = s_uv s_uw s_vw (float32 products)
-// rounded to a multiple of 2^-32, in 128-bit integers.
+// FIXED: sum of P exactly.  REAL: sum of S = s_uv s_uw s_vw, each s a 2^-30
+// fixed-point integer: s_uv s_uw is exact in int64 (2^-60), rounded to 2^-30,
+// times s_vw exact (2^-60), rounded to 2^-32; summed in 128-bit integers.
 template <bool kReal>
 struct Expect {
   using P = ExpectP;
@@ -232,8 +233,10 @@ struct Expect {
     if (!hit) return;
     cnt++;
     if (kReal) {
-      const float S = __uint_as_float(quv) * __uint_as_float(quw) * __uint_as_float(qvw);
-      acc.add(__float2ll_rn(S * 4294967296.0f));
+      const long long a = (long long)(int32_t)quv * (int32_t)quw;          // 2^-60
+      const long long a30 = (a + (1ll << 29)) >> 30;                        // 2^-30
+      const long long s60 = a30 * (long long)(int32_t)qvw;                  // 2^-60
+      acc.add((s60 + (1ll << 27)) >> 28);                                   // 2^-32
     } else {
       acc.add(tri_product(quv, quw, qvw));
     }
@@ -289,10 +292,12 @@ struct Adjoint {
     if (!hit) return;
     long long a_uv, a_uw, a_vw;
     if (kReal) {
-      const float su = __uint_as_float(quv), sw = __uint_as_float(quw), sv = __uint_as_float(qvw);
-      a_uv = __float2ll_rn(sw * sv * 1099511627776.0f);   // 2^40
-      a_uw = __float2ll_rn(su * sv * 1099511627776.0f);
-      a_vw = __float2ll_rn(su * sw * 1099511627776.0f);
+      // products of two 2^-30 fixed-point values are exact in int64 (2^-60);
+      // rounded to 2^-40 for accumulation
+      const long long su = (int32_t)quv, sw = (int32_t)quw, sv = (int32_t)qvw;
+      a_uv = (sw * sv + (1ll << 19)) >> 20;
+      a_uw = (su * sv + (1ll << 19)) >> 20;
+      a_vw = (su * sw + (1ll << 19)) >> 20;
     } else {
       a_uv = (long long)((int32_t)quw * (int32_t)qvw);    // exact, scale 2^-30
       a_uw = (long long)((int32_t)quv * (int32_t)qvw);
@@ -366,33 +371,42 @@ __global__ void __launch_bounds__(512) k_traverse(TravArgs a, typename V::P p) {
 }  // namespace
 
 TravArgs make_trav_args(const ubt_graph* g, int64_t L, bool with_pos) {
+  (void)with_pos;
   const Tuning& T = tuning();
   TravArgs a;
   a.row_ptr = g->row_ptr;
   a.adj = g->adj;
   a.giant_list = g->giant_list;
   a.hub_list = g->hub_list;
-  a.small_list = g->small_list;
+  a.med_list = g->med_list;
+  a.seg_row = g->seg_row;
+  a.seg_start = g->seg_start;
+  a.seg_first = g->seg_first;
   a.n_giant = (uint32_t)g->n_giant;
   a.n_hub = (uint32_t)g->n_hub;
-  a.n_small = (uint32_t)g->n_small;
+  a.n_med = (uint32_t)g->n_med;
+  a.n_srows = (uint32_t)g->n_srows;
+  a.n_segs = (uint32_t)g->n_segs;
+  a.n = (uint32_t)g->n;
+  a.m = (uint32_t)g->m;
   a.sc = g->scratch;
   a.gtab = g->gtab;
   a.gtab_slots = (uint32_t)g->gtab_slots;
   a.gtab_blocks = g->n_giant ? (uint32_t)g->gtab_blocks : 0u;
-  uint32_t hs = 0;
-  if (g->n_hub) {
-    hs = 32;
-    while (hs < 2 * (uint64_t)g->max_hub_len) hs <<= 1;
-  }
-  a.hub_slots = hs;
-  uint32_t ss = 32;
-  while (ss < 2 * (uint32_t)g->hub_threshold) ss <<= 1;
-  a.small_slots = ss;
-  a.small_batch = (uint32_t)std::max<int64_t>(1, T.small_batch);
-  a.table_words = with_pos ? 3u : 2u;
+  a.hub_slots = g->n_hub ? (uint32_t)table_slots(g->max_hub_len) : 0u;
+  // a warp table holds one medium list or the lists one segment touches
+  a.warp_slots = (uint32_t)std::max(table_slots(g->hub_threshold), table_slots(32 + 2 * (g->short_max - 1)));
+  a.unit = (uint32_t)std::min<int64_t>(32, std::max<int64_t>(1, T.block_unit));
+  a.batch = (uint32_t)std::max<int64_t>(1, T.small_batch);
   a.L = L;
   return a;
+}
+
+size_t traverse_smem(const TravArgs& a, int threads, int vis_smem) {
+  const size_t vis_bytes = (size_t)((vis_smem + 15) / 16) * 16;
+  const size_t hub_bytes = (size_t)a.hub_slots * 3 * 4;
+  const size_t warp_bytes = (size_t)(threads / 32) * a.warp_slots * 3 * 4;
+  return vis_bytes + std::max(hub_bytes, warp_bytes);
 }
 
 template <class V>
@@ -400,10 +414,7 @@ ubt_status launch_traverse(const ubt_graph* g, const typename V::P& p, int64_t L
   const Tuning& T = tuning();
   TravArgs a = make_trav_args(g, L, V::kPos);
   int threads = (int)std::min<int64_t>(512, std::max<int64_t>(64, T.hub_threads / 32 * 32));
-  const size_t vis_bytes = (size_t)((V::kSmem + 15) / 16) * 16;
-  const size_t hub_bytes = (size_t)a.hub_slots * a.table_words * 4;
-  const size_t small_bytes = (size_t)(threads / 32) * a.small_slots * a.table_words * 4;
-  const size_t smem = vis_bytes + std::max(hub_bytes, small_bytes);
+  const size_t smem = traverse_smem(a, threads, V::kSmem);
   UBT_CUDA(cudaFuncSetAttribute(k_traverse<V>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
   int per_sm = 0;
   UBT_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_traverse<V>, threads, smem));
@@ -541,5 +552,41 @@ extern "C" ubt_status ubt_traversal_stats(ubt_graph* g, const double* h_tau, int
   h_out[1] = (int64_t)h[0];
   h_out[2] = (int64_t)h[1];
   h_out[3] = (int64_t)h[2];
+  return UBT_OK;
+}
+
+extern "C" ubt_status ubt_query_guard(ubt_graph* g, int64_t* h_word, void* stream) {
+  if (!g || !h_word) return UBT_ERR_INVALID_ARG;
+  cudaStream_t s = (cudaStream_t)stream;
+  unsigned long long w = 0;
+  UBT_CUDA(cudaMemcpyAsync(&w, &g->scratch->guard, sizeof(w), cudaMemcpyDeviceToHost, s));
+  UBT_CUDA(cudaMemsetAsync(&g->scratch->guard, 0, sizeof(w), s));
+  UBT_CUDA(cudaStreamSynchronize(s));
+  *h_word = (int64_t)w;
+  return UBT_OK;
+}
+
+extern "C" ubt_status ubt_graph_export(const ubt_graph* g, uint32_t* h_row_ptr, uint64_t* h_adj, uint32_t* h_eid,
+                                       uint32_t* h_lists, int64_t* h_list_sizes, void* stream) {
+  if (!g) return UBT_ERR_INVALID_ARG;
+  cudaStream_t s = (cudaStream_t)stream;
+  if (h_row_ptr)
+    UBT_CUDA(cudaMemcpyAsync(h_row_ptr, g->row_ptr, sizeof(uint32_t) * (g->n + 1), cudaMemcpyDeviceToHost, s));
+  if (h_adj && g->m)
+    UBT_CUDA(cudaMemcpyAsync(h_adj, g->adj, sizeof(uint64_t) * g->m, cudaMemcpyDeviceToHost, s));
+  if (h_eid && g->m)
+    UBT_CUDA(cudaMemcpyAsync(h_eid, g->eid, sizeof(uint32_t) * g->m, cudaMemcpyDeviceToHost, s));
+  const int64_t tasks = g->n_giant + g->n_hub + g->n_med;
+  if (h_lists && tasks)
+    UBT_CUDA(cudaMemcpyAsync(h_lists, g->giant_list, sizeof(uint32_t) * tasks, cudaMemcpyDeviceToHost, s));
+  if (h_lists && g->n_srows)
+    UBT_CUDA(cudaMemcpyAsync(h_lists + tasks, g->seg_row, sizeof(uint32_t) * g->n_srows, cudaMemcpyDeviceToHost, s));
+  if (h_list_sizes) {
+    h_list_sizes[0] = g->n_giant;
+    h_list_sizes[1] = g->n_hub;
+    h_list_sizes[2] = g->n_med;
+    h_list_sizes[3] = g->n_srows;
+  }
+  UBT_CUDA(cudaStreamSynchronize(s));
   return UBT_OK;
 }

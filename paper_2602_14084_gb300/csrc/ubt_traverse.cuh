@@ -2,23 +2,31 @@
 //
 // Forward edge iteration under Node Order (Alg. 1, Sec. 4): triangle {u,v,w}
 // with u < v < w in Node Order is found exactly once, from u, as
-// w in N>(u) n N>(v) for v in N>(u).
+// w in N>(u) n N>(v) for v in N>(u).  Each forward edge (u, v) is a "pair";
+// its work is to probe every w of N>(v) against N>(u).
 //
-// GPU layout of that loop:
-//   * u's forward list is loaded once into an open-addressing hash table
-//     (neighbour -> edge value [, CSR position]) in shared memory: a whole
-//     thread block shares it when the list is long ("hub" task), a single warp
-//     owns a small one otherwise.  Lists too long for shared memory use a
-//     per-block table in global memory ("giant" task).
-//   * The out-neighbours v of u are taken 32 at a time by one warp.  Their
-//     lists N>(v) are streamed with coalesced 8-byte loads: long lists one at
-//     a time by the whole warp, short lists concatenated ("flattened") so that
-//     every lane has an entry to probe.  Each streamed entry w is probed in
-//     u's table; a hit is a triangle, handed to the visitor with the three
-//     edge values and CSR positions.
+// GPU layout of that loop (one persistent kernel, four kinds of task):
+//   * N>(u) is loaded into an open-addressing hash table (neighbour -> edge
+//     value, CSR position) in shared memory, at most 1/4 full so that most
+//     misses end at the first slot.
+//   * The pairs of a task are handed to one warp 32 at a time.  The lists N>(v)
+//     are streamed with coalesced 8-byte loads: long lists one after another
+//     by the whole warp, short lists concatenated ("flattened") so that every
+//     lane has an entry; two entries per lane are in flight at once.  Each
+//     entry w is probed in u's table; a hit is a triangle and goes to the
+//     visitor with the three edge values and CSR positions.
+//   * Task kinds, by |N>(u)|:
+//       giant   longer than the shared-memory table: whole block, table in a
+//               per-block slice of global memory
+//       hub     whole block, shared table, warps take `unit` pairs at a time
+//       medium  one warp, its own table
+//       short   segments: the short lists, concatenated in vertex order, are
+//               cut into runs of 32 pairs; one warp takes a run, puts every
+//               list the run touches into one table and probes with the row
+//               of each pair's u (CSR positions identify the row)
 //   * Probability pruning (FIXED graphs, level L > 0): every list is sorted by
 //     |q| descending, so the entries that cannot reach |P| >= L are suffixes:
-//       u's table and v-loop:  |q_e| * qmax(u) * 2^15 >= L   (Lemma 2: each
+//       u's table and pairs:   |q_e| * qmax(u) * 2^15 >= L   (Lemma 2: each
 //                              edge bounds the product of the triangle)
 //       v's list for pair u-v: |q_vw| * |q_uv| * qmax(u) >= L (order-free form
 //                              of Lemma 3: the other two edges bound it)
@@ -38,20 +46,33 @@ struct TravArgs {
   const uint64_t* adj;
   const uint32_t* giant_list;
   const uint32_t* hub_list;
-  const uint32_t* small_list;
-  uint32_t n_giant, n_hub, n_small;
+  const uint32_t* med_list;
+  const uint32_t* seg_row;     // short lists' vertices, in vertex order
+  const uint32_t* seg_start;   // start of each short list in the concatenation
+  const uint32_t* seg_first;   // first short list touching each 32-pair segment (kEmpty: none)
+  uint32_t n_giant, n_hub, n_med, n_srows, n_segs;
+  uint32_t n, m;            // vertices, edges (bounds of the self-checks)
   Scratch* sc;              // task counters (zeroed before launch)
   uint32_t* gtab;           // giant tables: gtab_blocks x gtab_slots x 3 words
   uint32_t gtab_slots;      // power of two
   uint32_t gtab_blocks;
   uint32_t hub_slots;       // shared-memory hub table capacity (power of two)
-  uint32_t small_slots;     // per-warp table capacity (power of two)
-  uint32_t small_batch;     // small tasks taken per grab
-  uint32_t table_words;     // 2 (key, value) or 3 (+ CSR position)
+  uint32_t warp_slots;      // per-warp table capacity (power of two)
+  uint32_t unit;            // pairs per warp step in block tasks
+  uint32_t batch;           // warp tasks / segments taken per grab
   int64_t L;                // prune level, 0 = none
 };
 
 __device__ __forceinline__ uint32_t hash_slot(uint32_t w, int shift) { return (w * 0x9E3779B1u) >> shift; }
+
+// Self-checks record the first violated invariant in Scratch::guard and skip
+// the offending access: 1 probe limit (find), 2 probe limit (insert),
+// 3 neighbour id >= n, 4 list offsets out of order or past m, 5 table larger
+// than its region.
+enum : unsigned long long { kGuardFind = 1, kGuardInsert = 2, kGuardVertex = 3, kGuardList = 4, kGuardTable = 5 };
+static __device__ __noinline__ void guard_fail(Scratch* sc, unsigned long long code, unsigned long long info) {
+  atomicCAS(&sc->guard, 0ull, (code << 56) | (info & ((1ull << 56) - 1)));
+}
 
 __device__ __forceinline__ int64_t qabs(uint32_t valbits) {
   const int32_t q = (int32_t)valbits;
@@ -71,6 +92,7 @@ __device__ __forceinline__ uint32_t prune_prefix(const uint64_t* __restrict__ ro
   return hi;
 }
 
+// Hash table: key = neighbour id, val = edge value bits, pos = CSR position.
 struct Table {
   uint32_t* key;
   uint32_t* val;
@@ -79,85 +101,117 @@ struct Table {
   int shift;
 };
 
-__device__ __forceinline__ Table make_table(uint32_t* base, uint32_t cap, uint32_t slots, bool with_pos) {
+__device__ __forceinline__ Table make_table(uint32_t* base, uint32_t cap, uint32_t slots) {
   Table t;
   t.key = base;
   t.val = base + cap;
-  t.pos = with_pos ? base + 2 * cap : nullptr;
+  t.pos = base + 2 * cap;
   t.mask = slots - 1;
   t.shift = 32 - (31 - __clz((int)slots));
   return t;
 }
 
-__device__ __forceinline__ void table_insert(const Table& t, uint32_t w, uint32_t val, uint32_t pos) {
+// at most 1/4 full
+__device__ __forceinline__ uint32_t slots_for(uint32_t entries) {
+  uint32_t s = 32;
+  while (s < 4 * entries) s <<= 1;
+  return s;
+}
+
+// The table always has free slots (capacity >= 4x its entries), so both loops
+// end within `mask + 1` steps; the step limit is a self-check.
+__device__ __forceinline__ void table_insert(const Table& t, uint32_t w, uint32_t val, uint32_t pos, Scratch* sc) {
   uint32_t h = hash_slot(w, t.shift);
-  while (true) {
+  for (uint32_t it = 0; it <= t.mask; it++) {
     const uint32_t old = atomicCAS(&t.key[h], kEmpty, w);
     if (old == kEmpty) {
       t.val[h] = val;
-      if (t.pos) t.pos[h] = pos;
+      t.pos[h] = pos;
       return;
     }
     h = (h + 1) & t.mask;
   }
+  guard_fail(sc, kGuardInsert, w);
 }
 
-__device__ __forceinline__ bool table_find(const Table& t, uint32_t w, uint32_t& val, uint32_t& pos) {
+// Find w among the entries whose CSR position lies in [rs, rs + rlen) (the
+// row of one u; a table holding a single row passes rlen = ~0).
+__device__ __forceinline__ bool table_find(const Table& t, uint32_t w, uint32_t rs, uint32_t rlen, uint32_t& val,
+                                           uint32_t& pos, Scratch* sc) {
   uint32_t h = hash_slot(w, t.shift);
-  while (true) {
+  for (uint32_t it = 0; it <= t.mask; it++) {
     const uint32_t k = t.key[h];
     if (k == w) {
-      val = t.val[h];
-      if (t.pos) pos = t.pos[h];
-      return true;
+      const uint32_t p = t.pos[h];
+      if (p - rs < rlen) {
+        val = t.val[h];
+        pos = p;
+        return true;
+      }
+    } else if (k == kEmpty) {
+      return false;
     }
-    if (k == kEmpty) return false;
     h = (h + 1) & t.mask;
   }
+  guard_fail(sc, kGuardFind, w);
+  return false;
 }
 
-__device__ __forceinline__ uint32_t slots_for(uint32_t len) {
-  uint32_t s = 32;
-  while (s < 2 * len) s <<= 1;
-  return s;
-}
+// Per-lane description of one pair (u, v) handed to probe_pairs.
+struct Pair {
+  uint32_t u, v, puv, quv;  // vertices, CSR position and value of the u-v edge
+  uint32_t urs, ulen;       // u's row as seen by the table (for row matching)
+  int64_t qmax;             // largest |q| of u's list (pruning)
+  bool ok;
+};
 
-// One warp: the out-neighbours at CSR positions [cs, cs + cnt) of u (cnt <= 32).
+// One warp probes the lists of up to 32 pairs (one per lane, `ok` lanes).
 template <class V>
-__device__ __forceinline__ void process_chunk(const TravArgs& a, V& vis, const Table& t, uint32_t u, int64_t qmax_u,
-                                              uint32_t cs, uint32_t cnt) {
+__device__ __forceinline__ void probe_pairs(const TravArgs& a, V& vis, const Table& t, const Pair& pr) {
   const int lane = threadIdx.x & 31;
-  uint32_t v = 0, vs = 0, dv = 0, quv = 0, puv = 0;
-  if ((uint32_t)lane < cnt) {
-    puv = cs + lane;
-    const uint64_t e = a.adj[puv];
-    v = adj_col(e);
-    quv = adj_valbits(e);
-    vs = a.row_ptr[v];
-    dv = a.row_ptr[v + 1] - vs;
-    if (a.L > 0) dv = prune_prefix(a.adj + vs, dv, qabs(quv) * qmax_u, a.L);
+  uint32_t vs = 0, dv = 0;
+  if (pr.ok) {
+    if (pr.v < a.n) {
+      vs = a.row_ptr[pr.v];
+      const uint32_t ve = a.row_ptr[pr.v + 1];
+      if (ve >= vs && ve <= a.m) {
+        dv = ve - vs;
+        if (a.L > 0) dv = prune_prefix(a.adj + vs, dv, qabs(pr.quv) * pr.qmax, a.L);
+      } else {
+        guard_fail(a.sc, kGuardList, pr.v);
+      }
+    } else {
+      guard_fail(a.sc, kGuardVertex, pr.v);
+    }
   }
-  // long lists: one at a time, the whole warp streams it
-  unsigned longm = __ballot_sync(kFull, dv >= 24);
+  // long lists: one at a time, the whole warp streams it, two entries per lane
+  constexpr uint32_t kLong = 48;
+  unsigned longm = __ballot_sync(kFull, dv >= kLong);
   while (longm) {
     const int j = __ffs(longm) - 1;
     longm &= longm - 1;
-    const uint32_t vj = __shfl_sync(kFull, v, j);
+    const uint32_t uj = __shfl_sync(kFull, pr.u, j);
+    const uint32_t vj = __shfl_sync(kFull, pr.v, j);
     const uint32_t vsj = __shfl_sync(kFull, vs, j);
     const uint32_t dvj = __shfl_sync(kFull, dv, j);
-    const uint32_t qj = __shfl_sync(kFull, quv, j);
-    const uint32_t pj = __shfl_sync(kFull, puv, j);
-    for (uint32_t off = 0; off < dvj; off += 32) {
-      const uint32_t i = off + lane;
-      const bool act = i < dvj;
-      uint64_t e2 = act ? a.adj[vsj + i] : 0ull;
-      uint32_t quw = 0, puw = 0;
-      const bool hit = act && table_find(t, adj_col(e2), quw, puw);
-      vis.step(hit, u, vj, adj_col(e2), qj, quw, adj_valbits(e2), pj, puw, vsj + i);
+    const uint32_t qj = __shfl_sync(kFull, pr.quv, j);
+    const uint32_t pj = __shfl_sync(kFull, pr.puv, j);
+    const uint32_t rsj = __shfl_sync(kFull, pr.urs, j);
+    const uint32_t rlj = __shfl_sync(kFull, pr.ulen, j);
+    for (uint32_t off = 0; off < dvj; off += 64) {
+      const uint32_t i0 = off + lane, i1 = off + 32 + lane;
+      const bool a0 = i0 < dvj, a1 = i1 < dvj;
+      const uint64_t e0 = a0 ? a.adj[vsj + i0] : 0ull;
+      const uint64_t e1 = a1 ? a.adj[vsj + i1] : 0ull;
+      uint32_t q0 = 0, p0 = 0, q1 = 0, p1 = 0;
+      const bool h0 = a0 && table_find(t, adj_col(e0), rsj, rlj, q0, p0, a.sc);
+      const bool h1 = a1 && table_find(t, adj_col(e1), rsj, rlj, q1, p1, a.sc);
+      vis.step(h0, uj, vj, adj_col(e0), qj, q0, adj_valbits(e0), pj, p0, vsj + i0);
+      if (off + 32 < dvj) vis.step(h1, uj, vj, adj_col(e1), qj, q1, adj_valbits(e1), pj, p1, vsj + i1);
     }
   }
-  // short lists: concatenated so that every lane probes one entry
-  const uint32_t ds = dv >= 24 ? 0u : dv;
+  // short lists: concatenated so that every lane probes one entry per half-step
+  const uint32_t ds = dv >= kLong ? 0u : dv;
   uint32_t incl = ds;
 #pragma unroll
   for (int d = 1; d < 32; d <<= 1) {
@@ -166,106 +220,250 @@ __device__ __forceinline__ void process_chunk(const TravArgs& a, V& vis, const T
   }
   const uint32_t total = __shfl_sync(kFull, incl, 31);
   const uint32_t excl = incl - ds;
-  for (uint32_t base = 0; base < total; base += 32) {
-    const uint32_t f = base + lane;
-    const bool act = f < total;
-    // owner: number of lanes whose inclusive end is <= f
-    int j = 0;
+  for (uint32_t base = 0; base < total; base += 64) {
+    uint32_t f[2], jj[2];
+    bool act[2];
+    uint64_t e[2];
 #pragma unroll
-    for (int s = 16; s > 0; s >>= 1) {
-      const uint32_t tj = __shfl_sync(kFull, incl, j + s - 1);
-      if (tj <= f) j += s;
+    for (int s = 0; s < 2; s++) {
+      f[s] = base + 32 * s + lane;
+      act[s] = f[s] < total;
+      // owner: number of lanes whose inclusive end is <= f
+      int j = 0;
+#pragma unroll
+      for (int b = 16; b > 0; b >>= 1) {
+        const uint32_t tj = __shfl_sync(kFull, incl, j + b - 1);
+        if (tj <= f[s]) j += b;
+      }
+      jj[s] = (uint32_t)(j > 31 ? 31 : j);
+      const uint32_t vsj = __shfl_sync(kFull, vs, jj[s]);
+      const uint32_t exj = __shfl_sync(kFull, excl, jj[s]);
+      e[s] = act[s] ? a.adj[vsj + (f[s] - exj)] : 0ull;
+      f[s] = vsj + (f[s] - exj);  // now the CSR position of the entry
     }
-    j = j > 31 ? 31 : j;
-    const uint32_t vj = __shfl_sync(kFull, v, j);
-    const uint32_t vsj = __shfl_sync(kFull, vs, j);
-    const uint32_t exj = __shfl_sync(kFull, excl, j);
-    const uint32_t qj = __shfl_sync(kFull, quv, j);
-    const uint32_t pj = __shfl_sync(kFull, puv, j);
-    const uint32_t pvw = vsj + (f - exj);
-    uint64_t e2 = act ? a.adj[pvw] : 0ull;
-    uint32_t quw = 0, puw = 0;
-    const bool hit = act && table_find(t, adj_col(e2), quw, puw);
-    vis.step(hit, u, vj, adj_col(e2), qj, quw, adj_valbits(e2), pj, puw, pvw);
+#pragma unroll
+    for (int s = 0; s < 2; s++) {
+      const int j = (int)jj[s];
+      const uint32_t rsj = __shfl_sync(kFull, pr.urs, j);
+      const uint32_t rlj = __shfl_sync(kFull, pr.ulen, j);
+      uint32_t quw = 0, puw = 0;
+      const bool hit = act[s] && table_find(t, adj_col(e[s]), rsj, rlj, quw, puw, a.sc);
+      const uint32_t uj = __shfl_sync(kFull, pr.u, j);
+      const uint32_t vj = __shfl_sync(kFull, pr.v, j);
+      const uint32_t qj = __shfl_sync(kFull, pr.quv, j);
+      const uint32_t pj = __shfl_sync(kFull, pr.puv, j);
+      if (s == 0 || base + 32 < total)
+        vis.step(hit, uj, vj, adj_col(e[s]), qj, quw, adj_valbits(e[s]), pj, puw, f[s]);
+    }
   }
+}
+
+// Pair of this lane among the pairs [cs, cs + cnt) of a single-row table.
+__device__ __forceinline__ Pair row_pair(const TravArgs& a, uint32_t u, int64_t qmax, uint32_t cs, uint32_t cnt) {
+  const int lane = threadIdx.x & 31;
+  Pair pr;
+  pr.u = u;
+  pr.urs = 0;
+  pr.ulen = ~0u;
+  pr.qmax = qmax;
+  pr.ok = (uint32_t)lane < cnt;
+  pr.puv = cs + lane;
+  const uint64_t e = pr.ok ? a.adj[pr.puv] : 0ull;
+  pr.v = adj_col(e);
+  pr.quv = adj_valbits(e);
+  return pr;
+}
+
+// u's list length after pruning (and qmax); identical in every calling thread
+__device__ __forceinline__ uint32_t pruned_len(const TravArgs& a, uint32_t rs, uint32_t len, int64_t& qmax) {
+  qmax = 0;
+  if (a.L > 0 && len > 0) {
+    qmax = qabs(adj_valbits(a.adj[rs]));
+    return prune_prefix(a.adj + rs, len, qmax * 32768, a.L);
+  }
+  return len;
 }
 
 // A whole block handles u; `tab` is shared memory (hub) or a global slice (giant).
 template <class V>
-__device__ __forceinline__ void block_task(const TravArgs& a, V& vis, uint32_t u, uint32_t* tab, uint32_t cap, uint32_t* s_misc) {
-  const int tid = threadIdx.x, lane = tid & 31, wid = tid >> 5, nw = blockDim.x >> 5;
-  const uint32_t rs = a.row_ptr[u], re = a.row_ptr[u + 1];
-  uint32_t len = re - rs;
-  int64_t qmax = 0;
-  if (a.L > 0 && len > 0) {
-    qmax = qabs(adj_valbits(a.adj[rs]));
-    if (tid == 0) s_misc[0] = prune_prefix(a.adj + rs, len, qmax * 32768, a.L);
-    __syncthreads();
-    len = s_misc[0];
-    __syncthreads();
+__device__ __forceinline__ void block_task(const TravArgs& a, V& vis, uint32_t u, uint32_t* tab, uint32_t cap,
+                                           uint32_t* s_misc) {
+  const int tid = threadIdx.x, lane = tid & 31;
+  if (u >= a.n) {
+    if (tid == 0) guard_fail(a.sc, kGuardVertex, u);
+    return;
   }
-  if (len == 0) return;
+  const uint32_t rs = a.row_ptr[u], re = a.row_ptr[u + 1];
+  if (re < rs || re > a.m) {
+    if (tid == 0) guard_fail(a.sc, kGuardList, u);
+    return;
+  }
+  int64_t qmax = 0;
+  if (tid == 0) s_misc[0] = pruned_len(a, rs, re - rs, qmax);
+  __syncthreads();
+  const uint32_t len = s_misc[0];
+  if (a.L > 0 && len > 0) qmax = qabs(adj_valbits(a.adj[rs]));
   const uint32_t slots = slots_for(len);
-  const Table t = make_table(tab, cap, slots, a.table_words == 3);
+  if (len == 0 || slots > cap) {
+    if (len && tid == 0) guard_fail(a.sc, kGuardTable, u);
+    __syncthreads();
+    return;
+  }
+  const Table t = make_table(tab, cap, slots);
   for (uint32_t i = tid; i < slots; i += blockDim.x) t.key[i] = kEmpty;
   if (tid == 0) s_misc[1] = 0;
   __syncthreads();
   for (uint32_t i = tid; i < len; i += blockDim.x) {
     const uint64_t e = a.adj[rs + i];
-    table_insert(t, adj_col(e), adj_valbits(e), rs + i);
+    table_insert(t, adj_col(e), adj_valbits(e), rs + i, a.sc);
   }
   __syncthreads();
   vis.task_begin(u);
-  const uint32_t nchunks = (len + 31) / 32;
+  const uint32_t units = (len + a.unit - 1) / a.unit;
   while (true) {
     uint32_t c = 0;
     if (lane == 0) c = atomicAdd(&s_misc[1], 1u);
     c = __shfl_sync(kFull, c, 0);
-    if (c >= nchunks) break;
-    const uint32_t cs = c * 32;
-    process_chunk(a, vis, t, u, qmax, rs + cs, min(32u, len - cs));
+    if (c >= units) break;
+    const uint32_t cs = c * a.unit;
+    probe_pairs(a, vis, t, row_pair(a, u, qmax, rs + cs, min(a.unit, len - cs)));
   }
-  (void)wid;
-  (void)nw;
   vis.task_end(u);
   __syncthreads();
 }
 
-// One warp handles u (list of at most hub_threshold entries).
+// One warp handles u (a medium list).
 template <class V>
 __device__ __forceinline__ void warp_task(const TravArgs& a, V& vis, uint32_t u, uint32_t* tab) {
   const int lane = threadIdx.x & 31;
-  const uint32_t rs = a.row_ptr[u], re = a.row_ptr[u + 1];
-  uint32_t len = re - rs;
-  int64_t qmax = 0;
-  if (a.L > 0 && len > 0) {
-    qmax = qabs(adj_valbits(a.adj[rs]));
-    // prefix of entries with |q| * qmax * 2^15 >= L, by ballot over the list
-    uint32_t first_fail = len;
-    for (uint32_t off = 0; off < len; off += 32) {
-      const uint32_t i = off + lane;
-      const bool fail = i < len && qabs(adj_valbits(a.adj[rs + i])) * qmax * 32768 < a.L;
-      const unsigned b = __ballot_sync(kFull, fail);
-      if (b) {
-        first_fail = off + __ffs(b) - 1;
-        break;
-      }
-    }
-    len = first_fail;
+  if (u >= a.n) {
+    if (lane == 0) guard_fail(a.sc, kGuardVertex, u);
+    return;
   }
+  const uint32_t rs = a.row_ptr[u], re = a.row_ptr[u + 1];
+  if (re < rs || re > a.m) {
+    if (lane == 0) guard_fail(a.sc, kGuardList, u);
+    return;
+  }
+  int64_t qmax = 0;
+  const uint32_t len = pruned_len(a, rs, re - rs, qmax);
   if (len == 0) return;
   const uint32_t slots = slots_for(len);
-  const Table t = make_table(tab, a.small_slots, slots, a.table_words == 3);
+  if (slots > a.warp_slots) {
+    if (lane == 0) guard_fail(a.sc, kGuardTable, u);
+    return;
+  }
+  const Table t = make_table(tab, a.warp_slots, slots);
   for (uint32_t i = lane; i < slots; i += 32) t.key[i] = kEmpty;
   __syncwarp();
   for (uint32_t i = lane; i < len; i += 32) {
     const uint64_t e = a.adj[rs + i];
-    table_insert(t, adj_col(e), adj_valbits(e), rs + i);
+    table_insert(t, adj_col(e), adj_valbits(e), rs + i, a.sc);
   }
   __syncwarp();
   vis.task_begin(u);
-  for (uint32_t cs = 0; cs < len; cs += 32) process_chunk(a, vis, t, u, qmax, rs + cs, min(32u, len - cs));
+  for (uint32_t cs = 0; cs < len; cs += 32) probe_pairs(a, vis, t, row_pair(a, u, qmax, rs + cs, min(32u, len - cs)));
   vis.task_end(u);
+  __syncwarp();
+}
+
+// One warp handles segment k: pairs [32k, 32k + 32) of the concatenated short lists.
+template <class V>
+__device__ __forceinline__ void segment_task(const TravArgs& a, V& vis, uint32_t k, uint32_t* tab) {
+  const int lane = threadIdx.x & 31;
+  const uint32_t r0 = a.seg_first[k];
+  if (r0 == kEmpty) return;
+  const uint32_t sp0 = 32 * k, sp1 = sp0 + 32;
+  // lane i describes short list r0 + i, if that list starts before the segment ends
+  const uint32_t r = r0 + lane;
+  uint32_t ss = 0xFFFFFFFFu, u = 0, rs = 0, raw = 0, len = 0;
+  int64_t qmax = 0;
+  bool row = false;
+  if (r < a.n_srows && a.seg_start[r] < sp1) {
+    ss = a.seg_start[r];
+    u = a.seg_row[r];
+    if (u < a.n) {
+      rs = a.row_ptr[u];
+      const uint32_t re = a.row_ptr[u + 1];
+      if (re >= rs && re <= a.m) {
+        row = true;
+        raw = re - rs;
+      } else {
+        guard_fail(a.sc, kGuardList, u);
+      }
+    } else {
+      guard_fail(a.sc, kGuardVertex, u);
+    }
+  }
+  if (__ballot_sync(kFull, row) == 0) return;
+  if (row) len = pruned_len(a, rs, raw, qmax);
+  // table: every entry of the touched lists (their pruned prefixes)
+  const uint32_t tl = row ? len : 0u;
+  uint32_t incl = tl;
+#pragma unroll
+  for (int d = 1; d < 32; d <<= 1) {
+    const uint32_t y = __shfl_up_sync(kFull, incl, d);
+    if (lane >= d) incl += y;
+  }
+  const uint32_t total = __shfl_sync(kFull, incl, 31);
+  const uint32_t slots = slots_for(total);
+  if (slots > a.warp_slots) {
+    if (lane == 0) guard_fail(a.sc, kGuardTable, k);
+    return;
+  }
+  const Table t = make_table(tab, a.warp_slots, slots);
+  for (uint32_t i = lane; i < slots; i += 32) t.key[i] = kEmpty;
+  __syncwarp();
+  const uint32_t excl = incl - tl;
+  for (uint32_t base = 0; base < total; base += 32) {
+    const uint32_t f = base + lane;
+    int j = 0;
+#pragma unroll
+    for (int b = 16; b > 0; b >>= 1) {
+      const uint32_t tj = __shfl_sync(kFull, incl, j + b - 1);
+      if (tj <= f) j += b;
+    }
+    j = j > 31 ? 31 : j;
+    const uint32_t rsj = __shfl_sync(kFull, rs, j);
+    const uint32_t exj = __shfl_sync(kFull, excl, j);
+    if (f < total) {
+      const uint32_t p = rsj + (f - exj);
+      const uint64_t e = a.adj[p];
+      table_insert(t, adj_col(e), adj_valbits(e), p, a.sc);
+    }
+  }
+  __syncwarp();
+  // the segment's pairs: lane e takes position sp0 + e of the concatenation;
+  // its list is the last one that starts at or before that position
+  const uint32_t sp = sp0 + lane;
+  int j = 0;  // number of lists starting at or before sp
+#pragma unroll
+  for (int b = 16; b > 0; b >>= 1) {
+    const uint32_t sj = __shfl_sync(kFull, ss, j + b - 1);
+    if (sj <= sp) j += b;
+  }
+  const bool have = j > 0;
+  j = have ? j - 1 : 0;
+  const uint32_t ssj = __shfl_sync(kFull, ss, j);
+  const uint32_t rsj = __shfl_sync(kFull, rs, j);
+  const uint32_t rawj = __shfl_sync(kFull, raw, j);
+  Pair pr;
+  pr.u = __shfl_sync(kFull, u, j);
+  pr.urs = rsj;
+  pr.ulen = __shfl_sync(kFull, len, j);
+  pr.qmax = __shfl_sync(kFull, qmax, j);
+  const bool rowj = __shfl_sync(kFull, (int)row, j) != 0;
+  const uint32_t off = sp - ssj;
+  // a pair outside its list's pruned prefix cannot be in a classified triangle
+  pr.ok = have && rowj && off < rawj && off < pr.ulen;
+  pr.puv = rsj + off;
+  const uint64_t e = pr.ok ? a.adj[pr.puv] : 0ull;
+  pr.v = adj_col(e);
+  pr.quv = adj_valbits(e);
+  const uint32_t u0 = __shfl_sync(kFull, u, 0);
+  vis.task_begin(u0);
+  probe_pairs(a, vis, t, pr);
+  vis.task_end(u0);
   __syncwarp();
 }
 
@@ -296,15 +494,24 @@ __device__ void traverse(const TravArgs& a, V& vis, char* smem_tables) {
     if (task >= a.n_hub) break;
     block_task(a, vis, a.hub_list[task], tab, a.hub_slots, s_misc);
   }
-  // phase 2: small lists, one warp each, `small_batch` consecutive tasks per grab
-  uint32_t* wtab = tab + (size_t)wid * a.small_slots * a.table_words;
+  uint32_t* wtab = tab + (size_t)wid * a.warp_slots * 3;
+  // phase 2: medium lists, one warp each
   while (true) {
     unsigned long long t0 = 0;
-    if (lane == 0) t0 = atomicAdd(&a.sc->task[2], (unsigned long long)a.small_batch);
+    if (lane == 0) t0 = atomicAdd(&a.sc->task[2], (unsigned long long)a.batch);
     t0 = __shfl_sync(kFull, t0, 0);
-    if (t0 >= a.n_small) break;
-    const uint32_t t1 = (uint32_t)min((unsigned long long)a.n_small, t0 + a.small_batch);
-    for (uint32_t t = (uint32_t)t0; t < t1; t++) warp_task(a, vis, a.small_list[t], wtab);
+    if (t0 >= a.n_med) break;
+    const uint32_t t1 = (uint32_t)min((unsigned long long)a.n_med, t0 + a.batch);
+    for (uint32_t t = (uint32_t)t0; t < t1; t++) warp_task(a, vis, a.med_list[t], wtab);
+  }
+  // phase 3: segments of short lists
+  while (true) {
+    unsigned long long t0 = 0;
+    if (lane == 0) t0 = atomicAdd(&a.sc->task[3], (unsigned long long)a.batch);
+    t0 = __shfl_sync(kFull, t0, 0);
+    if (t0 >= a.n_segs) break;
+    const uint32_t t1 = (uint32_t)min((unsigned long long)a.n_segs, t0 + a.batch);
+    for (uint32_t t = (uint32_t)t0; t < t1; t++) segment_task(a, vis, t, wtab);
   }
   __syncthreads();
   vis.block_end();

@@ -23,6 +23,7 @@
 namespace ubt {
 
 TravArgs make_trav_args(const ubt_graph* g, int64_t L, bool with_pos);
+size_t traverse_smem(const TravArgs& a, int threads, int vis_smem);
 
 namespace {
 
@@ -379,10 +380,7 @@ ubt_status launch_w(const ubt_graph* g, const typename V::P& p, cudaStream_t s) 
   const Tuning& T = tuning();
   TravArgs a = make_trav_args(g, 0, true);
   const int threads = (int)std::min<int64_t>(512, std::max<int64_t>(64, T.hub_threads / 32 * 32));
-  const size_t vis_bytes = (size_t)((V::kSmem + 15) / 16) * 16;
-  const size_t hub_bytes = (size_t)a.hub_slots * a.table_words * 4;
-  const size_t small_bytes = (size_t)(threads / 32) * a.small_slots * a.table_words * 4;
-  const size_t smem = vis_bytes + std::max(hub_bytes, small_bytes);
+  const size_t smem = traverse_smem(a, threads, V::kSmem);
   UBT_CUDA(cudaFuncSetAttribute(k_traverse_w<V>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
   int per_sm = 0;
   UBT_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_traverse_w<V>, threads, smem));

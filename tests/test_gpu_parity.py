@@ -52,10 +52,12 @@ def test_counts_bit_exact(ubt, case, prune):
     G = ubt.Graph(n, s, d, k=k)
     ob, ou = oracle.count_threshold(n, s, d, k, TAUS)
     gb, gu = G.count_threshold(TAUS, prune=prune)
+    assert G.guard() == 0
     assert np.array_equal(gb, ob) and np.array_equal(gu, ou), (name, gb, ob, gu, ou)
     for i, t in enumerate(TAUS):  # single-threshold launches
         b1, u1 = G.count_threshold([t], prune=prune)
         assert (int(b1[0]), int(u1[0])) == (int(ob[i]), int(ou[i])), (name, t)
+    assert G.guard() == 0
 
 
 @pytest.mark.parametrize("case", PARITY, ids=[c[0] for c in PARITY])
@@ -70,6 +72,7 @@ def test_enumeration_bit_exact(ubt, case):
             assert np.array_equal(uvw, ouvw), (name, tau, which, prune)
             assert np.array_equal(cls, ocls)
             assert np.array_equal(pb, opb)
+    assert G.guard() == 0
 
 
 def test_enumeration_capacity(ubt, er2k):
@@ -199,19 +202,30 @@ def test_giant_lists_use_global_tables(ubt):
         ubt.set_tuning("smem_table_max", old)
 
 
-@pytest.mark.parametrize("thr", [2, 8, 200])
-def test_hub_threshold_variants(ubt, thr):
-    old = ubt.get_tuning("hub_threshold")
+@pytest.mark.parametrize("knobs", [{"hub_threshold": 2}, {"hub_threshold": 200}, {"short_max": 2},
+                                   {"short_max": 32, "hub_threshold": 32}, {"block_unit": 1}, {"block_unit": 32},
+                                   {"small_batch": 1, "hub_threads": 64}, {"hub_threads": 512}])
+def test_task_split_variants(ubt, knobs):
+    """Every way of splitting the work into block / warp / segment tasks gives
+    the same bit-exact counts and expected-count sums."""
+    old = {k: ubt.get_tuning(k) for k in knobs}
     try:
-        ubt.set_tuning("hub_threshold", thr)
+        for k, v in knobs.items():
+            ubt.set_tuning(k, v)
         s, d = mixed_graph(2000, 25000, 31)
         k = synth.k_uniform(s.size, 32)
         G = ubt.Graph(2000, s, d, k=k)
         ob, ou = oracle.count_threshold(2000, s, d, k, TAUS)
-        gb, gu = G.count_threshold(TAUS, prune=1)
-        assert np.array_equal(gb, ob) and np.array_equal(gu, ou)
+        for prune in (0, 1):
+            gb, gu = G.count_threshold(TAUS, prune=prune)
+            assert np.array_equal(gb, ob) and np.array_equal(gu, ou), prune
+        T, S = oracle.expected_fixed(2000, s, d, k)
+        _, _, T2, sumP = G.expected_counts(with_exact=True)
+        assert T2 == T and S == T * (1 << 47) - 4 * sumP
+        assert G.guard() == 0
     finally:
-        ubt.set_tuning("hub_threshold", old)
+        for k, v in old.items():
+            ubt.set_tuning(k, v)
 
 
 def test_degenerate_graphs(ubt):

@@ -303,15 +303,17 @@ ubt_status ubt_graph_export(const ubt_graph* g, uint32_t* h_row_ptr, uint64_t* h
  * UBT_ERR_INVALID_ARG.  Names:
  *   "short_max"       forward lists of 2..short_max entries are concatenated
  *                     and processed in 32-pair segments, one warp each
- *                     (2..32, default 16)
+ *                     (2..32, default 8)
  *   "hub_threshold"   longer lists than this are whole-block tasks; lists
- *                     between short_max and it are one-warp tasks (default 64)
- *   "hub_threads"     threads per block of the traversal (64..512, /32)
+ *                     between short_max and it are one-warp tasks (default 128)
+ *   "hub_threads"     threads per block of the traversal (64..512, /32,
+ *                     default 128)
  *   "blocks_per_sm"   cap on resident blocks per SM (1..32; occupancy decides
  *                     below it)
  *   "smem_table_max"  hash-table slots kept in shared memory (power of two);
  *                     longer lists use a table in global scratch
- *   "block_unit"      pairs a warp takes at a time inside a block task (1..32)
+ *   "block_unit"      pairs a warp takes at a time inside a block task (1..32,
+ *                     default 16)
  *   "world_words_per_pass"  64-world words per traversal of ubt_sample_worlds
  *                     (1, 2, 4, 8, 16, 32 or 64)
  *   "small_batch"     warp tasks / segments taken per grab of a task counter

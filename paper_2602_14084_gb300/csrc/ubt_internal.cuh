@@ -83,14 +83,14 @@ namespace ubt {
 // ---------------------------------------------------------------- tuning
 
 struct Tuning {
-  int64_t short_max = 16;         // lists up to this length go to segments
-  int64_t hub_threshold = 64;     // longer lists are whole-block tasks
-  int64_t hub_threads = 256;
+  int64_t short_max = 8;          // lists up to this length go to segments
+  int64_t hub_threshold = 128;    // longer lists are whole-block tasks
+  int64_t hub_threads = 128;
   int64_t blocks_per_sm = 32;     // cap on resident blocks (occupancy decides below it)
   int64_t smem_table_max = 8192;  // hash slots of a shared-memory table
   int64_t world_words_per_pass = 8;
   int64_t small_batch = 4;        // warp tasks taken per grab
-  int64_t block_unit = 8;         // pairs per warp step in block tasks
+  int64_t block_unit = 16;        // pairs per warp step in block tasks
   int64_t sort_smem_max = 4096;
 };
 Tuning& tuning();

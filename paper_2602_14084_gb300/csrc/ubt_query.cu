@@ -63,36 +63,74 @@ struct Acc128 {
 
 // ------------------------------------------------------------ visitors
 
-struct CountOneP {
-  int64_t B, U;
-  unsigned long long* out;  // [0] balanced, [1] unbalanced
+// Up to 8 thresholds: per-thread counters in registers, compared with every
+// threshold (padding thresholds never match).  32-bit counters are flushed to
+// the 64-bit globals before they can wrap.
+constexpr int kRegTau = 8;
+struct CountRegP {
+  int64_t B[kRegTau], U[kRegTau];
+  unsigned long long* out;  // [0, NT) balanced, [NT, 2 NT) unbalanced
 };
-struct CountOne {
-  using P = CountOneP;
+template <int NT>
+struct CountReg {
+  using P = CountRegP;
   static constexpr bool kPos = false;
   static constexpr int kSmem = 0;
-  P p;
-  unsigned long long bal = 0, unbal = 0;
-  __device__ CountOne(const P& p_, char*) : p(p_) {}
+  int64_t B[NT], U[NT];
+  unsigned long long* out;
+  uint32_t bal[NT], unbal[NT];
+  uint32_t since = 0;
+  __device__ CountReg(const P& p, char*) : out(p.out) {
+#pragma unroll
+    for (int i = 0; i < NT; i++) {
+      B[i] = p.B[i];
+      U[i] = p.U[i];
+      bal[i] = unbal[i] = 0;
+    }
+  }
   __device__ void block_init() {}
   __device__ __forceinline__ void step(bool hit, uint32_t, uint32_t, uint32_t, uint32_t quv, uint32_t quw,
                                        uint32_t qvw, uint32_t, uint32_t, uint32_t) {
     if (hit) {
       const int64_t P = tri_product(quv, quw, qvw);
-      bal += (P <= p.B);
-      unbal += (P > p.U);
+#pragma unroll
+      for (int i = 0; i < NT; i++) {
+        bal[i] += (P <= B[i]) ? 1u : 0u;
+        unbal[i] += (P > U[i]) ? 1u : 0u;
+      }
+      since++;
     }
   }
   __device__ void task_begin(uint32_t) {}
-  __device__ void task_end(uint32_t) {}
-  __device__ void block_end() {
-    const unsigned long long b = warp_sum(bal), u = warp_sum(unbal);
-    if ((threadIdx.x & 31) == 0) {
-      if (b) atomicAdd(&p.out[0], b);
-      if (u) atomicAdd(&p.out[1], u);
+  __device__ void flush() {
+#pragma unroll
+    for (int i = 0; i < NT; i++) {
+      const uint32_t b = __reduce_add_sync(kFull, bal[i]);
+      const uint32_t u = __reduce_add_sync(kFull, unbal[i]);
+      if ((threadIdx.x & 31) == 0) {
+        if (b) atomicAdd(&out[i], (unsigned long long)b);
+        if (u) atomicAdd(&out[NT + i], (unsigned long long)u);
+      }
+      bal[i] = unbal[i] = 0;
     }
+    since = 0;
   }
+  // a warp's 32 lanes sum to < 2^32 while every lane has fewer than 2^27 hits
+  __device__ void task_end(uint32_t) {
+    if (__any_sync(kFull, since >= (1u << 26))) flush();
+  }
+  __device__ void block_end() { flush(); }
 };
+
+__global__ void k_finish_reg(const unsigned long long* __restrict__ acc, int nt, int NT, const int* perm_unused,
+                             int64_t* __restrict__ out) {
+  const int i = threadIdx.x;
+  (void)perm_unused;
+  if (i < nt) {
+    out[i] = (int64_t)acc[i];
+    out[nt + i] = (int64_t)acc[NT + i];
+  }
+}
 
 // Many thresholds: per-block histograms of "how many thresholds does this
 // triangle satisfy" (B sorted descending, U ascending), suffix-summed later.
@@ -112,25 +150,33 @@ struct CountMulti {
   __device__ void block_init() {
     for (int i = threadIdx.x; i < 2 * 65; i += blockDim.x) h[i] = 0;
   }
+  // bin = number of thresholds the triangle meets (balanced bins 1..nt at
+  // h[1..nt], unbalanced at h[66..65+nt]); equal bins of a warp add once
   __device__ __forceinline__ void step(bool hit, uint32_t, uint32_t, uint32_t, uint32_t quv, uint32_t quw,
                                        uint32_t qvw, uint32_t, uint32_t, uint32_t) {
-    if (!hit) return;
-    const int64_t P = tri_product(quv, quw, qvw);
-    if (P <= p.B[0]) {
-      int lo = 0, hi = p.nt;  // B[lo] >= P, first index with B < P in (lo, hi]
-      while (hi - lo > 1) {
-        const int mid = (lo + hi) >> 1;
-        if (p.B[mid] >= P) lo = mid; else hi = mid;
+    int bin = -1;
+    if (hit) {
+      const int64_t P = tri_product(quv, quw, qvw);
+      if (P <= p.B[0]) {
+        int lo = 0, hi = p.nt;  // B[lo] >= P, first index with B < P in (lo, hi]
+        while (hi - lo > 1) {
+          const int mid = (lo + hi) >> 1;
+          if (p.B[mid] >= P) lo = mid; else hi = mid;
+        }
+        bin = hi;
+      } else if (P > p.U[0]) {
+        int lo = 0, hi = p.nt;
+        while (hi - lo > 1) {
+          const int mid = (lo + hi) >> 1;
+          if (p.U[mid] < P) lo = mid; else hi = mid;
+        }
+        bin = 65 + hi;
       }
-      atomicAdd(&h[hi], 1ull);
-    } else if (P > p.U[0]) {
-      int lo = 0, hi = p.nt;
-      while (hi - lo > 1) {
-        const int mid = (lo + hi) >> 1;
-        if (p.U[mid] < P) lo = mid; else hi = mid;
-      }
-      atomicAdd(&h[65 + hi], 1ull);
     }
+    const unsigned any = __ballot_sync(kFull, bin >= 0);
+    if (!any) return;
+    const unsigned same = __match_any_sync(kFull, bin);
+    if (bin >= 0 && (int)(threadIdx.x & 31) == __ffs(same) - 1) atomicAdd(&h[bin], (unsigned long long)__popc(same));
   }
   __device__ void task_begin(uint32_t) {}
   __device__ void task_end(uint32_t) {}
@@ -360,7 +406,7 @@ __global__ void k_trav_stats(int64_t n, const uint32_t* __restrict__ row_ptr, co
 // ------------------------------------------------------------ launching
 
 template <class V>
-__global__ void __launch_bounds__(512) k_traverse(TravArgs a, typename V::P p) {
+__global__ void __launch_bounds__(UBT_LB_THREADS, UBT_LB_MINB) k_traverse(TravArgs a, typename V::P p) {
   extern __shared__ __align__(16) char smem[];
   V vis(p, smem);
   vis.block_init();
@@ -413,7 +459,7 @@ template <class V>
 ubt_status launch_traverse(const ubt_graph* g, const typename V::P& p, int64_t L, cudaStream_t s) {
   const Tuning& T = tuning();
   TravArgs a = make_trav_args(g, L, V::kPos);
-  int threads = (int)std::min<int64_t>(512, std::max<int64_t>(64, T.hub_threads / 32 * 32));
+  int threads = (int)std::min<int64_t>(UBT_LB_THREADS, std::max<int64_t>(64, T.hub_threads / 32 * 32));
   const size_t smem = traverse_smem(a, threads, V::kSmem);
   UBT_CUDA(cudaFuncSetAttribute(k_traverse<V>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
   int per_sm = 0;
@@ -456,10 +502,26 @@ extern "C" ubt_status ubt_count_threshold(ubt_graph* g, const double* h_tau, int
   std::iota(order.begin(), order.end(), 0);
   std::stable_sort(order.begin(), order.end(), [&](int x, int y) { return lv[x].L < lv[y].L; });
   const int64_t L = prune ? lv[order[0]].L : 0;
-  if (n_tau == 1) {
-    UBT_CUDA(cudaMemsetAsync(d_counts, 0, 2 * sizeof(int64_t), s));
-    CountOneP p{lv[0].B, lv[0].U, (unsigned long long*)d_counts};
-    return launch_traverse<CountOne>(g, p, L, s);
+  if (n_tau <= kRegTau) {
+    const int NT = n_tau <= 1 ? 1 : n_tau <= 2 ? 2 : n_tau <= 4 ? 4 : 8;
+    CountRegP p;
+    for (int i = 0; i < kRegTau; i++) {
+      p.B[i] = i < n_tau ? lv[i].B : INT64_MIN;  // padding: never balanced
+      p.U[i] = i < n_tau ? lv[i].U : INT64_MAX;  // padding: never unbalanced
+    }
+    unsigned long long* acc = g->scratch->hist;
+    p.out = acc;
+    UBT_CUDA(cudaMemsetAsync(acc, 0, sizeof(unsigned long long) * 2 * NT, s));
+    switch (NT) {
+      case 1: st = launch_traverse<CountReg<1>>(g, p, L, s); break;
+      case 2: st = launch_traverse<CountReg<2>>(g, p, L, s); break;
+      case 4: st = launch_traverse<CountReg<4>>(g, p, L, s); break;
+      default: st = launch_traverse<CountReg<8>>(g, p, L, s); break;
+    }
+    if (st != UBT_OK) return st;
+    k_finish_reg<<<1, kRegTau, 0, s>>>(acc, n_tau, NT, nullptr, d_counts);
+    UBT_CUDA(cudaGetLastError());
+    return UBT_OK;
   }
   CountMultiP p;
   p.nt = n_tau;

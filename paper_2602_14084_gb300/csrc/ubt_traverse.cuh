@@ -7,8 +7,8 @@
 //
 // GPU layout of that loop (one persistent kernel, four kinds of task):
 //   * N>(u) is loaded into an open-addressing hash table (neighbour -> edge
-//     value, CSR position) in shared memory, at most 1/4 full so that most
-//     misses end at the first slot.
+//     value, CSR position) in shared memory: 4-slot buckets read with one
+//     16-byte load, at most 1/4 full, so nearly every probe is one load.
 //   * The pairs of a task are handed to one warp 32 at a time.  The lists N>(v)
 //     are streamed with coalesced 8-byte loads: long lists one after another
 //     by the whole warp, short lists concatenated ("flattened") so that every
@@ -38,6 +38,15 @@
 #pragma once
 
 #include "ubt_internal.cuh"
+
+// launch bounds of the traversal kernels: at most UBT_LB_THREADS threads per
+// block, at least UBT_LB_MINB resident blocks per SM (caps the registers)
+#ifndef UBT_LB_THREADS
+#define UBT_LB_THREADS 512
+#endif
+#ifndef UBT_LB_MINB
+#define UBT_LB_MINB 1
+#endif
 
 namespace ubt {
 
@@ -92,12 +101,14 @@ __device__ __forceinline__ uint32_t prune_prefix(const uint64_t* __restrict__ ro
   return hi;
 }
 
-// Hash table: key = neighbour id, val = edge value bits, pos = CSR position.
+// Hash table: key = neighbour id, val = edge value bits, pos = CSR position,
+// in buckets of 4 slots (one 16-byte load reads a bucket's keys); at most 1/4
+// of the slots are used, so nearly every lookup ends in its home bucket.
 struct Table {
   uint32_t* key;
   uint32_t* val;
   uint32_t* pos;
-  uint32_t mask;
+  uint32_t bmask;  // buckets - 1
   int shift;
 };
 
@@ -106,30 +117,34 @@ __device__ __forceinline__ Table make_table(uint32_t* base, uint32_t cap, uint32
   t.key = base;
   t.val = base + cap;
   t.pos = base + 2 * cap;
-  t.mask = slots - 1;
-  t.shift = 32 - (31 - __clz((int)slots));
+  const uint32_t nb = slots >> 2;
+  t.bmask = nb - 1;
+  t.shift = 32 - (31 - __clz((int)nb));
   return t;
 }
 
-// at most 1/4 full
+// slots for a list: a power of two >= 4x its entries (min 32, i.e. 8 buckets)
 __device__ __forceinline__ uint32_t slots_for(uint32_t entries) {
   uint32_t s = 32;
   while (s < 4 * entries) s <<= 1;
   return s;
 }
 
-// The table always has free slots (capacity >= 4x its entries), so both loops
-// end within `mask + 1` steps; the step limit is a self-check.
+// A bucket with a free slot ends every probe sequence, and there are more
+// buckets than entries, so both loops end within bmask + 1 buckets; the limit
+// is a self-check.
 __device__ __forceinline__ void table_insert(const Table& t, uint32_t w, uint32_t val, uint32_t pos, Scratch* sc) {
-  uint32_t h = hash_slot(w, t.shift);
-  for (uint32_t it = 0; it <= t.mask; it++) {
-    const uint32_t old = atomicCAS(&t.key[h], kEmpty, w);
-    if (old == kEmpty) {
-      t.val[h] = val;
-      t.pos[h] = pos;
-      return;
+  uint32_t b = hash_slot(w, t.shift);
+  for (uint32_t it = 0; it <= t.bmask; it++) {
+#pragma unroll
+    for (int i = 0; i < 4; i++) {
+      if (atomicCAS(&t.key[4 * b + i], kEmpty, w) == kEmpty) {
+        t.val[4 * b + i] = val;
+        t.pos[4 * b + i] = pos;
+        return;
+      }
     }
-    h = (h + 1) & t.mask;
+    b = (b + 1) & t.bmask;
   }
   guard_fail(sc, kGuardInsert, w);
 }
@@ -138,20 +153,22 @@ __device__ __forceinline__ void table_insert(const Table& t, uint32_t w, uint32_
 // row of one u; a table holding a single row passes rlen = ~0).
 __device__ __forceinline__ bool table_find(const Table& t, uint32_t w, uint32_t rs, uint32_t rlen, uint32_t& val,
                                            uint32_t& pos, Scratch* sc) {
-  uint32_t h = hash_slot(w, t.shift);
-  for (uint32_t it = 0; it <= t.mask; it++) {
-    const uint32_t k = t.key[h];
-    if (k == w) {
-      const uint32_t p = t.pos[h];
+  uint32_t b = hash_slot(w, t.shift);
+  for (uint32_t it = 0; it <= t.bmask; it++) {
+    const uint4 k = reinterpret_cast<const uint4*>(t.key)[b];
+    unsigned mt = (k.x == w ? 1u : 0u) | (k.y == w ? 2u : 0u) | (k.z == w ? 4u : 0u) | (k.w == w ? 8u : 0u);
+    while (mt) {
+      const uint32_t s = 4 * b + (__ffs(mt) - 1);
+      mt &= mt - 1;
+      const uint32_t p = t.pos[s];
       if (p - rs < rlen) {
-        val = t.val[h];
+        val = t.val[s];
         pos = p;
         return true;
       }
-    } else if (k == kEmpty) {
-      return false;
     }
-    h = (h + 1) & t.mask;
+    if ((k.x == kEmpty) | (k.y == kEmpty) | (k.z == kEmpty) | (k.w == kEmpty)) return false;
+    b = (b + 1) & t.bmask;
   }
   guard_fail(sc, kGuardFind, w);
   return false;

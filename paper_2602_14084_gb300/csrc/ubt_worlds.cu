@@ -225,7 +225,7 @@ struct Worlds {
 };
 
 template <class V>
-__global__ void __launch_bounds__(512) k_traverse_w(TravArgs a, typename V::P p) {
+__global__ void __launch_bounds__(UBT_LB_THREADS, UBT_LB_MINB) k_traverse_w(TravArgs a, typename V::P p) {
   extern __shared__ __align__(16) char smem[];
   V vis(p, smem);
   vis.block_init();
@@ -379,7 +379,7 @@ template <class V>
 ubt_status launch_w(const ubt_graph* g, const typename V::P& p, cudaStream_t s) {
   const Tuning& T = tuning();
   TravArgs a = make_trav_args(g, 0, true);
-  const int threads = (int)std::min<int64_t>(512, std::max<int64_t>(64, T.hub_threads / 32 * 32));
+  const int threads = (int)std::min<int64_t>(UBT_LB_THREADS, std::max<int64_t>(64, T.hub_threads / 32 * 32));
   const size_t smem = traverse_smem(a, threads, V::kSmem);
   UBT_CUDA(cudaFuncSetAttribute(k_traverse_w<V>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
   int per_sm = 0;

@@ -57,6 +57,7 @@ typedef int32_t ubt_status;
 #define UBT_ERR_TIMEOUT (-9)              /* reserved: a bounded device wait gave up */
 #define UBT_ERR_CUDA (-10)                /* a CUDA runtime call failed */
 #define UBT_ERR_UNSUPPORTED (-11)         /* operation not defined for this graph kind */
+#define UBT_ERR_SCRATCH_LIMIT (-12)       /* request larger than a fixed scratch array */
 
 /* Graph kinds (the `flags` of ubt_graph_workspace_size / ubt_create_graph). */
 #define UBT_GRAPH_FIXED 0   /* probabilities given as k (uint32, 0..65536) */
@@ -166,6 +167,29 @@ ubt_status ubt_graph_get_info(const ubt_graph* g, ubt_graph_info* h_info);
  */
 ubt_status ubt_count_threshold(ubt_graph* g, const double* h_tau, int32_t n_tau, int32_t prune,
                                int64_t* d_counts, void* stream);
+
+/*
+ * ubt_count_threshold_noalloc -- ASYNC after its first call on a device.  The
+ * same counts as ubt_count_threshold, for callers that cannot allocate device
+ * memory where they query (code that may only use buffers it is handed, or
+ * that must not call an allocator): the per-call scratch -- task counters,
+ * self-check word and per-threshold accumulators -- lives in a fixed 2 KiB
+ * array in the library's own device memory, which every GPU that loads the
+ * library holds until the process exits.  The paper has no counterpart; this
+ * is an interface for such callers.
+ *   Arguments as ubt_count_threshold, with 1 <= n_tau <= 8; more thresholds
+ *   return UBT_ERR_SCRATCH_LIMIT (the fixed array has room for 8).
+ *   No device memory is allocated or freed (no cudaMalloc, no allocating
+ *   library call); the array is cleared on `stream` at every call.
+ *   The first call on a device looks up the array's device address (once per
+ *   device, with that device current); make that first call before any
+ *   stream capture.
+ *   All calls share the one array: calls that overlap on the GPU (on
+ *   different streams, or on different graphs at the same time) race and
+ *   give wrong counts.  Issue them one after another on one stream.
+ */
+ubt_status ubt_count_threshold_noalloc(ubt_graph* g, const double* h_tau, int32_t n_tau, int32_t prune,
+                                       int64_t* d_counts, void* stream);
 
 /*
  * ubt_enumerate -- SYNC.  Enumeration problem (UBTE, Def. 7) at threshold t:

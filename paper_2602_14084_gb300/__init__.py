@@ -65,6 +65,7 @@ def lib():
             "ubt_destroy_graph": (I32, [P]),
             "ubt_graph_get_info": (I32, [P, ctypes.POINTER(_GraphInfo)]),
             "ubt_count_threshold": (I32, [P, P, I32, I32, P, P]),
+            "ubt_count_threshold_noalloc": (I32, [P, P, I32, I32, P, P]),
             "ubt_enumerate": (I32, [P, ctypes.c_double, I32, I32, P, I64, ctypes.POINTER(I64), P]),
             "ubt_expected_counts": (I32, [P, P, P, P]),
             "ubt_expected_counts_backward": (I32, [P, P, P, P]),

@@ -53,6 +53,7 @@ extern "C" const char* ubt_status_str(ubt_status s) {
     case UBT_ERR_TIMEOUT: return "device wait timed out";
     case UBT_ERR_CUDA: return g_last_error[0] ? g_last_error : "CUDA runtime error";
     case UBT_ERR_UNSUPPORTED: return "operation not supported for this graph kind";
+    case UBT_ERR_SCRATCH_LIMIT: return "request exceeds the fixed scratch array of this entry point";
     default: return "unknown status";
   }
 }

@@ -473,6 +473,57 @@ ubt_status launch_traverse(const ubt_graph* g, const typename V::P& p, int64_t L
   return UBT_OK;
 }
 
+// Threshold counts (at most kRegTau thresholds) whose per-call scratch -- the
+// task counters and guard word (`sc`) and the 2 x kRegTau accumulators
+// (`acc`) -- lives at the given device addresses instead of the graph's own
+// scratch area.  Used by the no-allocation entry point.
+ubt_status count_reg_at(const ubt_graph* g, const double* h_tau, int n_tau, int prune, int64_t* d_counts,
+                        Scratch* sc, unsigned long long* acc, cudaStream_t s) {
+  if (g->kind != UBT_GRAPH_FIXED) return UBT_ERR_UNSUPPORTED;
+  if (!h_tau || n_tau < 1 || n_tau > kRegTau) return UBT_ERR_INVALID_ARG;
+  Level lv[kRegTau];
+  int64_t L = INT64_MAX;
+  for (int i = 0; i < n_tau; i++) {
+    if (!tau_level(h_tau[i], &lv[i])) return UBT_ERR_TAU_OOB;
+    L = std::min(L, lv[i].L);
+  }
+  if (!prune) L = 0;
+  const int NT = n_tau <= 1 ? 1 : n_tau <= 2 ? 2 : n_tau <= 4 ? 4 : 8;
+  CountRegP p;
+  for (int i = 0; i < kRegTau; i++) {
+    p.B[i] = i < n_tau ? lv[i].B : INT64_MIN;
+    p.U[i] = i < n_tau ? lv[i].U : INT64_MAX;
+  }
+  p.out = acc;
+  TravArgs a = make_trav_args(g, L, false);
+  a.sc = sc;
+  const Tuning& T = tuning();
+  const int threads = (int)std::min<int64_t>(UBT_LB_THREADS, std::max<int64_t>(64, T.hub_threads / 32 * 32));
+  const size_t smem = traverse_smem(a, threads, 0);
+  int per_sm = 0;
+  switch (NT) {
+#define UBT_COUNT_AT(N)                                                                                      \
+  case N: {                                                                                                  \
+    UBT_CUDA(cudaFuncSetAttribute(k_traverse<CountReg<N>>, cudaFuncAttributeMaxDynamicSharedMemorySize,      \
+                                  (int)smem));                                                               \
+    UBT_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_traverse<CountReg<N>>, threads, smem)); \
+    if (per_sm < 1) return UBT_ERR_INVALID_ARG;                                                              \
+    per_sm = (int)std::min<int64_t>(per_sm, std::max<int64_t>(1, T.blocks_per_sm));                          \
+    k_traverse<CountReg<N>><<<g->sm_count * per_sm, threads, smem, s>>>(a, p);                               \
+    break;                                                                                                   \
+  }
+    UBT_COUNT_AT(1)
+    UBT_COUNT_AT(2)
+    UBT_COUNT_AT(4)
+    UBT_COUNT_AT(8)
+#undef UBT_COUNT_AT
+  }
+  UBT_CUDA(cudaGetLastError());
+  k_finish_reg<<<1, kRegTau, 0, s>>>(acc, n_tau, NT, nullptr, d_counts);
+  UBT_CUDA(cudaGetLastError());
+  return UBT_OK;
+}
+
 }  // namespace ubt
 
 using namespace ubt;

@@ -101,6 +101,31 @@ class Clocks:
                 "reasons": sorted(reasons), "samples": len(sm)}
 
 
+def csrc_digest():
+    """Digest of the CUDA sources: ncu counters apply only to the kernels they were taken on."""
+    import hashlib
+    h = hashlib.sha256()
+    d = os.path.join(ROOT, "paper_2602_14084_gb300", "csrc")
+    for f in sorted(os.listdir(d)):
+        if f.endswith((".cu", ".cuh")):
+            with open(os.path.join(d, f), "rb") as fh:
+                h.update(f.encode() + fh.read())
+    return h.hexdigest()[:16]
+
+
+def ncu_traffic(kernel, workload):
+    """DRAM bytes per launch (read + write) from the committed ncu summary of
+    this kernel and workload, or None when the kernels changed since."""
+    try:
+        with open(os.path.join(ROOT, "profiles", "dram_traffic.json")) as f:
+            rec = json.load(f).get("%s %s" % (kernel, workload))
+    except Exception:
+        return None
+    if not rec or rec.get("csrc_digest") != csrc_digest():
+        return None
+    return rec["dram_bytes_per_launch"]
+
+
 def dist_env():
     ws = int(os.environ.get("WORLD_SIZE", "1"))
     rank = int(os.environ.get("RANK", "0"))
@@ -180,11 +205,17 @@ def main():
     ap.add_argument("--extras", dest="extras", action="store_true", default=True)
     ap.add_argument("--no-extras", dest="extras", action="store_false")
     ap.add_argument("--no-cpu-baseline", dest="cpu", action="store_false", default=True)
-    ap.add_argument("--only", default=None, choices=["count", "count-unpruned", "worlds", "expected", "backward"],
-                    help="profiling driver: build the workload graph, run one form of the query "
+    ap.add_argument("--only", default=None,
+                    choices=["count", "count32", "count-unpruned", "worlds", "expected", "backward", "enumerate"],
+                    help="profiling driver: build the --workload graph, run one form of the query "
                          "--warmup + --steps times, print its mean time and exit")
+    ap.add_argument("--workload", default=WORKLOAD, choices=["cl1m", "rmat22", "rmat20", "cl4m", "er2k"])
+    ap.add_argument("--digest", action="store_true", help="print the CUDA-source digest and exit")
     args = ap.parse_args()
     args.warmup = max(args.warmup, 3)
+    if args.digest:
+        print(csrc_digest())
+        return 0
     if args.impl == "reference":
         return reference_arm(args)
 
@@ -202,9 +233,9 @@ def main():
     __graft_entry__.build()
     import paper_2602_14084_gb300 as ubt
 
-    g = make_graph(WORKLOAD)
     if args.only:
-        return profile_driver(ubt, g, args)
+        return profile_driver(ubt, args)
+    g = make_graph(WORKLOAD)
     t0 = time.perf_counter()
     G = ubt.Graph(g.n, g.src, g.dst, k=g.k)
     torch.cuda.synchronize()
@@ -261,9 +292,10 @@ def main():
     alg_bytes = 16 * st["table_entries"] + 8 * st["streamed"]
     pk, pk_kind = peaks()
     achieved = alg_bytes / t_step / 1e9
+    kname = "k_traverse<CountReg<4>>"
     roofline = {"bound": "hbm", "achieved": achieved, "peak": pk["hbm_gbs"], "unit": "GB/s",
-                "frac": achieved / pk["hbm_gbs"], "traffic": None,
-                "kernel": "k_traverse<CountMulti>", "peak_kind": pk_kind,
+                "frac": achieved / pk["hbm_gbs"], "traffic": ncu_traffic(kname, WORKLOAD),
+                "kernel": kname, "peak_kind": pk_kind,
                 "alg_bytes_per_launch": alg_bytes, "streamed_entries": st["streamed"],
                 "table_entries": st["table_entries"]}
     st0 = G.traversal_stats(TAUS, prune=False)
@@ -319,7 +351,9 @@ def main():
     }
 
     if args.extras and rank == 0:
-        line["extras"] = extras(ubt, G, g, T, args, flush)
+        del G, ews, hs, hd, hk
+        _release()
+        line["extras"] = extras(ubt, None, g, T, args, flush)
     if args.cpu and rank == 0:
         import oracle
         oracle.build()
@@ -339,16 +373,34 @@ def main():
     return 0
 
 
-def profile_driver(ubt, g, args):
-    """One form of the query on the workload graph, for ncu captures."""
+SWEEP32 = [0.51 + i * (0.48 / 31) for i in range(32)]   # 32 thresholds in [0.51, 0.99]
+
+
+def _events_ms(fn, steps, warmup, flush=None):
+    return 1e3 * float(np.mean(time_steps(fn, steps, warmup, flush)))
+
+
+def _release():
+    import gc
+    import torch
+    gc.collect()
+    torch.cuda.synchronize()
+    torch.cuda.empty_cache()
+
+
+def profile_driver(ubt, args):
+    """One form of the query on one workload graph, for ncu captures."""
     import torch
     import synth
+    g = make_graph(args.workload)
     if args.only in ("expected", "backward"):
-        p = synth.p_uniform_f32(g.m, 5)
-        G = ubt.Graph(g.n, g.src, g.dst, p=torch.from_numpy(p).cuda())
+        p = g.p if g.p is not None else synth.p_uniform_f32(g.m, 5)
+        G = ubt.Graph(g.n, g.src, g.dst, p=torch.from_numpy(np.ascontiguousarray(p)).cuda())
     else:
-        G = ubt.Graph(g.n, g.src, g.dst, k=g.k)
-    counts = torch.empty(2 * len(TAUS), dtype=torch.int64, device="cuda")
+        k = g.k if g.k is not None else synth.quantise(g.p)
+        G = ubt.Graph(g.n, g.src, g.dst, k=k)
+    taus = SWEEP32 if args.only == "count32" else TAUS
+    counts = torch.empty(2 * len(taus), dtype=torch.int64, device="cuda")
     eo = torch.empty(2, dtype=torch.float64, device="cuda")
     gout = torch.tensor([1.0, 0.0], dtype=torch.float64, device="cuda")
     grad = torch.empty(g.m, dtype=torch.float32, device="cuda")
@@ -356,49 +408,131 @@ def profile_driver(ubt, g, args):
     if args.only == "worlds":
         wws = torch.empty(G.sample_worlds_workspace(W), dtype=torch.uint8, device="cuda")
         wout = torch.empty(W, dtype=torch.int64, device="cuda")
+    if args.only == "enumerate":
+        nb, nu = G.count_threshold([0.9])
+        cap = int(nb[0] + nu[0])
+        rec = torch.empty(max(cap, 1) * ubt.TRI_REC_DTYPE.itemsize, dtype=torch.uint8, device="cuda")
+        found = ctypes.c_int64(0)
     fn = {
-        "count": lambda: G.count_threshold_(TAUS, counts, prune=True),
-        "count-unpruned": lambda: G.count_threshold_(TAUS, counts, prune=False),
-        "worlds": lambda: G.sample_worlds_(7, W, wout, None, wws) if args.only == "worlds" else None,
+        "count": lambda: G.count_threshold_(taus, counts, prune=True),
+        "count32": lambda: G.count_threshold_(taus, counts, prune=True),
+        "count-unpruned": lambda: G.count_threshold_(taus, counts, prune=False),
+        "worlds": lambda: G.sample_worlds_(7, W, wout, None, wws),
         "expected": lambda: G.expected_counts_(eo),
         "backward": lambda: G.expected_counts_backward_(gout, grad),
+        "enumerate": lambda: ubt.lib().ubt_enumerate(G.handle, 0.9, 3, 1, ctypes.c_void_p(rec.data_ptr()), cap,
+                                                     ctypes.byref(found), None),
     }[args.only]
     times = time_steps(fn, args.steps, args.warmup)
-    print(json.dumps({"only": args.only, "ms": 1e3 * float(np.mean(times)), "guard": G.guard()}))
+    print(json.dumps({"only": args.only, "workload": args.workload, "ms": 1e3 * float(np.mean(times)),
+                      "guard": G.guard()}))
     return 0
 
 
-def extras(ubt, G, g, T, args, flush):
-    """Other forms of the path on the same GPU: MC sign worlds and expected
-    counts forward + backward on the cl1m graph (full-size workloads of their
-    own are run by the dedicated benchmarks in tests and profiles)."""
+def extra_rmat22(ubt, args, flush):
+    """R-MAT scale 22: the 32-threshold sweep in one traversal, and
+    enumeration at t = 0.9 into a device buffer."""
     import torch
-    out = {}
-    # Monte-Carlo sign worlds, W = 4096
+    g = make_graph("rmat22")
+    t0 = time.perf_counter()
+    G = ubt.Graph(g.n, g.src, g.dst, k=g.k)
+    torch.cuda.synchronize()
+    build_s = time.perf_counter() - t0
+    _, _, T, _ = G.expected_counts(with_exact=True)
+    out = torch.empty(2 * len(SWEEP32), dtype=torch.int64, device="cuda")
+    steps = max(3, args.steps // 4)
+    ms = _events_ms(lambda: G.count_threshold_(SWEEP32, out, prune=True), steps, 1, flush)
+    b, u = out.cpu().numpy()[:32], out.cpu().numpy()[32:]
+    b0, u0 = G.count_threshold(SWEEP32, prune=False)
+    assert np.array_equal(b, b0) and np.array_equal(u, u0), "pruned and unpruned sweeps differ"
+    assert np.all(np.diff(b) <= 0) and np.all(np.diff(u) <= 0), "counts not monotone in t"
+    st = G.traversal_stats(SWEEP32, prune=True)
+    alg = 16 * st["table_entries"] + 8 * st["streamed"]
+    pk, pk_kind = peaks()
+    nb9, nu9 = G.count_threshold([0.9])
+    cap = int(nb9[0] + nu9[0])
+    rec = torch.empty(max(cap, 1) * ubt.TRI_REC_DTYPE.itemsize, dtype=torch.uint8, device="cuda")
+    found = ctypes.c_int64(0)
+
+    def enum():
+        r = ubt.lib().ubt_enumerate(G.handle, 0.9, 3, 1, ctypes.c_void_p(rec.data_ptr()), cap, ctypes.byref(found),
+                                    ctypes.c_void_p(torch.cuda.current_stream().cuda_stream))
+        assert r == 0, r
+
+    ems = _events_ms(enum, steps, 1, flush)
+    assert found.value == cap
+    res = {"workload": "R-MAT scale 22, edge factor 16, (0.57,0.19,0.19,0.05), P+ ~ 0.5 Beta(8,2) + 0.5 Beta(2,8)",
+           "n": g.n, "m": g.m, "triangles": T, "build_s": build_s,
+           "sweep32": {"ms": ms, "triangles_per_s": T / (ms / 1e3), "alg_bytes": alg,
+                       "streamed_entries": st["streamed"], "achieved_gbs": alg / (ms / 1e3) / 1e9,
+                       "frac_hbm": alg / (ms / 1e3) / 1e9 / pk["hbm_gbs"], "peak_kind": pk_kind,
+                       "bal_at_0.51": int(b[0]), "bal_at_0.99": int(b[-1])},
+           "enumerate_0.9": {"ms": ems, "records": cap, "record_bytes": 24 * cap,
+                             "triangles_per_s": T / (ems / 1e3)}}
+    del G, rec
+    _release()
+    return res
+
+
+def extra_worlds(ubt, args, flush):
+    """R-MAT scale 20 with k ~ U{0..65536}: W = 4096 bit-sliced sign worlds."""
+    import torch
+    g = make_graph("rmat20")
+    G = ubt.Graph(g.n, g.src, g.dst, k=g.k)
+    eb, eu, T, _ = G.expected_counts(with_exact=True)
     W = 4096
-    wsz = G.sample_worlds_workspace(W)
-    wws = torch.empty(wsz, dtype=torch.uint8, device="cuda")
+    wws = torch.empty(G.sample_worlds_workspace(W), dtype=torch.uint8, device="cuda")
     wout = torch.empty(W, dtype=torch.int64, device="cuda")
     wt = torch.empty(1, dtype=torch.int64, device="cuda")
-    tw = time_steps(lambda: G.sample_worlds_(7, W, wout, wt, wws), max(3, args.steps // 4), 1, flush)
-    out["mc_worlds"] = {"W": W, "ms": 1e3 * float(np.mean(tw)), "world_triangles_per_s": T * W / float(np.mean(tw)),
-                        "words_per_pass": ubt.get_tuning("world_words_per_pass")}
-    # expected counts forward + backward on a REAL graph (p ~ U[0,1] float32)
-    import synth
-    p = synth.p_uniform_f32(g.m, 5)
-    pt = torch.from_numpy(p).cuda()
-    Gp = ubt.Graph(g.n, g.src, g.dst, p=pt)
-    eo = torch.empty(2, dtype=torch.float64, device="cuda")
-    gout = torch.tensor([1.0, 0.0], dtype=torch.float64, device="cuda")
-    grad = torch.empty(g.m, dtype=torch.float32, device="cuda")
+    ms = _events_ms(lambda: G.sample_worlds_(7, W, wout, wt, wws), max(3, args.steps // 4), 1, flush)
+    c = wout.cpu().numpy().astype(np.float64)
+    z = (c.mean() - eb) / (c.std(ddof=1) / np.sqrt(W))
+    res = {"workload": "R-MAT scale 20, edge factor 16, k ~ U{0..65536}", "n": g.n, "m": g.m, "triangles": T,
+           "W": W, "ms": ms, "world_triangles_per_s": T * W / (ms / 1e3),
+           "words_per_pass": ubt.get_tuning("world_words_per_pass"),
+           "mc_mean_minus_exact_in_standard_errors": float(z)}
+    del G, wws
+    _release()
+    return res
 
-    def fb():
-        Gp.expected_counts_(eo)
-        Gp.expected_counts_backward_(gout, grad)
 
-    tf = time_steps(lambda: Gp.expected_counts_(eo), max(3, args.steps // 4), 1, flush)
-    tfb = time_steps(fb, max(3, args.steps // 4), 1, flush)
-    out["expected_fwd_bwd"] = {"fwd_ms": 1e3 * float(np.mean(tf)), "fwd_bwd_ms": 1e3 * float(np.mean(tfb))}
+def extra_grad(ubt, args, flush):
+    """Chung-Lu n = 4e6, gamma 2.3, p ~ U[0,1] float32: expected counts
+    forward and the hand-written adjoint backward through autograd."""
+    import torch
+    g = make_graph("cl4m")
+    pt = torch.from_numpy(g.p).cuda().requires_grad_(True)
+    G = ubt.Graph(g.n, g.src, g.dst, p=pt.detach())
+    steps = max(3, args.steps // 4)
+
+    def fwd():
+        with torch.no_grad():
+            ubt.expected_counts(G, pt)
+
+    def fwd_bwd():
+        pt.grad = None
+        eb, eu = ubt.expected_counts(G, pt)
+        (eb - eu).backward()
+
+    fms = _events_ms(fwd, steps, 1, flush)
+    fbms = _events_ms(fwd_bwd, steps, 1, flush)
+    eb, eu = ubt.expected_counts(G, pt)
+    res = {"workload": "Chung-Lu n=4,000,000 gamma=2.3 mean-deg 20 cap 50,000, p ~ U[0,1] float32",
+           "n": g.n, "m": g.m, "triangles": int(round(eb.item() + eu.item())), "fwd_ms": fms, "fwd_bwd_ms": fbms,
+           "via": "torch.autograd.Function -> ubt_expected_counts / ubt_expected_counts_backward"}
+    del G, pt
+    _release()
+    return res
+
+
+def extras(ubt, G, g, T, args, flush):
+    """The other workloads of the path, each on its own graph."""
+    out = {}
+    for name, fn in (("c3_rmat22", extra_rmat22), ("c4_rmat20_worlds", extra_worlds), ("c5_cl4m_grad", extra_grad)):
+        try:
+            out[name] = fn(ubt, args, flush)
+        except Exception as e:  # report, do not hide: the line says what failed
+            out[name] = {"error": repr(e)[:300]}
     return out
 
 

@@ -330,8 +330,10 @@ ubt_status ubt_graph_export(const ubt_graph* g, uint32_t* h_row_ptr, uint64_t* h
  *                     (2..32, default 8)
  *   "hub_threshold"   longer lists than this are whole-block tasks; lists
  *                     between short_max and it are one-warp tasks (default 128)
- *   "hub_threads"     threads per block of the traversal (64..512, /32,
- *                     default 128)
+ *   "block_threads"   threads per block of the block-task kernel (long
+ *                     lists; 64..512, /32, default 512)
+ *   "warp_threads"    threads per block of the warp-task kernel (medium and
+ *                     short lists; 64..512, /32, default 128)
  *   "blocks_per_sm"   cap on resident blocks per SM (1..32; occupancy decides
  *                     below it)
  *   "smem_table_max"  hash-table slots kept in shared memory (power of two);

@@ -66,9 +66,12 @@ extern "C" ubt_status ubt_set_tuning(const char* name, int64_t value) {
   if (!strcmp(name, "hub_threshold")) {
     if (value < 2 || value > 4096) return UBT_ERR_INVALID_ARG;
     t.hub_threshold = value;
-  } else if (!strcmp(name, "hub_threads")) {
+  } else if (!strcmp(name, "block_threads")) {
     if (value < 64 || value > 512 || value % 32) return UBT_ERR_INVALID_ARG;
-    t.hub_threads = value;
+    t.block_threads = value;
+  } else if (!strcmp(name, "warp_threads")) {
+    if (value < 64 || value > 512 || value % 32) return UBT_ERR_INVALID_ARG;
+    t.warp_threads = value;
   } else if (!strcmp(name, "blocks_per_sm")) {
     if (value < 1 || value > 32) return UBT_ERR_INVALID_ARG;
     t.blocks_per_sm = value;
@@ -100,7 +103,8 @@ extern "C" ubt_status ubt_get_tuning(const char* name, int64_t* h_value) {
   if (!name || !h_value) return UBT_ERR_INVALID_ARG;
   const Tuning& t = tuning();
   if (!strcmp(name, "hub_threshold")) *h_value = t.hub_threshold;
-  else if (!strcmp(name, "hub_threads")) *h_value = t.hub_threads;
+  else if (!strcmp(name, "block_threads")) *h_value = t.block_threads;
+  else if (!strcmp(name, "warp_threads")) *h_value = t.warp_threads;
   else if (!strcmp(name, "blocks_per_sm")) *h_value = t.blocks_per_sm;
   else if (!strcmp(name, "smem_table_max")) *h_value = t.smem_table_max;
   else if (!strcmp(name, "world_words_per_pass")) *h_value = t.world_words_per_pass;

@@ -25,6 +25,21 @@ constexpr uint32_t kEmpty = 0xFFFFFFFFu;
 constexpr int kWarp = 32;
 constexpr unsigned kFull = 0xFFFFFFFFu;
 
+#ifdef __CUDACC__
+// lane index and mask of the lower lanes; not volatile, so the compiler keeps
+// them in registers instead of re-reading special registers in loops
+__device__ __forceinline__ uint32_t lane_id() {
+  uint32_t l;
+  asm("mov.u32 %0, %%laneid;" : "=r"(l));
+  return l;
+}
+__device__ __forceinline__ uint32_t lanemask_lt() {
+  uint32_t m;
+  asm("mov.u32 %0, %%lanemask_lt;" : "=r"(m));
+  return m;
+}
+#endif
+
 __host__ __device__ inline uint32_t adj_col(uint64_t e) { return (uint32_t)e; }
 __host__ __device__ inline int32_t adj_q(uint64_t e) { return (int32_t)(uint32_t)(e >> 32); }
 __host__ __device__ inline uint32_t adj_valbits(uint64_t e) { return (uint32_t)(e >> 32); }
@@ -42,7 +57,7 @@ struct Scratch {
   unsigned long long err;           // device-side error word (build)
   unsigned long long guard;         // first failed self-check of a query (0 = none)
   unsigned long long pad[6];
-  unsigned long long hist[2 * 65];  // multi-threshold histograms (bal, unbal)
+  unsigned long long hist[2 * 65];  // per-threshold accumulators (bal [0,64), unbal [64,128))
 };
 constexpr size_t kScratchHeader = 16 * sizeof(unsigned long long);  // zeroed per query
 
@@ -85,7 +100,8 @@ namespace ubt {
 struct Tuning {
   int64_t short_max = 8;          // lists up to this length go to segments
   int64_t hub_threshold = 128;    // longer lists are whole-block tasks
-  int64_t hub_threads = 128;
+  int64_t block_threads = 512;    // threads of the block-task kernel
+  int64_t warp_threads = 128;     // threads of the warp-task kernel (at most 128)
   int64_t blocks_per_sm = 32;     // cap on resident blocks (occupancy decides below it)
   int64_t smem_table_max = 8192;  // hash slots of a shared-memory table
   int64_t world_words_per_pass = 8;

@@ -71,16 +71,24 @@ struct CountRegP {
   int64_t B[kRegTau], U[kRegTau];
   unsigned long long* out;  // [0, NT) balanced, [NT, 2 NT) unbalanced
 };
+// A warp collects the products P of its triangles in a shared-memory queue
+// and counts them 32 at a time, so the counting runs on full warps.
+constexpr int kHitQueue = 64;
+
 template <int NT>
 struct CountReg {
   using P = CountRegP;
   static constexpr bool kPos = false;
-  static constexpr int kSmem = 0;
+  static constexpr int kRegCap = 64;
+  static __host__ __device__ int smem_bytes(int threads) { return (threads / 32) * kHitQueue * 8; }
   int64_t B[NT], U[NT];
   unsigned long long* out;
+  long long* q;  // this warp's queue of products
+  uint32_t qn = 0;
   uint32_t bal[NT], unbal[NT];
   uint32_t since = 0;
-  __device__ CountReg(const P& p, char*) : out(p.out) {
+  __device__ CountReg(const P& p, char* smem) : out(p.out) {
+    q = (long long*)smem + (threadIdx.x >> 5) * kHitQueue;
 #pragma unroll
     for (int i = 0; i < NT; i++) {
       B[i] = p.B[i];
@@ -89,17 +97,42 @@ struct CountReg {
     }
   }
   __device__ void block_init() {}
+  __device__ __forceinline__ void count(long long P) {
+#pragma unroll
+    for (int i = 0; i < NT; i++) {
+      bal[i] += (P <= B[i]) ? 1u : 0u;
+      unbal[i] += (P > U[i]) ? 1u : 0u;
+    }
+    since++;
+  }
+  // count the first 32 queued products, move the rest to the front
+  __device__ void drain32() {
+    const int lane = (int)lane_id();
+    __syncwarp();
+    const long long mine = q[lane];
+    const uint32_t rest = qn - 32;
+    const long long moved = (uint32_t)lane < rest ? q[32 + lane] : 0;
+    __syncwarp();
+    if ((uint32_t)lane < rest) q[lane] = moved;
+    qn = rest;
+    __syncwarp();
+    count(mine);
+  }
+  __device__ void drain_all() {
+    const int lane = (int)lane_id();
+    __syncwarp();
+    if ((uint32_t)lane < qn) count(q[lane]);
+    qn = 0;
+    __syncwarp();
+  }
   __device__ __forceinline__ void step(bool hit, uint32_t, uint32_t, uint32_t, uint32_t quv, uint32_t quw,
                                        uint32_t qvw, uint32_t, uint32_t, uint32_t) {
-    if (hit) {
-      const int64_t P = tri_product(quv, quw, qvw);
-#pragma unroll
-      for (int i = 0; i < NT; i++) {
-        bal[i] += (P <= B[i]) ? 1u : 0u;
-        unbal[i] += (P > U[i]) ? 1u : 0u;
-      }
-      since++;
-    }
+    const unsigned m = __ballot_sync(kFull, hit);
+    if (!m) return;
+    const int lane = (int)lane_id();
+    if (hit) q[qn + __popc(m & lanemask_lt())] = tri_product(quv, quw, qvw);
+    qn += __popc(m);
+    if (qn >= 32) drain32();
   }
   __device__ void task_begin(uint32_t) {}
   __device__ void flush() {
@@ -107,7 +140,7 @@ struct CountReg {
     for (int i = 0; i < NT; i++) {
       const uint32_t b = __reduce_add_sync(kFull, bal[i]);
       const uint32_t u = __reduce_add_sync(kFull, unbal[i]);
-      if ((threadIdx.x & 31) == 0) {
+      if (lane_id() == 0) {
         if (b) atomicAdd(&out[i], (unsigned long long)b);
         if (u) atomicAdd(&out[NT + i], (unsigned long long)u);
       }
@@ -115,11 +148,14 @@ struct CountReg {
     }
     since = 0;
   }
-  // a warp's 32 lanes sum to < 2^32 while every lane has fewer than 2^27 hits
+  // a warp's 32 lanes sum to < 2^32 while every lane has counted fewer than 2^26
   __device__ void task_end(uint32_t) {
     if (__any_sync(kFull, since >= (1u << 26))) flush();
   }
-  __device__ void block_end() { flush(); }
+  __device__ void block_end() {
+    drain_all();
+    flush();
+  }
 };
 
 __global__ void k_finish_reg(const unsigned long long* __restrict__ acc, int nt, int NT, const int* perm_unused,
@@ -132,58 +168,93 @@ __global__ void k_finish_reg(const unsigned long long* __restrict__ acc, int nt,
   }
 }
 
-// Many thresholds: per-block histograms of "how many thresholds does this
-// triangle satisfy" (B sorted descending, U ascending), suffix-summed later.
+// Many thresholds (up to 64): products are queued per warp as in CountReg;
+// when 32 are queued, lane i compares its own thresholds i and i + 32 with all
+// 32 products (read as shared-memory broadcasts), so the counting needs no
+// atomics and no divergence.  Counts are per threshold, in ascending order.
 struct CountMultiP {
   int nt;
   int64_t B[kMaxTau];
   int64_t U[kMaxTau];
-  unsigned long long* hist;  // global 2 x 65
+  unsigned long long* out;  // global: [0, 64) balanced, [64, 128) unbalanced
 };
 struct CountMulti {
   using P = CountMultiP;
   static constexpr bool kPos = false;
-  static constexpr int kSmem = 2 * 65 * 8 + 16;
-  const P& p;
-  unsigned long long* h;
-  __device__ CountMulti(const P& p_, char* smem) : p(p_), h((unsigned long long*)smem) {}
-  __device__ void block_init() {
-    for (int i = threadIdx.x; i < 2 * 65; i += blockDim.x) h[i] = 0;
+  static constexpr int kRegCap = 64;
+  static __host__ __device__ int smem_bytes(int threads) { return (threads / 32) * kHitQueue * 8; }
+  unsigned long long* out;
+  long long* q;   // this warp's queue of products
+  uint32_t qn = 0;
+  int64_t B0, U0, B1, U1;  // this lane's thresholds (padding never met)
+  uint32_t b0 = 0, u0 = 0, b1 = 0, u1 = 0;
+  uint32_t since = 0;
+  bool two;
+  __device__ CountMulti(const P& p, char* smem) : out(p.out) {
+    const int lane = (int)lane_id();
+    q = (long long*)smem + (threadIdx.x >> 5) * kHitQueue;
+    B0 = lane < p.nt ? p.B[lane] : INT64_MIN;
+    U0 = lane < p.nt ? p.U[lane] : INT64_MAX;
+    B1 = lane + 32 < p.nt ? p.B[lane + 32] : INT64_MIN;
+    U1 = lane + 32 < p.nt ? p.U[lane + 32] : INT64_MAX;
+    two = p.nt > 32;
   }
-  // bin = number of thresholds the triangle meets (balanced bins 1..nt at
-  // h[1..nt], unbalanced at h[66..65+nt]); equal bins of a warp add once
-  __device__ __forceinline__ void step(bool hit, uint32_t, uint32_t, uint32_t, uint32_t quv, uint32_t quw,
-                                       uint32_t qvw, uint32_t, uint32_t, uint32_t) {
-    int bin = -1;
-    if (hit) {
-      const int64_t P = tri_product(quv, quw, qvw);
-      if (P <= p.B[0]) {
-        int lo = 0, hi = p.nt;  // B[lo] >= P, first index with B < P in (lo, hi]
-        while (hi - lo > 1) {
-          const int mid = (lo + hi) >> 1;
-          if (p.B[mid] >= P) lo = mid; else hi = mid;
-        }
-        bin = hi;
-      } else if (P > p.U[0]) {
-        int lo = 0, hi = p.nt;
-        while (hi - lo > 1) {
-          const int mid = (lo + hi) >> 1;
-          if (p.U[mid] < P) lo = mid; else hi = mid;
-        }
-        bin = 65 + hi;
+  __device__ void block_init() {}
+  __device__ __forceinline__ void count_n(uint32_t n) {
+    for (uint32_t j = 0; j < n; j++) {
+      const long long P = q[j];
+      b0 += (P <= B0) ? 1u : 0u;
+      u0 += (P > U0) ? 1u : 0u;
+      if (two) {
+        b1 += (P <= B1) ? 1u : 0u;
+        u1 += (P > U1) ? 1u : 0u;
       }
     }
-    const unsigned any = __ballot_sync(kFull, bin >= 0);
-    if (!any) return;
-    const unsigned same = __match_any_sync(kFull, bin);
-    if (bin >= 0 && (int)(threadIdx.x & 31) == __ffs(same) - 1) atomicAdd(&h[bin], (unsigned long long)__popc(same));
+    since += n;
+  }
+  __device__ void drain32() {
+    const int lane = (int)lane_id();
+    __syncwarp();
+    count_n(32);
+    const uint32_t rest = qn - 32;
+    const long long moved = (uint32_t)lane < rest ? q[32 + lane] : 0;
+    __syncwarp();
+    if ((uint32_t)lane < rest) q[lane] = moved;
+    qn = rest;
+    __syncwarp();
+  }
+  __device__ void drain_all() {
+    __syncwarp();
+    count_n(qn);
+    qn = 0;
+    __syncwarp();
+  }
+  __device__ __forceinline__ void step(bool hit, uint32_t, uint32_t, uint32_t, uint32_t quv, uint32_t quw,
+                                       uint32_t qvw, uint32_t, uint32_t, uint32_t) {
+    const unsigned m = __ballot_sync(kFull, hit);
+    if (!m) return;
+    const int lane = (int)lane_id();
+    if (hit) q[qn + __popc(m & lanemask_lt())] = tri_product(quv, quw, qvw);
+    qn += __popc(m);
+    if (qn >= 32) drain32();
   }
   __device__ void task_begin(uint32_t) {}
-  __device__ void task_end(uint32_t) {}
+  __device__ void flush() {
+    const int lane = (int)lane_id();
+    if (b0) atomicAdd(&out[lane], (unsigned long long)b0);
+    if (u0) atomicAdd(&out[64 + lane], (unsigned long long)u0);
+    if (b1) atomicAdd(&out[32 + lane], (unsigned long long)b1);
+    if (u1) atomicAdd(&out[96 + lane], (unsigned long long)u1);
+    b0 = u0 = b1 = u1 = 0;
+    since = 0;
+  }
+  // every counter stays below 2^32 while it has seen fewer than 2^31 products
+  __device__ void task_end(uint32_t) {
+    if (since >= (1u << 31)) flush();
+  }
   __device__ void block_end() {
-    __syncthreads();
-    for (int i = threadIdx.x; i < 2 * 65; i += blockDim.x)
-      if (h[i]) atomicAdd(&p.hist[i], h[i]);
+    drain_all();
+    flush();
   }
 };
 
@@ -192,17 +263,11 @@ struct FinishMulti {
   int perm[kMaxTau];  // caller index of the i-th smallest threshold
 };
 
-__global__ void k_finish_multi(const unsigned long long* __restrict__ hist, FinishMulti f, int64_t* __restrict__ out) {
-  // balanced count of sorted threshold i = sum_{k > i} hist_b[k] (same for unbalanced)
+__global__ void k_finish_multi(const unsigned long long* __restrict__ acc, FinishMulti f, int64_t* __restrict__ out) {
   const int i = threadIdx.x;
   if (i < f.nt) {
-    unsigned long long b = 0, u = 0;
-    for (int k = i + 1; k <= f.nt; k++) {
-      b += hist[k];
-      u += hist[65 + k];
-    }
-    out[f.perm[i]] = (int64_t)b;
-    out[f.nt + f.perm[i]] = (int64_t)u;
+    out[f.perm[i]] = (int64_t)acc[i];
+    out[f.nt + f.perm[i]] = (int64_t)acc[64 + i];
   }
 }
 
@@ -216,7 +281,8 @@ struct EnumP {
 struct Enum {
   using P = EnumP;
   static constexpr bool kPos = false;
-  static constexpr int kSmem = 0;
+  static constexpr int kRegCap = 64;
+  static __host__ __device__ int smem_bytes(int) { return 0; }
   P p;
   __device__ Enum(const P& p_, char*) : p(p_) {}
   __device__ void block_init() {}
@@ -231,13 +297,13 @@ struct Enum {
     }
     const unsigned m = __ballot_sync(kFull, cls != 0);
     if (!m) return;
-    const int lane = threadIdx.x & 31;
+    const int lane = (int)lane_id();
     const int leader = __ffs(m) - 1;
     unsigned long long base = 0;
     if (lane == leader) base = atomicAdd(p.cursor, (unsigned long long)__popc(m));
     base = __shfl_sync(kFull, base, leader);
     if (cls) {
-      const unsigned long long idx = base + __popc(m & ((1u << lane) - 1u));
+      const unsigned long long idx = base + __popc(m & lanemask_lt());
       if (idx < p.cap) {
         uint32_t a = u, b = v, c = w, t;
         if (a > b) { t = a; a = b; b = t; }
@@ -268,7 +334,8 @@ template <bool kReal>
 struct Expect {
   using P = ExpectP;
   static constexpr bool kPos = false;
-  static constexpr int kSmem = 0;
+  static constexpr int kRegCap = 64;
+  static __host__ __device__ int smem_bytes(int) { return 0; }
   P p;
   Acc128 acc;
   unsigned long long cnt = 0;
@@ -292,7 +359,7 @@ struct Expect {
   __device__ void block_end() {
     acc.warp_reduce();
     const unsigned long long c = warp_sum(cnt);
-    if ((threadIdx.x & 31) == 0 && c) {
+    if (lane_id() == 0 && c) {
       atomicAdd(p.tri, c);
       acc.flush(p.sum_lo, p.sum_hi);
     }
@@ -329,7 +396,8 @@ template <bool kReal>
 struct Adjoint {
   using P = AdjointP;
   static constexpr bool kPos = true;
-  static constexpr int kSmem = 0;
+  static constexpr int kRegCap = 64;
+  static __host__ __device__ int smem_bytes(int) { return 0; }
   P p;
   __device__ Adjoint(const P& p_, char*) : p(p_) {}
   __device__ void block_init() {}
@@ -368,7 +436,7 @@ __global__ void k_finish_adjoint(int64_t m, const unsigned long long* __restrict
 // traversal sizes (same pruning rules as the traversal); one warp per vertex
 __global__ void k_trav_stats(int64_t n, const uint32_t* __restrict__ row_ptr, const uint64_t* __restrict__ adj,
                              int64_t L, unsigned long long* out) {
-  const int lane = threadIdx.x & 31;
+  const int lane = (int)lane_id();
   const int64_t warps = (int64_t)gridDim.x * (blockDim.x >> 5);
   unsigned long long tab = 0, str = 0, tasks = 0;
   for (int64_t u = blockIdx.x * (int64_t)(blockDim.x >> 5) + (threadIdx.x >> 5); u < n; u += warps) {
@@ -405,15 +473,6 @@ __global__ void k_trav_stats(int64_t n, const uint32_t* __restrict__ row_ptr, co
 
 // ------------------------------------------------------------ launching
 
-template <class V>
-__global__ void __launch_bounds__(UBT_LB_THREADS, UBT_LB_MINB) k_traverse(TravArgs a, typename V::P p) {
-  extern __shared__ __align__(16) char smem[];
-  V vis(p, smem);
-  vis.block_init();
-  __syncthreads();
-  traverse(a, vis, smem + ((V::kSmem + 15) / 16) * 16);
-}
-
 }  // namespace
 
 TravArgs make_trav_args(const ubt_graph* g, int64_t L, bool with_pos) {
@@ -448,29 +507,9 @@ TravArgs make_trav_args(const ubt_graph* g, int64_t L, bool with_pos) {
   return a;
 }
 
-size_t traverse_smem(const TravArgs& a, int threads, int vis_smem) {
-  const size_t vis_bytes = (size_t)((vis_smem + 15) / 16) * 16;
-  const size_t hub_bytes = (size_t)a.hub_slots * 3 * 4;
-  const size_t warp_bytes = (size_t)(threads / 32) * a.warp_slots * 3 * 4;
-  return vis_bytes + std::max(hub_bytes, warp_bytes);
-}
-
 template <class V>
 ubt_status launch_traverse(const ubt_graph* g, const typename V::P& p, int64_t L, cudaStream_t s) {
-  const Tuning& T = tuning();
-  TravArgs a = make_trav_args(g, L, V::kPos);
-  int threads = (int)std::min<int64_t>(UBT_LB_THREADS, std::max<int64_t>(64, T.hub_threads / 32 * 32));
-  const size_t smem = traverse_smem(a, threads, V::kSmem);
-  UBT_CUDA(cudaFuncSetAttribute(k_traverse<V>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
-  int per_sm = 0;
-  UBT_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_traverse<V>, threads, smem));
-  if (per_sm < 1) return UBT_ERR_INVALID_ARG;
-  per_sm = (int)std::min<int64_t>(per_sm, std::max<int64_t>(1, T.blocks_per_sm));
-  const int grid = g->sm_count * per_sm;
-  UBT_CUDA(cudaMemsetAsync(g->scratch, 0, kScratchHeader / 2, s));  // task counters
-  k_traverse<V><<<grid, threads, smem, s>>>(a, p);
-  UBT_CUDA(cudaGetLastError());
-  return UBT_OK;
+  return launch_traversal<V>(g, make_trav_args(g, L, V::kPos), p, s);
 }
 
 // Threshold counts (at most kRegTau thresholds) whose per-call scratch -- the
@@ -497,28 +536,14 @@ ubt_status count_reg_at(const ubt_graph* g, const double* h_tau, int n_tau, int 
   p.out = acc;
   TravArgs a = make_trav_args(g, L, false);
   a.sc = sc;
-  const Tuning& T = tuning();
-  const int threads = (int)std::min<int64_t>(UBT_LB_THREADS, std::max<int64_t>(64, T.hub_threads / 32 * 32));
-  const size_t smem = traverse_smem(a, threads, 0);
-  int per_sm = 0;
+  ubt_status st = UBT_OK;
   switch (NT) {
-#define UBT_COUNT_AT(N)                                                                                      \
-  case N: {                                                                                                  \
-    UBT_CUDA(cudaFuncSetAttribute(k_traverse<CountReg<N>>, cudaFuncAttributeMaxDynamicSharedMemorySize,      \
-                                  (int)smem));                                                               \
-    UBT_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_traverse<CountReg<N>>, threads, smem)); \
-    if (per_sm < 1) return UBT_ERR_INVALID_ARG;                                                              \
-    per_sm = (int)std::min<int64_t>(per_sm, std::max<int64_t>(1, T.blocks_per_sm));                          \
-    k_traverse<CountReg<N>><<<g->sm_count * per_sm, threads, smem, s>>>(a, p);                               \
-    break;                                                                                                   \
+    case 1: st = launch_traversal<CountReg<1>>(g, a, p, s); break;
+    case 2: st = launch_traversal<CountReg<2>>(g, a, p, s); break;
+    case 4: st = launch_traversal<CountReg<4>>(g, a, p, s); break;
+    default: st = launch_traversal<CountReg<8>>(g, a, p, s); break;
   }
-    UBT_COUNT_AT(1)
-    UBT_COUNT_AT(2)
-    UBT_COUNT_AT(4)
-    UBT_COUNT_AT(8)
-#undef UBT_COUNT_AT
-  }
-  UBT_CUDA(cudaGetLastError());
+  if (st != UBT_OK) return st;
   k_finish_reg<<<1, kRegTau, 0, s>>>(acc, n_tau, NT, nullptr, d_counts);
   UBT_CUDA(cudaGetLastError());
   return UBT_OK;
@@ -580,7 +605,7 @@ extern "C" ubt_status ubt_count_threshold(ubt_graph* g, const double* h_tau, int
     p.B[i] = lv[order[i]].B;
     p.U[i] = lv[order[i]].U;
   }
-  p.hist = g->scratch->hist;
+  p.out = g->scratch->hist;
   UBT_CUDA(cudaMemsetAsync(g->scratch->hist, 0, sizeof(g->scratch->hist), s));
   st = launch_traverse<CountMulti>(g, p, L, s);
   if (st != UBT_OK) return st;

@@ -32,10 +32,12 @@
 //                              of Lemma 3: the other two edges bound it)
 //     qmax(u) is the largest |q| in N>(u) (its first entry).
 //
-// Visitors implement: block_init / task_begin / step (called by all 32 lanes
-// of a warp, converged, once per probed entry with a hit flag) / task_end /
-// block_end.
+// Visitors implement: smem_bytes(threads) (shared memory they need) /
+// block_init / task_begin / step (called by all 32 lanes of a warp, converged,
+// once per probed entry with a hit flag) / task_end / block_end.
 #pragma once
+
+#include <algorithm>
 
 #include "ubt_internal.cuh"
 
@@ -132,7 +134,7 @@ __device__ __forceinline__ uint32_t slots_for(uint32_t entries) {
 
 // A bucket with a free slot ends every probe sequence, and there are more
 // buckets than entries, so both loops end within bmask + 1 buckets; the limit
-// is a self-check.
+// is a self-check.  Slots of a bucket are taken in order (first free slot).
 __device__ __forceinline__ void table_insert(const Table& t, uint32_t w, uint32_t val, uint32_t pos, Scratch* sc) {
   uint32_t b = hash_slot(w, t.shift);
   for (uint32_t it = 0; it <= t.bmask; it++) {
@@ -149,11 +151,49 @@ __device__ __forceinline__ void table_insert(const Table& t, uint32_t w, uint32_
   guard_fail(sc, kGuardInsert, w);
 }
 
-// Find w among the entries whose CSR position lies in [rs, rs + rlen) (the
-// row of one u; a table holding a single row passes rlen = ~0).
+// Find w in the table.  kRow: the table holds several rows (a segment) and
+// only entries whose CSR position lies in [rs, rs + rlen) -- the row of this
+// pair's u -- count.  kPos: also return the entry's CSR position.
+//
+// Inserts take the first free slot of a bucket and nothing is ever removed,
+// so a bucket's used slots are a prefix and a bucket has room iff its last
+// slot is empty; a key missing from a bucket with room is absent.  With at
+// most 1/4 of the slots used, nearly every lookup reads one bucket and takes
+// no branch.
+template <bool kRow, bool kPos>
 __device__ __forceinline__ bool table_find(const Table& t, uint32_t w, uint32_t rs, uint32_t rlen, uint32_t& val,
                                            uint32_t& pos, Scratch* sc) {
   uint32_t b = hash_slot(w, t.shift);
+  if (!kRow) {
+    const uint4 k = reinterpret_cast<const uint4*>(t.key)[b];
+    const bool m0 = k.x == w, m1 = k.y == w, m2 = k.z == w, m3 = k.w == w;
+    bool hit = m0 | m1 | m2 | m3;
+    uint32_t s = 4 * b + (m0 ? 0u : (m1 ? 1u : (m2 ? 2u : 3u)));
+    if (!hit && k.w != kEmpty) {  // the home bucket is full: continue in the next ones
+      bool ended = false;
+      for (uint32_t it = 1; it <= t.bmask; it++) {
+        b = (b + 1) & t.bmask;
+        const uint4 kk = reinterpret_cast<const uint4*>(t.key)[b];
+        const bool n0 = kk.x == w, n1 = kk.y == w, n2 = kk.z == w, n3 = kk.w == w;
+        if (n0 | n1 | n2 | n3) {
+          hit = true;
+          s = 4 * b + (n0 ? 0u : (n1 ? 1u : (n2 ? 2u : 3u)));
+          ended = true;
+          break;
+        }
+        if (kk.w == kEmpty) {
+          ended = true;
+          break;
+        }
+      }
+      if (!ended) guard_fail(sc, kGuardFind, w);
+    }
+    if (hit) {
+      val = t.val[s];
+      if (kPos) pos = t.pos[s];
+    }
+    return hit;
+  }
   for (uint32_t it = 0; it <= t.bmask; it++) {
     const uint4 k = reinterpret_cast<const uint4*>(t.key)[b];
     unsigned mt = (k.x == w ? 1u : 0u) | (k.y == w ? 2u : 0u) | (k.z == w ? 4u : 0u) | (k.w == w ? 8u : 0u);
@@ -167,7 +207,7 @@ __device__ __forceinline__ bool table_find(const Table& t, uint32_t w, uint32_t 
         return true;
       }
     }
-    if ((k.x == kEmpty) | (k.y == kEmpty) | (k.z == kEmpty) | (k.w == kEmpty)) return false;
+    if (k.w == kEmpty) return false;
     b = (b + 1) & t.bmask;
   }
   guard_fail(sc, kGuardFind, w);
@@ -182,10 +222,34 @@ struct Pair {
   bool ok;
 };
 
+// The whole warp probes entries [off, off + 32 U) of one long list N>(v),
+// U entries per lane, all loads issued before the probes.
+template <class V, bool kRow, int U>
+__device__ __forceinline__ void long_steps(const uint64_t* __restrict__ adj, Scratch* sc, V& vis, const Table& t,
+                                           int lane, uint32_t uj, uint32_t vj, uint32_t vsj, uint32_t dvj,
+                                           uint32_t qj, uint32_t pj, uint32_t rsj, uint32_t rlj, uint32_t off) {
+  uint64_t e[U];
+#pragma unroll
+  for (int s = 0; s < U; s++) {
+    const uint32_t i = off + 32 * s + lane;
+    e[s] = i < dvj ? adj[vsj + i] : 0ull;
+  }
+#pragma unroll
+  for (int s = 0; s < U; s++) {
+    const uint32_t i = off + 32 * s + lane;
+    uint32_t quw = 0, puw = 0;
+    const bool hit = i < dvj && table_find<kRow, V::kPos>(t, adj_col(e[s]), rsj, rlj, quw, puw, sc);
+    if (off + 32 * s < dvj) vis.step(hit, uj, vj, adj_col(e[s]), qj, quw, adj_valbits(e[s]), pj, puw, vsj + i);
+  }
+}
+
 // One warp probes the lists of up to 32 pairs (one per lane, `ok` lanes).
-template <class V>
+// kRow: the table is a segment table (entries must belong to the pair's row).
+template <class V, bool kRow>
 __device__ __forceinline__ void probe_pairs(const TravArgs& a, V& vis, const Table& t, const Pair& pr) {
-  const int lane = threadIdx.x & 31;
+  const int lane = (int)lane_id();
+  const uint64_t* __restrict__ adj = a.adj;
+  Scratch* const sc = a.sc;
   uint32_t vs = 0, dv = 0;
   if (pr.ok) {
     if (pr.v < a.n) {
@@ -201,7 +265,7 @@ __device__ __forceinline__ void probe_pairs(const TravArgs& a, V& vis, const Tab
       guard_fail(a.sc, kGuardVertex, pr.v);
     }
   }
-  // long lists: one at a time, the whole warp streams it, two entries per lane
+  // long lists: one at a time, the whole warp streams it, up to four entries per lane
   constexpr uint32_t kLong = 48;
   unsigned longm = __ballot_sync(kFull, dv >= kLong);
   while (longm) {
@@ -215,16 +279,14 @@ __device__ __forceinline__ void probe_pairs(const TravArgs& a, V& vis, const Tab
     const uint32_t pj = __shfl_sync(kFull, pr.puv, j);
     const uint32_t rsj = __shfl_sync(kFull, pr.urs, j);
     const uint32_t rlj = __shfl_sync(kFull, pr.ulen, j);
-    for (uint32_t off = 0; off < dvj; off += 64) {
-      const uint32_t i0 = off + lane, i1 = off + 32 + lane;
-      const bool a0 = i0 < dvj, a1 = i1 < dvj;
-      const uint64_t e0 = a0 ? a.adj[vsj + i0] : 0ull;
-      const uint64_t e1 = a1 ? a.adj[vsj + i1] : 0ull;
-      uint32_t q0 = 0, p0 = 0, q1 = 0, p1 = 0;
-      const bool h0 = a0 && table_find(t, adj_col(e0), rsj, rlj, q0, p0, a.sc);
-      const bool h1 = a1 && table_find(t, adj_col(e1), rsj, rlj, q1, p1, a.sc);
-      vis.step(h0, uj, vj, adj_col(e0), qj, q0, adj_valbits(e0), pj, p0, vsj + i0);
-      if (off + 32 < dvj) vis.step(h1, uj, vj, adj_col(e1), qj, q1, adj_valbits(e1), pj, p1, vsj + i1);
+    uint32_t off = 0;
+    while (dvj - off >= 128) {
+      long_steps<V, kRow, 4>(adj, sc, vis, t, lane, uj, vj, vsj, dvj, qj, pj, rsj, rlj, off);
+      off += 128;
+    }
+    while (off < dvj) {
+      long_steps<V, kRow, 2>(adj, sc, vis, t, lane, uj, vj, vsj, dvj, qj, pj, rsj, rlj, off);
+      off += 64;
     }
   }
   // short lists: concatenated so that every lane probes one entry per half-step
@@ -255,7 +317,7 @@ __device__ __forceinline__ void probe_pairs(const TravArgs& a, V& vis, const Tab
       jj[s] = (uint32_t)(j > 31 ? 31 : j);
       const uint32_t vsj = __shfl_sync(kFull, vs, jj[s]);
       const uint32_t exj = __shfl_sync(kFull, excl, jj[s]);
-      e[s] = act[s] ? a.adj[vsj + (f[s] - exj)] : 0ull;
+      e[s] = act[s] ? adj[vsj + (f[s] - exj)] : 0ull;
       f[s] = vsj + (f[s] - exj);  // now the CSR position of the entry
     }
 #pragma unroll
@@ -264,7 +326,7 @@ __device__ __forceinline__ void probe_pairs(const TravArgs& a, V& vis, const Tab
       const uint32_t rsj = __shfl_sync(kFull, pr.urs, j);
       const uint32_t rlj = __shfl_sync(kFull, pr.ulen, j);
       uint32_t quw = 0, puw = 0;
-      const bool hit = act[s] && table_find(t, adj_col(e[s]), rsj, rlj, quw, puw, a.sc);
+      const bool hit = act[s] && table_find<kRow, V::kPos>(t, adj_col(e[s]), rsj, rlj, quw, puw, sc);
       const uint32_t uj = __shfl_sync(kFull, pr.u, j);
       const uint32_t vj = __shfl_sync(kFull, pr.v, j);
       const uint32_t qj = __shfl_sync(kFull, pr.quv, j);
@@ -277,7 +339,7 @@ __device__ __forceinline__ void probe_pairs(const TravArgs& a, V& vis, const Tab
 
 // Pair of this lane among the pairs [cs, cs + cnt) of a single-row table.
 __device__ __forceinline__ Pair row_pair(const TravArgs& a, uint32_t u, int64_t qmax, uint32_t cs, uint32_t cnt) {
-  const int lane = threadIdx.x & 31;
+  const int lane = (int)lane_id();
   Pair pr;
   pr.u = u;
   pr.urs = 0;
@@ -336,14 +398,22 @@ __device__ __forceinline__ void block_task(const TravArgs& a, V& vis, uint32_t u
   }
   __syncthreads();
   vis.task_begin(u);
-  const uint32_t units = (len + a.unit - 1) / a.unit;
+  // warps take pairs `unit` at a time, fewer as the list runs out, so that
+  // they reach the closing barrier at about the same time
+  const uint32_t nw = blockDim.x >> 5;
   while (true) {
-    uint32_t c = 0;
-    if (lane == 0) c = atomicAdd(&s_misc[1], 1u);
+    uint32_t c = 0, cnt = 0;
+    if (lane == 0) {
+      const uint32_t seen = *(volatile uint32_t*)&s_misc[1];
+      const uint32_t rem = seen < len ? len - seen : 0u;
+      const uint32_t want = max(1u, min(a.unit, rem / (2 * nw)));
+      c = atomicAdd(&s_misc[1], want);
+      cnt = c < len ? min(want, len - c) : 0u;
+    }
     c = __shfl_sync(kFull, c, 0);
-    if (c >= units) break;
-    const uint32_t cs = c * a.unit;
-    probe_pairs(a, vis, t, row_pair(a, u, qmax, rs + cs, min(a.unit, len - cs)));
+    cnt = __shfl_sync(kFull, cnt, 0);
+    if (cnt == 0) break;
+    probe_pairs<V, false>(a, vis, t, row_pair(a, u, qmax, rs + c, cnt));
   }
   vis.task_end(u);
   __syncthreads();
@@ -352,7 +422,7 @@ __device__ __forceinline__ void block_task(const TravArgs& a, V& vis, uint32_t u
 // One warp handles u (a medium list).
 template <class V>
 __device__ __forceinline__ void warp_task(const TravArgs& a, V& vis, uint32_t u, uint32_t* tab) {
-  const int lane = threadIdx.x & 31;
+  const int lane = (int)lane_id();
   if (u >= a.n) {
     if (lane == 0) guard_fail(a.sc, kGuardVertex, u);
     return;
@@ -379,7 +449,8 @@ __device__ __forceinline__ void warp_task(const TravArgs& a, V& vis, uint32_t u,
   }
   __syncwarp();
   vis.task_begin(u);
-  for (uint32_t cs = 0; cs < len; cs += 32) probe_pairs(a, vis, t, row_pair(a, u, qmax, rs + cs, min(32u, len - cs)));
+  for (uint32_t cs = 0; cs < len; cs += 32)
+    probe_pairs<V, false>(a, vis, t, row_pair(a, u, qmax, rs + cs, min(32u, len - cs)));
   vis.task_end(u);
   __syncwarp();
 }
@@ -387,7 +458,7 @@ __device__ __forceinline__ void warp_task(const TravArgs& a, V& vis, uint32_t u,
 // One warp handles segment k: pairs [32k, 32k + 32) of the concatenated short lists.
 template <class V>
 __device__ __forceinline__ void segment_task(const TravArgs& a, V& vis, uint32_t k, uint32_t* tab) {
-  const int lane = threadIdx.x & 31;
+  const int lane = (int)lane_id();
   const uint32_t r0 = a.seg_first[k];
   if (r0 == kEmpty) return;
   const uint32_t sp0 = 32 * k, sp1 = sp0 + 32;
@@ -479,59 +550,134 @@ __device__ __forceinline__ void segment_task(const TravArgs& a, V& vis, uint32_t
   pr.quv = adj_valbits(e);
   const uint32_t u0 = __shfl_sync(kFull, u, 0);
   vis.task_begin(u0);
-  probe_pairs(a, vis, t, pr);
+  probe_pairs<V, true>(a, vis, t, pr);
   vis.task_end(u0);
   __syncwarp();
 }
 
+// The traversal runs as two persistent kernels, so that each can have the
+// block size and shared memory its tasks need: the block kernel (giant and
+// hub lists, one large table per block) and the warp kernel (medium lists and
+// short-list segments, one small table per warp).
+enum : int { kBlockTasks = 1, kWarpTasks = 2 };
+
 // Persistent traversal kernel body.  Shared memory: [visitor bytes][tables].
-template <class V>
+template <class V, int kPhases>
 __device__ void traverse(const TravArgs& a, V& vis, char* smem_tables) {
   __shared__ uint32_t s_misc[4];
   const int tid = threadIdx.x, lane = tid & 31, wid = tid >> 5;
   uint32_t* tab = (uint32_t*)smem_tables;
-  // phase 0: giant lists, tables in global memory (first gtab_blocks blocks)
-  if (blockIdx.x < a.gtab_blocks) {
-    uint32_t* gt = a.gtab + (size_t)blockIdx.x * a.gtab_slots * 3;
+  if (kPhases & kBlockTasks) {
+    // giant lists, tables in global memory (first gtab_blocks blocks)
+    if (blockIdx.x < a.gtab_blocks) {
+      uint32_t* gt = a.gtab + (size_t)blockIdx.x * a.gtab_slots * 3;
+      while (true) {
+        if (tid == 0) s_misc[2] = (uint32_t)atomicAdd(&a.sc->task[0], 1ull);
+        __syncthreads();
+        const uint32_t task = s_misc[2];
+        __syncthreads();
+        if (task >= a.n_giant) break;
+        block_task(a, vis, a.giant_list[task], gt, a.gtab_slots, s_misc);
+      }
+    }
+    // hub lists, block-wide shared-memory tables
     while (true) {
-      if (tid == 0) s_misc[2] = (uint32_t)atomicAdd(&a.sc->task[0], 1ull);
+      if (tid == 0) s_misc[2] = (uint32_t)atomicAdd(&a.sc->task[1], 1ull);
       __syncthreads();
       const uint32_t task = s_misc[2];
       __syncthreads();
-      if (task >= a.n_giant) break;
-      block_task(a, vis, a.giant_list[task], gt, a.gtab_slots, s_misc);
+      if (task >= a.n_hub) break;
+      block_task(a, vis, a.hub_list[task], tab, a.hub_slots, s_misc);
     }
   }
-  // phase 1: hub lists, block-wide shared-memory tables
-  while (true) {
-    if (tid == 0) s_misc[2] = (uint32_t)atomicAdd(&a.sc->task[1], 1ull);
-    __syncthreads();
-    const uint32_t task = s_misc[2];
-    __syncthreads();
-    if (task >= a.n_hub) break;
-    block_task(a, vis, a.hub_list[task], tab, a.hub_slots, s_misc);
-  }
-  uint32_t* wtab = tab + (size_t)wid * a.warp_slots * 3;
-  // phase 2: medium lists, one warp each
-  while (true) {
-    unsigned long long t0 = 0;
-    if (lane == 0) t0 = atomicAdd(&a.sc->task[2], (unsigned long long)a.batch);
-    t0 = __shfl_sync(kFull, t0, 0);
-    if (t0 >= a.n_med) break;
-    const uint32_t t1 = (uint32_t)min((unsigned long long)a.n_med, t0 + a.batch);
-    for (uint32_t t = (uint32_t)t0; t < t1; t++) warp_task(a, vis, a.med_list[t], wtab);
-  }
-  // phase 3: segments of short lists
-  while (true) {
-    unsigned long long t0 = 0;
-    if (lane == 0) t0 = atomicAdd(&a.sc->task[3], (unsigned long long)a.batch);
-    t0 = __shfl_sync(kFull, t0, 0);
-    if (t0 >= a.n_segs) break;
-    const uint32_t t1 = (uint32_t)min((unsigned long long)a.n_segs, t0 + a.batch);
-    for (uint32_t t = (uint32_t)t0; t < t1; t++) segment_task(a, vis, t, wtab);
+  if (kPhases & kWarpTasks) {
+    uint32_t* wtab = tab + (size_t)wid * a.warp_slots * 3;
+    // medium lists, one warp each
+    while (true) {
+      unsigned long long t0 = 0;
+      if (lane == 0) t0 = atomicAdd(&a.sc->task[2], (unsigned long long)a.batch);
+      t0 = __shfl_sync(kFull, t0, 0);
+      if (t0 >= a.n_med) break;
+      const uint32_t t1 = (uint32_t)min((unsigned long long)a.n_med, t0 + a.batch);
+      for (uint32_t t = (uint32_t)t0; t < t1; t++) warp_task(a, vis, a.med_list[t], wtab);
+    }
+    // segments of short lists
+    while (true) {
+      unsigned long long t0 = 0;
+      if (lane == 0) t0 = atomicAdd(&a.sc->task[3], (unsigned long long)a.batch);
+      t0 = __shfl_sync(kFull, t0, 0);
+      if (t0 >= a.n_segs) break;
+      const uint32_t t1 = (uint32_t)min((unsigned long long)a.n_segs, t0 + a.batch);
+      for (uint32_t t = (uint32_t)t0; t < t1; t++) segment_task(a, vis, t, wtab);
+    }
   }
   __syncthreads();
   vis.block_end();
 }
+
+// Shared memory of one block of a traversal kernel: visitor bytes + tables.
+inline size_t traverse_smem_bytes(const TravArgs& a, int phases, int threads, int vis_smem) {
+  const size_t vis_bytes = (size_t)((vis_smem + 15) / 16) * 16;
+  size_t tables = 0;
+  if (phases & kBlockTasks) tables = std::max(tables, (size_t)a.hub_slots * 3 * 4);
+  if (phases & kWarpTasks) tables = std::max(tables, (size_t)(threads / 32) * a.warp_slots * 3 * 4);
+  return vis_bytes + tables;
+}
+
+namespace {
+
+// Launch bounds per kernel: the block kernel runs 512-thread blocks, the warp
+// kernel 128-thread blocks, and a visitor's register cap (V::kRegCap) sets how
+// many of them must fit on one SM (65536 registers).
+template <class V, int kPhases>
+struct Bounds {
+  static constexpr int kThreads = (kPhases & kBlockTasks) ? UBT_LB_THREADS : 128;
+  static constexpr int kMinBlocks = 65536 / (kThreads * V::kRegCap) > 0 ? 65536 / (kThreads * V::kRegCap) : 1;
+};
+
+template <class V, int kPhases>
+__global__ void __launch_bounds__(Bounds<V, kPhases>::kThreads, Bounds<V, kPhases>::kMinBlocks)
+    k_traverse(TravArgs a, typename V::P p) {
+  extern __shared__ __align__(16) char smem[];
+  V vis(p, smem);
+  vis.block_init();
+  __syncthreads();
+  traverse<V, kPhases>(a, vis, smem + ((V::smem_bytes((int)blockDim.x) + 15) / 16) * 16);
+}
+
+template <class V, int kPhases>
+ubt_status launch_phase(const ubt_graph* g, const TravArgs& a, const typename V::P& p, int threads, cudaStream_t s) {
+  const Tuning& T = tuning();
+  threads = (int)std::min<int64_t>(Bounds<V, kPhases>::kThreads, std::max<int64_t>(64, threads / 32 * 32));
+  const size_t smem = traverse_smem_bytes(a, kPhases, threads, V::smem_bytes(threads));
+  UBT_CUDA(cudaFuncSetAttribute(k_traverse<V, kPhases>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+  int per_sm = 0;
+  UBT_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_traverse<V, kPhases>, threads, smem));
+  if (per_sm < 1) return UBT_ERR_INVALID_ARG;
+  per_sm = (int)std::min<int64_t>(per_sm, std::max<int64_t>(1, T.blocks_per_sm));
+  k_traverse<V, kPhases><<<g->sm_count * per_sm, threads, smem, s>>>(a, p);
+  UBT_CUDA(cudaGetLastError());
+  return UBT_OK;
+}
+
+// One traversal: the task counters in a.sc are cleared, then the block kernel
+// (if the graph has giant or hub lists) and the warp kernel (if it has medium
+// lists or segments) run one after the other on `s`.
+template <class V>
+ubt_status launch_traversal(const ubt_graph* g, const TravArgs& a, const typename V::P& p, cudaStream_t s) {
+  const Tuning& T = tuning();
+  UBT_CUDA(cudaMemsetAsync(a.sc, 0, kScratchHeader / 2, s));
+  if (a.n_giant + a.n_hub > 0) {
+    const ubt_status st = launch_phase<V, kBlockTasks>(g, a, p, (int)T.block_threads, s);
+    if (st != UBT_OK) return st;
+  }
+  if (a.n_med + a.n_segs > 0) {
+    const ubt_status st = launch_phase<V, kWarpTasks>(g, a, p, (int)T.warp_threads, s);
+    if (st != UBT_OK) return st;
+  }
+  return UBT_OK;
+}
+
+}  // namespace
 
 }  // namespace ubt

@@ -23,7 +23,6 @@
 namespace ubt {
 
 TravArgs make_trav_args(const ubt_graph* g, int64_t L, bool with_pos);
-size_t traverse_smem(const TravArgs& a, int threads, int vis_smem);
 
 namespace {
 
@@ -138,10 +137,12 @@ template <int SLOTS>
 struct Worlds {
   using P = WorldsP;
   static constexpr bool kPos = true;
+  static constexpr int kRegCap = 128;
   static constexpr int K = SLOTS == 1 ? 14 : 12;      // planes per slot
   static constexpr uint32_t kLimit = (1u << K) - 1u;  // increments before a flush
   static constexpr int kQueue = 64;
-  static constexpr int kSmem = 64 * 64 * 8 + 16 * kQueue * 12;  // counters + 16 warp queues
+  // counters + one queue per warp
+  static __host__ __device__ int smem_bytes(int threads) { return 64 * 64 * 8 + (threads / 32) * kQueue * 12; }
   P p;
   unsigned long long* cnt;  // shared: wp * 64 counters
   uint32_t* q;              // this warp's queue: 3 x kQueue positions
@@ -158,7 +159,7 @@ struct Worlds {
     for (int i = threadIdx.x; i < (int)p.wp * 64; i += blockDim.x) cnt[i] = 0;
   }
   __device__ __forceinline__ uint32_t word_of(int s) const {
-    const int lane = threadIdx.x & 31;
+    const int lane = (int)lane_id();
     return SLOTS == 2 ? (uint32_t)(lane + 32 * s) : (uint32_t)lane % p.wp;
   }
   __device__ void flush() {
@@ -175,7 +176,7 @@ struct Worlds {
   }
   __device__ void drain() {
     __syncwarp();
-    const int lane = threadIdx.x & 31;
+    const int lane = (int)lane_id();
     const unsigned long long* X = p.X;
     const uint32_t wp = p.wp;
     if (SLOTS == 2) {
@@ -203,9 +204,9 @@ struct Worlds {
                                        uint32_t puv, uint32_t puw, uint32_t pvw) {
     const unsigned m = __ballot_sync(kFull, hit);
     if (!m) return;
-    const int lane = threadIdx.x & 31;
+    const int lane = (int)lane_id();
     if (hit) {
-      const uint32_t at = qn + __popc(m & ((1u << lane) - 1u));
+      const uint32_t at = qn + __popc(m & lanemask_lt());
       q[at] = puv;
       q[kQueue + at] = puw;
       q[2 * kQueue + at] = pvw;
@@ -223,15 +224,6 @@ struct Worlds {
       if (cnt[i]) atomicAdd(&p.out[i], cnt[i]);
   }
 };
-
-template <class V>
-__global__ void __launch_bounds__(UBT_LB_THREADS, UBT_LB_MINB) k_traverse_w(TravArgs a, typename V::P p) {
-  extern __shared__ __align__(16) char smem[];
-  V vis(p, smem);
-  vis.block_init();
-  __syncthreads();
-  traverse(a, vis, smem + ((V::kSmem + 15) / 16) * 16);
-}
 
 __global__ void k_world_total(const unsigned long long* __restrict__ cnt, int64_t W, int64_t* total) {
   __shared__ unsigned long long s[1024];
@@ -266,7 +258,8 @@ struct BatchP {
 struct Batch {
   using P = BatchP;
   static constexpr bool kPos = true;
-  static constexpr int kSmem = 0;
+  static constexpr int kRegCap = 128;
+  static __host__ __device__ int smem_bytes(int) { return 0; }
   static constexpr int K = 8;
   P p;
   uint32_t g = kEmpty;
@@ -286,7 +279,7 @@ struct Batch {
   }
   __device__ void block_init() {}
   __device__ void flush() {
-    const int lane = threadIdx.x & 31;
+    const int lane = (int)lane_id();
     if (g == kEmpty) return;
 #pragma unroll
     for (int i = 0; i < kBatchTau; i++) {
@@ -345,7 +338,7 @@ struct Batch {
     // a lane's counters grow by at most one per call that has any hit
     if (__any_sync(kFull, hit) && ++since == (1u << K) - 1u) {
       if (p.X) {
-        const int lane = threadIdx.x & 31;
+        const int lane = (int)lane_id();
         for (int j = 0; j < 64; j++) {
           const uint32_t v = __reduce_add_sync(kFull, pl.count(j));
           if (lane == (j & 31) && v && g != kEmpty) atomicAdd(&p.worlds[(size_t)g * 64 + j], (unsigned long long)v);
@@ -377,19 +370,7 @@ __global__ void k_batch_finish(int64_t ng, int nt, const unsigned long long* __r
 
 template <class V>
 ubt_status launch_w(const ubt_graph* g, const typename V::P& p, cudaStream_t s) {
-  const Tuning& T = tuning();
-  TravArgs a = make_trav_args(g, 0, true);
-  const int threads = (int)std::min<int64_t>(UBT_LB_THREADS, std::max<int64_t>(64, T.hub_threads / 32 * 32));
-  const size_t smem = traverse_smem(a, threads, V::kSmem);
-  UBT_CUDA(cudaFuncSetAttribute(k_traverse_w<V>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
-  int per_sm = 0;
-  UBT_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_traverse_w<V>, threads, smem));
-  if (per_sm < 1) return UBT_ERR_INVALID_ARG;
-  per_sm = (int)std::min<int64_t>(per_sm, std::max<int64_t>(1, T.blocks_per_sm));
-  UBT_CUDA(cudaMemsetAsync(g->scratch, 0, kScratchHeader / 2, s));
-  k_traverse_w<V><<<g->sm_count * per_sm, threads, smem, s>>>(a, p);
-  UBT_CUDA(cudaGetLastError());
-  return UBT_OK;
+  return launch_traversal<V>(g, make_trav_args(g, 0, true), p, s);
 }
 
 size_t worlds_table_words(const ubt_graph* g, int64_t W) {

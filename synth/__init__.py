@@ -24,6 +24,10 @@ arrays is the edge id ``eid`` used everywhere else.
 """
 from __future__ import annotations
 
+import concurrent.futures as cf
+import os
+import threading
+
 import numpy as np
 
 __all__ = [
@@ -37,6 +41,47 @@ K_ONE = 65536  # fixed-point denominator: p = k / 65536, k in [0, 65536]
 
 def rng(seed: int) -> np.random.Generator:
     return np.random.Generator(np.random.PCG64(seed))
+
+
+def _workers() -> int:
+    return max(1, min(16, os.cpu_count() or 1))
+
+
+def _map(fn, items):
+    """Thread-pool map (numpy releases the GIL in the heavy loops); the result
+    does not depend on the number of workers."""
+    items = list(items)
+    if len(items) <= 1 or _workers() == 1:
+        return [fn(x) for x in items]
+    with cf.ThreadPoolExecutor(_workers()) as ex:
+        return list(ex.map(fn, items))
+
+
+def _chunk_rng(seed: int, chunk: int) -> np.random.Generator:
+    return np.random.Generator(np.random.PCG64(np.random.SeedSequence([seed, chunk])))
+
+
+def _merge_unique(parts) -> np.ndarray:
+    """Sorted distinct values of the union of sorted int64 arrays, computed in
+    key ranges in parallel."""
+    parts = [p for p in parts if p.size]
+    if not parts:
+        return np.zeros(0, dtype=np.int64)
+    total = sum(p.size for p in parts)
+    nr = max(1, min(4 * _workers(), total // (1 << 20)))
+    sample = np.sort(np.concatenate([p[:: max(1, p.size // 256)] for p in parts]))
+    splits = [None] + [int(sample[(i * sample.size) // nr]) for i in range(1, nr)] + [None]
+
+    def one(i):
+        lo, hi = splits[i], splits[i + 1]
+        seg = []
+        for p in parts:
+            a = 0 if lo is None else np.searchsorted(p, lo, side="left")
+            b = p.size if hi is None else np.searchsorted(p, hi, side="left")
+            seg.append(p[a:b])
+        return _sorted_unique(np.concatenate(seg))
+
+    return np.concatenate(_map(one, range(nr)))
 
 
 def _sorted_unique(keys: np.ndarray) -> np.ndarray:
@@ -105,7 +150,6 @@ def chung_lu(n: int, gamma: float, mean_deg: float, max_deg: float, seed: int):
     repeated pairs are dropped, so the realised edge count is a little below
     the nominal one and is whatever the returned arrays hold.
     """
-    g = rng(seed)
     base = (np.arange(n, dtype=np.float64) + 1.0) ** (-1.0 / (gamma - 1.0))
     lo, hi = 0.0, mean_deg * n / base.sum() * 1e4
     for _ in range(200):
@@ -118,41 +162,47 @@ def chung_lu(n: int, gamma: float, mean_deg: float, max_deg: float, seed: int):
     cdf = np.cumsum(w)
     cdf /= cdf[-1]
     draws = int(round(n * mean_deg / 2.0))
-    a = np.searchsorted(cdf, g.random(draws), side="right")
-    b = np.searchsorted(cdf, g.random(draws), side="right")
-    a = np.minimum(a, n - 1)
-    b = np.minimum(b, n - 1)
-    return _dedup_pairs(a, b, n)
+    chunk = 1 << 21
+
+    def one(c):
+        cnt = min(chunk, draws - c * chunk)
+        r = _chunk_rng(seed, c)
+        a = np.minimum(np.searchsorted(cdf, r.random(cnt), side="right"), n - 1).astype(np.int64)
+        b = np.minimum(np.searchsorted(cdf, r.random(cnt), side="right"), n - 1).astype(np.int64)
+        keep = a != b
+        a, b = a[keep], b[keep]
+        return _sorted_unique(np.minimum(a, b) * n + np.maximum(a, b))
+
+    key = _merge_unique(_map(one, range((draws + chunk - 1) // chunk)))
+    return (key // n).astype(np.uint32), (key % n).astype(np.uint32)
 
 
 def rmat(scale: int, edge_factor: int, a: float, b: float, c: float, seed: int,
-         chunk: int = 1 << 24):
+         chunk: int = 1 << 21):
     """R-MAT edge draws on 2^scale vertices, symmetrised and deduplicated.
 
     Each of the 2^scale * edge_factor draws picks one quadrant per level
-    with probabilities (a, b, c, 1-a-b-c).  Vertex labels are not permuted.
+    with probabilities (a, b, c, 1-a-b-c).  Draws come in chunks of 2^21, each
+    from its own seed (seed, chunk).  Vertex labels are not permuted.
     """
-    g = rng(seed)
     n = 1 << scale
     total = n * edge_factor
-    keys = []
     ab, abc = a + b, a + b + c
-    for start in range(0, total, chunk):
-        cnt = min(chunk, total - start)
+
+    def one(ci):
+        cnt = min(chunk, total - ci * chunk)
+        g = _chunk_rng(seed, ci)
         u = np.zeros(cnt, dtype=np.int64)
         v = np.zeros(cnt, dtype=np.int64)
         for _ in range(scale):
             r = g.random(cnt, dtype=np.float32)
-            ubit = r >= ab                      # quadrants c, d
-            vbit = ((r >= a) & (r < ab)) | (r >= abc)  # quadrants b, d
-            u = (u << 1) | ubit
-            v = (v << 1) | vbit
+            u = (u << 1) | (r >= ab)                       # quadrants c, d
+            v = (v << 1) | (((r >= a) & (r < ab)) | (r >= abc))  # quadrants b, d
         keep = u != v
         u, v = u[keep], v[keep]
-        lo = np.minimum(u, v)
-        hi = np.maximum(u, v)
-        keys.append(_sorted_unique(lo * n + hi))
-    key = _sorted_unique(np.concatenate(keys))
+        return _sorted_unique(np.minimum(u, v) * n + np.maximum(u, v))
+
+    key = _merge_unique(_map(one, range((total + chunk - 1) // chunk)))
     return (key // n).astype(np.uint32), (key % n).astype(np.uint32)
 
 
@@ -208,11 +258,12 @@ def csr_undirected(n: int, src, dst):
 def ego_nets(n: int, src, dst, count: int, smin: int, smax: int, seed: int):
     """Seeded batch of induced ego-net subgraphs of a parent graph.
 
-    For each ego-net: the size s is log-uniform in [smin, smax]; the centre is
-    a uniformly chosen vertex with degree >= s - 1 (if none exists, the
-    highest-degree vertex and s = deg + 1); the vertex set is the centre plus
-    s - 1 of its neighbours chosen by a seeded shuffle; the subgraph is the
-    one the parent induces on that set.
+    For ego-net i (drawn from its own seed (seed, i)): the size s is
+    log-uniform in [smin, smax]; the centre is a uniformly chosen vertex with
+    degree >= s - 1 (if none exists, the highest-degree vertex and
+    s = deg + 1); the vertex set is the centre plus s - 1 of its neighbours
+    chosen by a seeded shuffle; the subgraph is the one the parent induces on
+    that set.
 
     Returns a dict of concatenated arrays:
       v_off (count+1, int64): vertex offsets; graph i owns local ids
@@ -222,16 +273,14 @@ def ego_nets(n: int, src, dst, count: int, smin: int, smax: int, seed: int):
       eid (uint32): the parent edge id of each subgraph edge.
       vid (uint32): parent vertex id of each global vertex.
     """
-    g = rng(seed)
     off, nbr, eidx = csr_undirected(n, src, dst)
     deg = np.diff(off)
     order_by_deg = np.argsort(deg, kind="stable")
     sorted_deg = deg[order_by_deg]
-    mark = np.full(n, -1, dtype=np.int64)
-    v_off = [0]
-    e_off = [0]
-    out_src, out_dst, out_eid, out_vid = [], [], [], []
-    for _ in range(count):
+    local = threading.local()
+
+    def one(i):
+        g = _chunk_rng(seed, i)
         s = int(round(np.exp(g.uniform(np.log(smin), np.log(smax)))))
         first = np.searchsorted(sorted_deg, s - 1, side="left")
         if first >= n:
@@ -242,33 +291,33 @@ def ego_nets(n: int, src, dst, count: int, smin: int, smax: int, seed: int):
         nb = nbr[off[centre]:off[centre + 1]].astype(np.int64)
         pick = g.permutation(nb.size)[: s - 1]
         verts = np.unique(np.concatenate([[centre], nb[pick]]))
-        mark[verts] = np.arange(verts.size)
-        # induced edges: scan every member's adjacency, keep member neighbours with larger id
-        starts = off[verts]
-        lens = deg[verts]
+        # induced edges: every member's neighbours that are members with a larger id
+        mark = getattr(local, "mark", None)
+        if mark is None:
+            mark = local.mark = np.full(n, -1, dtype=np.int32)
+        mark[verts] = np.arange(verts.size, dtype=np.int32)
+        starts, lens = off[verts], deg[verts]
         tot = int(lens.sum())
-        rep = np.repeat(np.arange(verts.size), lens)
-        idx = np.arange(tot) - np.repeat(np.cumsum(lens) - lens, lens) + np.repeat(starts, lens)
-        w = nbr[idx].astype(np.int64)
-        u = verts[rep]
-        keep = (mark[w] >= 0) & (w > u)
-        lu = mark[u[keep]]
-        lw = mark[w[keep]]
-        base = v_off[-1]
-        out_src.append((lu + base).astype(np.uint32))
-        out_dst.append((lw + base).astype(np.uint32))
-        out_eid.append(eidx[idx[keep]].astype(np.uint32))
-        out_vid.append(verts.astype(np.uint32))
+        rep = np.repeat(np.arange(verts.size, dtype=np.int32), lens)
+        idx = np.arange(tot, dtype=np.int64) + np.repeat(starts - (np.cumsum(lens) - lens), lens)
+        lw = mark[nbr[idx]]
+        keep = lw > rep
         mark[verts] = -1
-        v_off.append(base + verts.size)
-        e_off.append(e_off[-1] + int(keep.sum()))
+        return verts, rep[keep].astype(np.int64), lw[keep].astype(np.int64), eidx[idx[keep]]
+
+    parts = _map(one, range(count))
+    v_off = np.zeros(count + 1, dtype=np.int64)
+    e_off = np.zeros(count + 1, dtype=np.int64)
+    v_off[1:] = np.cumsum([p[0].size for p in parts])
+    e_off[1:] = np.cumsum([p[1].size for p in parts])
+    cat = lambda xs, dt: np.concatenate(xs).astype(dt) if xs else np.zeros(0, dt)
     return {
-        "v_off": np.asarray(v_off, dtype=np.int64),
-        "e_off": np.asarray(e_off, dtype=np.int64),
-        "src": np.concatenate(out_src) if out_src else np.zeros(0, np.uint32),
-        "dst": np.concatenate(out_dst) if out_dst else np.zeros(0, np.uint32),
-        "eid": np.concatenate(out_eid) if out_eid else np.zeros(0, np.uint32),
-        "vid": np.concatenate(out_vid) if out_vid else np.zeros(0, np.uint32),
+        "v_off": v_off,
+        "e_off": e_off,
+        "src": cat([p[1] + v_off[i] for i, p in enumerate(parts)], np.uint32),
+        "dst": cat([p[2] + v_off[i] for i, p in enumerate(parts)], np.uint32),
+        "eid": cat([p[3] for p in parts], np.uint32),
+        "vid": cat([p[0] for p in parts], np.uint32),
     }
 
 

@@ -496,6 +496,60 @@ def extra_worlds(ubt, args, flush):
     return res
 
 
+EGO_TAUS = [0.6, 0.75, 0.9]
+
+
+def extra_ego(ubt, args, flush):
+    """10,000 ego nets (50..5,000 vertices, log-uniform) of R-MAT scale 20,
+    answered per graph -- counts at 3 thresholds, exact expected counts and
+    the 64 worlds of world word 0 -- by one replay of a captured CUDA graph."""
+    import torch
+    import synth
+    g = make_graph("rmat20")
+    t0 = time.perf_counter()
+    sel = synth.ego_select(g.n, g.src, g.dst, 10000, 50, 5000, 1)
+    eg = synth.ego_induce_torch(g.n, g.src, g.dst, sel, device="cuda")
+    torch.cuda.synchronize()
+    gen_s = time.perf_counter() - t0
+    kp = torch.from_numpy(g.k.view(np.int32)).cuda()
+    kb = kp[eg["eid"].long()]
+    t0 = time.perf_counter()
+    G = ubt.Graph(int(eg["v_off"][-1].item()), eg["src"], eg["dst"], k=kb, edge_key=eg["eid"],
+                  vertex_offsets=eg["v_off"])
+    torch.cuda.synchronize()
+    build_s = time.perf_counter() - t0
+    ng = G.n_graphs
+    m_total = G.m
+    del kb, kp
+    eg = {k: v for k, v in eg.items() if k in ("v_off",)}
+    _release()
+    counts = torch.empty(ng * 2 * len(EGO_TAUS), dtype=torch.int64, device="cuda")
+    expect = torch.empty(ng * 2, dtype=torch.float64, device="cuda")
+    worlds = torch.empty(ng * 64, dtype=torch.int64, device="cuda")
+    side = torch.cuda.Stream()
+    side.wait_stream(torch.cuda.current_stream())
+    with torch.cuda.stream(side):
+        G.batch_query_(EGO_TAUS, 11, counts, expect, worlds, stream=side)  # warm-up outside capture
+    torch.cuda.current_stream().wait_stream(side)
+    direct_ms = _events_ms(lambda: G.batch_query_(EGO_TAUS, 11, counts, expect, worlds), max(3, args.steps // 4), 1)
+    ref = (counts.clone(), expect.clone(), worlds.clone())
+    graph = torch.cuda.CUDAGraph()
+    with torch.cuda.graph(graph, stream=side, capture_error_mode="thread_local"):
+        G.batch_query_(EGO_TAUS, 11, counts, expect, worlds, stream=side)
+    counts.zero_(), expect.zero_(), worlds.zero_()
+    replay_ms = _events_ms(graph.replay, max(3, args.steps // 4), 1)
+    same = bool(torch.equal(counts, ref[0]) and torch.equal(expect, ref[1]) and torch.equal(worlds, ref[2]))
+    tri = float((expect.view(ng, 2).sum(1)).sum().item())
+    res = {"workload": "10,000 ego nets of R-MAT scale 20 (50..5,000 vertices, log-uniform), parent edge keys",
+           "graphs": ng, "vertices": G.n, "edges": m_total, "triangles": int(round(tri)),
+           "generate_s": gen_s, "build_s": build_s, "direct_ms": direct_ms, "graph_replay_ms": replay_ms,
+           "replay_equals_direct": same, "triangles_per_s": tri / (replay_ms / 1e3),
+           "outputs": "per graph: counts at %s, E_bal/E_unbal, 64 world counts" % EGO_TAUS}
+    del G, graph, counts, expect, worlds
+    _release()
+    return res
+
+
 def extra_grad(ubt, args, flush):
     """Chung-Lu n = 4e6, gamma 2.3, p ~ U[0,1] float32: expected counts
     forward and the hand-written adjoint backward through autograd."""
@@ -528,7 +582,8 @@ def extra_grad(ubt, args, flush):
 def extras(ubt, G, g, T, args, flush):
     """The other workloads of the path, each on its own graph."""
     out = {}
-    for name, fn in (("c3_rmat22", extra_rmat22), ("c4_rmat20_worlds", extra_worlds), ("c5_cl4m_grad", extra_grad)):
+    for name, fn in (("c3_rmat22", extra_rmat22), ("c4_rmat20_worlds", extra_worlds), ("c4_ego10k", extra_ego),
+                     ("c5_cl4m_grad", extra_grad)):
         try:
             out[name] = fn(ubt, args, flush)
         except Exception as e:  # report, do not hide: the line says what failed

@@ -367,7 +367,9 @@ struct Expect {
 };
 
 __device__ double i128_to_double(unsigned long long lo, unsigned long long hi) {
-  // value = hi * 2^64 + lo with hi signed
+  // value = hi * 2^64 + lo with hi signed; values that fit in int64 convert
+  // with one rounding (the two-part sum would cancel for small negatives)
+  if ((hi == 0ull && !(lo >> 63)) || (hi == ~0ull && (lo >> 63))) return (double)(long long)lo;
   return (double)(long long)hi * 18446744073709551616.0 + (double)lo;
 }
 

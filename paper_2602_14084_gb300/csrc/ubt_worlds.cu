@@ -362,7 +362,9 @@ struct Batch {
 __global__ void k_batch_finish(int64_t ng, int nt, const unsigned long long* __restrict__ acc, double* expect) {
   for (int64_t gi = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; gi < ng; gi += (int64_t)gridDim.x * blockDim.x) {
     const unsigned long long T = acc[3 * gi], lo = acc[3 * gi + 1], hi = acc[3 * gi + 2];
-    const double sum = ((double)(long long)hi * 18446744073709551616.0 + (double)lo) * 0x1p-45;
+    const bool small = (hi == 0ull && !(lo >> 63)) || (hi == ~0ull && (lo >> 63));
+    const double sum = (small ? (double)(long long)lo : (double)(long long)hi * 18446744073709551616.0 + (double)lo) *
+                       0x1p-45;
     expect[2 * gi] = ((double)T - sum) * 0.5;
     expect[2 * gi + 1] = ((double)T + sum) * 0.5;
   }

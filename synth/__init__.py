@@ -15,7 +15,9 @@ Sec. 7.1, Table 2) are not available, so these generators stand in for them:
 * ``quantise``     -- real p in [0,1] -> k = round-half-even(p * 65536).
 * ``p_beta`` / ``p_beta_mixture`` / ``p_uniform_f32`` -- the P+ distributions
   the paper uses (uniform, Beta(0.5,0.5), sign-biased Betas; Sec. 7.1).
-* ``ego_nets``     -- batches of induced ego-net subgraphs of a parent graph.
+* ``ego_select`` / ``ego_induce`` / ``ego_induce_torch`` / ``ego_nets`` --
+  batches of induced ego-net subgraphs of a parent graph (member sets on the
+  CPU; induced edges on the CPU or, for large batches, with torch on a GPU).
 * ``bfs_induced``  -- induced subgraph grown in BFS order to a target size.
 
 Every graph is returned as ``(src, dst)`` uint32 arrays of an undirected
@@ -255,29 +257,22 @@ def csr_undirected(n: int, src, dst):
     return off, b.astype(np.uint32), e
 
 
-def ego_nets(n: int, src, dst, count: int, smin: int, smax: int, seed: int):
-    """Seeded batch of induced ego-net subgraphs of a parent graph.
+def ego_select(n: int, src, dst, count: int, smin: int, smax: int, seed: int):
+    """Seeded member sets of a batch of ego nets.
 
-    For ego-net i (drawn from its own seed (seed, i)): the size s is
+    For ego net i (drawn from its own seed (seed, i)): the size s is
     log-uniform in [smin, smax]; the centre is a uniformly chosen vertex with
     degree >= s - 1 (if none exists, the highest-degree vertex and
-    s = deg + 1); the vertex set is the centre plus s - 1 of its neighbours
-    chosen by a seeded shuffle; the subgraph is the one the parent induces on
-    that set.
+    s = deg + 1); the members are the centre plus s - 1 of its neighbours
+    chosen uniformly without replacement.
 
-    Returns a dict of concatenated arrays:
-      v_off (count+1, int64): vertex offsets; graph i owns local ids
-          [0, n_i) stored globally at [v_off[i], v_off[i+1]).
-      e_off (count+1, int64): edge offsets into src/dst/eid.
-      src, dst (uint32): GLOBAL vertex ids (local id + v_off of its graph).
-      eid (uint32): the parent edge id of each subgraph edge.
-      vid (uint32): parent vertex id of each global vertex.
+    Returns {"v_off": int64 [count + 1], "vid": uint32 [members]} with every
+    ego net's members sorted by parent id.
     """
-    off, nbr, eidx = csr_undirected(n, src, dst)
+    off, nbr, _ = csr_undirected(n, src, dst)
     deg = np.diff(off)
     order_by_deg = np.argsort(deg, kind="stable")
     sorted_deg = deg[order_by_deg]
-    local = threading.local()
 
     def one(i):
         g = _chunk_rng(seed, i)
@@ -289,9 +284,36 @@ def ego_nets(n: int, src, dst, count: int, smin: int, smax: int, seed: int):
         else:
             centre = int(order_by_deg[g.integers(first, n)])
         nb = nbr[off[centre]:off[centre + 1]].astype(np.int64)
-        pick = g.permutation(nb.size)[: s - 1]
-        verts = np.unique(np.concatenate([[centre], nb[pick]]))
-        # induced edges: every member's neighbours that are members with a larger id
+        pick = g.choice(nb.size, size=min(s - 1, nb.size), replace=False)
+        return np.unique(np.concatenate([[centre], nb[pick]]))
+
+    sets = _map(one, range(count))
+    v_off = np.zeros(count + 1, dtype=np.int64)
+    v_off[1:] = np.cumsum([x.size for x in sets])
+    vid = np.concatenate(sets).astype(np.uint32) if sets else np.zeros(0, np.uint32)
+    return {"v_off": v_off, "vid": vid}
+
+
+def ego_induce(n: int, src, dst, sel, which=None):
+    """Subgraphs the parent induces on the member sets of `sel` (all of them,
+    or the ego nets listed in `which`), as one batch.
+
+    Returns a dict of concatenated arrays:
+      v_off (count+1, int64): vertex offsets; graph i owns global ids
+          [v_off[i], v_off[i+1]), in the order of its sorted member list.
+      e_off (count+1, int64): edge offsets into src/dst/eid.
+      src, dst (uint32): GLOBAL vertex ids, src < dst; edges of a graph come
+          in member order, then in the parent's adjacency order.
+      eid (uint32): the parent edge id of each subgraph edge.
+      vid (uint32): parent vertex id of each global vertex.
+    """
+    off, nbr, eidx = csr_undirected(n, src, dst)
+    deg = np.diff(off)
+    idxs = range(sel["v_off"].size - 1) if which is None else list(which)
+    local = threading.local()
+
+    def one(i):
+        verts = sel["vid"][sel["v_off"][i]:sel["v_off"][i + 1]].astype(np.int64)
         mark = getattr(local, "mark", None)
         if mark is None:
             mark = local.mark = np.full(n, -1, dtype=np.int32)
@@ -305,7 +327,8 @@ def ego_nets(n: int, src, dst, count: int, smin: int, smax: int, seed: int):
         mark[verts] = -1
         return verts, rep[keep].astype(np.int64), lw[keep].astype(np.int64), eidx[idx[keep]]
 
-    parts = _map(one, range(count))
+    parts = _map(one, idxs)
+    count = len(parts)
     v_off = np.zeros(count + 1, dtype=np.int64)
     e_off = np.zeros(count + 1, dtype=np.int64)
     v_off[1:] = np.cumsum([p[0].size for p in parts])
@@ -319,6 +342,78 @@ def ego_nets(n: int, src, dst, count: int, smin: int, smax: int, seed: int):
         "eid": cat([p[3] for p in parts], np.uint32),
         "vid": cat([p[0] for p in parts], np.uint32),
     }
+
+
+def ego_induce_torch(n: int, src, dst, sel, device="cuda", chunk=1 << 27):
+    """ego_induce for all ego nets of `sel`, computed with torch on `device`;
+    the same arrays as ego_induce, as torch tensors (int64 offsets, int32
+    vertex / edge ids holding the uint32 values).
+
+    Membership is a bitmap per ego net (count x n bits); the members'
+    adjacency lists are expanded in chunks of about `chunk` entries.
+    """
+    import torch
+    dev = torch.device(device)
+    s = torch.from_numpy(np.asarray(src, dtype=np.int64)).to(dev)
+    d = torch.from_numpy(np.asarray(dst, dtype=np.int64)).to(dev)
+    m = s.numel()
+    a = torch.cat([s, d])
+    b = torch.cat([d, s])
+    e = torch.cat([torch.arange(m, device=dev), torch.arange(m, device=dev)])
+    order = torch.argsort(a * n + b)
+    a, b, e = a[order], b[order], e[order]
+    deg = torch.bincount(a, minlength=n)
+    off = torch.zeros(n + 1, dtype=torch.int64, device=dev)
+    off[1:] = torch.cumsum(deg, 0)
+    del a, order
+    v_off = torch.from_numpy(np.asarray(sel["v_off"], dtype=np.int64)).to(dev)
+    vid = torch.from_numpy(np.asarray(sel["vid"], dtype=np.int64)).to(dev)
+    G = v_off.numel() - 1
+    N = vid.numel()
+    gid = torch.repeat_interleave(torch.arange(G, device=dev), v_off[1:] - v_off[:-1])
+    words = (n + 63) // 64
+    bitmap = torch.zeros(G * words, dtype=torch.int64, device=dev)
+    one = torch.ones(1, dtype=torch.int64, device=dev)
+    bitmap.scatter_reduce_(0, gid * words + (vid >> 6), torch.bitwise_left_shift(one, vid & 63), reduce="sum")
+    key = gid * n + vid  # sorted: members sorted within each ego net, nets in order
+    lens = deg[vid]
+    ends = torch.cumsum(lens, 0)
+    out_src, out_dst, out_eid = [], [], []
+    lo = 0
+    total = int(ends[-1].item()) if N else 0
+    while lo < N:
+        start_e = int(ends[lo - 1].item()) if lo else 0
+        hi = int(torch.searchsorted(ends, torch.tensor([start_e + chunk], device=dev)).item())
+        hi = max(hi, lo + 1)
+        hi = min(hi, N)
+        ln = lens[lo:hi]
+        rep = torch.repeat_interleave(torch.arange(lo, hi, device=dev), ln)
+        excl = torch.cumsum(ln, 0) - ln
+        pos = torch.arange(rep.numel(), device=dev) - torch.repeat_interleave(excl, ln) + off[vid[rep]]
+        w = b[pos]
+        g = gid[rep]
+        bit = torch.bitwise_right_shift(bitmap[g * words + (w >> 6)], w & 63) & 1
+        keep = (bit == 1) & (w > vid[rep])
+        rk, wk, gk = rep[keep], w[keep], g[keep]
+        out_src.append(rk)
+        out_dst.append(torch.searchsorted(key, gk * n + wk))
+        out_eid.append(e[pos[keep]])
+        lo = hi
+        del rep, excl, pos, w, g, bit, keep
+    src_g = torch.cat(out_src) if out_src else torch.zeros(0, dtype=torch.int64, device=dev)
+    dst_g = torch.cat(out_dst) if out_dst else torch.zeros(0, dtype=torch.int64, device=dev)
+    eid_g = torch.cat(out_eid) if out_eid else torch.zeros(0, dtype=torch.int64, device=dev)
+    e_cnt = torch.bincount(gid[src_g], minlength=G) if src_g.numel() else torch.zeros(G, dtype=torch.int64, device=dev)
+    e_off = torch.zeros(G + 1, dtype=torch.int64, device=dev)
+    e_off[1:] = torch.cumsum(e_cnt, 0)
+    del bitmap
+    return {"v_off": v_off, "e_off": e_off, "src": src_g.to(torch.int32), "dst": dst_g.to(torch.int32),
+            "eid": eid_g.to(torch.int32), "vid": vid.to(torch.int32), "total_adjacency": total}
+
+
+def ego_nets(n: int, src, dst, count: int, smin: int, smax: int, seed: int):
+    """ego_select followed by ego_induce (all ego nets, on the CPU)."""
+    return ego_induce(n, src, dst, ego_select(n, src, dst, count, smin, smax, seed))
 
 
 def bfs_induced(n: int, src, dst, start: int, min_edges: int):

@@ -182,6 +182,56 @@ def test_batch_of_ego_nets(ubt):
         assert np.array_equal(worlds[gi], ow), gi
 
 
+def test_batch_from_torch_extraction_and_cuda_graph_capture(ubt):
+    """The batch built from the GPU ego-net extraction equals the CPU one, and
+    a batch query captured in a CUDA graph and replayed gives the same answers
+    as a direct call (and as the oracle on sampled ego nets)."""
+    import torch
+    n = 1 << 14
+    ps, pd = synth.rmat(14, 16, 0.57, 0.19, 0.19, 21)
+    pk = synth.k_uniform(ps.size, 22)
+    sel = synth.ego_select(n, ps, pd, 120, 20, 1500, 23)
+    cpu = synth.ego_induce(n, ps, pd, sel)
+    gpu = synth.ego_induce_torch(n, ps, pd, sel, device="cuda", chunk=1 << 18)
+    for key in ("v_off", "e_off", "src", "dst", "eid", "vid"):
+        assert np.array_equal(gpu[key].cpu().numpy().astype(np.int64), cpu[key].astype(np.int64)), key
+    k = torch.from_numpy(pk.view(np.int32)).cuda()[gpu["eid"].long()]
+    G = ubt.Graph(int(cpu["v_off"][-1]), gpu["src"], gpu["dst"], k=k, edge_key=gpu["eid"], vertex_offsets=gpu["v_off"])
+    taus = [0.6, 0.75, 0.9]
+    ng = G.n_graphs
+    c = torch.empty(ng * 6, dtype=torch.int64, device="cuda")
+    e = torch.empty(ng * 2, dtype=torch.float64, device="cuda")
+    w = torch.empty(ng * 64, dtype=torch.int64, device="cuda")
+    side = torch.cuda.Stream()
+    side.wait_stream(torch.cuda.current_stream())
+    with torch.cuda.stream(side):
+        G.batch_query_(taus, 3, c, e, w, stream=side)
+    torch.cuda.synchronize()
+    ref = (c.clone(), e.clone(), w.clone())
+    graph = torch.cuda.CUDAGraph()
+    with torch.cuda.graph(graph, stream=side, capture_error_mode="thread_local"):
+        G.batch_query_(taus, 3, c, e, w, stream=side)
+    for x in (c, e, w):
+        x.zero_()
+    graph.replay()
+    graph.replay()
+    torch.cuda.synchronize()
+    assert torch.equal(c, ref[0]) and torch.equal(e, ref[1]) and torch.equal(w, ref[2])
+    cn, en, wn = c.cpu().numpy().reshape(ng, 2, 3), e.cpu().numpy().reshape(ng, 2), w.cpu().numpy().reshape(ng, 64)
+    kk = pk[cpu["eid"]]
+    for gi in [0, 1, 17, 60, ng - 1]:
+        v0, v1 = int(cpu["v_off"][gi]), int(cpu["v_off"][gi + 1])
+        e0, e1 = int(cpu["e_off"][gi]), int(cpu["e_off"][gi + 1])
+        ls, ld, lk = cpu["src"][e0:e1] - v0, cpu["dst"][e0:e1] - v0, kk[e0:e1]
+        ob, ou = oracle.count_threshold(v1 - v0, ls, ld, lk, taus)
+        assert np.array_equal(cn[gi, 0], ob) and np.array_equal(cn[gi, 1], ou), gi
+        T, S = oracle.expected_fixed(v1 - v0, ls, ld, lk)
+        assert abs(en[gi, 0] - S / float(1 << 48)) <= 1e-12 * max(1.0, T)
+        ow = oracle.world_counts(v1 - v0, ls, ld, lk, 3, [0], ekey=cpu["eid"][e0:e1])
+        assert np.array_equal(wn[gi], ow), gi
+    assert G.guard() == 0
+
+
 def test_giant_lists_use_global_tables(ubt):
     """Lists longer than the shared-memory table go through the global-table path."""
     old = ubt.get_tuning("smem_table_max")

@@ -113,6 +113,31 @@ def csrc_digest():
     return h.hexdigest()[:16]
 
 
+def tuned(ubt, query, variant, make, run, args, budget_s=None):
+    """Knob setting of one benchmark query: from the package's shipped tunings
+    when this GPU and graph shape are in it, else by a bounded autotuner
+    search (written to the package's tunings with --tune).  Applies it and
+    returns the autotuner's record (without the trial list)."""
+    from paper_2602_14084_gb300 import autotune as at
+    G0 = make()
+    info, ng = G0.info(), getattr(G0, "n_graphs", 1)
+    G0.close()
+    del G0
+    if args.no_tune:
+        return {"source": "defaults", "config": at.current(at.QUERY_KNOBS[query])}
+    path = at.shipped_cache_path() if args.tune else at.default_cache_path()
+    rec = at.tune(make, run, query, info, variant=variant, n_graphs=ng, cache_path=path,
+                  use_cache=not args.tune, budget_s=budget_s or args.tune_budget,
+                  reps=3 if query in ("worlds", "batch") else 5, warmup=1 if query in ("worlds", "batch") else 2,
+                  log=lambda msg: print(msg, file=sys.stderr, flush=True))
+    if args.tune:
+        at.save_cache(path, {rec["key"]: {k: rec[k] for k in ("config", "ms", "start_ms", "trials", "rounds",
+                                                                "stopped")}})
+    return rec
+
+
+
+
 def ncu_traffic(kernel, workload):
     """DRAM bytes per launch (read + write) from the committed ncu summary of
     this kernel and workload, or None when the kernels changed since."""
@@ -211,6 +236,12 @@ def main():
                          "--warmup + --steps times, print its mean time and exit")
     ap.add_argument("--workload", default=WORKLOAD, choices=["cl1m", "rmat22", "rmat20", "cl4m", "er2k"])
     ap.add_argument("--digest", action="store_true", help="print the CUDA-source digest and exit")
+    ap.add_argument("--tune", action="store_true",
+                    help="search the knobs of every benchmark query (no cache) and store the results in the "
+                         "package's shipped tunings, then run the benchmark with them")
+    ap.add_argument("--no-tune", dest="no_tune", action="store_true", help="run with the library's default knobs")
+    ap.add_argument("--tune-budget", type=float, default=60.0, help="seconds of autotuner search per query "
+                    "when the shipped tunings do not cover this GPU and graph")
     args = ap.parse_args()
     args.warmup = max(args.warmup, 3)
     if args.digest:
@@ -235,15 +266,20 @@ def main():
 
     if args.only:
         return profile_driver(ubt, args)
+    from paper_2602_14084_gb300 import autotune as at
+    args.lib_defaults = at.current()
     g = make_graph(WORKLOAD)
+    src_d = torch.from_numpy(g.src.view(np.int32)).cuda()
+    dst_d = torch.from_numpy(g.dst.view(np.int32)).cuda()
+    k_d = torch.from_numpy(g.k.view(np.int32)).cuda()
+    counts = torch.empty(2 * len(TAUS), dtype=torch.int64, device="cuda")
+    tuning = tuned(ubt, "count", at.count_variant(len(TAUS), True), lambda: ubt.Graph(g.n, src_d, dst_d, k=k_d),
+                   lambda G_: G_.count_threshold_(TAUS, counts, prune=True), args)
     t0 = time.perf_counter()
     G = ubt.Graph(g.n, g.src, g.dst, k=g.k)
     torch.cuda.synchronize()
     build_s = time.perf_counter() - t0
     # rebuild timed with events (first build includes library/context warm-up)
-    src_d = torch.from_numpy(g.src.view(np.int32)).cuda()
-    dst_d = torch.from_numpy(g.dst.view(np.int32)).cuda()
-    k_d = torch.from_numpy(g.k.view(np.int32)).cuda()
     a = torch.cuda.Event(enable_timing=True)
     b = torch.cuda.Event(enable_timing=True)
     a.record()
@@ -255,7 +291,6 @@ def main():
 
     info = G.info()
     _, _, T, _ = G.expected_counts(with_exact=True)
-    counts = torch.empty(2 * len(TAUS), dtype=torch.int64, device="cuda")
     cb, cu = G.count_threshold(TAUS, prune=True)
     ub_, uu_ = G.count_threshold(TAUS, prune=False)
     assert np.array_equal(cb, ub_) and np.array_equal(cu, uu_), "pruned and unpruned counts differ"
@@ -344,6 +379,7 @@ def main():
         "gpu_launches": 2 * args.steps,
         "clocks": clk,
         "build_ms": build_ms,
+        "tuning": {k: tuning[k] for k in ("source", "config", "key") if k in tuning},
         "unpruned": {"ms_per_step": 1e3 * float(np.mean(times_unpruned)),
                      "value": T / float(np.mean(times_unpruned)), "streamed_entries": st0["streamed"],
                      "alg_bytes": 16 * st0["table_entries"] + 8 * st0["streamed"]},
@@ -351,7 +387,7 @@ def main():
     }
 
     if args.extras and rank == 0:
-        del G, ews, hs, hd, hk
+        del G, ews, hs, hd, hk, src_d, dst_d, k_d
         _release()
         line["extras"] = extras(ubt, None, g, T, args, flush)
     if args.cpu and rank == 0:
@@ -392,14 +428,29 @@ def profile_driver(ubt, args):
     """One form of the query on one workload graph, for ncu captures."""
     import torch
     import synth
+    from paper_2602_14084_gb300 import autotune as at
     g = make_graph(args.workload)
-    if args.only in ("expected", "backward"):
-        p = g.p if g.p is not None else synth.p_uniform_f32(g.m, 5)
-        G = ubt.Graph(g.n, g.src, g.dst, p=torch.from_numpy(np.ascontiguousarray(p)).cuda())
-    else:
-        k = g.k if g.k is not None else synth.quantise(g.p)
-        G = ubt.Graph(g.n, g.src, g.dst, k=k)
     taus = SWEEP32 if args.only == "count32" else TAUS
+
+    def build():
+        if args.only in ("expected", "backward"):
+            p = g.p if g.p is not None else synth.p_uniform_f32(g.m, 5)
+            return ubt.Graph(g.n, g.src, g.dst, p=torch.from_numpy(np.ascontiguousarray(p)).cuda())
+        k = g.k if g.k is not None else synth.quantise(g.p)
+        return ubt.Graph(g.n, g.src, g.dst, k=k)
+
+    # the knobs the benchmark would use (cached tunings only: no search here)
+    G = build()
+    q = {"count": "count", "count32": "count", "count-unpruned": "count", "worlds": "worlds"}.get(args.only)
+    rec = None
+    if q and not args.no_tune:
+        var = {"count": at.count_variant(len(TAUS), True), "count32": at.count_variant(32, True),
+               "count-unpruned": at.count_variant(len(TAUS), False), "worlds": "W4096"}[args.only]
+        rec = at.lookup(q, G.info(), var)
+        if rec:
+            at.apply(rec["config"])
+            G.close()
+            G = build()
     counts = torch.empty(2 * len(taus), dtype=torch.int64, device="cuda")
     eo = torch.empty(2, dtype=torch.float64, device="cuda")
     gout = torch.tensor([1.0, 0.0], dtype=torch.float64, device="cuda")
@@ -425,7 +476,7 @@ def profile_driver(ubt, args):
     }[args.only]
     times = time_steps(fn, args.steps, args.warmup)
     print(json.dumps({"only": args.only, "workload": args.workload, "ms": 1e3 * float(np.mean(times)),
-                      "guard": G.guard()}))
+                      "guard": G.guard(), "tuning": rec["config"] if rec else "defaults"}))
     return 0
 
 
@@ -433,13 +484,16 @@ def extra_rmat22(ubt, args, flush):
     """R-MAT scale 22: the 32-threshold sweep in one traversal, and
     enumeration at t = 0.9 into a device buffer."""
     import torch
+    from paper_2602_14084_gb300 import autotune as at
     g = make_graph("rmat22")
+    out = torch.empty(2 * len(SWEEP32), dtype=torch.int64, device="cuda")
+    tuning = tuned(ubt, "count", at.count_variant(len(SWEEP32), True), lambda: ubt.Graph(g.n, g.src, g.dst, k=g.k),
+                   lambda G_: G_.count_threshold_(SWEEP32, out, prune=True), args)
     t0 = time.perf_counter()
     G = ubt.Graph(g.n, g.src, g.dst, k=g.k)
     torch.cuda.synchronize()
     build_s = time.perf_counter() - t0
     _, _, T, _ = G.expected_counts(with_exact=True)
-    out = torch.empty(2 * len(SWEEP32), dtype=torch.int64, device="cuda")
     steps = max(3, args.steps // 4)
     ms = _events_ms(lambda: G.count_threshold_(SWEEP32, out, prune=True), steps, 1, flush)
     b, u = out.cpu().numpy()[:32], out.cpu().numpy()[32:]
@@ -468,7 +522,8 @@ def extra_rmat22(ubt, args, flush):
                        "frac_hbm": alg / (ms / 1e3) / 1e9 / pk["hbm_gbs"], "peak_kind": pk_kind,
                        "bal_at_0.51": int(b[0]), "bal_at_0.99": int(b[-1])},
            "enumerate_0.9": {"ms": ems, "records": cap, "record_bytes": 24 * cap,
-                             "triangles_per_s": T / (ems / 1e3)}}
+                             "triangles_per_s": T / (ems / 1e3)},
+           "tuning": {k: tuning[k] for k in ("source", "config") if k in tuning}}
     del G, rec
     _release()
     return res
@@ -478,19 +533,32 @@ def extra_worlds(ubt, args, flush):
     """R-MAT scale 20 with k ~ U{0..65536}: W = 4096 bit-sliced sign worlds."""
     import torch
     g = make_graph("rmat20")
-    G = ubt.Graph(g.n, g.src, g.dst, k=g.k)
-    eb, eu, T, _ = G.expected_counts(with_exact=True)
     W = 4096
-    wws = torch.empty(G.sample_worlds_workspace(W), dtype=torch.uint8, device="cuda")
     wout = torch.empty(W, dtype=torch.int64, device="cuda")
     wt = torch.empty(1, dtype=torch.int64, device="cuda")
+    wbuf = {}
+
+    def run(G_):
+        # the workspace depends on the words per pass: sized per call
+        need = G_.sample_worlds_workspace(W)
+        if wbuf.get("n", -1) < need:
+            wbuf["ws"] = torch.empty(need, dtype=torch.uint8, device="cuda")
+            wbuf["n"] = need
+        return G_.sample_worlds_(7, W, wout, wt, wbuf["ws"])
+
+    tuning = tuned(ubt, "worlds", "W%d" % W, lambda: ubt.Graph(g.n, g.src, g.dst, k=g.k), run, args)
+    wbuf.clear()
+    G = ubt.Graph(g.n, g.src, g.dst, k=g.k)
+    eb, eu, T, _ = G.expected_counts(with_exact=True)
+    wws = torch.empty(G.sample_worlds_workspace(W), dtype=torch.uint8, device="cuda")
     ms = _events_ms(lambda: G.sample_worlds_(7, W, wout, wt, wws), max(3, args.steps // 4), 1, flush)
     c = wout.cpu().numpy().astype(np.float64)
     z = (c.mean() - eb) / (c.std(ddof=1) / np.sqrt(W))
     res = {"workload": "R-MAT scale 20, edge factor 16, k ~ U{0..65536}", "n": g.n, "m": g.m, "triangles": T,
            "W": W, "ms": ms, "world_triangles_per_s": T * W / (ms / 1e3),
            "words_per_pass": ubt.get_tuning("world_words_per_pass"),
-           "mc_mean_minus_exact_in_standard_errors": float(z)}
+           "mc_mean_minus_exact_in_standard_errors": float(z),
+           "tuning": {k: tuning[k] for k in ("source", "config") if k in tuning}}
     del G, wws
     _release()
     return res
@@ -581,11 +649,13 @@ def extra_grad(ubt, args, flush):
 
 def extras(ubt, G, g, T, args, flush):
     """The other workloads of the path, each on its own graph."""
+    from paper_2602_14084_gb300 import autotune as at
     out = {}
     for name, fn in (("c3_rmat22", extra_rmat22), ("c4_rmat20_worlds", extra_worlds), ("c4_ego10k", extra_ego),
                      ("c5_cl4m_grad", extra_grad)):
         try:
-            out[name] = fn(ubt, args, flush)
+            with at.tuning_scope(args.lib_defaults):  # each workload starts from the library defaults
+                out[name] = fn(ubt, args, flush)
         except Exception as e:  # report, do not hide: the line says what failed
             out[name] = {"error": repr(e)[:300]}
     return out

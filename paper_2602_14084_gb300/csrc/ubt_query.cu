@@ -168,64 +168,87 @@ __global__ void k_finish_reg(const unsigned long long* __restrict__ acc, int nt,
   }
 }
 
-// Many thresholds (up to 64): products are queued per warp as in CountReg;
-// when 32 are queued, lane i compares its own thresholds i and i + 32 with all
-// 32 products (read as shared-memory broadcasts), so the counting needs no
-// atomics and no divergence.  Counts are per threshold, in ascending order.
+// Many thresholds (up to 64), tested all at once.  The 2 nt levels -- every B
+// and every U, sorted ascending (each B <= 0 <= each U) -- cut the integers
+// into 2 nt + 1 intervals; a product P falls in interval r = #{levels < P}.
+// Products are queued per warp as in CountReg; 32 at a time, each lane finds
+// the interval of one product by binary search and adds 1 to that interval's
+// bin (a block-wide shared histogram).  Then, with B_(k) and U_(k) the k-th
+// smallest levels of each kind,
+//   #{P <= B_(k)} = #{r <= k}           (P <= B_(k) iff fewer than k+1 B's are < P)
+//   #{P >  U_(k)} = #{r > nt + k}       (P >  U_(k) iff at least k+1 U's are < P,
+//                                        and then every B is < P too)
+static_assert(UBT_LB_THREADS <= 512, "CountMulti's 32-bit bins assume at most 16 warps a block");
+constexpr int kMultiLevels = 256;  // padded table of levels: 2^K > 2 kMaxTau
+constexpr int kMultiBins = 2 * kMaxTau + 1;
 struct CountMultiP {
   int nt;
-  int64_t B[kMaxTau];
-  int64_t U[kMaxTau];
-  unsigned long long* out;  // global: [0, 64) balanced, [64, 128) unbalanced
+  int half;                        // 2^(K-1), with 2^K the smallest power of two > 2 nt
+  int64_t S[2 * kMaxTau];          // the 2 nt levels, ascending
+  unsigned long long* out;         // global bins [0, 2 nt]
 };
 struct CountMulti {
   using P = CountMultiP;
   static constexpr bool kPos = false;
   static constexpr int kRegCap = 64;
-  static __host__ __device__ int smem_bytes(int threads) { return (threads / 32) * kHitQueue * 8; }
+  static __host__ __device__ int smem_bytes(int threads) {
+    return kMultiLevels * 8 + ((kMultiBins * 4 + 15) / 16) * 16 + (threads / 32) * kHitQueue * 8;
+  }
   unsigned long long* out;
-  long long* q;   // this warp's queue of products
+  const long long* S;  // shared: levels, padded with INT64_MAX
+  uint32_t* bins;      // shared: block histogram
+  long long* q;        // shared: this warp's queue of products
   uint32_t qn = 0;
-  int64_t B0, U0, B1, U1;  // this lane's thresholds (padding never met)
-  uint32_t b0 = 0, u0 = 0, b1 = 0, u1 = 0;
-  uint32_t since = 0;
-  bool two;
-  __device__ CountMulti(const P& p, char* smem) : out(p.out) {
-    const int lane = (int)lane_id();
-    q = (long long*)smem + (threadIdx.x >> 5) * kHitQueue;
-    B0 = lane < p.nt ? p.B[lane] : INT64_MIN;
-    U0 = lane < p.nt ? p.U[lane] : INT64_MAX;
-    B1 = lane + 32 < p.nt ? p.B[lane + 32] : INT64_MIN;
-    U1 = lane + 32 < p.nt ? p.U[lane + 32] : INT64_MAX;
-    two = p.nt > 32;
+  uint32_t since = 0;  // products this warp binned since its last flush (warp-uniform)
+  int nt, half;
+  __device__ CountMulti(const P& p, char* smem) : out(p.out), nt(p.nt), half(p.half) {
+    long long* s = (long long*)smem;
+    S = s;
+    bins = (uint32_t*)(smem + kMultiLevels * 8);
+    q = (long long*)(smem + kMultiLevels * 8 + ((kMultiBins * 4 + 15) / 16) * 16) + (threadIdx.x >> 5) * kHitQueue;
+    for (int i = threadIdx.x; i < kMultiLevels; i += blockDim.x) s[i] = i < 2 * p.nt ? p.S[i] : INT64_MAX;
+    for (int i = threadIdx.x; i < kMultiBins; i += blockDim.x) bins[i] = 0;
   }
   __device__ void block_init() {}
-  __device__ __forceinline__ void count_n(uint32_t n) {
-    for (uint32_t j = 0; j < n; j++) {
-      const long long P = q[j];
-      b0 += (P <= B0) ? 1u : 0u;
-      u0 += (P > U0) ? 1u : 0u;
-      if (two) {
-        b1 += (P <= B1) ? 1u : 0u;
-        u1 += (P > U1) ? 1u : 0u;
-      }
+  // interval of P: the largest r with S[r - 1] < P (S[-1] = -inf); the padding
+  // is never < P, and 2^K > 2 nt, so r = #{levels < P}
+  __device__ __forceinline__ void bin(long long P) {
+    int r = 0;
+    for (int b = half; b > 0; b >>= 1)
+      if (S[r + b - 1] < P) r += b;
+    atomicAdd(&bins[r], 1u);
+  }
+  // Bins are moved to the global counters with exchanges, so a flush by one
+  // warp never loses another warp's increments.  A warp flushes once it has
+  // binned 2^26 products, so a bin holds fewer than 16 x (2^26 + 32) < 2^32
+  // (at most 16 warps a block).
+  __device__ void flush() {
+#pragma unroll 1
+    for (int i = (int)lane_id(); i <= 2 * nt; i += 32) {
+      const uint32_t v = atomicExch(&bins[i], 0u);
+      if (v) atomicAdd(&out[i], (unsigned long long)v);
     }
-    since += n;
+    since = 0;
   }
   __device__ void drain32() {
     const int lane = (int)lane_id();
     __syncwarp();
-    count_n(32);
+    const long long mine = q[lane];
     const uint32_t rest = qn - 32;
     const long long moved = (uint32_t)lane < rest ? q[32 + lane] : 0;
     __syncwarp();
     if ((uint32_t)lane < rest) q[lane] = moved;
     qn = rest;
     __syncwarp();
+    bin(mine);
+    since += 32;
+    if (since >= (1u << 26)) flush();
   }
   __device__ void drain_all() {
+    const int lane = (int)lane_id();
     __syncwarp();
-    count_n(qn);
+    if ((uint32_t)lane < qn) bin(q[lane]);
+    since += qn;
     qn = 0;
     __syncwarp();
   }
@@ -233,28 +256,16 @@ struct CountMulti {
                                        uint32_t qvw, uint32_t, uint32_t, uint32_t) {
     const unsigned m = __ballot_sync(kFull, hit);
     if (!m) return;
-    const int lane = (int)lane_id();
     if (hit) q[qn + __popc(m & lanemask_lt())] = tri_product(quv, quw, qvw);
     qn += __popc(m);
     if (qn >= 32) drain32();
   }
   __device__ void task_begin(uint32_t) {}
-  __device__ void flush() {
-    const int lane = (int)lane_id();
-    if (b0) atomicAdd(&out[lane], (unsigned long long)b0);
-    if (u0) atomicAdd(&out[64 + lane], (unsigned long long)u0);
-    if (b1) atomicAdd(&out[32 + lane], (unsigned long long)b1);
-    if (u1) atomicAdd(&out[96 + lane], (unsigned long long)u1);
-    b0 = u0 = b1 = u1 = 0;
-    since = 0;
-  }
-  // every counter stays below 2^32 while it has seen fewer than 2^31 products
-  __device__ void task_end(uint32_t) {
-    if (since >= (1u << 31)) flush();
-  }
+  __device__ void task_end(uint32_t) {}
   __device__ void block_end() {
     drain_all();
-    flush();
+    __syncthreads();
+    if (threadIdx.x < 32) flush();
   }
 };
 
@@ -263,11 +274,16 @@ struct FinishMulti {
   int perm[kMaxTau];  // caller index of the i-th smallest threshold
 };
 
-__global__ void k_finish_multi(const unsigned long long* __restrict__ acc, FinishMulti f, int64_t* __restrict__ out) {
+// bins -> counts: the i-th smallest t has the (nt-1-i)-th smallest B and the
+// i-th smallest U
+__global__ void k_finish_multi(const unsigned long long* __restrict__ bins, FinishMulti f, int64_t* __restrict__ out) {
   const int i = threadIdx.x;
   if (i < f.nt) {
-    out[f.perm[i]] = (int64_t)acc[i];
-    out[f.nt + f.perm[i]] = (int64_t)acc[64 + i];
+    unsigned long long b = 0, u = 0;
+    for (int r = 0; r <= f.nt - 1 - i; r++) b += bins[r];
+    for (int r = f.nt + i + 1; r <= 2 * f.nt; r++) u += bins[r];
+    out[f.perm[i]] = (int64_t)b;
+    out[f.nt + f.perm[i]] = (int64_t)u;
   }
 }
 
@@ -603,9 +619,11 @@ extern "C" ubt_status ubt_count_threshold(ubt_graph* g, const double* h_tau, int
   }
   CountMultiP p;
   p.nt = n_tau;
+  p.half = 1;
+  while (2 * p.half <= 2 * n_tau) p.half *= 2;  // 2 half > 2 nt
   for (int i = 0; i < n_tau; i++) {
-    p.B[i] = lv[order[i]].B;
-    p.U[i] = lv[order[i]].U;
+    p.S[i] = lv[order[n_tau - 1 - i]].B;  // B ascending: t descending
+    p.S[n_tau + i] = lv[order[i]].U;      // U ascending: t ascending
   }
   p.out = g->scratch->hist;
   UBT_CUDA(cudaMemsetAsync(g->scratch->hist, 0, sizeof(g->scratch->hist), s));

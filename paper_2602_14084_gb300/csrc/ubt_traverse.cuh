@@ -223,8 +223,9 @@ struct Pair {
 };
 
 // The whole warp probes entries [off, off + 32 U) of one long list N>(v),
-// U entries per lane, all loads issued before the probes.
-template <class V, bool kRow, int U>
+// U entries per lane, all loads issued before the probes.  kAll: all 32 U
+// entries exist (no bounds tests).
+template <class V, bool kRow, int U, bool kAll>
 __device__ __forceinline__ void long_steps(const uint64_t* __restrict__ adj, Scratch* sc, V& vis, const Table& t,
                                            int lane, uint32_t uj, uint32_t vj, uint32_t vsj, uint32_t dvj,
                                            uint32_t qj, uint32_t pj, uint32_t rsj, uint32_t rlj, uint32_t off) {
@@ -232,14 +233,14 @@ __device__ __forceinline__ void long_steps(const uint64_t* __restrict__ adj, Scr
 #pragma unroll
   for (int s = 0; s < U; s++) {
     const uint32_t i = off + 32 * s + lane;
-    e[s] = i < dvj ? adj[vsj + i] : 0ull;
+    e[s] = (kAll || i < dvj) ? adj[vsj + i] : 0ull;
   }
 #pragma unroll
   for (int s = 0; s < U; s++) {
     const uint32_t i = off + 32 * s + lane;
     uint32_t quw = 0, puw = 0;
-    const bool hit = i < dvj && table_find<kRow, V::kPos>(t, adj_col(e[s]), rsj, rlj, quw, puw, sc);
-    if (off + 32 * s < dvj) vis.step(hit, uj, vj, adj_col(e[s]), qj, quw, adj_valbits(e[s]), pj, puw, vsj + i);
+    const bool hit = (kAll || i < dvj) && table_find<kRow, V::kPos>(t, adj_col(e[s]), rsj, rlj, quw, puw, sc);
+    if (kAll || off + 32 * s < dvj) vis.step(hit, uj, vj, adj_col(e[s]), qj, quw, adj_valbits(e[s]), pj, puw, vsj + i);
   }
 }
 
@@ -281,11 +282,11 @@ __device__ __forceinline__ void probe_pairs(const TravArgs& a, V& vis, const Tab
     const uint32_t rlj = __shfl_sync(kFull, pr.ulen, j);
     uint32_t off = 0;
     while (dvj - off >= 128) {
-      long_steps<V, kRow, 4>(adj, sc, vis, t, lane, uj, vj, vsj, dvj, qj, pj, rsj, rlj, off);
+      long_steps<V, kRow, 4, true>(adj, sc, vis, t, lane, uj, vj, vsj, dvj, qj, pj, rsj, rlj, off);
       off += 128;
     }
     while (off < dvj) {
-      long_steps<V, kRow, 2>(adj, sc, vis, t, lane, uj, vj, vsj, dvj, qj, pj, rsj, rlj, off);
+      long_steps<V, kRow, 2, false>(adj, sc, vis, t, lane, uj, vj, vsj, dvj, qj, pj, rsj, rlj, off);
       off += 64;
     }
   }

@@ -166,6 +166,7 @@ struct Worlds {
 #pragma unroll
     for (int s = 0; s < SLOTS; s++) {
       const uint32_t w = word_of(s);
+#pragma unroll 1
       for (int j = 0; j < 64; j++) {
         const uint32_t v = pl[s].count(j);
         if (v) atomicAdd(&cnt[w * 64 + j], (unsigned long long)v);

@@ -60,6 +60,30 @@ def test_counts_bit_exact(ubt, case, prune):
     assert G.guard() == 0
 
 
+SWEEP32 = [0.51 + i * (0.48 / 31) for i in range(32)]
+MANY = {
+    "sweep32": SWEEP32,
+    "nine": [0.9, 0.5, 0.55, 0.6, 0.65, 0.7, 0.8, 0.95, 1.0],
+    # 64 thresholds, unsorted, with repeats and both ends of [0.5, 1]
+    "sixty_four": [float(x) for x in np.random.default_rng(7).permutation(
+        np.concatenate([np.linspace(0.5, 1.0, 48), [0.5, 1.0, 0.75, 0.75], np.linspace(0.52, 0.98, 12)]))],
+}
+
+
+@pytest.mark.parametrize("case", PARITY, ids=[c[0] for c in PARITY])
+@pytest.mark.parametrize("which", sorted(MANY))
+def test_counts_many_thresholds_bit_exact(ubt, case, which):
+    """More than 8 thresholds: one traversal bins every product among all levels."""
+    name, n, s, d, k = case
+    taus = MANY[which]
+    G = ubt.Graph(n, s, d, k=k)
+    ob, ou = oracle.count_threshold(n, s, d, k, taus)
+    for prune in (0, 1):
+        gb, gu = G.count_threshold(taus, prune=prune)
+        assert np.array_equal(gb, ob) and np.array_equal(gu, ou), (name, which, prune)
+    assert G.guard() == 0
+
+
 @pytest.mark.parametrize("case", PARITY, ids=[c[0] for c in PARITY])
 def test_enumeration_bit_exact(ubt, case):
     name, n, s, d, k = case

@@ -21,6 +21,11 @@ namespace {
 
 constexpr int kMaxTau = 64;
 
+// register cap of the counting visitors' kernels (launch bounds)
+#ifndef UBT_COUNT_REGCAP
+#define UBT_COUNT_REGCAP 64
+#endif
+
 __device__ __forceinline__ int64_t tri_product(uint32_t a, uint32_t b, uint32_t c) {
   // |q| <= 2^15, so q_a q_b fits int32 (<= 2^30); the third factor widens to int64
   return (int64_t)((int32_t)a * (int32_t)b) * (int64_t)(int32_t)c;
@@ -72,14 +77,43 @@ struct CountRegP {
   unsigned long long* out;  // [0, NT) balanced, [NT, 2 NT) unbalanced
 };
 // A warp collects the products P of its triangles in a shared-memory queue
-// and counts them 32 at a time, so the counting runs on full warps.
-constexpr int kHitQueue = 64;
+// and counts them 32 at a time, so the counting runs on full warps.  The
+// queue holds fewer than 32 between steps; a step adds at most 32 and a
+// batched pair of steps at most 64.
+constexpr int kHitQueue = 96;
+
+// Appends the products of two probe steps' hits to a warp queue (q, qn); the
+// caller drains it below 32 afterwards.  All lanes, converged.
+__device__ __forceinline__ void enqueue_pair(long long* q, uint32_t& qn, bool h0, bool h1, uint32_t quv,
+                                             uint32_t quw0, uint32_t qvw0, uint32_t quw1, uint32_t qvw1) {
+  const unsigned lt = lanemask_lt();
+  const unsigned m0 = __ballot_sync(kFull, h0);
+  const unsigned m1 = __ballot_sync(kFull, h1);
+  const uint32_t n0 = qn + __popc(m0);
+  if (h0) q[qn + __popc(m0 & lt)] = tri_product(quv, quw0, qvw0);
+  if (h1) q[n0 + __popc(m1 & lt)] = tri_product(quv, quw1, qvw1);
+  qn = n0 + __popc(m1);
+}
+
+// Moves queue entries [32, qn) (fewer than 64) to the front.
+__device__ __forceinline__ void queue_shift32(long long* q, uint32_t& qn) {
+  const uint32_t lane = lane_id();
+  const uint32_t rest = qn - 32;
+  const long long a = lane < rest ? q[32 + lane] : 0;
+  const long long b = lane + 32 < rest ? q[64 + lane] : 0;
+  __syncwarp();
+  if (lane < rest) q[lane] = a;
+  if (lane + 32 < rest) q[32 + lane] = b;
+  qn = rest;
+  __syncwarp();
+}
 
 template <int NT>
 struct CountReg {
   using P = CountRegP;
   static constexpr bool kPos = false;
-  static constexpr int kRegCap = 64;
+  static constexpr bool kBatched = true;
+  static constexpr int kRegCap = UBT_COUNT_REGCAP;
   static __host__ __device__ int smem_bytes(int threads) { return (threads / 32) * kHitQueue * 8; }
   int64_t B[NT], U[NT];
   unsigned long long* out;
@@ -110,12 +144,7 @@ struct CountReg {
     const int lane = (int)lane_id();
     __syncwarp();
     const long long mine = q[lane];
-    const uint32_t rest = qn - 32;
-    const long long moved = (uint32_t)lane < rest ? q[32 + lane] : 0;
-    __syncwarp();
-    if ((uint32_t)lane < rest) q[lane] = moved;
-    qn = rest;
-    __syncwarp();
+    queue_shift32(q, qn);
     count(mine);
   }
   __device__ void drain_all() {
@@ -133,6 +162,18 @@ struct CountReg {
     if (hit) q[qn + __popc(m & lanemask_lt())] = tri_product(quv, quw, qvw);
     qn += __popc(m);
     if (qn >= 32) drain32();
+  }
+  template <int U>
+  __device__ __forceinline__ void steps(const bool (&hit)[U], uint32_t quv, const uint32_t (&quw)[U],
+                                        const uint32_t (&qvw)[U]) {
+    static_assert(U % 2 == 0, "steps come in pairs");
+#pragma unroll
+    for (int s = 0; s < U; s += 2) {
+      if (__any_sync(kFull, hit[s] || hit[s + 1])) {
+        enqueue_pair(q, qn, hit[s], hit[s + 1], quv, quw[s], qvw[s], quw[s + 1], qvw[s + 1]);
+        while (qn >= 32) drain32();
+      }
+    }
   }
   __device__ void task_begin(uint32_t) {}
   __device__ void flush() {
@@ -190,7 +231,8 @@ struct CountMultiP {
 struct CountMulti {
   using P = CountMultiP;
   static constexpr bool kPos = false;
-  static constexpr int kRegCap = 64;
+  static constexpr bool kBatched = true;
+  static constexpr int kRegCap = UBT_COUNT_REGCAP;
   static __host__ __device__ int smem_bytes(int threads) {
     return kMultiLevels * 8 + ((kMultiBins * 4 + 15) / 16) * 16 + (threads / 32) * kHitQueue * 8;
   }
@@ -234,12 +276,7 @@ struct CountMulti {
     const int lane = (int)lane_id();
     __syncwarp();
     const long long mine = q[lane];
-    const uint32_t rest = qn - 32;
-    const long long moved = (uint32_t)lane < rest ? q[32 + lane] : 0;
-    __syncwarp();
-    if ((uint32_t)lane < rest) q[lane] = moved;
-    qn = rest;
-    __syncwarp();
+    queue_shift32(q, qn);
     bin(mine);
     since += 32;
     if (since >= (1u << 26)) flush();
@@ -259,6 +296,18 @@ struct CountMulti {
     if (hit) q[qn + __popc(m & lanemask_lt())] = tri_product(quv, quw, qvw);
     qn += __popc(m);
     if (qn >= 32) drain32();
+  }
+  template <int U>
+  __device__ __forceinline__ void steps(const bool (&hit)[U], uint32_t quv, const uint32_t (&quw)[U],
+                                        const uint32_t (&qvw)[U]) {
+    static_assert(U % 2 == 0, "steps come in pairs");
+#pragma unroll
+    for (int s = 0; s < U; s += 2) {
+      if (__any_sync(kFull, hit[s] || hit[s + 1])) {
+        enqueue_pair(q, qn, hit[s], hit[s + 1], quv, quw[s], qvw[s], quw[s + 1], qvw[s + 1]);
+        while (qn >= 32) drain32();
+      }
+    }
   }
   __device__ void task_begin(uint32_t) {}
   __device__ void task_end(uint32_t) {}
@@ -297,6 +346,7 @@ struct EnumP {
 struct Enum {
   using P = EnumP;
   static constexpr bool kPos = false;
+  static constexpr bool kBatched = false;
   static constexpr int kRegCap = 64;
   static __host__ __device__ int smem_bytes(int) { return 0; }
   P p;
@@ -350,6 +400,7 @@ template <bool kReal>
 struct Expect {
   using P = ExpectP;
   static constexpr bool kPos = false;
+  static constexpr bool kBatched = false;
   static constexpr int kRegCap = 64;
   static __host__ __device__ int smem_bytes(int) { return 0; }
   P p;
@@ -414,6 +465,7 @@ template <bool kReal>
 struct Adjoint {
   using P = AdjointP;
   static constexpr bool kPos = true;
+  static constexpr bool kBatched = false;
   static constexpr int kRegCap = 64;
   static __host__ __device__ int smem_bytes(int) { return 0; }
   P p;

@@ -34,7 +34,9 @@
 //
 // Visitors implement: smem_bytes(threads) (shared memory they need) /
 // block_init / task_begin / step (called by all 32 lanes of a warp, converged,
-// once per probed entry with a hit flag) / task_end / block_end.
+// once per probed entry with a hit flag) / task_end / block_end.  Visitors
+// with kBatched also take the hits of U probes of one long list at once
+// (steps<U>: hit flags and the u-w and v-w edge values; u-v is common).
 #pragma once
 
 #include <algorithm>
@@ -235,12 +237,28 @@ __device__ __forceinline__ void long_steps(const uint64_t* __restrict__ adj, Scr
     const uint32_t i = off + 32 * s + lane;
     e[s] = (kAll || i < dvj) ? adj[vsj + i] : 0ull;
   }
+  if constexpr (V::kBatched) {
+    // all U probes first, then the visitor takes their hits together
+    bool hit[U];
+    uint32_t quw[U], qvw[U];
 #pragma unroll
-  for (int s = 0; s < U; s++) {
-    const uint32_t i = off + 32 * s + lane;
-    uint32_t quw = 0, puw = 0;
-    const bool hit = (kAll || i < dvj) && table_find<kRow, V::kPos>(t, adj_col(e[s]), rsj, rlj, quw, puw, sc);
-    if (kAll || off + 32 * s < dvj) vis.step(hit, uj, vj, adj_col(e[s]), qj, quw, adj_valbits(e[s]), pj, puw, vsj + i);
+    for (int s = 0; s < U; s++) {
+      const uint32_t i = off + 32 * s + lane;
+      uint32_t puw = 0;
+      quw[s] = 0;
+      qvw[s] = adj_valbits(e[s]);
+      hit[s] = (kAll || i < dvj) && table_find<kRow, false>(t, adj_col(e[s]), rsj, rlj, quw[s], puw, sc);
+    }
+    vis.template steps<U>(hit, qj, quw, qvw);
+  } else {
+#pragma unroll
+    for (int s = 0; s < U; s++) {
+      const uint32_t i = off + 32 * s + lane;
+      uint32_t quw = 0, puw = 0;
+      const bool hit = (kAll || i < dvj) && table_find<kRow, V::kPos>(t, adj_col(e[s]), rsj, rlj, quw, puw, sc);
+      if (kAll || off + 32 * s < dvj)
+        vis.step(hit, uj, vj, adj_col(e[s]), qj, quw, adj_valbits(e[s]), pj, puw, vsj + i);
+    }
   }
 }
 

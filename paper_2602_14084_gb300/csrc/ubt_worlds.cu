@@ -137,6 +137,7 @@ template <int SLOTS>
 struct Worlds {
   using P = WorldsP;
   static constexpr bool kPos = true;
+  static constexpr bool kBatched = false;
   static constexpr int kRegCap = 128;
   static constexpr int K = SLOTS == 1 ? 14 : 12;      // planes per slot
   static constexpr uint32_t kLimit = (1u << K) - 1u;  // increments before a flush
@@ -259,6 +260,7 @@ struct BatchP {
 struct Batch {
   using P = BatchP;
   static constexpr bool kPos = true;
+  static constexpr bool kBatched = false;
   static constexpr int kRegCap = 128;
   static __host__ __device__ int smem_bytes(int) { return 0; }
   static constexpr int K = 8;

@@ -138,6 +138,13 @@ def tuned(ubt, query, variant, make, run, args, budget_s=None):
 
 
 
+def alg_bytes_of(st):
+    """Algorithmic bytes of one traversal (ubt_traversal_stats sizes): 8 B per
+    table entry, 24 B per pair (its pair word, its edge's CSR entry and the
+    streamed list's two offsets), 8 B per streamed entry."""
+    return 8 * st["table_entries"] + 24 * st["pairs"] + 8 * st["streamed"]
+
+
 def ncu_traffic(kernel, workload):
     """DRAM bytes per launch (read + write) from the committed ncu summary of
     this kernel and workload, or None when the kernels changed since."""
@@ -321,10 +328,10 @@ def main():
     times_unpruned = time_steps(step_unpruned, max(3, args.steps // 4), 1, flush)
 
     # roofline of the dominant kernel (the traversal): algorithmic bytes =
-    # 16 B per forward-list entry loaded (table + row offsets of v) + 8 B per
-    # streamed entry of N>(v)
+    # 8 B per table entry loaded + 24 B per pair (pair word, its edge's entry,
+    # the streamed list's offsets) + 8 B per streamed entry
     st = G.traversal_stats(TAUS, prune=True)
-    alg_bytes = 16 * st["table_entries"] + 8 * st["streamed"]
+    alg_bytes = alg_bytes_of(st)
     pk, pk_kind = peaks()
     achieved = alg_bytes / t_step / 1e9
     kname = "k_traverse<CountReg<4>>"
@@ -332,7 +339,8 @@ def main():
                 "frac": achieved / pk["hbm_gbs"], "traffic": ncu_traffic(kname, WORKLOAD),
                 "kernel": kname, "peak_kind": pk_kind,
                 "alg_bytes_per_launch": alg_bytes, "streamed_entries": st["streamed"],
-                "table_entries": st["table_entries"]}
+                "table_entries": st["table_entries"], "pairs": st["pairs"],
+                "alg1_probes": info["wedges"]}
     st0 = G.traversal_stats(TAUS, prune=False)
 
     # end to end through the C ABI from pinned host buffers
@@ -382,7 +390,7 @@ def main():
         "tuning": {k: tuning[k] for k in ("source", "config", "key") if k in tuning},
         "unpruned": {"ms_per_step": 1e3 * float(np.mean(times_unpruned)),
                      "value": T / float(np.mean(times_unpruned)), "streamed_entries": st0["streamed"],
-                     "alg_bytes": 16 * st0["table_entries"] + 8 * st0["streamed"]},
+                     "alg_bytes": alg_bytes_of(st0)},
         "graph": info,
     }
 
@@ -501,7 +509,7 @@ def extra_rmat22(ubt, args, flush):
     assert np.array_equal(b, b0) and np.array_equal(u, u0), "pruned and unpruned sweeps differ"
     assert np.all(np.diff(b) <= 0) and np.all(np.diff(u) <= 0), "counts not monotone in t"
     st = G.traversal_stats(SWEEP32, prune=True)
-    alg = 16 * st["table_entries"] + 8 * st["streamed"]
+    alg = alg_bytes_of(st)
     pk, pk_kind = peaks()
     nb9, nu9 = G.count_threshold([0.9])
     cap = int(nb9[0] + nu9[0])

@@ -80,8 +80,11 @@ typedef struct {
     int64_t m;                /* undirected edges */
     int64_t max_out_degree;   /* largest forward list under Node Order */
     int64_t hub_vertices;     /* vertices handled by a whole thread block */
-    int64_t wedges;           /* sum over forward edges (u,v) of |N>(v)| */
+    int64_t wedges;           /* sum over forward edges (u,v) of |N>(v)|: the
+                                 entries Alg. 1 probes */
     int64_t kind;             /* UBT_GRAPH_FIXED or UBT_GRAPH_REAL */
+    int64_t probes;           /* entries the traversal probes without pruning:
+                                 sum over pairs of the streamed list's length */
 } ubt_graph_info;
 
 /* Optional extras for ubt_create_graph (pass NULL for none). */
@@ -314,26 +317,41 @@ ubt_status ubt_query_guard(ubt_graph* g, int64_t* h_word, void* stream);
  *              value: q = 32768 - k as int32 for FIXED graphs, round(s 2^30)
  *              as int32 for REAL graphs)
  *   h_eid      uint32[m] input edge index of every entry
- *   h_lists    uint32[tasks] the work lists: giant, hub and medium tasks,
- *              then the short lists in vertex order
- *   h_list_sizes int64[4] the four sizes
+ *   h_lists    uint32[tasks] the work lists: owners of giant, hub and
+ *              medium tasks
+ *   h_list_sizes int64[4] the three list sizes and 0
  */
 ubt_status ubt_graph_export(const ubt_graph* g, uint32_t* h_row_ptr, uint64_t* h_adj, uint32_t* h_eid,
                             uint32_t* h_lists, int64_t* h_list_sizes, void* stream);
 
 /*
+ * ubt_graph_export_pairs -- SYNC.  Copies the pair partition to host memory
+ * (any pointer may be NULL).  Every forward edge x-s is one pair of the
+ * traversal, owned by the endpoint x whose list is the hash table while the
+ * list of s is streamed: the earlier vertex u of the edge u -> v (Alg. 1) or,
+ * with the "pull" tuning on and |N>(v)| > |N>(u)|, the later vertex v.  Both
+ * intersect N>(u) and N>(v), so each triangle is found once either way.
+ *   h_pair_ptr uint32[n + 1] pairs of owner x are [h_pair_ptr[x], h_pair_ptr[x + 1])
+ *   h_pairs    uint64[m] streamed vertex s (low 32 bits) and CSR position of
+ *              the edge (high 32 bits); order within an owner is unspecified
+ */
+ubt_status ubt_graph_export_pairs(const ubt_graph* g, uint32_t* h_pair_ptr, uint64_t* h_pairs, void* stream);
+
+/*
  * ubt_set_tuning / ubt_get_tuning -- process-wide launch parameters that the
  * autotuner picks (they change speed, never results).  Unknown names return
  * UBT_ERR_INVALID_ARG.  Names:
- *   "short_max"       forward lists of 2..short_max entries are concatenated
- *                     and processed in 32-pair segments, one warp each
- *                     (2..32, default 8)
- *   "hub_threshold"   longer lists than this are whole-block tasks; lists
- *                     between short_max and it are one-warp tasks (default 128)
- *   "block_threads"   threads per block of the block-task kernel (long
- *                     lists; 64..512, /32, default 512)
- *   "warp_threads"    threads per block of the warp-task kernel (medium and
- *                     short lists; 64..512, /32, default 128)
+ *   "pull"            1 (default): a pair is owned by the endpoint whose
+ *                     list is longer, so the shorter list is streamed; 0:
+ *                     always by the earlier vertex (Alg. 1 as written)
+ *   "hub_threshold"   owners with longer lists than this are whole-block
+ *                     tasks (default 128)
+ *   "block_work"      owners whose pairs stream more entries than this are
+ *                     whole-block tasks too (default 16384)
+ *   "block_threads"   threads per block of the block-task kernel (64..512,
+ *                     /32, default 512)
+ *   "warp_threads"    threads per block of the warp-task kernel (64..512,
+ *                     /32, default 128)
  *   "blocks_per_sm"   cap on resident blocks per SM (1..32; occupancy decides
  *                     below it)
  *   "smem_table_max"  hash-table slots kept in shared memory (power of two);
@@ -342,12 +360,13 @@ ubt_status ubt_graph_export(const ubt_graph* g, uint32_t* h_row_ptr, uint64_t* h
  *                     default 16)
  *   "world_words_per_pass"  64-world words per traversal of ubt_sample_worlds
  *                     (1, 2, 4, 8, 16, 32 or 64)
- *   "small_batch"     warp tasks / segments taken per grab of a task counter
+ *   "small_batch"     warp tasks taken per grab of a task counter
  *   "sort_smem_max"   longest forward list sorted in shared memory during the
  *                     build (power of two, 64..4096); longer lists are sorted
  *                     in a global-memory slice
- * Build-time knobs (short_max, hub_threshold, smem_table_max, sort_smem_max)
- * apply to * graphs created afterwards; query the workspace size after setting them.
+ * Build-time knobs (pull, hub_threshold, block_work, smem_table_max,
+ * sort_smem_max) apply to graphs created afterwards; query the workspace size
+ * after setting them.
  */
 ubt_status ubt_set_tuning(const char* name, int64_t value);
 ubt_status ubt_get_tuning(const char* name, int64_t* h_value);

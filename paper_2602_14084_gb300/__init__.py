@@ -45,7 +45,8 @@ class _GraphOpts(ctypes.Structure):
 
 class _GraphInfo(ctypes.Structure):
     _fields_ = [("n", ctypes.c_int64), ("m", ctypes.c_int64), ("max_out_degree", ctypes.c_int64),
-                ("hub_vertices", ctypes.c_int64), ("wedges", ctypes.c_int64), ("kind", ctypes.c_int64)]
+                ("hub_vertices", ctypes.c_int64), ("wedges", ctypes.c_int64), ("kind", ctypes.c_int64),
+                ("probes", ctypes.c_int64)]
 
 
 def lib():
@@ -77,6 +78,7 @@ def lib():
             "ubt_traversal_stats": (I32, [P, P, I32, I32, P, P]),
             "ubt_query_guard": (I32, [P, ctypes.POINTER(I64), P]),
             "ubt_graph_export": (I32, [P, P, P, P, P, P, P]),
+            "ubt_graph_export_pairs": (I32, [P, P, P, P]),
             "ubt_set_tuning": (I32, [ctypes.c_char_p, I64]),
             "ubt_get_tuning": (I32, [ctypes.c_char_p, ctypes.POINTER(I64)]),
         }
@@ -230,9 +232,14 @@ class Graph:
         c = lambda a: a.ctypes.data_as(ctypes.c_void_p)
         _check(lib().ubt_graph_export(self._h, c(rp), c(adj), c(eid), c(lists), None, _stream(stream)),
                "ubt_graph_export")
+        pp = np.zeros(self.n + 1, dtype=np.uint32)
+        pw = np.zeros(max(self.m, 1), dtype=np.uint64)
+        _check(lib().ubt_graph_export_pairs(self._h, c(pp), c(pw), _stream(stream)), "ubt_graph_export_pairs")
         return {"row_ptr": rp, "col": (adj[: self.m] & 0xFFFFFFFF).astype(np.uint32),
                 "val": (adj[: self.m] >> 32).astype(np.uint32).view(np.int32), "eid": eid[: self.m],
-                "lists": lists[: int(sizes.sum())], "list_sizes": sizes}
+                "lists": lists[: int(sizes.sum())], "list_sizes": sizes, "pair_ptr": pp,
+                "pair_streamed": (pw[: self.m] & 0xFFFFFFFF).astype(np.uint32),
+                "pair_pos": (pw[: self.m] >> 32).astype(np.uint32)}
 
     # ---------------------------------------------------------------- queries
 

@@ -7,8 +7,9 @@ they only move work between task kinds, warps and blocks -- but the best
 setting depends on the graph's degree distribution, the query and the GPU.
 This module picks them by measurement:
 
-* knobs that act when a graph is built (``BUILD_KNOBS``: the short-list and
-  hub-list length limits and the shared-memory table limit) and knobs that
+* knobs that act when a graph is built (``BUILD_KNOBS``: the pair
+  partition, the block-task limits on list length and streamed work, the
+  shared-memory table limit) and knobs that
   act on every query (``RUN_KNOBS``: block shapes, blocks per SM, work-grab
   sizes, sign-world words per pass);
 * coordinate descent over a small candidate list per knob, starting from the
@@ -39,8 +40,9 @@ import numpy as np
 
 # candidate values per knob (the library validates each against its limits)
 BUILD_KNOBS: Dict[str, List[int]] = {
-    "short_max": [2, 4, 8, 16, 32],
+    "pull": [1, 0],
     "hub_threshold": [32, 64, 128, 256, 512],
+    "block_work": [1 << 12, 1 << 14, 1 << 16, 1 << 18, 1 << 20],
     "smem_table_max": [4096, 8192, 16384],
 }
 RUN_KNOBS: Dict[str, List[int]] = {
@@ -53,13 +55,13 @@ RUN_KNOBS: Dict[str, List[int]] = {
 }
 # knobs that matter per query kind (others are left as they are)
 QUERY_KNOBS: Dict[str, List[str]] = {
-    "count": ["hub_threshold", "short_max", "block_unit", "small_batch", "blocks_per_sm", "block_threads",
-              "warp_threads", "smem_table_max"],
-    "expected": ["hub_threshold", "short_max", "block_unit", "small_batch", "blocks_per_sm", "block_threads",
-                 "warp_threads", "smem_table_max"],
-    "worlds": ["world_words_per_pass", "hub_threshold", "short_max", "block_unit", "small_batch",
+    "count": ["hub_threshold", "block_work", "block_unit", "small_batch", "blocks_per_sm", "block_threads",
+              "warp_threads", "smem_table_max", "pull"],
+    "expected": ["hub_threshold", "block_work", "block_unit", "small_batch", "blocks_per_sm", "block_threads",
+                 "warp_threads", "smem_table_max", "pull"],
+    "worlds": ["world_words_per_pass", "hub_threshold", "block_work", "block_unit", "small_batch",
                "blocks_per_sm"],
-    "batch": ["short_max", "small_batch", "warp_threads", "blocks_per_sm"],
+    "batch": ["block_work", "small_batch", "warp_threads", "blocks_per_sm"],
 }
 ALL_KNOBS = {**BUILD_KNOBS, **RUN_KNOBS}
 

@@ -84,9 +84,12 @@ extern "C" ubt_status ubt_set_tuning(const char* name, int64_t value) {
   } else if (!strcmp(name, "small_batch")) {
     if (value < 1 || value > 1024) return UBT_ERR_INVALID_ARG;
     t.small_batch = value;
-  } else if (!strcmp(name, "short_max")) {
-    if (value < 2 || value > 32) return UBT_ERR_INVALID_ARG;
-    t.short_max = value;
+  } else if (!strcmp(name, "pull")) {
+    if (value < 0 || value > 1) return UBT_ERR_INVALID_ARG;
+    t.pull = value;
+  } else if (!strcmp(name, "block_work")) {
+    if (value < 1 || value > (1ll << 40)) return UBT_ERR_INVALID_ARG;
+    t.block_work = value;
   } else if (!strcmp(name, "block_unit")) {
     if (value < 1 || value > 32) return UBT_ERR_INVALID_ARG;
     t.block_unit = value;
@@ -110,7 +113,8 @@ extern "C" ubt_status ubt_get_tuning(const char* name, int64_t* h_value) {
   else if (!strcmp(name, "world_words_per_pass")) *h_value = t.world_words_per_pass;
   else if (!strcmp(name, "small_batch")) *h_value = t.small_batch;
   else if (!strcmp(name, "sort_smem_max")) *h_value = t.sort_smem_max;
-  else if (!strcmp(name, "short_max")) *h_value = t.short_max;
+  else if (!strcmp(name, "pull")) *h_value = t.pull;
+  else if (!strcmp(name, "block_work")) *h_value = t.block_work;
   else if (!strcmp(name, "block_unit")) *h_value = t.block_unit;
   else return UBT_ERR_INVALID_ARG;
   return UBT_OK;

@@ -8,10 +8,13 @@
 //   sort       each list by neighbour id (duplicate check), then -- FIXED
 //              graphs -- by |q| descending so that pruned entries (Lemma 2)
 //              form a suffix of every list
-//   work lists vertices with >= 2 forward entries, split by list length into
-//              block tasks and warp tasks (ordered by decreasing wedge count)
-//              and short lists (concatenated in vertex order, cut into
-//              32-pair segments that never cross a batch graph)
+//   pairs      every forward edge x-s is a pair owned by one endpoint: the
+//              one whose list becomes the hash table while the other
+//              endpoint's list is streamed through it (the shorter list is
+//              streamed); pairs grouped by owner
+//   work lists owners (>= 2 forward entries, >= 1 pair) split by list length
+//              and streamed work into block tasks and warp tasks, each
+//              ordered by decreasing work
 #include <math.h>
 #include <string.h>
 
@@ -232,49 +235,95 @@ __global__ void k_collect_long(int64_t n, const uint32_t* __restrict__ row_ptr, 
   }
 }
 
-// Task classes by forward-list length (0 = none: fewer than 2 entries)
-enum : uint8_t { kClsShort = 0, kClsMedium = 1, kClsHub = 2, kClsGiant = 3 };
-constexpr uint8_t kNoTask = 0xFF, kShortTask = 0xFE;
-constexpr int kLgMax = 47;  // wedge-count buckets 2^0 .. 2^47
+// Owner of the pair of forward edge u -> v (u before v in Node Order, du and
+// dv their forward-list lengths).  Alg. 1 probes every w of N>(v) in a table
+// of N>(u) ("push", owner u).  Probing N>(u) in a table of N>(v) ("pull",
+// owner v) intersects the same two lists, so the triangle {u, v, w} is still
+// found exactly once, from its two earliest vertices; pull is taken when it
+// streams the shorter list.
+__device__ inline uint32_t pair_owner(uint32_t u, uint32_t v, uint32_t du, uint32_t dv, int pull) {
+  return (pull && dv > du) ? v : u;
+}
 
-// Per vertex: wedge count sum_{v in N>(u)} |N>(v)|, its log2 bucket and class.
-//   bucket[u] = lg * 4 + cls for medium / hub / giant lists, kShortTask for
-//   short lists, kNoTask for lists of fewer than 2 entries.
-// stats: [0] wedges, [1] longest list, [2] longest hub list, [3] short lists,
-//        [4 + lg * 4 + cls] bucket sizes
-__global__ void k_row_stats(int64_t n, const uint32_t* __restrict__ row_ptr, const uint64_t* __restrict__ adj,
-                            uint32_t short_max, uint32_t hub_thr, uint32_t giant_thr, uint8_t* __restrict__ bucket,
-                            uint32_t* __restrict__ short_flag, unsigned long long* stats) {
+// pairs per owner (one warp per row u)
+__global__ void k_pair_count(int64_t n, const uint32_t* __restrict__ row_ptr, const uint64_t* __restrict__ adj,
+                             int pull, uint32_t* __restrict__ pcount) {
   const int lane = threadIdx.x & 31;
   const int64_t warps = (int64_t)gridDim.x * (blockDim.x >> 5);
   for (int64_t u = blockIdx.x * (int64_t)(blockDim.x >> 5) + (threadIdx.x >> 5); u < n; u += warps) {
     const uint32_t rs = row_ptr[u], re = row_ptr[u + 1];
-    const uint32_t len = re - rs;
-    unsigned long long w = 0;
     for (uint32_t i = rs + lane; i < re; i += 32) {
       const uint32_t v = adj_col(adj[i]);
-      w += row_ptr[v + 1] - row_ptr[v];
+      atomicAdd(&pcount[pair_owner((uint32_t)u, v, re - rs, row_ptr[v + 1] - row_ptr[v], pull)], 1u);
+    }
+  }
+}
+
+// pair words grouped by owner: the streamed vertex and the edge's CSR position
+__global__ void k_pair_fill(int64_t n, const uint32_t* __restrict__ row_ptr, const uint64_t* __restrict__ adj,
+                            int pull, const uint32_t* __restrict__ pair_ptr, uint32_t* __restrict__ pfill,
+                            uint64_t* __restrict__ pairs) {
+  const int lane = threadIdx.x & 31;
+  const int64_t warps = (int64_t)gridDim.x * (blockDim.x >> 5);
+  for (int64_t u = blockIdx.x * (int64_t)(blockDim.x >> 5) + (threadIdx.x >> 5); u < n; u += warps) {
+    const uint32_t rs = row_ptr[u], re = row_ptr[u + 1];
+    for (uint32_t i = rs + lane; i < re; i += 32) {
+      const uint32_t v = adj_col(adj[i]);
+      const uint32_t x = pair_owner((uint32_t)u, v, re - rs, row_ptr[v + 1] - row_ptr[v], pull);
+      const uint32_t streamed = x == (uint32_t)u ? v : (uint32_t)u;
+      pairs[pair_ptr[x] + atomicAdd(&pfill[x], 1u)] = ((uint64_t)i << 32) | streamed;
+    }
+  }
+}
+
+// Task classes (by the owner's list length and streamed work)
+enum : uint8_t { kClsMedium = 1, kClsHub = 2, kClsGiant = 3 };
+constexpr uint8_t kNoTask = 0xFF;
+constexpr int kLgMax = 47;  // work buckets 2^0 .. 2^47
+
+// Per owner x: streamed work sum over its pairs of |N>(s)|, its log2 bucket
+// and class; bucket[x] = lg * 4 + cls, or kNoTask (fewer than 2 list entries
+// or no pairs: no triangle can be found there).
+// stats: [0] oriented wedges sum_u sum_{v in N>(u)} |N>(v)| (Alg. 1's probes),
+//        [1] longest list, [2] longest list of a block task, [3] streamed
+//        work of all pairs, [4 + lg * 4 + cls] bucket sizes
+__global__ void k_row_stats(int64_t n, const uint32_t* __restrict__ row_ptr, const uint64_t* __restrict__ adj,
+                            const uint32_t* __restrict__ pair_ptr, const uint64_t* __restrict__ pairs,
+                            uint32_t hub_thr, uint32_t giant_thr, unsigned long long block_work,
+                            uint8_t* __restrict__ bucket, unsigned long long* stats) {
+  const int lane = threadIdx.x & 31;
+  const int64_t warps = (int64_t)gridDim.x * (blockDim.x >> 5);
+  for (int64_t x = blockIdx.x * (int64_t)(blockDim.x >> 5) + (threadIdx.x >> 5); x < n; x += warps) {
+    const uint32_t rs = row_ptr[x], re = row_ptr[x + 1];
+    const uint32_t len = re - rs;
+    const uint32_t ps = pair_ptr[x], pe = pair_ptr[x + 1];
+    unsigned long long wedge = 0, w = 0;
+    for (uint32_t i = rs + lane; i < re; i += 32) {
+      const uint32_t v = adj_col(adj[i]);
+      wedge += row_ptr[v + 1] - row_ptr[v];
+    }
+    for (uint32_t i = ps + lane; i < pe; i += 32) {
+      const uint32_t sv = (uint32_t)pairs[i];
+      w += row_ptr[sv + 1] - row_ptr[sv];
     }
 #pragma unroll
-    for (int d = 16; d > 0; d >>= 1) w += __shfl_xor_sync(kFull, w, d);
+    for (int d = 16; d > 0; d >>= 1) {
+      wedge += __shfl_xor_sync(kFull, wedge, d);
+      w += __shfl_xor_sync(kFull, w, d);
+    }
     if (lane == 0) {
       uint8_t b = kNoTask;
-      uint32_t sf = 0;
-      if (len >= 2 && len <= short_max) {
-        b = kShortTask;
-        sf = 1;
-        atomicAdd(&stats[3], 1ull);
-      } else if (len >= 2) {
-        const int cls = len > giant_thr ? kClsGiant : (len > hub_thr ? kClsHub : kClsMedium);
+      if (len >= 2 && pe > ps) {
+        const int cls = len > giant_thr ? kClsGiant : ((len > hub_thr || w > block_work) ? kClsHub : kClsMedium);
         int lg = w ? 63 - __clzll(w) : 0;
         lg = lg > kLgMax ? kLgMax : lg;
         b = (uint8_t)(lg * 4 + cls);
         atomicAdd(&stats[4 + b], 1ull);
         if (cls == kClsHub) atomicMax(&stats[2], (unsigned long long)len);
       }
-      bucket[u] = b;
-      short_flag[u] = sf;
-      atomicAdd(&stats[0], w);
+      bucket[x] = b;
+      atomicAdd(&stats[0], wedge);
+      atomicAdd(&stats[3], w);
       atomicMax(&stats[1], (unsigned long long)len);
     }
   }
@@ -284,44 +333,8 @@ __global__ void k_fill_lists(int64_t n, const uint8_t* __restrict__ bucket, unsi
                              uint32_t* __restrict__ lists) {
   for (int64_t u = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; u < n; u += (int64_t)gridDim.x * blockDim.x) {
     const uint8_t b = bucket[u];
-    if (b == kNoTask || b == kShortTask) continue;
+    if (b == kNoTask) continue;
     lists[atomicAdd(&cursor[b], 1ull)] = (uint32_t)u;
-  }
-}
-
-// short lists in vertex order (stable compaction by the scanned flags) and
-// their lengths; per batch graph, the sum of its short-list lengths
-__global__ void k_short_rows(int64_t n, const uint32_t* __restrict__ flag, const uint32_t* __restrict__ idx,
-                             const uint32_t* __restrict__ row_ptr, const uint32_t* __restrict__ vgraph,
-                             uint32_t* __restrict__ seg_row, uint32_t* __restrict__ slen, uint32_t* __restrict__ gsum) {
-  for (int64_t u = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; u < n; u += (int64_t)gridDim.x * blockDim.x) {
-    if (!flag[u]) continue;
-    const uint32_t r = idx[u];
-    const uint32_t len = row_ptr[u + 1] - row_ptr[u];
-    seg_row[r] = (uint32_t)u;
-    slen[r] = len;
-    if (vgraph) atomicAdd(&gsum[vgraph[u]], len);
-  }
-}
-
-// padding that starts every batch graph's short lists on a multiple of 32
-__global__ void k_graph_pad(int64_t ng, uint32_t* gsum) {
-  for (int64_t g = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; g < ng; g += (int64_t)gridDim.x * blockDim.x)
-    gsum[g] = ((gsum[g] + 31u) & ~31u) - gsum[g];
-}
-
-__global__ void k_seg_first(int64_t nr, const uint32_t* __restrict__ seg_row, uint32_t* __restrict__ seg_start,
-                            const uint32_t* __restrict__ slen, const uint32_t* __restrict__ vgraph,
-                            const uint32_t* __restrict__ gpad, uint32_t* __restrict__ seg_first) {
-  for (int64_t r = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; r < nr; r += (int64_t)gridDim.x * blockDim.x) {
-    uint32_t st = seg_start[r];
-    if (vgraph) {
-      st += gpad[vgraph[seg_row[r]]];
-      seg_start[r] = st;
-    }
-    const uint32_t k0 = st / 32, k1 = (st + slen[r] - 1) / 32;
-    atomicMin(&seg_first[k0], (uint32_t)r);
-    if (k1 != k0) atomicMin(&seg_first[k1], (uint32_t)r);
   }
 }
 
@@ -332,11 +345,9 @@ struct BuildLayout {
   uint64_t* adj;
   uint32_t* eid;
   uint32_t* ekey;
-  uint32_t* lists;       // giant | hub | medium lists
-  uint32_t* seg_row;     // short lists, vertex order
-  uint32_t* seg_start;   // their starts in the concatenation (+ total)
-  uint32_t* seg_first;   // first short list touching each segment
-  int64_t seg_cap;
+  uint32_t* pair_ptr;
+  uint64_t* pairs;
+  uint32_t* lists;       // giant | hub | medium tasks
   uint32_t* vgraph;
   unsigned long long* gacc;
   unsigned long long* bacc;
@@ -347,7 +358,6 @@ struct BuildLayout {
   uint32_t* scan_tmp;
   uint32_t* mid_rows;
   uint32_t* huge_rows;
-  uint32_t* gsum;
   uint8_t* bucket;
   unsigned long long* stats;   // 4 + 4*48 counters, 4*48 cursors, 2 counters
   char* sort_tmp;
@@ -379,11 +389,9 @@ BuildLayout layout(void* ws, size_t cap, int64_t n, int64_t m, const ubt_graph_o
   L.adj = c.take<uint64_t>(std::max<int64_t>(m, 1));
   L.eid = c.take<uint32_t>(std::max<int64_t>(m, 1));
   L.ekey = has_key ? c.take<uint32_t>(std::max<int64_t>(m, 1)) : nullptr;
+  L.pair_ptr = c.take<uint32_t>(n + 1);
+  L.pairs = c.take<uint64_t>(std::max<int64_t>(m, 1));
   L.lists = c.take<uint32_t>(n1);
-  L.seg_row = c.take<uint32_t>(n1);
-  L.seg_start = c.take<uint32_t>(n + 1);
-  L.seg_cap = (m + 32 * (ng + 1)) / 32 + 2;
-  L.seg_first = c.take<uint32_t>(L.seg_cap);
   L.vgraph = batch ? c.take<uint32_t>(n1) : nullptr;
   L.gacc = c.take<unsigned long long>(std::max<int64_t>(m, 1));
   // per graph: T, sum_lo, sum_hi (expected counts) of a batch
@@ -395,7 +403,6 @@ BuildLayout layout(void* ws, size_t cap, int64_t n, int64_t m, const ubt_graph_o
   L.scan_tmp = c.take<uint32_t>(scan_tmp_words(std::max(n, ng)) + 2);
   L.mid_rows = c.take<uint32_t>(n1);
   L.huge_rows = c.take<uint32_t>(n1);
-  L.gsum = batch ? c.take<uint32_t>(ng + 1) : nullptr;
   L.bucket = c.take<uint8_t>(n1);
   L.stats = c.take<unsigned long long>(2 * kStats + 2);
   const int64_t lb = list_bound(n, m);
@@ -467,9 +474,10 @@ extern "C" ubt_status ubt_create_graph(int64_t n, int64_t m, const uint32_t* d_s
   if (ws_bytes < L.total) return UBT_ERR_WORKSPACE_TOO_SMALL;
   cudaStream_t s = (cudaStream_t)stream;
   const Tuning& T = tuning();
-  const int64_t short_max = std::min<int64_t>(std::max<int64_t>(2, T.short_max), 32);
-  const int64_t hub_thr = std::max<int64_t>(short_max, T.hub_threshold);
+  const int64_t hub_thr = std::max<int64_t>(2, T.hub_threshold);
   const int64_t giant_thr = std::max<int64_t>(hub_thr, T.smem_table_max / 4);
+  const int pull = T.pull ? 1 : 0;
+  const int64_t block_work = std::max<int64_t>(1, T.block_work);
 
   UBT_CUDA(cudaMemsetAsync(L.scratch, 0, sizeof(Scratch), s));
   UBT_CUDA(cudaMemsetAsync(&L.scratch->err, 0xFF, sizeof(unsigned long long), s));
@@ -528,24 +536,32 @@ extern "C" ubt_status ubt_create_graph(int64_t n, int64_t m, const uint32_t* d_s
   UBT_CUDA(cudaStreamSynchronize(s));
   st = status_from_err(err);
   if (st != UBT_OK) return st;
-  // 4. work lists: giant | hub | medium tasks, each by decreasing wedge-count
-  //    bucket; short lists concatenated in vertex order and cut into segments
+  // 4. pairs grouped by owner
+  UBT_CUDA(cudaMemsetAsync(L.pair_ptr, 0, sizeof(uint32_t) * (n + 1), s));
+  if (n > 0) {
+    UBT_CUDA(cudaMemsetAsync(L.fill, 0, sizeof(uint32_t) * (n + 1), s));
+    if (m > 0) k_pair_count<<<grid_w, thr, 0, s>>>(n, L.row_ptr, L.adj, pull, L.fill);
+    UBT_CUDA(exclusive_scan_u32(L.fill, L.pair_ptr, n, L.scan_tmp, s));
+    UBT_CUDA(cudaMemsetAsync(L.fill, 0, sizeof(uint32_t) * (n + 1), s));
+    if (m > 0) k_pair_fill<<<grid_w, thr, 0, s>>>(n, L.row_ptr, L.adj, pull, L.pair_ptr, L.fill, L.pairs);
+    UBT_CUDA(cudaGetLastError());
+  }
+  // 5. work lists: giant | hub | medium tasks, each by decreasing work bucket
   unsigned long long stats[kStats];
   memset(stats, 0, sizeof(stats));
   if (n > 0) {
-    k_row_stats<<<grid_w, thr, 0, s>>>(n, L.row_ptr, L.adj, (uint32_t)short_max, (uint32_t)hub_thr,
-                                      (uint32_t)giant_thr, L.bucket, L.fill, L.stats);
+    k_row_stats<<<grid_w, thr, 0, s>>>(n, L.row_ptr, L.adj, L.pair_ptr, L.pairs, (uint32_t)hub_thr,
+                                      (uint32_t)giant_thr, (unsigned long long)block_work, L.bucket, L.stats);
     UBT_CUDA(cudaMemcpyAsync(stats, L.stats, sizeof(stats), cudaMemcpyDeviceToHost, s));
     UBT_CUDA(cudaStreamSynchronize(s));
   }
   unsigned long long cursor[4 * (kLgMax + 1)];
   int64_t count_cls[4] = {0, 0, 0, 0};
   for (int b = 0; b < 4 * (kLgMax + 1); b++) count_cls[b % 4] += (int64_t)stats[4 + b];
-  int64_t run[4];
+  int64_t run[4] = {0, 0, 0, 0};
   run[kClsGiant] = 0;
   run[kClsHub] = count_cls[kClsGiant];
   run[kClsMedium] = count_cls[kClsGiant] + count_cls[kClsHub];
-  run[kClsShort] = 0;
   for (int lg = kLgMax; lg >= 0; lg--) {
     for (int cls = 1; cls < 4; cls++) {
       const int b = lg * 4 + cls;
@@ -553,37 +569,14 @@ extern "C" ubt_status ubt_create_graph(int64_t n, int64_t m, const uint32_t* d_s
       run[cls] += (int64_t)stats[4 + b];
     }
   }
-  const int64_t n_srows = (int64_t)stats[3];
-  uint32_t seg_total = 0;
   if (n > 0) {
     unsigned long long* dcur = L.stats + kStats;
     UBT_CUDA(cudaMemcpyAsync(dcur, cursor, sizeof(cursor), cudaMemcpyHostToDevice, s));
     k_fill_lists<<<grid_v, thr, 0, s>>>(n, L.bucket, dcur, L.lists);
-    // short lists: compaction in vertex order, then their starts
-    UBT_CUDA(exclusive_scan_u32(L.fill, L.deg, n, L.scan_tmp, s));
-    if (batch) UBT_CUDA(cudaMemsetAsync(L.gsum, 0, sizeof(uint32_t) * (ng + 1), s));
-    k_short_rows<<<grid_v, thr, 0, s>>>(n, L.fill, L.deg, L.row_ptr, L.vgraph, L.seg_row, L.mid_rows, L.gsum);
-    UBT_CUDA(exclusive_scan_u32(L.mid_rows, L.seg_start, n_srows, L.scan_tmp, s));
-    if (batch) {
-      const int grid_g = (int)std::min<int64_t>(std::max<int64_t>((ng + thr - 1) / thr, 1), (int64_t)sms * 32);
-      k_graph_pad<<<grid_g, thr, 0, s>>>(ng, L.gsum);
-      UBT_CUDA(exclusive_scan_u32(L.gsum, L.gsum, ng, L.scan_tmp, s));
-    }
-    uint32_t tot[2] = {0, 0};
-    UBT_CUDA(cudaMemcpyAsync(&tot[0], L.seg_start + n_srows, sizeof(uint32_t), cudaMemcpyDeviceToHost, s));
-    if (batch) UBT_CUDA(cudaMemcpyAsync(&tot[1], L.gsum + ng, sizeof(uint32_t), cudaMemcpyDeviceToHost, s));
-    UBT_CUDA(cudaMemsetAsync(L.seg_first, 0xFF, sizeof(uint32_t) * L.seg_cap, s));
-    if (n_srows > 0) {
-      const int grid_r = (int)std::min<int64_t>((n_srows + thr - 1) / thr, (int64_t)sms * 32);
-      k_seg_first<<<grid_r, thr, 0, s>>>(n_srows, L.seg_row, L.seg_start, L.mid_rows, L.vgraph, L.gsum,
-                                        L.seg_first);
-    }
     UBT_CUDA(cudaGetLastError());
     UBT_CUDA(cudaStreamSynchronize(s));
-    seg_total = tot[0] + tot[1];
   }
-  const int64_t n_segs = ((int64_t)seg_total + 31) / 32;
-  if (n_segs > L.seg_cap) return UBT_ERR_INVALID_ARG;
+  (void)ng;
 
   ubt_graph* g = new (std::nothrow) ubt_graph();
   if (!g) return UBT_ERR_INVALID_ARG;
@@ -595,17 +588,14 @@ extern "C" ubt_status ubt_create_graph(int64_t n, int64_t m, const uint32_t* d_s
   g->adj = L.adj;
   g->eid = L.eid;
   g->ekey = L.ekey ? L.ekey : L.eid;
+  g->pair_ptr = L.pair_ptr;
+  g->pairs = L.pairs;
   g->giant_list = L.lists;
   g->n_giant = count_cls[kClsGiant];
   g->hub_list = L.lists + count_cls[kClsGiant];
   g->n_hub = count_cls[kClsHub];
   g->med_list = L.lists + count_cls[kClsGiant] + count_cls[kClsHub];
   g->n_med = count_cls[kClsMedium];
-  g->seg_row = L.seg_row;
-  g->seg_start = L.seg_start;
-  g->seg_first = L.seg_first;
-  g->n_srows = n_srows;
-  g->n_segs = n_segs;
   g->vgraph = L.vgraph;
   g->gacc = L.gacc;
   g->bacc = L.bacc;
@@ -616,9 +606,11 @@ extern "C" ubt_status ubt_create_graph(int64_t n, int64_t m, const uint32_t* d_s
   g->wedges = (int64_t)stats[0];
   g->max_out = (int64_t)stats[1];
   g->max_hub_len = (int64_t)stats[2];
-  g->short_max = short_max;
+  g->probes = (int64_t)stats[3];
   g->hub_threshold = hub_thr;
   g->giant_threshold = giant_thr;
+  g->block_work = block_work;
+  g->pull = pull;
   g->device = dev;
   g->sm_count = sms;
   *h_out = g;
@@ -639,5 +631,6 @@ extern "C" ubt_status ubt_graph_get_info(const ubt_graph* g, ubt_graph_info* h_i
   h_info->hub_vertices = g->n_hub + g->n_giant;
   h_info->wedges = g->wedges;
   h_info->kind = g->kind;
+  h_info->probes = g->probes;
   return UBT_OK;
 }

@@ -20,6 +20,12 @@ namespace ubt {
 // entries a pruning level removes form a suffix of the row (Lemma 2); REAL
 // rows by neighbour id.
 // eid[pos] is the input index of the edge stored at CSR position pos.
+//
+// Pairs: every forward edge x-s is one pair of the traversal, owned by the
+// endpoint whose list becomes the hash table (the other endpoint's list is
+// streamed through it).  pair_ptr / pairs group the pairs by owner; a pair
+// word holds the streamed vertex s (low 32 bits) and the CSR position of the
+// edge (high 32 bits).
 
 constexpr uint32_t kEmpty = 0xFFFFFFFFu;
 constexpr int kWarp = 32;
@@ -73,12 +79,11 @@ struct ubt_graph {
   uint64_t* adj = nullptr;          // m
   uint32_t* eid = nullptr;          // m: input edge index per CSR position
   uint32_t* ekey = nullptr;         // m: Philox key per CSR position
-  uint32_t* giant_list = nullptr;   // lists too long for a shared-memory table
-  uint32_t* hub_list = nullptr;     // long lists: whole-block tasks
-  uint32_t* med_list = nullptr;     // medium lists: one-warp tasks
-  uint32_t* seg_row = nullptr;      // short lists (vertex order)
-  uint32_t* seg_start = nullptr;    // their starts in the concatenation
-  uint32_t* seg_first = nullptr;    // first short list of every 32-pair segment
+  uint32_t* pair_ptr = nullptr;     // n + 1: pairs of owner x are [pair_ptr[x], pair_ptr[x+1])
+  uint64_t* pairs = nullptr;        // m: streamed vertex | CSR position << 32
+  uint32_t* giant_list = nullptr;   // owners whose list is too long for a shared-memory table
+  uint32_t* hub_list = nullptr;     // long lists or heavy owners: whole-block tasks
+  uint32_t* med_list = nullptr;     // the other owners: one-warp tasks
   uint32_t* vgraph = nullptr;       // batch: graph id of every vertex (or null)
   unsigned long long* gacc = nullptr;   // m: backward accumulators
   unsigned long long* bacc = nullptr;   // batch accumulators
@@ -87,9 +92,9 @@ struct ubt_graph {
   int64_t gtab_blocks = 0;          // blocks that have one
   ubt::Scratch* scratch = nullptr;
   // sizes recorded at build time
-  int64_t n_giant = 0, n_hub = 0, n_med = 0, n_srows = 0, n_segs = 0;
-  int64_t max_out = 0, max_hub_len = 0, wedges = 0;
-  int64_t short_max = 0, hub_threshold = 0, giant_threshold = 0;
+  int64_t n_giant = 0, n_hub = 0, n_med = 0;
+  int64_t max_out = 0, max_hub_len = 0, wedges = 0, probes = 0;
+  int64_t hub_threshold = 0, giant_threshold = 0, block_work = 0, pull = 1;
   int device = 0, sm_count = 0;
 };
 
@@ -98,8 +103,9 @@ namespace ubt {
 // ---------------------------------------------------------------- tuning
 
 struct Tuning {
-  int64_t short_max = 8;          // lists up to this length go to segments
-  int64_t hub_threshold = 128;    // longer lists are whole-block tasks
+  int64_t pull = 1;               // 1: each pair streams the shorter list; 0: always N>(v) (Alg. 1)
+  int64_t block_work = 1 << 14;   // owners streaming more entries are whole-block tasks
+  int64_t hub_threshold = 128;    // owners with longer lists are whole-block tasks
   int64_t block_threads = 512;    // threads of the block-task kernel
   int64_t warp_threads = 128;     // threads of the warp-task kernel (at most 128)
   int64_t blocks_per_sm = 32;     // cap on resident blocks (occupancy decides below it)

@@ -503,41 +503,51 @@ __global__ void k_finish_adjoint(int64_t m, const unsigned long long* __restrict
     grad[eid[i]] = (float)(g * (double)(long long)acc[i]);
 }
 
-// traversal sizes (same pruning rules as the traversal); one warp per vertex
+// traversal sizes (same task and pruning rules as the traversal); one warp
+// per owner.  out: [0] table entries, [1] pairs probed, [2] streamed
+// entries, [3] tasks
 __global__ void k_trav_stats(int64_t n, const uint32_t* __restrict__ row_ptr, const uint64_t* __restrict__ adj,
-                             int64_t L, unsigned long long* out) {
+                             const uint32_t* __restrict__ pair_ptr, const uint64_t* __restrict__ pairs, int64_t L,
+                             unsigned long long* out) {
   const int lane = (int)lane_id();
   const int64_t warps = (int64_t)gridDim.x * (blockDim.x >> 5);
-  unsigned long long tab = 0, str = 0, tasks = 0;
-  for (int64_t u = blockIdx.x * (int64_t)(blockDim.x >> 5) + (threadIdx.x >> 5); u < n; u += warps) {
-    const uint32_t rs = row_ptr[u];
-    uint32_t len = row_ptr[u + 1] - rs;
-    if (len < 2) continue;
+  unsigned long long tab = 0, npairs = 0, str = 0, tasks = 0;
+  for (int64_t x = blockIdx.x * (int64_t)(blockDim.x >> 5) + (threadIdx.x >> 5); x < n; x += warps) {
+    const uint32_t rs = row_ptr[x];
+    uint32_t len = row_ptr[x + 1] - rs;
+    const uint32_t ps = pair_ptr[x], pe = pair_ptr[x + 1];
+    if (len < 2 || pe == ps) continue;
     int64_t qmax = 0;
     if (L > 0) {
       qmax = qabs(adj_valbits(adj[rs]));
-      len = prune_prefix(adj + rs, len, qmax * 32768, L);
+      len = prune_prefix(adj + rs, len, 1ll << 30, L);
     }
+    if (len == 0) continue;
     if (lane == 0) {
       tab += len;
       tasks += 1;
     }
-    for (uint32_t i = lane; i < len; i += 32) {
-      const uint64_t e = adj[rs + i];
-      const uint32_t v = adj_col(e);
-      const uint32_t vs = row_ptr[v];
-      uint32_t dv = row_ptr[v + 1] - vs;
-      if (L > 0) dv = prune_prefix(adj + vs, dv, qabs(adj_valbits(e)) * qmax, L);
+    for (uint32_t i = ps + lane; i < pe; i += 32) {
+      const uint64_t d = pairs[i];
+      const uint32_t sv = (uint32_t)d;
+      const int64_t qe = qabs(adj_valbits(adj[(uint32_t)(d >> 32)]));
+      if (L > 0 && qe * (1ll << 30) < L) continue;
+      const uint32_t vs = row_ptr[sv];
+      uint32_t dv = row_ptr[sv + 1] - vs;
+      if (L > 0) dv = prune_prefix(adj + vs, dv, qe * qmax, L);
+      npairs += 1;
       str += dv;
     }
   }
   tab = warp_sum(tab);
+  npairs = warp_sum(npairs);
   str = warp_sum(str);
   tasks = warp_sum(tasks);
   if (lane == 0) {
     atomicAdd(&out[0], tab);
-    atomicAdd(&out[1], str);
-    atomicAdd(&out[2], tasks);
+    atomicAdd(&out[1], npairs);
+    atomicAdd(&out[2], str);
+    atomicAdd(&out[3], tasks);
   }
 }
 
@@ -551,17 +561,14 @@ TravArgs make_trav_args(const ubt_graph* g, int64_t L, bool with_pos) {
   TravArgs a;
   a.row_ptr = g->row_ptr;
   a.adj = g->adj;
+  a.pair_ptr = g->pair_ptr;
+  a.pairs = g->pairs;
   a.giant_list = g->giant_list;
   a.hub_list = g->hub_list;
   a.med_list = g->med_list;
-  a.seg_row = g->seg_row;
-  a.seg_start = g->seg_start;
-  a.seg_first = g->seg_first;
   a.n_giant = (uint32_t)g->n_giant;
   a.n_hub = (uint32_t)g->n_hub;
   a.n_med = (uint32_t)g->n_med;
-  a.n_srows = (uint32_t)g->n_srows;
-  a.n_segs = (uint32_t)g->n_segs;
   a.n = (uint32_t)g->n;
   a.m = (uint32_t)g->m;
   a.sc = g->scratch;
@@ -569,8 +576,8 @@ TravArgs make_trav_args(const ubt_graph* g, int64_t L, bool with_pos) {
   a.gtab_slots = (uint32_t)g->gtab_slots;
   a.gtab_blocks = g->n_giant ? (uint32_t)g->gtab_blocks : 0u;
   a.hub_slots = g->n_hub ? (uint32_t)table_slots(g->max_hub_len) : 0u;
-  // a warp table holds one medium list or the lists one segment touches
-  a.warp_slots = (uint32_t)std::max(table_slots(g->hub_threshold), table_slots(32 + 2 * (g->short_max - 1)));
+  // a warp table holds one medium task's list (at most hub_threshold entries)
+  a.warp_slots = (uint32_t)table_slots(g->hub_threshold);
   a.unit = (uint32_t)std::min<int64_t>(32, std::max<int64_t>(1, T.block_unit));
   a.batch = (uint32_t)std::max<int64_t>(1, T.small_batch);
   a.L = L;
@@ -749,19 +756,16 @@ extern "C" ubt_status ubt_traversal_stats(ubt_graph* g, const double* h_tau, int
   }
   cudaStream_t s = (cudaStream_t)stream;
   unsigned long long* d = &g->scratch->hist[0];
-  UBT_CUDA(cudaMemsetAsync(d, 0, 3 * sizeof(unsigned long long), s));
+  UBT_CUDA(cudaMemsetAsync(d, 0, 4 * sizeof(unsigned long long), s));
   if (g->n > 0) {
     const int grid = (int)std::min<int64_t>((g->n + 7) / 8, (int64_t)g->sm_count * 16);
-    k_trav_stats<<<grid, 256, 0, s>>>(g->n, g->row_ptr, g->adj, L, d);
+    k_trav_stats<<<grid, 256, 0, s>>>(g->n, g->row_ptr, g->adj, g->pair_ptr, g->pairs, L, d);
     UBT_CUDA(cudaGetLastError());
   }
-  unsigned long long h[3];
+  unsigned long long h[4];
   UBT_CUDA(cudaMemcpyAsync(h, d, sizeof(h), cudaMemcpyDeviceToHost, s));
   UBT_CUDA(cudaStreamSynchronize(s));
-  h_out[0] = (int64_t)h[0];
-  h_out[1] = (int64_t)h[0];
-  h_out[2] = (int64_t)h[1];
-  h_out[3] = (int64_t)h[2];
+  for (int i = 0; i < 4; i++) h_out[i] = (int64_t)h[i];
   return UBT_OK;
 }
 
@@ -789,14 +793,24 @@ extern "C" ubt_status ubt_graph_export(const ubt_graph* g, uint32_t* h_row_ptr, 
   const int64_t tasks = g->n_giant + g->n_hub + g->n_med;
   if (h_lists && tasks)
     UBT_CUDA(cudaMemcpyAsync(h_lists, g->giant_list, sizeof(uint32_t) * tasks, cudaMemcpyDeviceToHost, s));
-  if (h_lists && g->n_srows)
-    UBT_CUDA(cudaMemcpyAsync(h_lists + tasks, g->seg_row, sizeof(uint32_t) * g->n_srows, cudaMemcpyDeviceToHost, s));
   if (h_list_sizes) {
     h_list_sizes[0] = g->n_giant;
     h_list_sizes[1] = g->n_hub;
     h_list_sizes[2] = g->n_med;
-    h_list_sizes[3] = g->n_srows;
+    h_list_sizes[3] = 0;
   }
+  UBT_CUDA(cudaStreamSynchronize(s));
+  return UBT_OK;
+}
+
+extern "C" ubt_status ubt_graph_export_pairs(const ubt_graph* g, uint32_t* h_pair_ptr, uint64_t* h_pairs,
+                                             void* stream) {
+  if (!g) return UBT_ERR_INVALID_ARG;
+  cudaStream_t s = (cudaStream_t)stream;
+  if (h_pair_ptr)
+    UBT_CUDA(cudaMemcpyAsync(h_pair_ptr, g->pair_ptr, sizeof(uint32_t) * (g->n + 1), cudaMemcpyDeviceToHost, s));
+  if (h_pairs && g->m)
+    UBT_CUDA(cudaMemcpyAsync(h_pairs, g->pairs, sizeof(uint64_t) * g->m, cudaMemcpyDeviceToHost, s));
   UBT_CUDA(cudaStreamSynchronize(s));
   return UBT_OK;
 }

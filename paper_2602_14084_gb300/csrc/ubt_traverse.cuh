@@ -1,42 +1,47 @@
 // ubt_traverse.cuh -- the triangle traversal every query runs.
 //
 // Forward edge iteration under Node Order (Alg. 1, Sec. 4): triangle {u,v,w}
-// with u < v < w in Node Order is found exactly once, from u, as
-// w in N>(u) n N>(v) for v in N>(u).  Each forward edge (u, v) is a "pair";
-// its work is to probe every w of N>(v) against N>(u).
+// with u < v < w in Node Order is found exactly once, from its pair (u, v),
+// as w in N>(u) n N>(v).  Every forward edge is one pair.  Alg. 1 streams
+// N>(v) through a table of N>(u); streaming N>(u) through a table of N>(v)
+// intersects the same two lists, and the build gives each pair to the
+// endpoint (its "owner" x) whose list is the longer, so that the shorter list
+// N>(s) is streamed (the pair partition of ubt_build.cu).
 //
-// GPU layout of that loop (one persistent kernel, four kinds of task):
-//   * N>(u) is loaded into an open-addressing hash table (neighbour -> edge
+// GPU layout of that loop (two persistent kernels, three kinds of task):
+//   * N>(x) is loaded into an open-addressing hash table (neighbour -> edge
 //     value, CSR position) in shared memory: 4-slot buckets read with one
 //     16-byte load, at most 1/4 full, so nearly every probe is one load.
-//   * The pairs of a task are handed to one warp 32 at a time.  The lists N>(v)
+//   * The pairs of x are handed to one warp 32 at a time.  The lists N>(s)
 //     are streamed with coalesced 8-byte loads: long lists one after another
 //     by the whole warp, short lists concatenated ("flattened") so that every
-//     lane has an entry; two entries per lane are in flight at once.  Each
-//     entry w is probed in u's table; a hit is a triangle and goes to the
-//     visitor with the three edge values and CSR positions.
-//   * Task kinds, by |N>(u)|:
-//       giant   longer than the shared-memory table: whole block, table in a
-//               per-block slice of global memory
-//       hub     whole block, shared table, warps take `unit` pairs at a time
-//       medium  one warp, its own table
-//       short   segments: the short lists, concatenated in vertex order, are
-//               cut into runs of 32 pairs; one warp takes a run, puts every
-//               list the run touches into one table and probes with the row
-//               of each pair's u (CSR positions identify the row)
+//     lane has an entry.  Each entry w is probed in x's table; a hit is a
+//     triangle and goes to the visitor with the three edge values and CSR
+//     positions.
+//   * Task kinds, by owner:
+//       giant   list longer than the shared-memory table: whole block, table
+//               in a per-block slice of global memory
+//       hub     long list or heavy streamed work: whole block, shared table,
+//               warps take `unit` pairs at a time
+//       medium  the rest: one warp, its own table
 //   * Probability pruning (FIXED graphs, level L > 0): every list is sorted by
 //     |q| descending, so the entries that cannot reach |P| >= L are suffixes:
-//       u's table and pairs:   |q_e| * qmax(u) * 2^15 >= L   (Lemma 2: each
-//                              edge bounds the product of the triangle)
-//       v's list for pair u-v: |q_vw| * |q_uv| * qmax(u) >= L (order-free form
-//                              of Lemma 3: the other two edges bound it)
-//     qmax(u) is the largest |q| in N>(u) (its first entry).
+//       table and pairs:   |q_e| * 2^30 >= L              (Lemma 2: the other
+//                                                         two factors are at
+//                                                         most 2^15)
+//       streamed N>(s):    |q_sw| * |q_xs| * qmax(x) >= L (order-free form of
+//                                                         Lemma 3: the other
+//                                                         two edges bound it)
+//     qmax(x) is the largest |q| in N>(x) (its first entry).
 //
 // Visitors implement: smem_bytes(threads) (shared memory they need) /
 // block_init / task_begin / step (called by all 32 lanes of a warp, converged,
 // once per probed entry with a hit flag) / task_end / block_end.  Visitors
 // with kBatched also take the hits of U probes of one long list at once
-// (steps<U>: hit flags and the u-w and v-w edge values; u-v is common).
+// (steps<U>: hit flags and the two streamed-edge values; the pair's is common).
+// A visitor sees a triangle as (x, s, w): the pair edge x-s, the table edge
+// x-w and the streamed edge s-w; under pull x is the later vertex of the pair,
+// so visitors treat the three edges symmetrically (they all do).
 #pragma once
 
 #include <algorithm>
@@ -57,13 +62,12 @@ namespace ubt {
 struct TravArgs {
   const uint32_t* row_ptr;
   const uint64_t* adj;
+  const uint32_t* pair_ptr;    // pairs of owner x: [pair_ptr[x], pair_ptr[x + 1])
+  const uint64_t* pairs;       // streamed vertex | CSR position of the pair edge << 32
   const uint32_t* giant_list;
   const uint32_t* hub_list;
   const uint32_t* med_list;
-  const uint32_t* seg_row;     // short lists' vertices, in vertex order
-  const uint32_t* seg_start;   // start of each short list in the concatenation
-  const uint32_t* seg_first;   // first short list touching each 32-pair segment (kEmpty: none)
-  uint32_t n_giant, n_hub, n_med, n_srows, n_segs;
+  uint32_t n_giant, n_hub, n_med;
   uint32_t n, m;            // vertices, edges (bounds of the self-checks)
   Scratch* sc;              // task counters (zeroed before launch)
   uint32_t* gtab;           // giant tables: gtab_blocks x gtab_slots x 3 words
@@ -72,7 +76,7 @@ struct TravArgs {
   uint32_t hub_slots;       // shared-memory hub table capacity (power of two)
   uint32_t warp_slots;      // per-warp table capacity (power of two)
   uint32_t unit;            // pairs per warp step in block tasks
-  uint32_t batch;           // warp tasks / segments taken per grab
+  uint32_t batch;           // warp tasks taken per grab
   int64_t L;                // prune level, 0 = none
 };
 
@@ -153,84 +157,61 @@ __device__ __forceinline__ void table_insert(const Table& t, uint32_t w, uint32_
   guard_fail(sc, kGuardInsert, w);
 }
 
-// Find w in the table.  kRow: the table holds several rows (a segment) and
-// only entries whose CSR position lies in [rs, rs + rlen) -- the row of this
-// pair's u -- count.  kPos: also return the entry's CSR position.
+// Find w in the table (kPos: also return the entry's CSR position).
 //
 // Inserts take the first free slot of a bucket and nothing is ever removed,
 // so a bucket's used slots are a prefix and a bucket has room iff its last
 // slot is empty; a key missing from a bucket with room is absent.  With at
 // most 1/4 of the slots used, nearly every lookup reads one bucket and takes
 // no branch.
-template <bool kRow, bool kPos>
-__device__ __forceinline__ bool table_find(const Table& t, uint32_t w, uint32_t rs, uint32_t rlen, uint32_t& val,
-                                           uint32_t& pos, Scratch* sc) {
+template <bool kPos>
+__device__ __forceinline__ bool table_find(const Table& t, uint32_t w, uint32_t& val, uint32_t& pos, Scratch* sc) {
   uint32_t b = hash_slot(w, t.shift);
-  if (!kRow) {
-    const uint4 k = reinterpret_cast<const uint4*>(t.key)[b];
-    const bool m0 = k.x == w, m1 = k.y == w, m2 = k.z == w, m3 = k.w == w;
-    bool hit = m0 | m1 | m2 | m3;
-    uint32_t s = 4 * b + (m0 ? 0u : (m1 ? 1u : (m2 ? 2u : 3u)));
-    if (!hit && k.w != kEmpty) {  // the home bucket is full: continue in the next ones
-      bool ended = false;
-      for (uint32_t it = 1; it <= t.bmask; it++) {
-        b = (b + 1) & t.bmask;
-        const uint4 kk = reinterpret_cast<const uint4*>(t.key)[b];
-        const bool n0 = kk.x == w, n1 = kk.y == w, n2 = kk.z == w, n3 = kk.w == w;
-        if (n0 | n1 | n2 | n3) {
-          hit = true;
-          s = 4 * b + (n0 ? 0u : (n1 ? 1u : (n2 ? 2u : 3u)));
-          ended = true;
-          break;
-        }
-        if (kk.w == kEmpty) {
-          ended = true;
-          break;
-        }
+  const uint4 k = reinterpret_cast<const uint4*>(t.key)[b];
+  const bool m0 = k.x == w, m1 = k.y == w, m2 = k.z == w, m3 = k.w == w;
+  bool hit = m0 | m1 | m2 | m3;
+  uint32_t s = 4 * b + (m0 ? 0u : (m1 ? 1u : (m2 ? 2u : 3u)));
+  if (!hit && k.w != kEmpty) {  // the home bucket is full: continue in the next ones
+    bool ended = false;
+    for (uint32_t it = 1; it <= t.bmask; it++) {
+      b = (b + 1) & t.bmask;
+      const uint4 kk = reinterpret_cast<const uint4*>(t.key)[b];
+      const bool n0 = kk.x == w, n1 = kk.y == w, n2 = kk.z == w, n3 = kk.w == w;
+      if (n0 | n1 | n2 | n3) {
+        hit = true;
+        s = 4 * b + (n0 ? 0u : (n1 ? 1u : (n2 ? 2u : 3u)));
+        ended = true;
+        break;
       }
-      if (!ended) guard_fail(sc, kGuardFind, w);
-    }
-    if (hit) {
-      val = t.val[s];
-      if (kPos) pos = t.pos[s];
-    }
-    return hit;
-  }
-  for (uint32_t it = 0; it <= t.bmask; it++) {
-    const uint4 k = reinterpret_cast<const uint4*>(t.key)[b];
-    unsigned mt = (k.x == w ? 1u : 0u) | (k.y == w ? 2u : 0u) | (k.z == w ? 4u : 0u) | (k.w == w ? 8u : 0u);
-    while (mt) {
-      const uint32_t s = 4 * b + (__ffs(mt) - 1);
-      mt &= mt - 1;
-      const uint32_t p = t.pos[s];
-      if (p - rs < rlen) {
-        val = t.val[s];
-        pos = p;
-        return true;
+      if (kk.w == kEmpty) {
+        ended = true;
+        break;
       }
     }
-    if (k.w == kEmpty) return false;
-    b = (b + 1) & t.bmask;
+    if (!ended) guard_fail(sc, kGuardFind, w);
   }
-  guard_fail(sc, kGuardFind, w);
-  return false;
+  if (hit) {
+    val = t.val[s];
+    if (kPos) pos = t.pos[s];
+  }
+  return hit;
 }
 
-// Per-lane description of one pair (u, v) handed to probe_pairs.
+// Per-lane description of one pair handed to probe_pairs: owner x (its list
+// is the table), streamed vertex s, CSR position and value of the x-s edge.
 struct Pair {
-  uint32_t u, v, puv, quv;  // vertices, CSR position and value of the u-v edge
-  uint32_t urs, ulen;       // u's row as seen by the table (for row matching)
-  int64_t qmax;             // largest |q| of u's list (pruning)
+  uint32_t x, s, pe, qe;
+  int64_t qmax;  // largest |q| of x's list (pruning)
   bool ok;
 };
 
 // The whole warp probes entries [off, off + 32 U) of one long list N>(v),
 // U entries per lane, all loads issued before the probes.  kAll: all 32 U
 // entries exist (no bounds tests).
-template <class V, bool kRow, int U, bool kAll>
+template <class V, int U, bool kAll>
 __device__ __forceinline__ void long_steps(const uint64_t* __restrict__ adj, Scratch* sc, V& vis, const Table& t,
                                            int lane, uint32_t uj, uint32_t vj, uint32_t vsj, uint32_t dvj,
-                                           uint32_t qj, uint32_t pj, uint32_t rsj, uint32_t rlj, uint32_t off) {
+                                           uint32_t qj, uint32_t pj, uint32_t off) {
   uint64_t e[U];
 #pragma unroll
   for (int s = 0; s < U; s++) {
@@ -247,7 +228,7 @@ __device__ __forceinline__ void long_steps(const uint64_t* __restrict__ adj, Scr
       uint32_t puw = 0;
       quw[s] = 0;
       qvw[s] = adj_valbits(e[s]);
-      hit[s] = (kAll || i < dvj) && table_find<kRow, false>(t, adj_col(e[s]), rsj, rlj, quw[s], puw, sc);
+      hit[s] = (kAll || i < dvj) && table_find<false>(t, adj_col(e[s]), quw[s], puw, sc);
     }
     vis.template steps<U>(hit, qj, quw, qvw);
   } else {
@@ -255,7 +236,7 @@ __device__ __forceinline__ void long_steps(const uint64_t* __restrict__ adj, Scr
     for (int s = 0; s < U; s++) {
       const uint32_t i = off + 32 * s + lane;
       uint32_t quw = 0, puw = 0;
-      const bool hit = (kAll || i < dvj) && table_find<kRow, V::kPos>(t, adj_col(e[s]), rsj, rlj, quw, puw, sc);
+      const bool hit = (kAll || i < dvj) && table_find<V::kPos>(t, adj_col(e[s]), quw, puw, sc);
       if (kAll || off + 32 * s < dvj)
         vis.step(hit, uj, vj, adj_col(e[s]), qj, quw, adj_valbits(e[s]), pj, puw, vsj + i);
     }
@@ -263,25 +244,24 @@ __device__ __forceinline__ void long_steps(const uint64_t* __restrict__ adj, Scr
 }
 
 // One warp probes the lists of up to 32 pairs (one per lane, `ok` lanes).
-// kRow: the table is a segment table (entries must belong to the pair's row).
-template <class V, bool kRow>
+template <class V>
 __device__ __forceinline__ void probe_pairs(const TravArgs& a, V& vis, const Table& t, const Pair& pr) {
   const int lane = (int)lane_id();
   const uint64_t* __restrict__ adj = a.adj;
   Scratch* const sc = a.sc;
   uint32_t vs = 0, dv = 0;
   if (pr.ok) {
-    if (pr.v < a.n) {
-      vs = a.row_ptr[pr.v];
-      const uint32_t ve = a.row_ptr[pr.v + 1];
+    if (pr.s < a.n) {
+      vs = a.row_ptr[pr.s];
+      const uint32_t ve = a.row_ptr[pr.s + 1];
       if (ve >= vs && ve <= a.m) {
         dv = ve - vs;
-        if (a.L > 0) dv = prune_prefix(a.adj + vs, dv, qabs(pr.quv) * pr.qmax, a.L);
+        if (a.L > 0) dv = prune_prefix(a.adj + vs, dv, qabs(pr.qe) * pr.qmax, a.L);
       } else {
-        guard_fail(a.sc, kGuardList, pr.v);
+        guard_fail(a.sc, kGuardList, pr.s);
       }
     } else {
-      guard_fail(a.sc, kGuardVertex, pr.v);
+      guard_fail(a.sc, kGuardVertex, pr.s);
     }
   }
   // long lists: one at a time, the whole warp streams it, up to four entries per lane
@@ -290,21 +270,19 @@ __device__ __forceinline__ void probe_pairs(const TravArgs& a, V& vis, const Tab
   while (longm) {
     const int j = __ffs(longm) - 1;
     longm &= longm - 1;
-    const uint32_t uj = __shfl_sync(kFull, pr.u, j);
-    const uint32_t vj = __shfl_sync(kFull, pr.v, j);
+    const uint32_t uj = __shfl_sync(kFull, pr.x, j);
+    const uint32_t vj = __shfl_sync(kFull, pr.s, j);
     const uint32_t vsj = __shfl_sync(kFull, vs, j);
     const uint32_t dvj = __shfl_sync(kFull, dv, j);
-    const uint32_t qj = __shfl_sync(kFull, pr.quv, j);
-    const uint32_t pj = __shfl_sync(kFull, pr.puv, j);
-    const uint32_t rsj = __shfl_sync(kFull, pr.urs, j);
-    const uint32_t rlj = __shfl_sync(kFull, pr.ulen, j);
+    const uint32_t qj = __shfl_sync(kFull, pr.qe, j);
+    const uint32_t pj = __shfl_sync(kFull, pr.pe, j);
     uint32_t off = 0;
     while (dvj - off >= 128) {
-      long_steps<V, kRow, 4, true>(adj, sc, vis, t, lane, uj, vj, vsj, dvj, qj, pj, rsj, rlj, off);
+      long_steps<V, 4, true>(adj, sc, vis, t, lane, uj, vj, vsj, dvj, qj, pj, off);
       off += 128;
     }
     while (off < dvj) {
-      long_steps<V, kRow, 2, false>(adj, sc, vis, t, lane, uj, vj, vsj, dvj, qj, pj, rsj, rlj, off);
+      long_steps<V, 2, false>(adj, sc, vis, t, lane, uj, vj, vsj, dvj, qj, pj, off);
       off += 64;
     }
   }
@@ -342,68 +320,83 @@ __device__ __forceinline__ void probe_pairs(const TravArgs& a, V& vis, const Tab
 #pragma unroll
     for (int s = 0; s < 2; s++) {
       const int j = (int)jj[s];
-      const uint32_t rsj = __shfl_sync(kFull, pr.urs, j);
-      const uint32_t rlj = __shfl_sync(kFull, pr.ulen, j);
       uint32_t quw = 0, puw = 0;
-      const bool hit = act[s] && table_find<kRow, V::kPos>(t, adj_col(e[s]), rsj, rlj, quw, puw, sc);
-      const uint32_t uj = __shfl_sync(kFull, pr.u, j);
-      const uint32_t vj = __shfl_sync(kFull, pr.v, j);
-      const uint32_t qj = __shfl_sync(kFull, pr.quv, j);
-      const uint32_t pj = __shfl_sync(kFull, pr.puv, j);
+      const bool hit = act[s] && table_find<V::kPos>(t, adj_col(e[s]), quw, puw, sc);
+      const uint32_t uj = __shfl_sync(kFull, pr.x, j);
+      const uint32_t vj = __shfl_sync(kFull, pr.s, j);
+      const uint32_t qj = __shfl_sync(kFull, pr.qe, j);
+      const uint32_t pj = __shfl_sync(kFull, pr.pe, j);
       if (s == 0 || base + 32 < total)
         vis.step(hit, uj, vj, adj_col(e[s]), qj, quw, adj_valbits(e[s]), pj, puw, f[s]);
     }
   }
 }
 
-// Pair of this lane among the pairs [cs, cs + cnt) of a single-row table.
-__device__ __forceinline__ Pair row_pair(const TravArgs& a, uint32_t u, int64_t qmax, uint32_t cs, uint32_t cnt) {
+// This lane's pair among the pairs [ps, ps + cnt) of owner x.  A pair whose
+// edge fails Lemma 2 (|q_e| 2^30 < L) cannot be in a classified triangle.
+__device__ __forceinline__ Pair owner_pair(const TravArgs& a, uint32_t x, int64_t qmax, uint32_t ps, uint32_t cnt) {
   const int lane = (int)lane_id();
   Pair pr;
-  pr.u = u;
-  pr.urs = 0;
-  pr.ulen = ~0u;
+  pr.x = x;
   pr.qmax = qmax;
   pr.ok = (uint32_t)lane < cnt;
-  pr.puv = cs + lane;
-  const uint64_t e = pr.ok ? a.adj[pr.puv] : 0ull;
-  pr.v = adj_col(e);
-  pr.quv = adj_valbits(e);
+  const uint64_t d = pr.ok ? a.pairs[ps + lane] : 0ull;
+  pr.s = (uint32_t)d;
+  pr.pe = (uint32_t)(d >> 32);
+  if (pr.ok && pr.pe >= a.m) {
+    guard_fail(a.sc, kGuardList, x);
+    pr.ok = false;
+  }
+  const uint64_t e = pr.ok ? a.adj[pr.pe] : 0ull;
+  pr.qe = adj_valbits(e);
+  if (a.L > 0 && qabs(pr.qe) * (1ll << 30) < a.L) pr.ok = false;
   return pr;
 }
 
-// u's list length after pruning (and qmax); identical in every calling thread
-__device__ __forceinline__ uint32_t pruned_len(const TravArgs& a, uint32_t rs, uint32_t len, int64_t& qmax) {
+// Entries of x's list that go into its table (the Lemma 2 prefix) and qmax(x);
+// identical in every calling thread.
+__device__ __forceinline__ uint32_t table_len(const TravArgs& a, uint32_t rs, uint32_t len, int64_t& qmax) {
   qmax = 0;
   if (a.L > 0 && len > 0) {
     qmax = qabs(adj_valbits(a.adj[rs]));
-    return prune_prefix(a.adj + rs, len, qmax * 32768, a.L);
+    return prune_prefix(a.adj + rs, len, 1ll << 30, a.L);
   }
   return len;
 }
 
-// A whole block handles u; `tab` is shared memory (hub) or a global slice (giant).
+// Pair range of owner x, checked against the pair array's bounds.
+__device__ __forceinline__ bool pair_range(const TravArgs& a, uint32_t x, uint32_t& ps, uint32_t& np) {
+  ps = a.pair_ptr[x];
+  const uint32_t pe = a.pair_ptr[x + 1];
+  if (pe < ps || pe > a.m) return false;
+  np = pe - ps;
+  return true;
+}
+
+// A whole block handles owner x; `tab` is shared memory (hub) or a global
+// slice (giant).
 template <class V>
-__device__ __forceinline__ void block_task(const TravArgs& a, V& vis, uint32_t u, uint32_t* tab, uint32_t cap,
+__device__ __forceinline__ void block_task(const TravArgs& a, V& vis, uint32_t x, uint32_t* tab, uint32_t cap,
                                            uint32_t* s_misc) {
   const int tid = threadIdx.x, lane = tid & 31;
-  if (u >= a.n) {
-    if (tid == 0) guard_fail(a.sc, kGuardVertex, u);
+  if (x >= a.n) {
+    if (tid == 0) guard_fail(a.sc, kGuardVertex, x);
     return;
   }
-  const uint32_t rs = a.row_ptr[u], re = a.row_ptr[u + 1];
-  if (re < rs || re > a.m) {
-    if (tid == 0) guard_fail(a.sc, kGuardList, u);
+  const uint32_t rs = a.row_ptr[x], re = a.row_ptr[x + 1];
+  uint32_t ps = 0, np = 0;
+  if (re < rs || re > a.m || !pair_range(a, x, ps, np)) {
+    if (tid == 0) guard_fail(a.sc, kGuardList, x);
     return;
   }
   int64_t qmax = 0;
-  if (tid == 0) s_misc[0] = pruned_len(a, rs, re - rs, qmax);
+  if (tid == 0) s_misc[0] = table_len(a, rs, re - rs, qmax);
   __syncthreads();
   const uint32_t len = s_misc[0];
   if (a.L > 0 && len > 0) qmax = qabs(adj_valbits(a.adj[rs]));
   const uint32_t slots = slots_for(len);
-  if (len == 0 || slots > cap) {
-    if (len && tid == 0) guard_fail(a.sc, kGuardTable, u);
+  if (len == 0 || np == 0 || slots > cap) {
+    if (len && np && slots > cap && tid == 0) guard_fail(a.sc, kGuardTable, x);
     __syncthreads();
     return;
   }
@@ -416,47 +409,48 @@ __device__ __forceinline__ void block_task(const TravArgs& a, V& vis, uint32_t u
     table_insert(t, adj_col(e), adj_valbits(e), rs + i, a.sc);
   }
   __syncthreads();
-  vis.task_begin(u);
-  // warps take pairs `unit` at a time, fewer as the list runs out, so that
+  vis.task_begin(x);
+  // warps take pairs `unit` at a time, fewer as the pairs run out, so that
   // they reach the closing barrier at about the same time
   const uint32_t nw = blockDim.x >> 5;
   while (true) {
     uint32_t c = 0, cnt = 0;
     if (lane == 0) {
       const uint32_t seen = *(volatile uint32_t*)&s_misc[1];
-      const uint32_t rem = seen < len ? len - seen : 0u;
+      const uint32_t rem = seen < np ? np - seen : 0u;
       const uint32_t want = max(1u, min(a.unit, rem / (2 * nw)));
       c = atomicAdd(&s_misc[1], want);
-      cnt = c < len ? min(want, len - c) : 0u;
+      cnt = c < np ? min(want, np - c) : 0u;
     }
     c = __shfl_sync(kFull, c, 0);
     cnt = __shfl_sync(kFull, cnt, 0);
     if (cnt == 0) break;
-    probe_pairs<V, false>(a, vis, t, row_pair(a, u, qmax, rs + c, cnt));
+    probe_pairs<V>(a, vis, t, owner_pair(a, x, qmax, ps + c, cnt));
   }
-  vis.task_end(u);
+  vis.task_end(x);
   __syncthreads();
 }
 
-// One warp handles u (a medium list).
+// One warp handles owner x.
 template <class V>
-__device__ __forceinline__ void warp_task(const TravArgs& a, V& vis, uint32_t u, uint32_t* tab) {
+__device__ __forceinline__ void warp_task(const TravArgs& a, V& vis, uint32_t x, uint32_t* tab) {
   const int lane = (int)lane_id();
-  if (u >= a.n) {
-    if (lane == 0) guard_fail(a.sc, kGuardVertex, u);
+  if (x >= a.n) {
+    if (lane == 0) guard_fail(a.sc, kGuardVertex, x);
     return;
   }
-  const uint32_t rs = a.row_ptr[u], re = a.row_ptr[u + 1];
-  if (re < rs || re > a.m) {
-    if (lane == 0) guard_fail(a.sc, kGuardList, u);
+  const uint32_t rs = a.row_ptr[x], re = a.row_ptr[x + 1];
+  uint32_t ps = 0, np = 0;
+  if (re < rs || re > a.m || !pair_range(a, x, ps, np)) {
+    if (lane == 0) guard_fail(a.sc, kGuardList, x);
     return;
   }
   int64_t qmax = 0;
-  const uint32_t len = pruned_len(a, rs, re - rs, qmax);
-  if (len == 0) return;
+  const uint32_t len = table_len(a, rs, re - rs, qmax);
+  if (len == 0 || np == 0) return;
   const uint32_t slots = slots_for(len);
   if (slots > a.warp_slots) {
-    if (lane == 0) guard_fail(a.sc, kGuardTable, u);
+    if (lane == 0) guard_fail(a.sc, kGuardTable, x);
     return;
   }
   const Table t = make_table(tab, a.warp_slots, slots);
@@ -467,117 +461,17 @@ __device__ __forceinline__ void warp_task(const TravArgs& a, V& vis, uint32_t u,
     table_insert(t, adj_col(e), adj_valbits(e), rs + i, a.sc);
   }
   __syncwarp();
-  vis.task_begin(u);
-  for (uint32_t cs = 0; cs < len; cs += 32)
-    probe_pairs<V, false>(a, vis, t, row_pair(a, u, qmax, rs + cs, min(32u, len - cs)));
-  vis.task_end(u);
-  __syncwarp();
-}
-
-// One warp handles segment k: pairs [32k, 32k + 32) of the concatenated short lists.
-template <class V>
-__device__ __forceinline__ void segment_task(const TravArgs& a, V& vis, uint32_t k, uint32_t* tab) {
-  const int lane = (int)lane_id();
-  const uint32_t r0 = a.seg_first[k];
-  if (r0 == kEmpty) return;
-  const uint32_t sp0 = 32 * k, sp1 = sp0 + 32;
-  // lane i describes short list r0 + i, if that list starts before the segment ends
-  const uint32_t r = r0 + lane;
-  uint32_t ss = 0xFFFFFFFFu, u = 0, rs = 0, raw = 0, len = 0;
-  int64_t qmax = 0;
-  bool row = false;
-  if (r < a.n_srows && a.seg_start[r] < sp1) {
-    ss = a.seg_start[r];
-    u = a.seg_row[r];
-    if (u < a.n) {
-      rs = a.row_ptr[u];
-      const uint32_t re = a.row_ptr[u + 1];
-      if (re >= rs && re <= a.m) {
-        row = true;
-        raw = re - rs;
-      } else {
-        guard_fail(a.sc, kGuardList, u);
-      }
-    } else {
-      guard_fail(a.sc, kGuardVertex, u);
-    }
-  }
-  if (__ballot_sync(kFull, row) == 0) return;
-  if (row) len = pruned_len(a, rs, raw, qmax);
-  // table: every entry of the touched lists (their pruned prefixes)
-  const uint32_t tl = row ? len : 0u;
-  uint32_t incl = tl;
-#pragma unroll
-  for (int d = 1; d < 32; d <<= 1) {
-    const uint32_t y = __shfl_up_sync(kFull, incl, d);
-    if (lane >= d) incl += y;
-  }
-  const uint32_t total = __shfl_sync(kFull, incl, 31);
-  const uint32_t slots = slots_for(total);
-  if (slots > a.warp_slots) {
-    if (lane == 0) guard_fail(a.sc, kGuardTable, k);
-    return;
-  }
-  const Table t = make_table(tab, a.warp_slots, slots);
-  for (uint32_t i = lane; i < slots; i += 32) t.key[i] = kEmpty;
-  __syncwarp();
-  const uint32_t excl = incl - tl;
-  for (uint32_t base = 0; base < total; base += 32) {
-    const uint32_t f = base + lane;
-    int j = 0;
-#pragma unroll
-    for (int b = 16; b > 0; b >>= 1) {
-      const uint32_t tj = __shfl_sync(kFull, incl, j + b - 1);
-      if (tj <= f) j += b;
-    }
-    j = j > 31 ? 31 : j;
-    const uint32_t rsj = __shfl_sync(kFull, rs, j);
-    const uint32_t exj = __shfl_sync(kFull, excl, j);
-    if (f < total) {
-      const uint32_t p = rsj + (f - exj);
-      const uint64_t e = a.adj[p];
-      table_insert(t, adj_col(e), adj_valbits(e), p, a.sc);
-    }
-  }
-  __syncwarp();
-  // the segment's pairs: lane e takes position sp0 + e of the concatenation;
-  // its list is the last one that starts at or before that position
-  const uint32_t sp = sp0 + lane;
-  int j = 0;  // number of lists starting at or before sp
-#pragma unroll
-  for (int b = 16; b > 0; b >>= 1) {
-    const uint32_t sj = __shfl_sync(kFull, ss, j + b - 1);
-    if (sj <= sp) j += b;
-  }
-  const bool have = j > 0;
-  j = have ? j - 1 : 0;
-  const uint32_t ssj = __shfl_sync(kFull, ss, j);
-  const uint32_t rsj = __shfl_sync(kFull, rs, j);
-  const uint32_t rawj = __shfl_sync(kFull, raw, j);
-  Pair pr;
-  pr.u = __shfl_sync(kFull, u, j);
-  pr.urs = rsj;
-  pr.ulen = __shfl_sync(kFull, len, j);
-  pr.qmax = __shfl_sync(kFull, qmax, j);
-  const bool rowj = __shfl_sync(kFull, (int)row, j) != 0;
-  const uint32_t off = sp - ssj;
-  // a pair outside its list's pruned prefix cannot be in a classified triangle
-  pr.ok = have && rowj && off < rawj && off < pr.ulen;
-  pr.puv = rsj + off;
-  const uint64_t e = pr.ok ? a.adj[pr.puv] : 0ull;
-  pr.v = adj_col(e);
-  pr.quv = adj_valbits(e);
-  const uint32_t u0 = __shfl_sync(kFull, u, 0);
-  vis.task_begin(u0);
-  probe_pairs<V, true>(a, vis, t, pr);
-  vis.task_end(u0);
+  vis.task_begin(x);
+  for (uint32_t cs = 0; cs < np; cs += 32)
+    probe_pairs<V>(a, vis, t, owner_pair(a, x, qmax, ps + cs, min(32u, np - cs)));
+  vis.task_end(x);
   __syncwarp();
 }
 
 // The traversal runs as two persistent kernels, so that each can have the
 // block size and shared memory its tasks need: the block kernel (giant and
-// hub lists, one large table per block) and the warp kernel (medium lists and
-// short-list segments, one small table per warp).
+// hub tasks, one large table per block) and the warp kernel (medium tasks,
+// one small table per warp).
 enum : int { kBlockTasks = 1, kWarpTasks = 2 };
 
 // Persistent traversal kernel body.  Shared memory: [visitor bytes][tables].
@@ -611,7 +505,7 @@ __device__ void traverse(const TravArgs& a, V& vis, char* smem_tables) {
   }
   if (kPhases & kWarpTasks) {
     uint32_t* wtab = tab + (size_t)wid * a.warp_slots * 3;
-    // medium lists, one warp each
+    // medium tasks, one warp each
     while (true) {
       unsigned long long t0 = 0;
       if (lane == 0) t0 = atomicAdd(&a.sc->task[2], (unsigned long long)a.batch);
@@ -619,15 +513,6 @@ __device__ void traverse(const TravArgs& a, V& vis, char* smem_tables) {
       if (t0 >= a.n_med) break;
       const uint32_t t1 = (uint32_t)min((unsigned long long)a.n_med, t0 + a.batch);
       for (uint32_t t = (uint32_t)t0; t < t1; t++) warp_task(a, vis, a.med_list[t], wtab);
-    }
-    // segments of short lists
-    while (true) {
-      unsigned long long t0 = 0;
-      if (lane == 0) t0 = atomicAdd(&a.sc->task[3], (unsigned long long)a.batch);
-      t0 = __shfl_sync(kFull, t0, 0);
-      if (t0 >= a.n_segs) break;
-      const uint32_t t1 = (uint32_t)min((unsigned long long)a.n_segs, t0 + a.batch);
-      for (uint32_t t = (uint32_t)t0; t < t1; t++) segment_task(a, vis, t, wtab);
     }
   }
   __syncthreads();
@@ -681,7 +566,7 @@ ubt_status launch_phase(const ubt_graph* g, const TravArgs& a, const typename V:
 
 // One traversal: the task counters in a.sc are cleared, then the block kernel
 // (if the graph has giant or hub lists) and the warp kernel (if it has medium
-// lists or segments) run one after the other on `s`.
+// tasks) run one after the other on `s`.
 template <class V>
 ubt_status launch_traversal(const ubt_graph* g, const TravArgs& a, const typename V::P& p, cudaStream_t s) {
   const Tuning& T = tuning();
@@ -690,7 +575,7 @@ ubt_status launch_traversal(const ubt_graph* g, const TravArgs& a, const typenam
     const ubt_status st = launch_phase<V, kBlockTasks>(g, a, p, (int)T.block_threads, s);
     if (st != UBT_OK) return st;
   }
-  if (a.n_med + a.n_segs > 0) {
+  if (a.n_med > 0) {
     const ubt_status st = launch_phase<V, kWarpTasks>(g, a, p, (int)T.warp_threads, s);
     if (st != UBT_OK) return st;
   }

@@ -14,8 +14,9 @@ from paper_2602_14084_gb300 import autotune as at
 @pytest.fixture
 def knobs(monkeypatch):
     """A fake of the library's tuning state (ubt_set_tuning / ubt_get_tuning)."""
-    state = {"hub_threshold": 128, "short_max": 8, "block_unit": 16, "small_batch": 4, "blocks_per_sm": 32,
-             "block_threads": 512, "warp_threads": 128, "smem_table_max": 8192, "world_words_per_pass": 8}
+    state = {"hub_threshold": 128, "block_work": 1 << 14, "pull": 1, "block_unit": 16, "small_batch": 4,
+             "blocks_per_sm": 32, "block_threads": 512, "warp_threads": 128, "smem_table_max": 8192,
+             "world_words_per_pass": 8}
 
     def get(name):
         return state[name]
@@ -136,7 +137,7 @@ def test_tune_searches_applies_and_caches(knobs, tmp_path):
     assert rec["source"] == "search"
     assert rec["config"] == best
     assert knobs["hub_threshold"] == 64 and knobs["block_unit"] == 4  # applied
-    assert knobs["short_max"] == 8  # untouched
+    assert knobs["block_work"] == 1 << 14  # untouched
     stored = json.load(open(path))
     assert rec["key"] in stored and "FakeGPU-sm2|count:nt4-pruned|" in rec["key"]
     # second call: served from the cache, nothing measured, configuration applied again
@@ -156,7 +157,8 @@ def test_tuning_scope_restores(knobs):
 
 def test_candidate_values_are_within_the_library_limits():
     # the limits ubt_set_tuning enforces (include/ubt.h)
-    lim = {"hub_threshold": (2, 4096), "short_max": (2, 32), "block_unit": (1, 32), "small_batch": (1, 1024),
+    lim = {"hub_threshold": (2, 4096), "block_work": (1, 1 << 40), "pull": (0, 1), "block_unit": (1, 32),
+           "small_batch": (1, 1024),
            "block_threads": (64, 512), "warp_threads": (64, 512), "blocks_per_sm": (1, 32),
            "smem_table_max": (64, 1 << 20), "world_words_per_pass": (1, 64)}
     for k, vals in at.ALL_KNOBS.items():

@@ -24,7 +24,7 @@ def test_tune_count_searches_caches_and_keeps_results(tmp_path):
     path = str(tmp_path / "tune.json")
     try:
         rec = at.tune_count(n, s, d, k, TAUS, prune=True, cache_path=path, rounds=1, budget_s=60,
-                            knobs=["hub_threshold", "short_max", "block_unit", "blocks_per_sm"])
+                            knobs=["hub_threshold", "block_work", "block_unit", "blocks_per_sm"])
         assert rec["source"] == "search" and rec["ms"] <= rec["start_ms"]
         assert at.current(list(rec["config"])) == rec["config"]
         G = ubt.Graph(n, s, d, k=k)  # built under the tuned knobs
@@ -34,7 +34,7 @@ def test_tune_count_searches_caches_and_keeps_results(tmp_path):
         G.close()
         at.apply(saved)
         rec2 = at.tune_count(n, s, d, k, TAUS, prune=True, cache_path=path,
-                             knobs=["hub_threshold", "short_max", "block_unit", "blocks_per_sm"])
+                             knobs=["hub_threshold", "block_work", "block_unit", "blocks_per_sm"])
         assert rec2["source"] == "cache" and rec2["config"] == rec["config"]
     finally:
         at.apply(saved)

@@ -1,6 +1,6 @@
-"""The graph the GPU builds (forward CSR under Node Order, list order, work
-lists) checked entry by entry against a numpy construction of the same
-definitions."""
+"""The graph the GPU builds (forward CSR under Node Order, list order, pair
+partition, work lists) checked entry by entry against a numpy construction
+of the same definitions."""
 import numpy as np
 import pytest
 
@@ -45,15 +45,35 @@ def check_export(ubt, G, n, s, d, k=None, p=None):
         assert np.array_equal(want[eid], val)
         key = col
     assert np.all(key[1:][same] > key[:-1][same])
+    # pair partition: every forward edge is one pair, owned by the endpoint
+    # whose list is the table (the later one when pull is on and its list is
+    # longer), streaming the other endpoint's list
+    pull = ubt.get_tuning("pull")
+    du, dv = cnt[lo], cnt[hi]
+    own = np.where((pull == 1) & (dv > du), hi, lo)
+    streamed = np.where(own == hi, lo, hi)
+    pp = ex["pair_ptr"].astype(np.int64)
+    assert pp[0] == 0 and np.array_equal(np.diff(pp), np.bincount(own, minlength=n))
+    ppos = ex["pair_pos"].astype(np.int64)
+    assert np.array_equal(np.sort(ppos), np.arange(m))
+    e_of_pair = eid[ppos]  # input edge of every pair
+    pair_owner = np.repeat(np.arange(n), np.diff(pp))
+    assert np.array_equal(own[e_of_pair], pair_owner)
+    assert np.array_equal(streamed[e_of_pair], ex["pair_streamed"].astype(np.int64))
+    # work lists: owners with a table of >= 2 entries and at least one pair
+    work = np.bincount(pair_owner, weights=cnt[ex["pair_streamed"].astype(np.int64)], minlength=n)
     lists = ex["lists"].astype(np.int64)
-    assert np.array_equal(np.sort(lists), np.nonzero(cnt >= 2)[0])
+    npairs = np.diff(pp)
+    assert np.array_equal(np.sort(lists), np.nonzero((cnt >= 2) & (npairs >= 1))[0])
     ng, nh, nm, ns = [int(x) for x in ex["list_sizes"]]
+    assert ns == 0 and ng + nh + nm == lists.size
     thr = ubt.get_tuning("hub_threshold")
-    smax = ubt.get_tuning("short_max")
-    block, med, short = lists[:ng + nh], lists[ng + nh:ng + nh + nm], lists[ng + nh + nm:]
-    assert np.all(cnt[block] > thr)
-    assert np.all((cnt[med] > smax) & (cnt[med] <= thr))
-    assert np.all(cnt[short] <= smax) and np.all(np.diff(short) > 0)
+    bw = ubt.get_tuning("block_work")
+    gthr = max(thr, ubt.get_tuning("smem_table_max") // 4)
+    giant, block, med = lists[:ng], lists[ng:ng + nh], lists[ng + nh:]
+    assert np.all(cnt[giant] > gthr)
+    assert np.all((cnt[block] <= gthr) & ((cnt[block] > thr) | (work[block] > bw)))
+    assert np.all((cnt[med] <= thr) & (work[med] <= bw))
 
 
 @pytest.mark.parametrize("seed,n,m", [(1, 2000, 20000), (2, 5000, 100000), (3, 50, 1225)])
@@ -93,3 +113,17 @@ def test_long_lists_sorted_in_global_memory(ubt):
         check_export(ubt, ubt.Graph(3000, s, d, p=p), 3000, s, d, p=p)
     finally:
         ubt.set_tuning("sort_smem_max", old)
+
+
+@pytest.mark.parametrize("knobs", [{"pull": 0}, {"block_work": 1}, {"hub_threshold": 2, "block_work": 1 << 30}])
+def test_layout_under_other_partitions(ubt, knobs):
+    old = {k: ubt.get_tuning(k) for k in knobs}
+    try:
+        for k, v in knobs.items():
+            ubt.set_tuning(k, v)
+        s, d = mixed_graph(3000, 30000, 5)
+        k = synth.k_uniform(s.size, 6)
+        check_export(ubt, ubt.Graph(3000, s, d, k=k), 3000, s, d, k=k)
+    finally:
+        for k, v in old.items():
+            ubt.set_tuning(k, v)

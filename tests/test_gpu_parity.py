@@ -276,12 +276,13 @@ def test_giant_lists_use_global_tables(ubt):
         ubt.set_tuning("smem_table_max", old)
 
 
-@pytest.mark.parametrize("knobs", [{"hub_threshold": 2}, {"hub_threshold": 200}, {"short_max": 2},
-                                   {"short_max": 32, "hub_threshold": 32}, {"block_unit": 1}, {"block_unit": 32},
+@pytest.mark.parametrize("knobs", [{"hub_threshold": 2}, {"hub_threshold": 200}, {"pull": 0},
+                                   {"block_work": 1}, {"block_work": 1 << 30, "hub_threshold": 32},
+                                   {"block_unit": 1}, {"block_unit": 32},
                                    {"small_batch": 1, "warp_threads": 64, "block_threads": 64}, {"warp_threads": 512, "block_threads": 128}])
 def test_task_split_variants(ubt, knobs):
-    """Every way of splitting the work into block / warp / segment tasks gives
-    the same bit-exact counts and expected-count sums."""
+    """Every way of partitioning the pairs and splitting the work into block /
+    warp tasks gives the same bit-exact counts and expected-count sums."""
     old = {k: ubt.get_tuning(k) for k in knobs}
     try:
         for k, v in knobs.items():

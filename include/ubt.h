@@ -341,6 +341,9 @@ ubt_status ubt_graph_export_pairs(const ubt_graph* g, uint32_t* h_pair_ptr, uint
  * ubt_set_tuning / ubt_get_tuning -- process-wide launch parameters that the
  * autotuner picks (they change speed, never results).  Unknown names return
  * UBT_ERR_INVALID_ARG.  Names:
+ *   "count_visitor"   threshold counts: 0 (default) classify each triangle
+ *                     in the lane that finds it (binned by a slice table);
+ *                     1 queue products per warp and classify 32 at a time
  *   "pull"            1 (default): a pair is owned by the endpoint whose
  *                     list is longer, so the shorter list is streamed; 0:
  *                     always by the earlier vertex (Alg. 1 as written)

@@ -46,6 +46,7 @@ BUILD_KNOBS: Dict[str, List[int]] = {
     "smem_table_max": [4096, 8192, 16384],
 }
 RUN_KNOBS: Dict[str, List[int]] = {
+    "count_visitor": [0, 1],
     "block_unit": [1, 2, 4, 8, 16, 32],
     "small_batch": [1, 2, 4, 8, 16],
     "block_threads": [128, 256, 512],
@@ -55,8 +56,8 @@ RUN_KNOBS: Dict[str, List[int]] = {
 }
 # knobs that matter per query kind (others are left as they are)
 QUERY_KNOBS: Dict[str, List[str]] = {
-    "count": ["hub_threshold", "block_work", "block_unit", "small_batch", "blocks_per_sm", "block_threads",
-              "warp_threads", "smem_table_max", "pull"],
+    "count": ["count_visitor", "hub_threshold", "block_work", "block_unit", "small_batch", "blocks_per_sm",
+              "block_threads", "warp_threads", "smem_table_max", "pull"],
     "expected": ["hub_threshold", "block_work", "block_unit", "small_batch", "blocks_per_sm", "block_threads",
                  "warp_threads", "smem_table_max", "pull"],
     "worlds": ["world_words_per_pass", "hub_threshold", "block_work", "block_unit", "small_batch",

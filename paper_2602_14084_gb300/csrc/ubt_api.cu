@@ -84,6 +84,9 @@ extern "C" ubt_status ubt_set_tuning(const char* name, int64_t value) {
   } else if (!strcmp(name, "small_batch")) {
     if (value < 1 || value > 1024) return UBT_ERR_INVALID_ARG;
     t.small_batch = value;
+  } else if (!strcmp(name, "count_visitor")) {
+    if (value < 0 || value > 1) return UBT_ERR_INVALID_ARG;
+    t.count_visitor = value;
   } else if (!strcmp(name, "pull")) {
     if (value < 0 || value > 1) return UBT_ERR_INVALID_ARG;
     t.pull = value;
@@ -114,6 +117,7 @@ extern "C" ubt_status ubt_get_tuning(const char* name, int64_t* h_value) {
   else if (!strcmp(name, "small_batch")) *h_value = t.small_batch;
   else if (!strcmp(name, "sort_smem_max")) *h_value = t.sort_smem_max;
   else if (!strcmp(name, "pull")) *h_value = t.pull;
+  else if (!strcmp(name, "count_visitor")) *h_value = t.count_visitor;
   else if (!strcmp(name, "block_work")) *h_value = t.block_work;
   else if (!strcmp(name, "block_unit")) *h_value = t.block_unit;
   else return UBT_ERR_INVALID_ARG;

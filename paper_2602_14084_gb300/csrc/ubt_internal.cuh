@@ -104,6 +104,7 @@ namespace ubt {
 
 struct Tuning {
   int64_t pull = 1;               // 1: each pair streams the shorter list; 0: always N>(v) (Alg. 1)
+  int64_t count_visitor = 0;      // threshold counts: 0 binned in the finding lane, 1 queued per warp
   int64_t block_work = 1 << 14;   // owners streaming more entries are whole-block tasks
   int64_t hub_threshold = 128;    // owners with longer lists are whole-block tasks
   int64_t block_threads = 512;    // threads of the block-task kernel

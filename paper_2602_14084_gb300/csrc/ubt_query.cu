@@ -318,6 +318,103 @@ struct CountMulti {
   }
 };
 
+// Any number of thresholds (up to 64), classified in the lane that found the
+// triangle, without a queue.  The 2 nt levels S (every B and every U,
+// ascending) cut the integers into 2 nt + 1 intervals; P falls in interval
+// r = #{S_j < P}, counted in bin r (finished by k_finish_multi).  r is found
+// with a slice table: P + 2^45 in [0, 2^46] is cut into 2049 slices of 2^35;
+// slice i records b0 = #{S_j < its start} and the number c of levels inside
+// it, so r = b0 + #{S_j < P, b0 <= j < b0 + c} (c is 0 or 1 unless two
+// thresholds lie within 2^35 / 2^45 = 2^-10 of each other).  Bins 0 and 2 nt
+// (P classified at every threshold, the common case for confident edges)
+// are per-lane register counters; the others are shared 32-bit counters
+// with a carry word.
+constexpr int kSlices = 2049;
+struct CountBinsP {
+  int nt;
+  int64_t S[2 * kMaxTau];   // the 2 nt levels, ascending
+  unsigned long long* out;  // global bins [0, 2 nt]
+};
+struct CountBins {
+  using P = CountBinsP;
+  static constexpr bool kPos = false;
+  static constexpr bool kBatched = true;
+  static constexpr int kRegCap = UBT_COUNT_REGCAP;
+  static constexpr int kTabBytes = ((kSlices * 2 + 15) / 16) * 16;
+  static __host__ __device__ int smem_bytes(int) { return kTabBytes + 2 * kMaxTau * 8 + 2 * 2 * 144 * 4; }
+  const uint16_t* tab;  // shared: slice table, b0 | c << 8
+  const long long* S;   // shared: levels
+  uint32_t* lo;         // shared: bins, low words
+  uint32_t* hi;         // shared: bins, carries
+  unsigned long long* out;
+  unsigned long long first = 0, last = 0;  // bins 0 and 2 nt of this lane
+  int top;                                  // 2 nt
+  __device__ CountBins(const P& p, char* smem) : out(p.out), top(2 * p.nt) {
+    uint16_t* t = (uint16_t*)smem;
+    long long* sv = (long long*)(smem + kTabBytes);
+    uint32_t* b = (uint32_t*)(smem + kTabBytes + 2 * kMaxTau * 8);
+    tab = t;
+    S = sv;
+    lo = b;
+    hi = b + 144;
+    for (int i = threadIdx.x; i < 2 * p.nt; i += blockDim.x) sv[i] = p.S[i];
+    for (int i = threadIdx.x; i < 2 * 144; i += blockDim.x) b[i] = 0;
+    for (int i = threadIdx.x; i < kSlices; i += blockDim.x) {
+      const long long start = (long long)i * (1ll << 35) - (1ll << 45);
+      const long long end = start + (1ll << 35);
+      int b0 = 0, b1 = 0;  // #{S < start}, #{S < end}
+      for (int j = 0; j < 2 * p.nt; j++) {
+        b0 += p.S[j] < start ? 1 : 0;
+        b1 += p.S[j] < end ? 1 : 0;
+      }
+      t[i] = (uint16_t)(b0 | ((b1 - b0) << 8));
+    }
+  }
+  __device__ void block_init() {}
+  __device__ __forceinline__ void count(long long P) {
+    const uint32_t e = tab[(uint32_t)((unsigned long long)(P + (1ll << 45)) >> 35)];
+    int r = (int)(e & 0xFFu);
+    const int c = (int)(e >> 8);
+    if (c) {
+      const int b0 = r;
+      for (int j = 0; j < c; j++) r += S[b0 + j] < P ? 1 : 0;
+    }
+    if (r == 0) {
+      first++;
+    } else if (r == top) {
+      last++;
+    } else {
+      const uint32_t old = atomicAdd(&lo[r], 1u);
+      if (old == 0xFFFFFFFFu) atomicAdd(&hi[r], 1u);
+    }
+  }
+  __device__ __forceinline__ void step(bool hit, uint32_t, uint32_t, uint32_t, uint32_t quv, uint32_t quw,
+                                       uint32_t qvw, uint32_t, uint32_t, uint32_t) {
+    if (hit) count(tri_product(quv, quw, qvw));
+  }
+  template <int U>
+  __device__ __forceinline__ void steps(const bool (&hit)[U], uint32_t quv, const uint32_t (&quw)[U],
+                                        const uint32_t (&qvw)[U]) {
+#pragma unroll
+    for (int s = 0; s < U; s++)
+      if (hit[s]) count(tri_product(quv, quw[s], qvw[s]));
+  }
+  __device__ void task_begin(uint32_t) {}
+  __device__ void task_end(uint32_t) {}
+  __device__ void block_end() {
+    const unsigned long long f = warp_sum(first), l = warp_sum(last);
+    if (lane_id() == 0) {
+      if (f) atomicAdd(&out[0], f);
+      if (l) atomicAdd(&out[top], l);
+    }
+    __syncthreads();
+    for (int i = threadIdx.x + 1; i < top; i += blockDim.x) {
+      const unsigned long long v = ((unsigned long long)hi[i] << 32) | lo[i];
+      if (v) atomicAdd(&out[i], v);
+    }
+  }
+};
+
 struct FinishMulti {
   int nt;
   int perm[kMaxTau];  // caller index of the i-th smallest threshold
@@ -655,6 +752,24 @@ extern "C" ubt_status ubt_count_threshold(ubt_graph* g, const double* h_tau, int
   std::iota(order.begin(), order.end(), 0);
   std::stable_sort(order.begin(), order.end(), [&](int x, int y) { return lv[x].L < lv[y].L; });
   const int64_t L = prune ? lv[order[0]].L : 0;
+  if (tuning().count_visitor == 0) {
+    CountBinsP p;
+    p.nt = n_tau;
+    for (int i = 0; i < n_tau; i++) {
+      p.S[i] = lv[order[n_tau - 1 - i]].B;  // B ascending: t descending
+      p.S[n_tau + i] = lv[order[i]].U;      // U ascending: t ascending
+    }
+    p.out = g->scratch->hist;
+    UBT_CUDA(cudaMemsetAsync(g->scratch->hist, 0, sizeof(g->scratch->hist), s));
+    st = launch_traverse<CountBins>(g, p, L, s);
+    if (st != UBT_OK) return st;
+    FinishMulti f;
+    f.nt = n_tau;
+    for (int i = 0; i < n_tau; i++) f.perm[i] = order[i];
+    k_finish_multi<<<1, kMaxTau, 0, s>>>(g->scratch->hist, f, d_counts);
+    UBT_CUDA(cudaGetLastError());
+    return UBT_OK;
+  }
   if (n_tau <= kRegTau) {
     const int NT = n_tau <= 1 ? 1 : n_tau <= 2 ? 2 : n_tau <= 4 ? 4 : 8;
     CountRegP p;

@@ -14,7 +14,8 @@ from paper_2602_14084_gb300 import autotune as at
 @pytest.fixture
 def knobs(monkeypatch):
     """A fake of the library's tuning state (ubt_set_tuning / ubt_get_tuning)."""
-    state = {"hub_threshold": 128, "block_work": 1 << 14, "pull": 1, "block_unit": 16, "small_batch": 4,
+    state = {"hub_threshold": 128, "block_work": 1 << 14, "pull": 1, "count_visitor": 0, "block_unit": 16,
+             "small_batch": 4,
              "blocks_per_sm": 32, "block_threads": 512, "warp_threads": 128, "smem_table_max": 8192,
              "world_words_per_pass": 8}
 
@@ -157,7 +158,7 @@ def test_tuning_scope_restores(knobs):
 
 def test_candidate_values_are_within_the_library_limits():
     # the limits ubt_set_tuning enforces (include/ubt.h)
-    lim = {"hub_threshold": (2, 4096), "block_work": (1, 1 << 40), "pull": (0, 1), "block_unit": (1, 32),
+    lim = {"hub_threshold": (2, 4096), "block_work": (1, 1 << 40), "pull": (0, 1), "count_visitor": (0, 1), "block_unit": (1, 32),
            "small_batch": (1, 1024),
            "block_threads": (64, 512), "warp_threads": (64, 512), "blocks_per_sm": (1, 32),
            "smem_table_max": (64, 1 << 20), "world_words_per_pass": (1, 64)}

@@ -78,9 +78,15 @@ def test_counts_many_thresholds_bit_exact(ubt, case, which):
     taus = MANY[which]
     G = ubt.Graph(n, s, d, k=k)
     ob, ou = oracle.count_threshold(n, s, d, k, taus)
-    for prune in (0, 1):
-        gb, gu = G.count_threshold(taus, prune=prune)
-        assert np.array_equal(gb, ob) and np.array_equal(gu, ou), (name, which, prune)
+    old = ubt.get_tuning("count_visitor")
+    try:
+        for vis in (0, 1):
+            ubt.set_tuning("count_visitor", vis)
+            for prune in (0, 1):
+                gb, gu = G.count_threshold(taus, prune=prune)
+                assert np.array_equal(gb, ob) and np.array_equal(gu, ou), (name, which, vis, prune)
+    finally:
+        ubt.set_tuning("count_visitor", old)
     assert G.guard() == 0
 
 
@@ -278,7 +284,7 @@ def test_giant_lists_use_global_tables(ubt):
 
 @pytest.mark.parametrize("knobs", [{"hub_threshold": 2}, {"hub_threshold": 200}, {"pull": 0},
                                    {"block_work": 1}, {"block_work": 1 << 30, "hub_threshold": 32},
-                                   {"block_unit": 1}, {"block_unit": 32},
+                                   {"block_unit": 1}, {"block_unit": 32}, {"count_visitor": 1},
                                    {"small_batch": 1, "warp_threads": 64, "block_threads": 64}, {"warp_threads": 512, "block_threads": 128}])
 def test_task_split_variants(ubt, knobs):
     """Every way of partitioning the pairs and splitting the work into block /

@@ -18,6 +18,8 @@ Parity status of each function (what pins it, in the tests under
   grad_real                      -- central finite differences (exact: the
       expected count is affine in each p_e); closed form on K_n.
   philox4x64_10                  -- numpy's Philox bit generator.
+  local_counts                   -- sums over edges / vertices = 3 x the counts;
+      brute-force classification in exact rationals; closed forms on K_n.
   world_counts                   -- per-world recount from numpy Philox draws
       and brute-force listing; binomial bounds on the sign frequencies.
 The paper's worked example with numbers (Sec. 1, the two example triangles
@@ -80,6 +82,8 @@ def _L():
         lib.ubto_philox4x64_10.argtypes = [P, P, P]
         lib.ubto_world_word.restype = ctypes.c_uint64
         lib.ubto_world_word.argtypes = [ctypes.c_uint64, ctypes.c_uint32, ctypes.c_uint32, ctypes.c_uint32]
+        lib.ubto_local_counts.restype = ctypes.c_int
+        lib.ubto_local_counts.argtypes = [I64, I64, P, P, P, ctypes.c_int, P, P, P, P, P]
         lib.ubto_world_counts.restype = ctypes.c_int
         lib.ubto_world_counts.argtypes = [I64, I64, P, P, P, P, ctypes.c_uint64, ctypes.c_int, P, P]
         _lib = lib
@@ -176,6 +180,22 @@ def grad_real(n, src, dst, p, with_abs=False):
     ga = np.zeros(s.size, dtype=np.float64) if with_abs else None
     _check(_L().ubto_grad_real(n, s.size, _ptr(s), _ptr(d), _ptr(pp), _ptr(g), _ptr(ga)))
     return (g, ga) if with_abs else g
+
+
+def local_counts(n, src, dst, k, taus):
+    """Per-edge (input order) and per-vertex local counts of t-balanced and
+    t-unbalanced triangles: (edge_bal, edge_unbal) int64 (m, n_tau) and
+    (vtx_bal, vtx_unbal) int64 (n, n_tau)."""
+    s, d, kk = _u32(src), _u32(dst), _u32(k)
+    t = np.ascontiguousarray(np.atleast_1d(np.asarray(taus, dtype=np.float64)))
+    m = s.size
+    eb = np.zeros((max(m, 1), t.size), dtype=np.int64)
+    eu = np.zeros((max(m, 1), t.size), dtype=np.int64)
+    vb = np.zeros((max(n, 1), t.size), dtype=np.int64)
+    vu = np.zeros((max(n, 1), t.size), dtype=np.int64)
+    _check(_L().ubto_local_counts(n, m, _ptr(s), _ptr(d), _ptr(kk), t.size, _ptr(t), _ptr(eb), _ptr(eu),
+                                  _ptr(vb), _ptr(vu)))
+    return eb[:m], eu[:m], vb[:n], vu[:n]
 
 
 def philox4x64_10(ctr, key):

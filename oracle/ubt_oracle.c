@@ -22,6 +22,8 @@
  *  - expected counts  E_bal = sum_t P_bal(t), E_unbal = sum_t P_unbal(t), and
  *    dE_bal/dp_e from the term-wise derivative of the four-term sum
  *    (derived from the same equation; not in the paper)
+ *  - local counts |B_t(e)|, |B_t(v)|: classified triangles through an edge
+ *    or a vertex, the per-sample quantities of the samplers (Sec. 6)
  *  - Monte-Carlo sign worlds: a world is one draw of every edge sign; a
  *    triangle is balanced in a world iff it holds an odd number of positive
  *    edges (Def. 3, Sec. 3).  The draws come from Philox4x64-10 (Salmon,
@@ -438,6 +440,69 @@ int ubto_grad_real(int64_t n, int64_t m, const uint32_t* src, const uint32_t* ds
     for_each_triangle(&g, visit_grad, &c);
     fgraph_free(&g);
     return OR_OK;
+}
+
+/* ------------------------------------------------------------------------ */
+/* Local counts (the quantities the samplers of Sec. 6 estimate from)        */
+/* ------------------------------------------------------------------------ */
+
+typedef struct {
+    const uint32_t* k;
+    int n_tau;
+    const uint64_t* tb;
+    const uint64_t* tu;
+    int64_t* ebal;
+    int64_t* eunb;
+    int64_t* vbal;
+    int64_t* vunb;
+} local_ctx;
+static void visit_local(void* c, const tri_t* t) {
+    local_ctx* x = (local_ctx*)c;
+    uint64_t nb = nbal_fixed(x->k[t->e_ab], x->k[t->e_ac], x->k[t->e_bc]);
+    uint64_t nu = ONE48 - nb;
+    const uint32_t es[3] = {t->e_ab, t->e_ac, t->e_bc};
+    const uint32_t vs[3] = {t->a, t->b, t->c};
+    for (int i = 0; i < x->n_tau; i++) {
+        int b = nb >= x->tb[i], u = nu > x->tu[i];
+        for (int j = 0; j < 3; j++) {
+            if (x->ebal && b) x->ebal[(int64_t)es[j] * x->n_tau + i]++;
+            if (x->eunb && u) x->eunb[(int64_t)es[j] * x->n_tau + i]++;
+            if (x->vbal && b) x->vbal[(int64_t)vs[j] * x->n_tau + i]++;
+            if (x->vunb && u) x->vunb[(int64_t)vs[j] * x->n_tau + i]++;
+        }
+    }
+}
+
+/* Local counts for every edge and every vertex: the number of t-balanced /
+ * t-unbalanced triangles that contain it (|B_t(e)|, |B_t(v)| of Sec. 6),
+ * for each of n_tau thresholds.  Every triangle is listed once (Alg. 1) and
+ * credited to its three edges and three vertices.  Arrays are [item][tau]
+ * (edges in input order); any of them may be NULL. */
+int ubto_local_counts(int64_t n, int64_t m, const uint32_t* src, const uint32_t* dst,
+                      const uint32_t* k, int n_tau, const double* tau, int64_t* edge_bal,
+                      int64_t* edge_unbal, int64_t* vtx_bal, int64_t* vtx_unbal) {
+    int rc = check_k(m, k);
+    if (rc != OR_OK) return rc;
+    if (n_tau < 1) return OR_BAD_TAU;
+    uint64_t* tb = (uint64_t*)malloc(sizeof(uint64_t) * (size_t)n_tau);
+    uint64_t* tu = (uint64_t*)malloc(sizeof(uint64_t) * (size_t)n_tau);
+    if (!tb || !tu) { free(tb); free(tu); return OR_NOMEM; }
+    for (int i = 0; i < n_tau && rc == OR_OK; i++) rc = tau_levels(tau[i], &tb[i], &tu[i]);
+    if (rc == OR_OK) {
+        if (edge_bal) memset(edge_bal, 0, sizeof(int64_t) * (size_t)(m * n_tau));
+        if (edge_unbal) memset(edge_unbal, 0, sizeof(int64_t) * (size_t)(m * n_tau));
+        if (vtx_bal) memset(vtx_bal, 0, sizeof(int64_t) * (size_t)(n * n_tau));
+        if (vtx_unbal) memset(vtx_unbal, 0, sizeof(int64_t) * (size_t)(n * n_tau));
+        fgraph g;
+        rc = fgraph_build(&g, n, m, src, dst);
+        if (rc == OR_OK) {
+            local_ctx c = {k, n_tau, tb, tu, edge_bal, edge_unbal, vtx_bal, vtx_unbal};
+            for_each_triangle(&g, visit_local, &c);
+            fgraph_free(&g);
+        }
+    }
+    free(tb); free(tu);
+    return rc;
 }
 
 /* ------------------------------------------------------------------------ */

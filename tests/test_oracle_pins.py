@@ -397,3 +397,64 @@ def test_world_mean_estimates_expected_count():
     e_bal = S / float(1 << 48)
     sd = c.std(ddof=1) / math.sqrt(c.size)
     assert abs(c.mean() - e_bal) <= 6 * sd
+
+
+# ---------------------------------------------------------------- local counts (Sec. 6 samplers)
+
+@pytest.mark.parametrize("seed,n,m", [(41, 8, 14), (42, 7, 13)])
+def test_local_counts_match_all_sign_worlds(seed, n, m):
+    """|B_t(e)| and |B_t(v)|: classified triangles through an edge or a vertex,
+    from exact rational P_bal over every sign world and O(n^3) listing."""
+    s, d = small_graph(seed, n, m)
+    k = special_k(m, seed)
+    probs = [Fraction(int(x), ONE) for x in k]
+    worlds = world_prob_table(probs)
+    bv, be = brute_triangles(n, s, d)
+    taus = [0.5, 0.6, 0.8, 0.95]
+    want_eb = np.zeros((m, len(taus)), dtype=np.int64)
+    want_eu = np.zeros((m, len(taus)), dtype=np.int64)
+    want_vb = np.zeros((n, len(taus)), dtype=np.int64)
+    want_vu = np.zeros((n, len(taus)), dtype=np.int64)
+    for tri_v, tri_e in zip(bv, be):
+        pb = sum((pr for signs, pr in worlds if (signs[tri_e[0]] + signs[tri_e[1]] + signs[tri_e[2]]) % 2 == 1),
+                 Fraction(0))
+        for i, t in enumerate(taus):
+            if pb >= Fraction(t):
+                want_eb[tri_e, i] += 1
+                want_vb[tri_v, i] += 1
+            if 1 - pb > Fraction(t):
+                want_eu[tri_e, i] += 1
+                want_vu[tri_v, i] += 1
+    eb, eu, vb, vu = oracle.local_counts(n, s, d, k, taus)
+    assert np.array_equal(eb, want_eb) and np.array_equal(eu, want_eu)
+    assert np.array_equal(vb, want_vb) and np.array_equal(vu, want_vu)
+
+
+@pytest.mark.parametrize("seed", [43, 44])
+def test_local_counts_sum_to_three_times_the_counts(seed):
+    """Every triangle has three edges and three vertices."""
+    s, d = synth.er_graph(300, 6000, seed)
+    k = special_k(s.size, seed)
+    taus = [0.5, 0.55, 0.7, 0.9, 1.0]
+    bal, unbal = oracle.count_threshold(300, s, d, k, taus)
+    eb, eu, vb, vu = oracle.local_counts(300, s, d, k, taus)
+    assert np.array_equal(eb.sum(0), 3 * bal) and np.array_equal(eu.sum(0), 3 * unbal)
+    assert np.array_equal(vb.sum(0), 3 * bal) and np.array_equal(vu.sum(0), 3 * unbal)
+
+
+@pytest.mark.parametrize("n,k", [(7, 49152), (9, 1000), (6, 32768)])
+def test_local_counts_complete_graph(n, k):
+    """K_n with one P+: every edge is in n - 2 triangles, every vertex in
+    C(n-1, 2), all with P_bal = (1 - s^3)/2."""
+    pairs = [(a, b) for a in range(n) for b in range(a + 1, n)]
+    s = np.array([a for a, _ in pairs], dtype=np.uint32)
+    d = np.array([b for _, b in pairs], dtype=np.uint32)
+    kk = np.full(len(pairs), k, dtype=np.uint32)
+    sg = 1 - 2 * Fraction(k, ONE)
+    pbal = (1 - sg ** 3) / 2
+    taus = [0.5, 0.6, 0.9]
+    eb, eu, vb, vu = oracle.local_counts(n, s, d, kk, taus)
+    for i, t in enumerate(taus):
+        isb, isu = pbal >= Fraction(t), 1 - pbal > Fraction(t)
+        assert np.all(eb[:, i] == (n - 2) * isb) and np.all(eu[:, i] == (n - 2) * isu)
+        assert np.all(vb[:, i] == math.comb(n - 1, 2) * isb) and np.all(vu[:, i] == math.comb(n - 1, 2) * isu)

@@ -98,7 +98,13 @@ typedef struct {
      * first 0, last n).  Edges must not cross graphs.  NULL = one graph. */
     const int64_t* d_vertex_offsets;
     int64_t n_graphs;
+    /* UBT_OPT_UNDIRECTED: also build the undirected adjacency in Absolute
+     * Edge Order (FIXED graphs only), which ubt_count_aeo, ubt_enumerate_aeo,
+     * ubt_edge_local_counts and ubt_vertex_local_counts need. */
+    int64_t flags;
 } ubt_graph_opts;
+
+#define UBT_OPT_UNDIRECTED 1
 
 /* Human-readable name of a status code (static string). */
 const char* ubt_status_str(ubt_status s);
@@ -336,6 +342,65 @@ ubt_status ubt_graph_export(const ubt_graph* g, uint32_t* h_row_ptr, uint64_t* h
  *              the edge (high 32 bits); order within an owner is unspecified
  */
 ubt_status ubt_graph_export_pairs(const ubt_graph* g, uint32_t* h_pair_ptr, uint64_t* h_pairs, void* stream);
+
+/*
+ * ubt_count_aeo -- ASYNC.  The counting problem (Def. 8) answered by the
+ * improved method's edge iteration (Alg. 2): edges in Absolute Edge Order
+ * (Def. AEO: |P+ - 0.5| descending, ties by (min id, max id)), skipping every
+ * edge below a(t) (Lemma 2) and every partner edge below Lemma 3's cutoff for
+ * the smallest t; each triangle is found from its first edge in that order.
+ * Same arguments and results as ubt_count_threshold with prune = 1.  Needs a
+ * graph built with UBT_OPT_UNDIRECTED (else UBT_ERR_UNSUPPORTED).
+ */
+ubt_status ubt_count_aeo(ubt_graph* g, const double* h_tau, int32_t n_tau, int64_t* d_counts, void* stream);
+
+/*
+ * ubt_enumerate_aeo -- SYNC.  The enumeration problem (Def. 7) by the same
+ * iteration; arguments and results as ubt_enumerate with prune = 1.
+ */
+ubt_status ubt_enumerate_aeo(ubt_graph* g, double tau, int32_t which, ubt_tri_rec* d_out, int64_t capacity,
+                             int64_t* h_n_found, void* stream);
+
+/*
+ * ubt_edge_local_counts -- ASYNC.  Edge sampling (Algs. 5-6, Sec. 6): for
+ * each of k sampled edges, the number of t-balanced and t-unbalanced
+ * triangles that contain it (the improved local search: lists in Absolute
+ * Edge Order, stopped at the pruning cutoffs), and the estimator
+ * |E| / 3 * mean over the samples, for every threshold.
+ *   d_edges     device uint32[k] input edge indices (the caller's uniform
+ *               draws, repeats allowed); each < m
+ *   h_tau       host double[n_tau], 1 <= n_tau <= 64, each in [0.5, 1]
+ *   d_bal, d_unbal  device int64[k * n_tau], [sample][t]
+ *   d_estimate  device double[2 * n_tau] (balanced, then unbalanced), or NULL
+ * Needs UBT_OPT_UNDIRECTED.  An edge index >= m sets the query's self-check
+ * word (ubt_query_guard) and counts as no triangle.
+ */
+ubt_status ubt_edge_local_counts(ubt_graph* g, const uint32_t* d_edges, int64_t k, const double* h_tau,
+                                 int32_t n_tau, int64_t* d_bal, int64_t* d_unbal, double* d_estimate, void* stream);
+
+/*
+ * ubt_vertex_local_counts -- ASYNC.  Vertex sampling (Algs. 3-4): the same
+ * for k sampled vertices (triangles through each vertex; estimator |V| / 3 *
+ * mean).  d_vertices: device uint32[k], each < n.
+ */
+ubt_status ubt_vertex_local_counts(ubt_graph* g, const uint32_t* d_vertices, int64_t k, const double* h_tau,
+                                   int32_t n_tau, int64_t* d_bal, int64_t* d_unbal, double* d_estimate,
+                                   void* stream);
+
+/*
+ * ubt_graph_export_undirected -- SYNC.  Copies the undirected adjacency of a
+ * graph built with UBT_OPT_UNDIRECTED to host memory (any pointer may be
+ * NULL; UBT_ERR_UNSUPPORTED without the option).  Row x holds every edge at x,
+ * sorted by |q| descending then neighbour id (Absolute Edge Order restricted
+ * to the edges at x), packed like h_adj of ubt_graph_export.
+ *   h_uptr uint32[n+1]; h_uadj uint64[2m]; h_ueid uint32[2m] input edge index;
+ *   h_umir uint32[2m] position of the same edge in the other endpoint's row;
+ *   h_apair_ptr uint32[n+1], h_apairs uint64[m]: the edges ubt_count_aeo
+ *   handles from x (the endpoint with the longer row, ties to the larger id):
+ *   the other endpoint (low 32 bits), the edge's position in x's row (high).
+ */
+ubt_status ubt_graph_export_undirected(const ubt_graph* g, uint32_t* h_uptr, uint64_t* h_uadj, uint32_t* h_ueid,
+                                       uint32_t* h_umir, uint32_t* h_apair_ptr, uint64_t* h_apairs, void* stream);
 
 /*
  * ubt_set_tuning / ubt_get_tuning -- process-wide launch parameters that the

@@ -24,6 +24,7 @@ __all__ = ["Graph", "expected_counts", "count_host", "set_tuning", "get_tuning",
 _HERE = os.path.dirname(os.path.abspath(__file__))
 LIB_PATH = os.path.join(_HERE, "libubt.so")
 FIXED, REAL = 0, 1
+UBT_OPT_UNDIRECTED = 1
 
 # ubt_tri_rec: {uint32 u, v, w, cls; double p_bal}
 TRI_REC_DTYPE = np.dtype([("u", "<u4"), ("v", "<u4"), ("w", "<u4"), ("cls", "<u4"), ("p_bal", "<f8")])
@@ -40,7 +41,7 @@ class UbtError(RuntimeError):
 
 class _GraphOpts(ctypes.Structure):
     _fields_ = [("d_edge_key", ctypes.c_void_p), ("d_vertex_offsets", ctypes.c_void_p),
-                ("n_graphs", ctypes.c_int64)]
+                ("n_graphs", ctypes.c_int64), ("flags", ctypes.c_int64)]
 
 
 class _GraphInfo(ctypes.Structure):
@@ -79,6 +80,11 @@ def lib():
             "ubt_query_guard": (I32, [P, ctypes.POINTER(I64), P]),
             "ubt_graph_export": (I32, [P, P, P, P, P, P, P]),
             "ubt_graph_export_pairs": (I32, [P, P, P, P]),
+            "ubt_graph_export_undirected": (I32, [P, P, P, P, P, P, P, P]),
+            "ubt_count_aeo": (I32, [P, P, I32, P, P]),
+            "ubt_enumerate_aeo": (I32, [P, ctypes.c_double, I32, P, I64, ctypes.POINTER(I64), P]),
+            "ubt_edge_local_counts": (I32, [P, P, I64, P, I32, P, P, P, P]),
+            "ubt_vertex_local_counts": (I32, [P, P, I64, P, I32, P, P, P, P]),
             "ubt_set_tuning": (I32, [ctypes.c_char_p, I64]),
             "ubt_get_tuning": (I32, [ctypes.c_char_p, ctypes.POINTER(I64)]),
         }
@@ -142,7 +148,7 @@ class Graph:
     """
 
     def __init__(self, n, src, dst, k=None, p=None, edge_key=None, vertex_offsets=None, device="cuda",
-                 stream=None):
+                 stream=None, undirected=False):
         torch = _torch()
         if (k is None) == (p is None):
             raise ValueError("give exactly one of k or p")
@@ -160,8 +166,10 @@ class Graph:
                      else torch.from_numpy(np.ascontiguousarray(p, dtype=np.float32)).to(self.device)).contiguous()
         opts = None
         self._keep = []
-        if edge_key is not None or vertex_offsets is not None:
+        self.undirected = bool(undirected)
+        if edge_key is not None or vertex_offsets is not None or undirected:
             opts = _GraphOpts()
+            opts.flags = UBT_OPT_UNDIRECTED if undirected else 0
             if edge_key is not None:
                 ek = _dev_u32(edge_key, self.device)
                 self._keep.append(ek)
@@ -278,6 +286,81 @@ class Graph:
         _check(st, "ubt_enumerate")
         n = min(int(found.value), int(capacity))
         return buf[: n * TRI_REC_DTYPE.itemsize].cpu().numpy().view(TRI_REC_DTYPE)
+
+    # ------------------------------------------- Absolute Edge Order / sampling
+
+    def count_aeo_(self, taus, out, stream=None):
+        """ASYNC: ubt_count_aeo into `out` (int64 [2 * n_tau])."""
+        t = np.ascontiguousarray(np.atleast_1d(np.asarray(taus, dtype=np.float64)))
+        _check(lib().ubt_count_aeo(self._h, t.ctypes.data_as(ctypes.c_void_p), t.size, _ptr(out), _stream(stream)),
+               "ubt_count_aeo")
+        return out
+
+    def count_aeo(self, taus, stream=None):
+        """(balanced, unbalanced) int64 counts by the Absolute-Edge-Order iteration (Alg. 2)."""
+        torch = _torch()
+        nt = int(np.atleast_1d(taus).size)
+        out = torch.empty(2 * nt, dtype=torch.int64, device=self.device)
+        self.count_aeo_(taus, out, stream)
+        h = out.cpu().numpy()
+        return h[:nt].copy(), h[nt:].copy()
+
+    def enumerate_aeo(self, tau, which=3, capacity=None, stream=None):
+        """Records (TRI_REC_DTYPE) found by the Absolute-Edge-Order iteration."""
+        torch = _torch()
+        L = lib()
+        found = ctypes.c_int64(0)
+        if capacity is None:
+            st = L.ubt_enumerate_aeo(self._h, float(tau), int(which), None, 0, ctypes.byref(found), _stream(stream))
+            if st not in (0, -7):
+                _check(st, "ubt_enumerate_aeo")
+            capacity = int(found.value)
+        buf = torch.empty(max(capacity, 1) * TRI_REC_DTYPE.itemsize, dtype=torch.uint8, device=self.device)
+        _check(L.ubt_enumerate_aeo(self._h, float(tau), int(which), _ptr(buf), int(capacity), ctypes.byref(found),
+                                   _stream(stream)), "ubt_enumerate_aeo (found %d)" % found.value)
+        return buf.cpu().numpy()[: int(found.value) * TRI_REC_DTYPE.itemsize].view(TRI_REC_DTYPE)
+
+    def _local(self, fn, items, taus, stream):
+        torch = _torch()
+        it = _dev_u32(items, self.device)
+        t = np.ascontiguousarray(np.atleast_1d(np.asarray(taus, dtype=np.float64)))
+        k = int(it.numel())
+        bal = torch.empty(max(k, 1) * t.size, dtype=torch.int64, device=self.device)
+        unb = torch.empty(max(k, 1) * t.size, dtype=torch.int64, device=self.device)
+        est = torch.empty(2 * t.size, dtype=torch.float64, device=self.device)
+        _check(fn(self._h, _ptr(it), k, t.ctypes.data_as(ctypes.c_void_p), t.size, _ptr(bal), _ptr(unb), _ptr(est),
+                  _stream(stream)), "local counts")
+        nt = t.size
+        return (bal.cpu().numpy()[: k * nt].reshape(k, nt), unb.cpu().numpy()[: k * nt].reshape(k, nt),
+                est.cpu().numpy().reshape(2, nt))
+
+    def edge_local_counts(self, edges, taus, stream=None):
+        """Edge sampling (Algs. 5-6): per sampled edge (input index) the
+        t-balanced / t-unbalanced triangles through it, and the estimator
+        |E|/3 * mean: (bal (k, n_tau), unbal (k, n_tau), estimate (2, n_tau))."""
+        return self._local(lib().ubt_edge_local_counts, edges, taus, stream)
+
+    def vertex_local_counts(self, vertices, taus, stream=None):
+        """Vertex sampling (Algs. 3-4): as edge_local_counts, per sampled vertex,
+        estimator |V|/3 * mean."""
+        return self._local(lib().ubt_vertex_local_counts, vertices, taus, stream)
+
+    def export_undirected(self, stream=None):
+        """The undirected adjacency in Absolute Edge Order and the AEO edge owners."""
+        n, m = self.n, self.m
+        up = np.zeros(n + 1, dtype=np.uint32)
+        ua = np.zeros(max(2 * m, 1), dtype=np.uint64)
+        ue = np.zeros(max(2 * m, 1), dtype=np.uint32)
+        um = np.zeros(max(2 * m, 1), dtype=np.uint32)
+        ap = np.zeros(n + 1, dtype=np.uint32)
+        aw = np.zeros(max(m, 1), dtype=np.uint64)
+        c = lambda a: a.ctypes.data_as(ctypes.c_void_p)
+        _check(lib().ubt_graph_export_undirected(self._h, c(up), c(ua), c(ue), c(um), c(ap), c(aw), _stream(stream)),
+               "ubt_graph_export_undirected")
+        return {"uptr": up, "col": (ua[: 2 * m] & 0xFFFFFFFF).astype(np.uint32),
+                "val": (ua[: 2 * m] >> 32).astype(np.uint32).view(np.int32), "eid": ue[: 2 * m], "mirror": um[: 2 * m],
+                "apair_ptr": ap, "apair_other": (aw[:m] & 0xFFFFFFFF).astype(np.uint32),
+                "apair_pos": (aw[:m] >> 32).astype(np.uint32)}
 
     def expected_counts_(self, out, exact=None, stream=None):
         _check(lib().ubt_expected_counts(self._h, _ptr(out), _ptr(exact), _stream(stream)), "ubt_expected_counts")

@@ -1,0 +1,282 @@
+// ubt_aeo.cuh -- the edge iteration of Alg. 2 in Absolute Edge Order.
+//
+// Alg. 2 visits the edges in Absolute Edge Order (Def. AEO: a(e) = |P+ - 0.5|
+// descending, ties by (min id, max id)), stops at the first edge with
+// a(e) < a(t) (Lemma 2) and, for edge e = (u, v), intersects the neighbours
+// of u and of v reached through edges after e in the order whose value passes
+// Lemma 3's cutoff.  Each triangle is found once, from its first edge in the
+// order (the edge with the largest |q|).  In the fixed-point form
+// (|q| = |32768 - k| = 65536 a(e), L = ceil((2t - 1) 2^45)):
+//   Lemma 2   edge e can be in a classified triangle only if |q_e| 2^30 >= L
+//   Lemma 3   a partner edge f of e (after e) only if |q_f| |q_e|^2 >= L: the
+//             third edge is after e too, so |q| <= |q_e| for both partners
+//             and |P| <= |q_f| |q_e|^2.
+//
+// GPU layout.  The undirected rows hold every edge at x sorted by |q|
+// descending then neighbour id -- for one row this is exactly Absolute Edge
+// Order -- so "after e" is "at a later position of the row" and both cutoffs
+// are prefixes.  Edge e = x-y is handled by x (the endpoint with the longer
+// row), whose row prefix is a hash table (kept in shared memory, in chunks if
+// it is longer than one table); y's row is streamed from the position after
+// e (its mirror position + 1) to the Lemma 3 cutoff, and a hit w counts only
+// if x-w lies after e in x's row and passes the cutoff.  All edges are
+// processed in parallel: the order only decides which edge finds a triangle.
+#pragma once
+
+#include "ubt_traverse.cuh"
+
+namespace ubt {
+
+struct AeoArgs {
+  const uint32_t* uptr;       // undirected rows
+  const uint64_t* uadj;
+  const uint32_t* umir;       // mirror position of every entry
+  const uint32_t* apair_ptr;  // edges owned by x: [apair_ptr[x], apair_ptr[x + 1])
+  const uint64_t* apairs;     // streamed endpoint | position of the edge in x's row << 32
+  const uint32_t* alist;      // owners
+  uint32_t n_owners;
+  uint32_t n;
+  uint32_t m2;                // 2m, the number of row entries
+  Scratch* sc;
+  uint32_t cap;               // table slots (power of two)
+  uint32_t unit;              // edges a warp takes at a time
+  int64_t L;                  // pruning level (0: none)
+};
+
+// One lane's edge e = x-y: its row-x position and value, the Lemma 3
+// multiplier q_e^2, and the streamed range [vs, vs + dv) of y's row.
+struct AeoPair {
+  uint32_t x, y, pe, qe, vs, dv;
+  int64_t cut;
+  bool ok;
+};
+
+__device__ __forceinline__ AeoPair aeo_pair(const AeoArgs& a, uint32_t x, uint32_t idx, bool in, uint32_t tab_end) {
+  AeoPair pr;
+  pr.x = x;
+  pr.ok = in;
+  pr.vs = 0;
+  pr.dv = 0;
+  pr.cut = 0;
+  const uint64_t d = in ? a.apairs[idx] : 0ull;
+  pr.y = (uint32_t)d;
+  pr.pe = (uint32_t)(d >> 32);
+  if (pr.ok && (pr.pe >= a.m2 || pr.y >= a.n)) {
+    guard_fail(a.sc, kGuardList, x);
+    pr.ok = false;
+  }
+  // no table entry after e in this chunk: nothing to find
+  if (pr.pe + 1 >= tab_end) pr.ok = false;
+  const uint64_t e = pr.ok ? a.uadj[pr.pe] : 0ull;
+  pr.qe = adj_valbits(e);
+  const int64_t aq = qabs(pr.qe);
+  pr.cut = aq * aq;
+  if (a.L > 0 && aq * (1ll << 30) < a.L) pr.ok = false;  // Lemma 2
+  if (pr.ok) {
+    const uint32_t ys = a.uptr[pr.y], ye = a.uptr[pr.y + 1];
+    const uint32_t start = a.umir[pr.pe] + 1;
+    if (ye < ys || ye > a.m2 || start < ys || start > ye) {
+      guard_fail(a.sc, kGuardList, pr.y);
+      pr.ok = false;
+    } else {
+      const uint32_t end = a.L > 0 ? ys + prune_prefix(a.uadj + ys, ye - ys, pr.cut, a.L) : ye;  // Lemma 3
+      pr.vs = start;
+      pr.dv = end > start ? end - start : 0u;
+    }
+  }
+  return pr;
+}
+
+// A hit w of the table counts only if x-w lies after e in x's row and passes
+// Lemma 3's cutoff.
+__device__ __forceinline__ bool aeo_keep(const AeoArgs& a, uint32_t pw, uint32_t qxw, uint32_t pe, int64_t cut) {
+  return pw > pe && (a.L == 0 || qabs(qxw) * cut >= a.L);
+}
+
+// One warp streams the ranges of up to 32 edges (one per lane).
+template <class V>
+__device__ __forceinline__ void aeo_probe(const AeoArgs& a, V& vis, const Table& t, const AeoPair& pr) {
+  const int lane = (int)lane_id();
+  const uint64_t* __restrict__ adj = a.uadj;
+  Scratch* const sc = a.sc;
+  const uint32_t dv = pr.ok ? pr.dv : 0u;
+  constexpr uint32_t kLong = 48;
+  unsigned longm = __ballot_sync(kFull, dv >= kLong);
+  while (longm) {
+    const int j = __ffs(longm) - 1;
+    longm &= longm - 1;
+    const uint32_t xj = __shfl_sync(kFull, pr.x, j);
+    const uint32_t yj = __shfl_sync(kFull, pr.y, j);
+    const uint32_t vsj = __shfl_sync(kFull, pr.vs, j);
+    const uint32_t dvj = __shfl_sync(kFull, dv, j);
+    const uint32_t qj = __shfl_sync(kFull, pr.qe, j);
+    const uint32_t pj = __shfl_sync(kFull, pr.pe, j);
+    const long long cj = __shfl_sync(kFull, (long long)pr.cut, j);
+    for (uint32_t off = 0; off < dvj; off += 64) {
+      uint64_t e[2];
+#pragma unroll
+      for (int s = 0; s < 2; s++) {
+        const uint32_t i = off + 32 * s + lane;
+        e[s] = i < dvj ? adj[vsj + i] : 0ull;
+      }
+#pragma unroll
+      for (int s = 0; s < 2; s++) {
+        const uint32_t i = off + 32 * s + lane;
+        uint32_t qxw = 0, pxw = 0;
+        bool hit = i < dvj && table_find<true>(t, adj_col(e[s]), qxw, pxw, sc);
+        hit = hit && aeo_keep(a, pxw, qxw, pj, cj);
+        if (off + 32 * s < dvj) vis.step(hit, xj, yj, adj_col(e[s]), qj, qxw, adj_valbits(e[s]), pj, pxw, vsj + i);
+      }
+    }
+  }
+  // short ranges: concatenated so that every lane probes one entry per step
+  const uint32_t ds = dv >= kLong ? 0u : dv;
+  uint32_t incl = ds;
+#pragma unroll
+  for (int d = 1; d < 32; d <<= 1) {
+    const uint32_t y = __shfl_up_sync(kFull, incl, d);
+    if (lane >= d) incl += y;
+  }
+  const uint32_t total = __shfl_sync(kFull, incl, 31);
+  const uint32_t excl = incl - ds;
+  for (uint32_t base = 0; base < total; base += 32) {
+    const uint32_t f = base + lane;
+    const bool act = f < total;
+    int j = 0;
+#pragma unroll
+    for (int b = 16; b > 0; b >>= 1) {
+      const uint32_t tj = __shfl_sync(kFull, incl, j + b - 1);
+      if (tj <= f) j += b;
+    }
+    j = j > 31 ? 31 : j;
+    const uint32_t vsj = __shfl_sync(kFull, pr.vs, j);
+    const uint32_t exj = __shfl_sync(kFull, excl, j);
+    const uint32_t xj = __shfl_sync(kFull, pr.x, j);
+    const uint32_t yj = __shfl_sync(kFull, pr.y, j);
+    const uint32_t qj = __shfl_sync(kFull, pr.qe, j);
+    const uint32_t pj = __shfl_sync(kFull, pr.pe, j);
+    const long long cj = __shfl_sync(kFull, (long long)pr.cut, j);
+    const uint32_t pos = vsj + (f - exj);
+    const uint64_t e = act ? adj[pos] : 0ull;
+    uint32_t qxw = 0, pxw = 0;
+    bool hit = act && table_find<true>(t, adj_col(e), qxw, pxw, sc);
+    hit = hit && aeo_keep(a, pxw, qxw, pj, cj);
+    vis.step(hit, xj, yj, adj_col(e), qj, qxw, adj_valbits(e), pj, pxw, pos);
+  }
+}
+
+// One block handles owner x: its row's Lemma 2 prefix goes into the table,
+// chunk by chunk when it is longer than one table; for every chunk, every
+// edge x owns streams its range.
+template <class V>
+__device__ void aeo_task(const AeoArgs& a, V& vis, uint32_t x, uint32_t* tab, uint32_t* s_misc) {
+  const int tid = threadIdx.x, lane = tid & 31;
+  if (x >= a.n) {
+    if (tid == 0) guard_fail(a.sc, kGuardVertex, x);
+    return;
+  }
+  const uint32_t rs = a.uptr[x], re = a.uptr[x + 1];
+  const uint32_t ps = a.apair_ptr[x], pend = a.apair_ptr[x + 1];
+  if (re < rs || re > a.m2 || pend < ps || pend - ps > re - rs) {
+    if (tid == 0) guard_fail(a.sc, kGuardList, x);
+    return;
+  }
+  const uint32_t np = pend - ps;
+  if (tid == 0) s_misc[0] = a.L > 0 ? prune_prefix(a.uadj + rs, re - rs, 1ll << 30, a.L) : re - rs;  // Lemma 2
+  __syncthreads();
+  const uint32_t tlen = s_misc[0];
+  __syncthreads();
+  if (tlen < 2 || np == 0) return;
+  const uint32_t chunk = a.cap / 4;
+  const uint32_t nw = blockDim.x >> 5;
+  vis.task_begin(x);
+  for (uint32_t c0 = 0; c0 < tlen; c0 += chunk) {
+    const uint32_t c1 = min(tlen, c0 + chunk);
+    const uint32_t slots = slots_for(c1 - c0);
+    const Table t = make_table(tab, a.cap, slots);
+    for (uint32_t i = tid; i < slots; i += blockDim.x) t.key[i] = kEmpty;
+    if (tid == 0) s_misc[1] = 0;
+    __syncthreads();
+    for (uint32_t i = c0 + tid; i < c1; i += blockDim.x) {
+      const uint64_t e = a.uadj[rs + i];
+      table_insert(t, adj_col(e), adj_valbits(e), rs + i, a.sc);
+    }
+    __syncthreads();
+    while (true) {
+      uint32_t c = 0, cnt = 0;
+      if (lane == 0) {
+        const uint32_t seen = *(volatile uint32_t*)&s_misc[1];
+        const uint32_t rem = seen < np ? np - seen : 0u;
+        const uint32_t want = max(1u, min(a.unit, rem / (2 * nw)));
+        c = atomicAdd(&s_misc[1], want);
+        cnt = c < np ? min(want, np - c) : 0u;
+      }
+      c = __shfl_sync(kFull, c, 0);
+      cnt = __shfl_sync(kFull, cnt, 0);
+      if (cnt == 0) break;
+      aeo_probe<V>(a, vis, t, aeo_pair(a, x, ps + c + lane, (uint32_t)lane < cnt, rs + c1));
+    }
+    __syncthreads();
+  }
+  vis.task_end(x);
+  __syncthreads();
+}
+
+template <class V>
+__global__ void __launch_bounds__(512, 2) k_aeo(AeoArgs a, typename V::P p) {
+  extern __shared__ __align__(16) char smem[];
+  __shared__ uint32_t s_misc[4];
+  V vis(p, smem);
+  vis.block_init();
+  __syncthreads();
+  uint32_t* tab = (uint32_t*)(smem + ((V::smem_bytes((int)blockDim.x) + 15) / 16) * 16);
+  while (true) {
+    if (threadIdx.x == 0) s_misc[2] = (uint32_t)atomicAdd(&a.sc->task[0], 1ull);
+    __syncthreads();
+    const uint32_t task = s_misc[2];
+    __syncthreads();
+    if (task >= a.n_owners) break;
+    aeo_task(a, vis, a.alist[task], tab, s_misc);
+  }
+  __syncthreads();
+  vis.block_end();
+}
+
+namespace {
+
+template <class V>
+ubt_status launch_aeo(const ubt_graph* g, int64_t L, const typename V::P& p, cudaStream_t s) {
+  if (!g->uptr) return UBT_ERR_UNSUPPORTED;
+  const Tuning& T = tuning();
+  AeoArgs a;
+  a.uptr = g->uptr;
+  a.uadj = g->uadj;
+  a.umir = g->umir;
+  a.apair_ptr = g->apair_ptr;
+  a.apairs = g->apairs;
+  a.alist = g->alist;
+  a.n_owners = (uint32_t)g->n_aowners;
+  a.n = (uint32_t)g->n;
+  a.m2 = (uint32_t)(2 * g->m);
+  a.sc = g->scratch;
+  a.cap = (uint32_t)std::min<int64_t>(table_slots(std::max<int64_t>(g->max_udeg, 2)),
+                                      std::max<int64_t>(64, T.smem_table_max));
+  a.unit = (uint32_t)std::min<int64_t>(32, std::max<int64_t>(1, T.block_unit));
+  a.L = L;
+  UBT_CUDA(cudaMemsetAsync(a.sc, 0, kScratchHeader / 2, s));
+  if (a.n_owners == 0) return UBT_OK;
+  const int threads = 512;
+  const size_t smem = (size_t)((V::smem_bytes(threads) + 15) / 16) * 16 + (size_t)a.cap * 3 * 4;
+  UBT_CUDA(cudaFuncSetAttribute(k_aeo<V>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+  int per_sm = 0;
+  UBT_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_aeo<V>, threads, smem));
+  if (per_sm < 1) return UBT_ERR_INVALID_ARG;
+  per_sm = (int)std::min<int64_t>(per_sm, std::max<int64_t>(1, T.blocks_per_sm));
+  k_aeo<V><<<g->sm_count * per_sm, threads, smem, s>>>(a, p);
+  UBT_CUDA(cudaGetLastError());
+  return UBT_OK;
+}
+
+}  // namespace
+
+}  // namespace ubt

@@ -338,6 +338,146 @@ __global__ void k_fill_lists(int64_t n, const uint8_t* __restrict__ bucket, unsi
   }
 }
 
+// ---------------------------------------------------------------- undirected AEO adjacency
+
+// both directions of every edge, in row order of arrival (sorted below)
+__global__ void k_uscatter(int64_t m, const uint32_t* __restrict__ src, const uint32_t* __restrict__ dst,
+                           const uint32_t* __restrict__ k, const uint32_t* __restrict__ uptr,
+                           uint32_t* __restrict__ ufill, uint64_t* __restrict__ uadj, uint32_t* __restrict__ ueid) {
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < m; i += (int64_t)gridDim.x * blockDim.x) {
+    const uint32_t a = src[i], b = dst[i];
+    const uint32_t val = (uint32_t)(int32_t)(32768 - (int32_t)k[i]);
+    const uint32_t pa = uptr[a] + atomicAdd(&ufill[a], 1u);
+    const uint32_t pb = uptr[b] + atomicAdd(&ufill[b], 1u);
+    uadj[pa] = adj_pack(b, val);
+    ueid[pa] = (uint32_t)i;
+    uadj[pb] = adj_pack(a, val);
+    ueid[pb] = (uint32_t)i;
+  }
+}
+
+// Rows longer than the shared-memory sort limit: one block per row, sorted
+// in place in global memory by a bitonic network whose comparators all put
+// the smaller key first (the first comparator of every merge pairs i with its
+// mirror i ^ (kk - 1)); positions >= len act as +infinity, so comparators
+// that touch them never swap and are skipped.
+__global__ void k_sort_rows_inplace(const uint32_t* __restrict__ rows, uint32_t nrows,
+                                    const uint32_t* __restrict__ row_ptr, uint64_t* adj, uint32_t* eid) {
+  for (uint32_t r = blockIdx.x; r < nrows; r += gridDim.x) {
+    const uint32_t u = rows[r];
+    const uint32_t rs = row_ptr[u], len = row_ptr[u + 1] - rs;
+    uint32_t cap = 2;
+    while (cap < len) cap <<= 1;
+    for (uint32_t kk = 2; kk <= cap; kk <<= 1) {
+      for (uint32_t j = kk >> 1; j > 0; j >>= 1) {
+        for (uint32_t i = threadIdx.x; i < cap; i += blockDim.x) {
+          const uint32_t ixj = (j == (kk >> 1)) ? (i ^ (kk - 1)) : (i ^ j);
+          if (ixj > i && ixj < len) {
+            const uint64_t a = adj[rs + i], b = adj[rs + ixj];
+            if (key_by_absq(a) > key_by_absq(b)) {
+              adj[rs + i] = b;
+              adj[rs + ixj] = a;
+              const uint32_t t = eid[rs + i];
+              eid[rs + i] = eid[rs + ixj];
+              eid[rs + ixj] = t;
+            }
+          }
+        }
+        __syncthreads();
+      }
+    }
+  }
+}
+
+// epos[2e + side] = position of edge e in the row of its smaller (side 0) or
+// larger (side 1) endpoint; then umir[p] = the other one.  One warp per row.
+__global__ void k_uepos(int64_t n, const uint32_t* __restrict__ uptr, const uint64_t* __restrict__ uadj,
+                        const uint32_t* __restrict__ ueid, uint32_t* __restrict__ epos) {
+  const int lane = threadIdx.x & 31;
+  const int64_t warps = (int64_t)gridDim.x * (blockDim.x >> 5);
+  for (int64_t x = blockIdx.x * (int64_t)(blockDim.x >> 5) + (threadIdx.x >> 5); x < n; x += warps)
+    for (uint32_t p = uptr[x] + lane; p < uptr[x + 1]; p += 32)
+      epos[2 * (size_t)ueid[p] + ((uint32_t)x > adj_col(uadj[p]) ? 1 : 0)] = p;
+}
+__global__ void k_umirror(int64_t n, const uint32_t* __restrict__ uptr, const uint64_t* __restrict__ uadj,
+                          const uint32_t* __restrict__ ueid, const uint32_t* __restrict__ epos,
+                          uint32_t* __restrict__ umir) {
+  const int lane = threadIdx.x & 31;
+  const int64_t warps = (int64_t)gridDim.x * (blockDim.x >> 5);
+  for (int64_t x = blockIdx.x * (int64_t)(blockDim.x >> 5) + (threadIdx.x >> 5); x < n; x += warps)
+    for (uint32_t p = uptr[x] + lane; p < uptr[x + 1]; p += 32)
+      umir[p] = epos[2 * (size_t)ueid[p] + ((uint32_t)x > adj_col(uadj[p]) ? 0 : 1)];
+}
+
+// AEO traversal: edge x-y is handled by x, the endpoint with the longer list
+// (ties: the larger id), which holds the hash table; y's list is streamed.
+__device__ inline bool aeo_owns(uint32_t x, uint32_t y, uint32_t dx, uint32_t dy) {
+  return dx > dy || (dx == dy && x > y);
+}
+__global__ void k_apair_count(int64_t n, const uint32_t* __restrict__ uptr, const uint64_t* __restrict__ uadj,
+                              uint32_t* __restrict__ pcount) {
+  const int lane = threadIdx.x & 31;
+  const int64_t warps = (int64_t)gridDim.x * (blockDim.x >> 5);
+  for (int64_t x = blockIdx.x * (int64_t)(blockDim.x >> 5) + (threadIdx.x >> 5); x < n; x += warps) {
+    const uint32_t dx = uptr[x + 1] - uptr[x];
+    uint32_t c = 0;
+    for (uint32_t p = uptr[x] + lane; p < uptr[x + 1]; p += 32) {
+      const uint32_t y = adj_col(uadj[p]);
+      c += aeo_owns((uint32_t)x, y, dx, uptr[y + 1] - uptr[y]) ? 1u : 0u;
+    }
+    c = __reduce_add_sync(kFull, c);
+    if (lane == 0) pcount[x] = c;
+  }
+}
+// pair words in row order: streamed endpoint | position of the edge in x's row << 32
+__global__ void k_apair_fill(int64_t n, const uint32_t* __restrict__ uptr, const uint64_t* __restrict__ uadj,
+                             const uint32_t* __restrict__ apair_ptr, uint64_t* __restrict__ apairs,
+                             unsigned long long* __restrict__ work) {
+  const int lane = threadIdx.x & 31;
+  const int64_t warps = (int64_t)gridDim.x * (blockDim.x >> 5);
+  for (int64_t x = blockIdx.x * (int64_t)(blockDim.x >> 5) + (threadIdx.x >> 5); x < n; x += warps) {
+    const uint32_t dx = uptr[x + 1] - uptr[x];
+    uint32_t at = apair_ptr[x];
+    unsigned long long w = 0;
+    for (uint32_t base = uptr[x]; base < uptr[x + 1]; base += 32) {
+      const uint32_t p = base + lane;
+      bool own = false;
+      uint32_t y = 0;
+      if (p < uptr[x + 1]) {
+        y = adj_col(uadj[p]);
+        own = aeo_owns((uint32_t)x, y, dx, uptr[y + 1] - uptr[y]);
+      }
+      const unsigned msk = __ballot_sync(kFull, own);
+      if (own) {
+        apairs[at + __popc(msk & lanemask_lt())] = ((uint64_t)p << 32) | y;
+        w += uptr[y + 1] - uptr[y];
+      }
+      at += __popc(msk);
+    }
+#pragma unroll
+    for (int d = 16; d > 0; d >>= 1) w += __shfl_xor_sync(kFull, w, d);
+    if (lane == 0) work[x] = w;
+  }
+}
+// owners by decreasing log2 of their streamed work
+__global__ void k_afill_lists(int64_t n, const uint32_t* __restrict__ apair_ptr,
+                              const unsigned long long* __restrict__ work, unsigned long long* cursor,
+                              uint32_t* __restrict__ lists, int count_only) {
+  for (int64_t x = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; x < n; x += (int64_t)gridDim.x * blockDim.x) {
+    if (apair_ptr[x + 1] == apair_ptr[x]) continue;
+    const unsigned long long w = work[x];
+    const int lg = w ? 63 - __clzll(w) : 0;
+    if (count_only) atomicAdd(&cursor[lg], 1ull);
+    else lists[atomicAdd(&cursor[lg], 1ull)] = (uint32_t)x;
+  }
+}
+__global__ void k_max_row(int64_t n, const uint32_t* __restrict__ ptr, unsigned long long* out) {
+  unsigned long long best = 0;
+  for (int64_t x = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; x < n; x += (int64_t)gridDim.x * blockDim.x)
+    best = max(best, (unsigned long long)(ptr[x + 1] - ptr[x]));
+  atomicMax(out, best);
+}
+
 struct BuildLayout {
   // persistent
   Scratch* scratch;
@@ -349,6 +489,15 @@ struct BuildLayout {
   uint64_t* pairs;
   uint32_t* lists;       // giant | hub | medium tasks
   uint32_t* vgraph;
+  uint32_t* uptr;        // undirected AEO adjacency (optional)
+  uint64_t* uadj;
+  uint32_t* ueid;
+  uint32_t* umir;
+  uint32_t* uepos;
+  uint32_t* apair_ptr;
+  uint64_t* apairs;
+  uint32_t* alist;
+  unsigned long long* awork;
   unsigned long long* gacc;
   unsigned long long* bacc;
   uint32_t* gtab;
@@ -393,6 +542,16 @@ BuildLayout layout(void* ws, size_t cap, int64_t n, int64_t m, const ubt_graph_o
   L.pairs = c.take<uint64_t>(std::max<int64_t>(m, 1));
   L.lists = c.take<uint32_t>(n1);
   L.vgraph = batch ? c.take<uint32_t>(n1) : nullptr;
+  const bool und = opts && (opts->flags & UBT_OPT_UNDIRECTED);
+  L.uptr = und ? c.take<uint32_t>(n + 1) : nullptr;
+  L.uadj = und ? c.take<uint64_t>(std::max<int64_t>(2 * m, 1)) : nullptr;
+  L.ueid = und ? c.take<uint32_t>(std::max<int64_t>(2 * m, 1)) : nullptr;
+  L.umir = und ? c.take<uint32_t>(std::max<int64_t>(2 * m, 1)) : nullptr;
+  L.uepos = und ? c.take<uint32_t>(std::max<int64_t>(2 * m, 1)) : nullptr;
+  L.apair_ptr = und ? c.take<uint32_t>(n + 1) : nullptr;
+  L.apairs = und ? c.take<uint64_t>(std::max<int64_t>(m, 1)) : nullptr;
+  L.alist = und ? c.take<uint32_t>(n1) : nullptr;
+  L.awork = und ? c.take<unsigned long long>(n1) : nullptr;
   L.gacc = c.take<unsigned long long>(std::max<int64_t>(m, 1));
   // per graph: T, sum_lo, sum_hi (expected counts) of a batch
   L.bacc = c.take<unsigned long long>(3 * std::max<int64_t>(ng, 1));
@@ -464,6 +623,9 @@ extern "C" ubt_status ubt_create_graph(int64_t n, int64_t m, const uint32_t* d_s
     return UBT_ERR_INVALID_ARG;
   }
   if (m > 0 && (!d_src || !d_dst)) return UBT_ERR_INVALID_ARG;
+  const bool und = opts && (opts->flags & UBT_OPT_UNDIRECTED);
+  if (opts && (opts->flags & ~(int64_t)UBT_OPT_UNDIRECTED)) return UBT_ERR_INVALID_ARG;
+  if (und && flags != UBT_GRAPH_FIXED) return UBT_ERR_UNSUPPORTED;
   if (!d_workspace || ((uintptr_t)d_workspace & 255)) return UBT_ERR_INVALID_ARG;
   const bool batch = opts && opts->d_vertex_offsets;
   if (batch && opts->n_graphs < 1) return UBT_ERR_INVALID_ARG;
@@ -577,6 +739,63 @@ extern "C" ubt_status ubt_create_graph(int64_t n, int64_t m, const uint32_t* d_s
     UBT_CUDA(cudaStreamSynchronize(s));
   }
   (void)ng;
+  // 6. undirected adjacency in Absolute Edge Order, its mirror positions and
+  //    the AEO pair partition (optional)
+  int64_t n_aowners = 0, max_udeg = 0;
+  if (und && n > 0) {
+    UBT_CUDA(exclusive_scan_u32(L.deg, L.uptr, n, L.scan_tmp, s));
+    UBT_CUDA(cudaMemsetAsync(L.fill, 0, sizeof(uint32_t) * (n + 1), s));
+    if (m > 0) k_uscatter<<<grid_e, thr, 0, s>>>(m, d_src, d_dst, d_k, L.uptr, L.fill, L.uadj, L.ueid);
+    k_sort_short_rows<<<grid_w, thr, 0, s>>>(n, L.uptr, L.uadj, L.ueid, nullptr, 1, &L.scratch->err);
+    const uint32_t sort_smem = (uint32_t)tuning().sort_smem_max;
+    UBT_CUDA(cudaMemsetAsync(lcount, 0, 2 * sizeof(unsigned long long), s));
+    k_collect_long<<<grid_v, thr, 0, s>>>(n, L.uptr, sort_smem, L.mid_rows, L.huge_rows, lcount);
+    unsigned long long lc[2] = {0, 0};
+    UBT_CUDA(cudaMemcpyAsync(lc, lcount, sizeof(lc), cudaMemcpyDeviceToHost, s));
+    UBT_CUDA(cudaStreamSynchronize(s));
+    if (lc[0]) {
+      const size_t smem = (size_t)std::max<uint32_t>(sort_smem, 64) * 24;
+      UBT_CUDA(cudaFuncSetAttribute(k_sort_long_rows<false>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+      const int g2 = (int)std::min<unsigned long long>(lc[0], (unsigned long long)sms * 8);
+      k_sort_long_rows<false><<<g2, 512, smem, s>>>(L.mid_rows, (uint32_t)lc[0], L.uptr, L.uadj, L.ueid, nullptr,
+                                                    1, &L.scratch->err, nullptr, 0);
+    }
+    if (lc[1]) {
+      const int g2 = (int)std::min<unsigned long long>(lc[1], (unsigned long long)sms * 2);
+      k_sort_rows_inplace<<<g2, 1024, 0, s>>>(L.huge_rows, (uint32_t)lc[1], L.uptr, L.uadj, L.ueid);
+    }
+    k_uepos<<<grid_w, thr, 0, s>>>(n, L.uptr, L.uadj, L.ueid, L.uepos);
+    k_umirror<<<grid_w, thr, 0, s>>>(n, L.uptr, L.uadj, L.ueid, L.uepos, L.umir);
+    UBT_CUDA(cudaMemsetAsync(L.fill, 0, sizeof(uint32_t) * (n + 1), s));
+    k_apair_count<<<grid_w, thr, 0, s>>>(n, L.uptr, L.uadj, L.fill);
+    UBT_CUDA(exclusive_scan_u32(L.fill, L.apair_ptr, n, L.scan_tmp, s));
+    k_apair_fill<<<grid_w, thr, 0, s>>>(n, L.uptr, L.uadj, L.apair_ptr, L.apairs, L.awork);
+    unsigned long long* acur = L.stats;  // kLgMax + 1 cursors
+    UBT_CUDA(cudaMemsetAsync(acur, 0, sizeof(unsigned long long) * (kLgMax + 2), s));
+    k_afill_lists<<<grid_v, thr, 0, s>>>(n, L.apair_ptr, L.awork, acur, L.alist, 1);
+    unsigned long long acount[kLgMax + 2];
+    UBT_CUDA(cudaMemcpyAsync(acount, acur, sizeof(acount), cudaMemcpyDeviceToHost, s));
+    UBT_CUDA(cudaStreamSynchronize(s));
+    unsigned long long run = 0;
+    for (int lg = kLgMax; lg >= 0; lg--) {
+      const unsigned long long c = acount[lg];
+      acount[lg] = run;
+      run += c;
+    }
+    n_aowners = (int64_t)run;
+    acount[kLgMax + 1] = 0;
+    UBT_CUDA(cudaMemcpyAsync(acur, acount, sizeof(acount), cudaMemcpyHostToDevice, s));
+    k_afill_lists<<<grid_v, thr, 0, s>>>(n, L.apair_ptr, L.awork, acur, L.alist, 0);
+    k_max_row<<<grid_v, thr, 0, s>>>(n, L.uptr, &acur[kLgMax + 1]);
+    unsigned long long mx = 0;
+    UBT_CUDA(cudaMemcpyAsync(&mx, &acur[kLgMax + 1], sizeof(mx), cudaMemcpyDeviceToHost, s));
+    UBT_CUDA(cudaMemcpyAsync(&err, &L.scratch->err, sizeof(err), cudaMemcpyDeviceToHost, s));
+    UBT_CUDA(cudaGetLastError());
+    UBT_CUDA(cudaStreamSynchronize(s));
+    max_udeg = (int64_t)mx;
+    st = status_from_err(err);
+    if (st != UBT_OK) return st;
+  }
 
   ubt_graph* g = new (std::nothrow) ubt_graph();
   if (!g) return UBT_ERR_INVALID_ARG;
@@ -597,6 +816,16 @@ extern "C" ubt_status ubt_create_graph(int64_t n, int64_t m, const uint32_t* d_s
   g->med_list = L.lists + count_cls[kClsGiant] + count_cls[kClsHub];
   g->n_med = count_cls[kClsMedium];
   g->vgraph = L.vgraph;
+  g->uptr = L.uptr;
+  g->uadj = L.uadj;
+  g->ueid = L.ueid;
+  g->umir = L.umir;
+  g->uepos = L.uepos;
+  g->apair_ptr = L.apair_ptr;
+  g->apairs = L.apairs;
+  g->alist = L.alist;
+  g->n_aowners = n_aowners;
+  g->max_udeg = max_udeg;
   g->gacc = L.gacc;
   g->bacc = L.bacc;
   g->gtab = L.gtab;

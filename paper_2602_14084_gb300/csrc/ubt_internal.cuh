@@ -85,6 +85,19 @@ struct ubt_graph {
   uint32_t* hub_list = nullptr;     // long lists or heavy owners: whole-block tasks
   uint32_t* med_list = nullptr;     // the other owners: one-warp tasks
   uint32_t* vgraph = nullptr;       // batch: graph id of every vertex (or null)
+  // undirected adjacency in Absolute Edge Order (UBT_OPT_UNDIRECTED; else null):
+  // row x holds every edge at x, |q| descending then neighbour id (Def. AEO
+  // restricted to the edges at x), packed like adj
+  uint32_t* uptr = nullptr;         // n + 1
+  uint64_t* uadj = nullptr;         // 2m
+  uint32_t* ueid = nullptr;         // 2m: input edge index
+  uint32_t* umir = nullptr;         // 2m: position of the same edge in the other endpoint's row
+  uint32_t* uepos = nullptr;        // 2m: [2e + side] position of input edge e in the row of its
+                                    //     smaller-id (side 0) / larger-id (side 1) endpoint
+  uint32_t* apair_ptr = nullptr;    // n + 1: edges owned by x in the AEO traversal
+  uint64_t* apairs = nullptr;       // m: streamed endpoint | position of the edge in x's row << 32
+  uint32_t* alist = nullptr;        // owners, by decreasing streamed work
+  int64_t n_aowners = 0, max_udeg = 0;
   unsigned long long* gacc = nullptr;   // m: backward accumulators
   unsigned long long* bacc = nullptr;   // batch accumulators
   uint32_t* gtab = nullptr;         // global hash tables for very long lists

@@ -1,0 +1,287 @@
+// ubt_local.cu -- local counts of sampled edges and vertices, and the
+// sampling estimators built on them (Sec. 6).
+//
+// Edge sampling (Algs. 5-6): for k edges drawn uniformly, the local counts
+// |B_t(e)| / |U_t(e)| (t-balanced / t-unbalanced triangles through e) are
+// extrapolated as |E| |B_t(e)| / 3 and averaged.  Vertex sampling (Algs.
+// 3-4): the same with the triangles through a vertex and |V| |B_t(v)| / 3.
+// Both are unbiased: every triangle has three edges and three vertices.  The
+// samples are the caller's (the method's random draws are inputs here).
+//
+// The improved local searches of Algs. 4 and 6 scan neighbour lists in
+// Absolute Edge Order and stop at the pruning cutoffs; here the undirected
+// rows (|q| descending, UBT_OPT_UNDIRECTED) make every cutoff a prefix:
+//   edge e = x-y:  w with |q_xw| |q_e| 2^15 >= L on both rows (the third
+//                  factor is at most 2^15), nothing if |q_e| 2^30 < L
+//   vertex v:      its row's Lemma 2 prefix; for each a there, a's row up to
+//                  |q_ab| |q_va| qmax(v) >= L, and b counts once, at the later
+//                  of the two positions in v's row
+// One block per sample: the longer list (edge) or v's row (vertex) becomes a
+// shared-memory hash table, in chunks when it is longer than one table, and
+// the other lists are streamed through it.  Every triangle found is placed
+// among the sorted threshold levels by binary search and counted in a
+// per-sample shared histogram, turned into per-threshold counts at the end.
+#include <algorithm>
+#include <numeric>
+#include <vector>
+
+#include "ubt_traverse.cuh"
+
+namespace ubt {
+
+namespace {
+
+constexpr int kLocalTau = 64;
+constexpr int kLocalSub = 256;  // streamed entries per warp task of an edge sample
+
+struct LocalP {
+  int nt;
+  int half;                     // 2^(K-1) with 2^K > 2 nt
+  int64_t S[2 * kLocalTau];     // levels: every B and every U, ascending
+  int perm[kLocalTau];          // caller index of the i-th smallest t
+};
+
+struct LocalArgs {
+  const uint32_t* uptr;
+  const uint64_t* uadj;
+  const uint32_t* uepos;        // 2m: positions of every edge in its endpoints' rows
+  const uint32_t* items;        // sampled edges (input index) or vertices
+  uint32_t n_items;
+  int vertex_mode;
+  uint32_t n, m, m2;
+  int64_t L;
+  uint32_t cap;                 // table slots
+  Scratch* sc;
+  int64_t* bal;                 // [item][t]
+  int64_t* unbal;
+};
+
+// interval of P among the levels: #{S_j < P} (levels padded with +inf)
+__device__ __forceinline__ int level_of(const long long* S, int half, long long P) {
+  int r = 0;
+  for (int b = half; b > 0; b >>= 1)
+    if (S[r + b - 1] < P) r += b;
+  return r;
+}
+
+__global__ void __launch_bounds__(512, 2) k_local(LocalArgs a, LocalP p) {
+  extern __shared__ __align__(16) char smem[];
+  __shared__ uint32_t s_misc[8];
+  long long* S = (long long*)smem;                       // 256 padded levels
+  unsigned long long* bins = (unsigned long long*)(smem + 256 * 8);  // 2 nt + 1 (<= 129) bins
+  uint32_t* tab = (uint32_t*)(bins + 144);
+  const int tid = threadIdx.x, lane = tid & 31, wid = tid >> 5, nw = blockDim.x >> 5;
+  for (int i = tid; i < 256; i += blockDim.x) S[i] = i < 2 * p.nt ? p.S[i] : INT64_MAX;
+  __syncthreads();
+  while (true) {
+    if (tid == 0) s_misc[0] = (uint32_t)atomicAdd(&a.sc->task[0], 1ull);
+    for (int i = tid; i <= 2 * p.nt; i += blockDim.x) bins[i] = 0;
+    __syncthreads();
+    const uint32_t item = s_misc[0];
+    if (item >= a.n_items) break;
+    // the sample: table row x (its prefix tlen), the pair's value and, for an
+    // edge, the streamed row y (its prefix ylen)
+    uint32_t x = 0, y = 0, tlen = 0, ylen = 0, qe = 0, npv = 0;
+    int64_t qmax = 0;
+    bool ok = true;
+    const uint32_t id = a.items[item];
+    if (!a.vertex_mode) {
+      if (id >= a.m) {
+        if (tid == 0) guard_fail(a.sc, kGuardList, id);
+        ok = false;
+      } else {
+        const uint32_t p0 = a.uepos[2 * (size_t)id], p1 = a.uepos[2 * (size_t)id + 1];
+        const uint32_t lo = adj_col(a.uadj[p1]), hi = adj_col(a.uadj[p0]);  // endpoints
+        qe = adj_valbits(a.uadj[p0]);
+        const uint32_t dlo = a.uptr[lo + 1] - a.uptr[lo], dhi = a.uptr[hi + 1] - a.uptr[hi];
+        x = dhi >= dlo ? hi : lo;
+        y = x == hi ? lo : hi;
+        const int64_t c = qabs(qe) * 32768;
+        if (a.L > 0 && qabs(qe) * (1ll << 30) < a.L) ok = false;  // Lemma 2 on e
+        tlen = a.uptr[x + 1] - a.uptr[x];
+        ylen = a.uptr[y + 1] - a.uptr[y];
+        if (a.L > 0) {
+          tlen = prune_prefix(a.uadj + a.uptr[x], tlen, c, a.L);
+          ylen = prune_prefix(a.uadj + a.uptr[y], ylen, c, a.L);
+        }
+        npv = (ylen + kLocalSub - 1) / kLocalSub;
+      }
+    } else {
+      if (id >= a.n) {
+        if (tid == 0) guard_fail(a.sc, kGuardVertex, id);
+        ok = false;
+      } else {
+        x = id;
+        tlen = a.uptr[x + 1] - a.uptr[x];
+        if (a.L > 0 && tlen > 0) {
+          qmax = qabs(adj_valbits(a.uadj[a.uptr[x]]));
+          tlen = prune_prefix(a.uadj + a.uptr[x], tlen, 1ll << 30, a.L);  // Lemma 2
+        }
+        npv = tlen;
+      }
+    }
+    const uint32_t rs = a.uptr[x];
+    const uint32_t chunk = a.cap / 4;
+    for (uint32_t c0 = 0; ok && c0 < tlen; c0 += chunk) {
+      const uint32_t c1 = min(tlen, c0 + chunk);
+      const uint32_t slots = slots_for(c1 - c0);
+      const Table t = make_table(tab, a.cap, slots);
+      for (uint32_t i = tid; i < slots; i += blockDim.x) t.key[i] = kEmpty;
+      __syncthreads();
+      for (uint32_t i = c0 + tid; i < c1; i += blockDim.x) {
+        const uint64_t e = a.uadj[rs + i];
+        table_insert(t, adj_col(e), adj_valbits(e), rs + i, a.sc);
+      }
+      __syncthreads();
+      for (uint32_t v = wid; v < npv; v += nw) {
+        // the streamed range of this warp task and the pair it belongs to
+        uint32_t s0, s1, qp, pp = 0;
+        if (!a.vertex_mode) {
+          s0 = a.uptr[y] + v * kLocalSub;
+          s1 = a.uptr[y] + min(ylen, (v + 1) * kLocalSub);
+          qp = qe;
+        } else {
+          pp = rs + v;                      // x-a at position pp of x's row
+          if (pp + 1 >= rs + c1) continue;  // no table entry after it in this chunk
+          const uint64_t ea = a.uadj[pp];
+          const uint32_t av = adj_col(ea);
+          qp = adj_valbits(ea);
+          if (av >= a.n) {
+            if (lane == 0) guard_fail(a.sc, kGuardVertex, av);
+            continue;
+          }
+          s0 = a.uptr[av];
+          uint32_t len = a.uptr[av + 1] - s0;
+          if (a.L > 0) len = prune_prefix(a.uadj + s0, len, qabs(qp) * qmax, a.L);
+          s1 = s0 + len;
+        }
+        for (uint32_t b0 = s0; b0 < s1; b0 += 32) {
+          const uint32_t pos = b0 + lane;
+          const bool act = pos < s1;
+          const uint64_t e = act ? a.uadj[pos] : 0ull;
+          uint32_t qt = 0, pt = 0;
+          bool hit = act && table_find<true>(t, adj_col(e), qt, pt, a.sc);
+          if (a.vertex_mode) hit = hit && pt > pp;  // each triangle once: at the later position
+          if (hit) {
+            const long long P = (long long)((int32_t)qp * (int32_t)qt) * (long long)(int32_t)adj_valbits(e);
+            atomicAdd(&bins[level_of(S, p.half, P)], 1ull);
+          }
+        }
+      }
+      __syncthreads();
+    }
+    __syncthreads();
+    // histogram -> counts: the i-th smallest t has the (nt-1-i)-th smallest B
+    // and the i-th smallest U
+    if (tid < p.nt) {
+      const int i = tid;
+      long long b = 0, u = 0;
+      for (int r = 0; r <= p.nt - 1 - i; r++) b += bins[r];
+      for (int r = p.nt + i + 1; r <= 2 * p.nt; r++) u += bins[r];
+      a.bal[(size_t)item * p.nt + p.perm[i]] = b;
+      a.unbal[(size_t)item * p.nt + p.perm[i]] = u;
+    }
+    __syncthreads();
+  }
+}
+
+// estimate[t] = scale / k * sum over samples of the local count
+__global__ void k_local_estimate(const int64_t* __restrict__ bal, const int64_t* __restrict__ unbal, uint32_t k,
+                                 int nt, double scale, double* __restrict__ est) {
+  const int t = blockIdx.x;
+  double sb = 0.0, su = 0.0;
+  for (uint32_t i = threadIdx.x; i < k; i += blockDim.x) {
+    sb += (double)bal[(size_t)i * nt + t];
+    su += (double)unbal[(size_t)i * nt + t];
+  }
+  __shared__ double rb[256], ru[256];
+  rb[threadIdx.x] = sb;
+  ru[threadIdx.x] = su;
+  __syncthreads();
+  for (int d = blockDim.x / 2; d > 0; d >>= 1) {
+    if ((int)threadIdx.x < d) {
+      rb[threadIdx.x] += rb[threadIdx.x + d];
+      ru[threadIdx.x] += ru[threadIdx.x + d];
+    }
+    __syncthreads();
+  }
+  if (threadIdx.x == 0) {
+    est[t] = k ? rb[0] * scale / (double)k : 0.0;
+    est[nt + t] = k ? ru[0] * scale / (double)k : 0.0;
+  }
+}
+
+ubt_status local_counts(ubt_graph* g, const uint32_t* d_items, int64_t k, int vertex_mode, const double* h_tau,
+                        int32_t n_tau, int64_t* d_bal, int64_t* d_unbal, double* d_est, cudaStream_t s) {
+  if (!g || k < 0 || (k > 0 && (!d_items || !d_bal || !d_unbal))) return UBT_ERR_INVALID_ARG;
+  if (!h_tau || n_tau < 1 || n_tau > kLocalTau || k >= 0xFFFFFFFFll) return UBT_ERR_INVALID_ARG;
+  if (g->kind != UBT_GRAPH_FIXED || !g->uptr) return UBT_ERR_UNSUPPORTED;
+  std::vector<Level> lv(n_tau);
+  for (int i = 0; i < n_tau; i++)
+    if (!tau_level(h_tau[i], &lv[i])) return UBT_ERR_TAU_OOB;
+  std::vector<int> order(n_tau);
+  std::iota(order.begin(), order.end(), 0);
+  std::stable_sort(order.begin(), order.end(), [&](int x, int y) { return lv[x].L < lv[y].L; });
+  LocalP p;
+  p.nt = n_tau;
+  p.half = 1;
+  while (2 * p.half <= 2 * n_tau) p.half *= 2;
+  for (int i = 0; i < n_tau; i++) {
+    p.S[i] = lv[order[n_tau - 1 - i]].B;
+    p.S[n_tau + i] = lv[order[i]].U;
+    p.perm[i] = order[i];
+  }
+  const Tuning& T = tuning();
+  LocalArgs a;
+  a.uptr = g->uptr;
+  a.uadj = g->uadj;
+  a.uepos = g->uepos;
+  a.items = d_items;
+  a.n_items = (uint32_t)k;
+  a.vertex_mode = vertex_mode;
+  a.n = (uint32_t)g->n;
+  a.m = (uint32_t)g->m;
+  a.m2 = (uint32_t)(2 * g->m);
+  a.L = lv[order[0]].L;
+  a.cap = (uint32_t)std::min<int64_t>(table_slots(std::max<int64_t>(g->max_udeg, 2)),
+                                      std::max<int64_t>(64, T.smem_table_max));
+  a.sc = g->scratch;
+  a.bal = d_bal;
+  a.unbal = d_unbal;
+  UBT_CUDA(cudaMemsetAsync(a.sc, 0, kScratchHeader / 2, s));
+  if (k > 0) {
+    const int threads = 512;
+    const size_t smem = 256 * 8 + 144 * 8 + (size_t)a.cap * 3 * 4;
+    UBT_CUDA(cudaFuncSetAttribute(k_local, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+    int per_sm = 0;
+    UBT_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_local, threads, smem));
+    if (per_sm < 1) return UBT_ERR_INVALID_ARG;
+    const int64_t blocks = std::min<int64_t>((int64_t)g->sm_count * per_sm, k);
+    k_local<<<(int)blocks, threads, smem, s>>>(a, p);
+    UBT_CUDA(cudaGetLastError());
+  }
+  if (d_est) {
+    const double scale = (vertex_mode ? (double)g->n : (double)g->m) / 3.0;
+    k_local_estimate<<<n_tau, 256, 0, s>>>(d_bal, d_unbal, (uint32_t)k, n_tau, scale, d_est);
+    UBT_CUDA(cudaGetLastError());
+  }
+  return UBT_OK;
+}
+
+}  // namespace
+
+}  // namespace ubt
+
+using namespace ubt;
+
+extern "C" ubt_status ubt_edge_local_counts(ubt_graph* g, const uint32_t* d_edges, int64_t k, const double* h_tau,
+                                            int32_t n_tau, int64_t* d_bal, int64_t* d_unbal, double* d_estimate,
+                                            void* stream) {
+  return local_counts(g, d_edges, k, 0, h_tau, n_tau, d_bal, d_unbal, d_estimate, (cudaStream_t)stream);
+}
+
+extern "C" ubt_status ubt_vertex_local_counts(ubt_graph* g, const uint32_t* d_vertices, int64_t k,
+                                              const double* h_tau, int32_t n_tau, int64_t* d_bal, int64_t* d_unbal,
+                                              double* d_estimate, void* stream) {
+  return local_counts(g, d_vertices, k, 1, h_tau, n_tau, d_bal, d_unbal, d_estimate, (cudaStream_t)stream);
+}

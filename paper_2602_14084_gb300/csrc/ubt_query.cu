@@ -13,6 +13,7 @@
 #include <numeric>
 #include <vector>
 
+#include "ubt_aeo.cuh"
 #include "ubt_traverse.cuh"
 
 namespace ubt {
@@ -739,14 +740,23 @@ ubt_status check_taus(const double* h_tau, int n_tau, std::vector<Level>& lv) {
 
 }  // namespace
 
-extern "C" ubt_status ubt_count_threshold(ubt_graph* g, const double* h_tau, int32_t n_tau, int32_t prune,
-                                          int64_t* d_counts, void* stream) {
+namespace {
+
+// Threshold counts through the degree-ordered traversal, or through the edge
+// iteration in Absolute Edge Order (aeo).
+template <class V>
+ubt_status launch_count(const ubt_graph* g, const typename V::P& p, int64_t L, bool aeo, cudaStream_t s) {
+  return aeo ? launch_aeo<V>(g, L, p, s) : launch_traverse<V>(g, p, L, s);
+}
+
+ubt_status count_impl(ubt_graph* g, const double* h_tau, int32_t n_tau, int32_t prune, int64_t* d_counts,
+                      bool aeo, cudaStream_t s) {
   if (!g || !d_counts) return UBT_ERR_INVALID_ARG;
   if (g->kind != UBT_GRAPH_FIXED) return UBT_ERR_UNSUPPORTED;
+  if (aeo && !g->uptr) return UBT_ERR_UNSUPPORTED;
   std::vector<Level> lv;
   ubt_status st = check_taus(h_tau, n_tau, lv);
   if (st != UBT_OK) return st;
-  cudaStream_t s = (cudaStream_t)stream;
   // thresholds in ascending t: B descending, U ascending
   std::vector<int> order(n_tau);
   std::iota(order.begin(), order.end(), 0);
@@ -761,7 +771,7 @@ extern "C" ubt_status ubt_count_threshold(ubt_graph* g, const double* h_tau, int
     }
     p.out = g->scratch->hist;
     UBT_CUDA(cudaMemsetAsync(g->scratch->hist, 0, sizeof(g->scratch->hist), s));
-    st = launch_traverse<CountBins>(g, p, L, s);
+    st = launch_count<CountBins>(g, p, L, aeo, s);
     if (st != UBT_OK) return st;
     FinishMulti f;
     f.nt = n_tau;
@@ -781,10 +791,10 @@ extern "C" ubt_status ubt_count_threshold(ubt_graph* g, const double* h_tau, int
     p.out = acc;
     UBT_CUDA(cudaMemsetAsync(acc, 0, sizeof(unsigned long long) * 2 * NT, s));
     switch (NT) {
-      case 1: st = launch_traverse<CountReg<1>>(g, p, L, s); break;
-      case 2: st = launch_traverse<CountReg<2>>(g, p, L, s); break;
-      case 4: st = launch_traverse<CountReg<4>>(g, p, L, s); break;
-      default: st = launch_traverse<CountReg<8>>(g, p, L, s); break;
+      case 1: st = launch_count<CountReg<1>>(g, p, L, aeo, s); break;
+      case 2: st = launch_count<CountReg<2>>(g, p, L, aeo, s); break;
+      case 4: st = launch_count<CountReg<4>>(g, p, L, aeo, s); break;
+      default: st = launch_count<CountReg<8>>(g, p, L, aeo, s); break;
     }
     if (st != UBT_OK) return st;
     k_finish_reg<<<1, kRegTau, 0, s>>>(acc, n_tau, NT, nullptr, d_counts);
@@ -801,7 +811,7 @@ extern "C" ubt_status ubt_count_threshold(ubt_graph* g, const double* h_tau, int
   }
   p.out = g->scratch->hist;
   UBT_CUDA(cudaMemsetAsync(g->scratch->hist, 0, sizeof(g->scratch->hist), s));
-  st = launch_traverse<CountMulti>(g, p, L, s);
+  st = launch_count<CountMulti>(g, p, L, aeo, s);
   if (st != UBT_OK) return st;
   FinishMulti f;
   f.nt = n_tau;
@@ -811,22 +821,48 @@ extern "C" ubt_status ubt_count_threshold(ubt_graph* g, const double* h_tau, int
   return UBT_OK;
 }
 
-extern "C" ubt_status ubt_enumerate(ubt_graph* g, double tau, int32_t which, int32_t prune, ubt_tri_rec* d_out,
-                                    int64_t capacity, int64_t* h_n_found, void* stream) {
+}  // namespace
+
+extern "C" ubt_status ubt_count_threshold(ubt_graph* g, const double* h_tau, int32_t n_tau, int32_t prune,
+                                          int64_t* d_counts, void* stream) {
+  return count_impl(g, h_tau, n_tau, prune, d_counts, false, (cudaStream_t)stream);
+}
+
+extern "C" ubt_status ubt_count_aeo(ubt_graph* g, const double* h_tau, int32_t n_tau, int64_t* d_counts,
+                                    void* stream) {
+  return count_impl(g, h_tau, n_tau, 1, d_counts, true, (cudaStream_t)stream);
+}
+
+namespace {
+
+ubt_status enumerate_impl(ubt_graph* g, double tau, int32_t which, int32_t prune, ubt_tri_rec* d_out,
+                          int64_t capacity, int64_t* h_n_found, bool aeo, cudaStream_t s) {
   if (!g || !h_n_found || capacity < 0 || (capacity > 0 && !d_out)) return UBT_ERR_INVALID_ARG;
   if (which < 1 || which > 3) return UBT_ERR_INVALID_ARG;
   if (g->kind != UBT_GRAPH_FIXED) return UBT_ERR_UNSUPPORTED;
+  if (aeo && !g->uptr) return UBT_ERR_UNSUPPORTED;
   Level lv;
   if (!tau_level(tau, &lv)) return UBT_ERR_TAU_OOB;
-  cudaStream_t s = (cudaStream_t)stream;
   EnumP p{lv.B, lv.U, which, d_out, (unsigned long long)capacity, &g->scratch->enum_cursor};
-  ubt_status st = launch_traverse<Enum>(g, p, prune ? lv.L : 0, s);
+  ubt_status st = aeo ? launch_aeo<Enum>(g, lv.L, p, s) : launch_traverse<Enum>(g, p, prune ? lv.L : 0, s);
   if (st != UBT_OK) return st;
   unsigned long long found = 0;
   UBT_CUDA(cudaMemcpyAsync(&found, &g->scratch->enum_cursor, sizeof(found), cudaMemcpyDeviceToHost, s));
   UBT_CUDA(cudaStreamSynchronize(s));
   *h_n_found = (int64_t)found;
   return found > (unsigned long long)capacity ? UBT_ERR_CAPACITY : UBT_OK;
+}
+
+}  // namespace
+
+extern "C" ubt_status ubt_enumerate(ubt_graph* g, double tau, int32_t which, int32_t prune, ubt_tri_rec* d_out,
+                                    int64_t capacity, int64_t* h_n_found, void* stream) {
+  return enumerate_impl(g, tau, which, prune, d_out, capacity, h_n_found, false, (cudaStream_t)stream);
+}
+
+extern "C" ubt_status ubt_enumerate_aeo(ubt_graph* g, double tau, int32_t which, ubt_tri_rec* d_out,
+                                        int64_t capacity, int64_t* h_n_found, void* stream) {
+  return enumerate_impl(g, tau, which, 1, d_out, capacity, h_n_found, true, (cudaStream_t)stream);
 }
 
 extern "C" ubt_status ubt_expected_counts(ubt_graph* g, double* d_out, int64_t* d_exact, void* stream) {
@@ -914,6 +950,25 @@ extern "C" ubt_status ubt_graph_export(const ubt_graph* g, uint32_t* h_row_ptr, 
     h_list_sizes[2] = g->n_med;
     h_list_sizes[3] = 0;
   }
+  UBT_CUDA(cudaStreamSynchronize(s));
+  return UBT_OK;
+}
+
+extern "C" ubt_status ubt_graph_export_undirected(const ubt_graph* g, uint32_t* h_uptr, uint64_t* h_uadj,
+                                                  uint32_t* h_ueid, uint32_t* h_umir, uint32_t* h_apair_ptr,
+                                                  uint64_t* h_apairs, void* stream) {
+  if (!g) return UBT_ERR_INVALID_ARG;
+  if (!g->uptr) return UBT_ERR_UNSUPPORTED;
+  cudaStream_t s = (cudaStream_t)stream;
+  const size_t m2 = (size_t)(2 * g->m);
+  if (h_uptr) UBT_CUDA(cudaMemcpyAsync(h_uptr, g->uptr, sizeof(uint32_t) * (g->n + 1), cudaMemcpyDeviceToHost, s));
+  if (h_uadj && m2) UBT_CUDA(cudaMemcpyAsync(h_uadj, g->uadj, sizeof(uint64_t) * m2, cudaMemcpyDeviceToHost, s));
+  if (h_ueid && m2) UBT_CUDA(cudaMemcpyAsync(h_ueid, g->ueid, sizeof(uint32_t) * m2, cudaMemcpyDeviceToHost, s));
+  if (h_umir && m2) UBT_CUDA(cudaMemcpyAsync(h_umir, g->umir, sizeof(uint32_t) * m2, cudaMemcpyDeviceToHost, s));
+  if (h_apair_ptr)
+    UBT_CUDA(cudaMemcpyAsync(h_apair_ptr, g->apair_ptr, sizeof(uint32_t) * (g->n + 1), cudaMemcpyDeviceToHost, s));
+  if (h_apairs && g->m)
+    UBT_CUDA(cudaMemcpyAsync(h_apairs, g->apairs, sizeof(uint64_t) * g->m, cudaMemcpyDeviceToHost, s));
   UBT_CUDA(cudaStreamSynchronize(s));
   return UBT_OK;
 }

@@ -655,12 +655,106 @@ def extra_grad(ubt, args, flush):
     return res
 
 
+AEO_TAUS = [0.55, 0.6, 0.7, 0.8, 0.9, 0.95]
+
+
+def extra_aeo(ubt, args, flush, name):
+    """Absolute-Edge-Order iteration (Alg. 2) against the degree-ordered
+    pruned traversal, one threshold at a time (the paper's Fig. 6 axis)."""
+    import torch
+    g = make_graph(name)
+    k = g.k if g.k is not None else __import__("synth").quantise(g.p)
+    t0 = time.perf_counter()
+    G = ubt.Graph(g.n, g.src, g.dst, k=k, undirected=True)
+    torch.cuda.synchronize()
+    build_s = time.perf_counter() - t0
+    out = torch.empty(2, dtype=torch.int64, device="cuda")
+    steps = max(3, args.steps // 4)
+    rows = []
+    for t in AEO_TAUS:
+        ms_deg = _events_ms(lambda: G.count_threshold_([t], out, prune=True), steps, 1, flush)
+        a = out.cpu().numpy().copy()
+        ms_aeo = _events_ms(lambda: G.count_aeo_([t], out), steps, 1, flush)
+        b = out.cpu().numpy().copy()
+        assert np.array_equal(a, b), "AEO and degree-ordered counts differ"
+        rows.append({"t": t, "degree_ms": ms_deg, "aeo_ms": ms_aeo, "balanced": int(a[0]), "unbalanced": int(a[1])})
+    res = {"workload": name, "n": g.n, "m": g.m, "build_with_undirected_s": build_s, "per_t": rows}
+    del G
+    _release()
+    return res
+
+
+def extra_sampling(ubt, args, flush):
+    """Edge (eImpr) and vertex (vImpr) sampling on the Chung-Lu n=1e6 graph:
+    10,000 uniform samples per estimate, t = 0.8; time per estimate and the
+    mean absolute percentage error over 10 seeds against the exact counts."""
+    import torch
+    g = make_graph("cl1m")
+    G = ubt.Graph(g.n, g.src, g.dst, k=g.k, undirected=True)
+    tau = [0.8]
+    exact_b, exact_u = G.count_threshold(tau)
+    K = 10000
+    res = {"workload": "cl1m, t = 0.8, 10,000 samples per estimate", "exact_balanced": int(exact_b[0]),
+           "exact_unbalanced": int(exact_u[0])}
+    for kind in ("edge", "vertex"):
+        fn = G.edge_local_counts if kind == "edge" else G.vertex_local_counts
+        top = g.m if kind == "edge" else g.n
+        ests, times = [], []
+        for seed in range(10):
+            smp = torch.from_numpy(np.random.default_rng(1000 + seed).integers(0, top, size=K).astype(np.int32)).cuda()
+            torch.cuda.synchronize()
+            a = torch.cuda.Event(enable_timing=True)
+            b = torch.cuda.Event(enable_timing=True)
+            a.record()
+            _, _, est = fn(smp, tau)
+            b.record()
+            b.synchronize()
+            times.append(a.elapsed_time(b))
+            ests.append(est[:, 0])
+        ests = np.array(ests)
+        ape_b = np.abs(ests[:, 0] - exact_b[0]) / max(1, exact_b[0])
+        ape_u = np.abs(ests[:, 1] - exact_u[0]) / max(1, exact_u[0])
+        res[kind] = {"ms_per_estimate_median": float(np.median(times)), "mape_balanced": float(ape_b.mean()),
+                     "mape_unbalanced": float(ape_u.mean()),
+                     "note": "time includes the D2H of the per-sample counts"}
+    del G
+    _release()
+    return res
+
+
+def extra_topk(ubt, args, flush):
+    """Top-k most balanced / most unbalanced triangles of the Chung-Lu n=1e6
+    graph (Sec. 5's top-k adaptation; the whole search, enumeration and sort)."""
+    import torch
+    g = make_graph("cl1m")
+    G = ubt.Graph(g.n, g.src, g.dst, k=g.k)
+    res = {"workload": "cl1m"}
+    for K in (1000, 100000):
+        for which in (1, 2):
+            G.topk(K, which)  # warm-up
+            times = []
+            for _ in range(3):
+                torch.cuda.synchronize()
+                t0 = time.perf_counter()
+                rec = G.topk(K, which)
+                times.append(1e3 * (time.perf_counter() - t0))
+            res["K%d_%s" % (K, "bal" if which == 1 else "unbal")] = {
+                "ms_median": float(np.median(times)), "kth_p_bal": float(rec["p_bal"][-1]),
+                "note": "host wall time of the synchronous call, D2H of the K records included"}
+    del G
+    _release()
+    return res
+
+
 def extras(ubt, G, g, T, args, flush):
     """The other workloads of the path, each on its own graph."""
     from paper_2602_14084_gb300 import autotune as at
     out = {}
     for name, fn in (("c3_rmat22", extra_rmat22), ("c4_rmat20_worlds", extra_worlds), ("c4_ego10k", extra_ego),
-                     ("c5_cl4m_grad", extra_grad)):
+                     ("c5_cl4m_grad", extra_grad),
+                     ("aeo_vs_degree_cl1m", lambda u, a, f: extra_aeo(u, a, f, "cl1m")),
+                     ("aeo_vs_degree_rmat22", lambda u, a, f: extra_aeo(u, a, f, "rmat22")),
+                     ("sampling_cl1m", extra_sampling), ("topk_cl1m", extra_topk)):
         try:
             with at.tuning_scope(args.lib_defaults):  # each workload starts from the library defaults
                 out[name] = fn(ubt, args, flush)

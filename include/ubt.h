@@ -403,6 +403,25 @@ ubt_status ubt_graph_export_undirected(const ubt_graph* g, uint32_t* h_uptr, uin
                                        uint32_t* h_umir, uint32_t* h_apair_ptr, uint64_t* h_apairs, void* stream);
 
 /*
+ * ubt_topk_workspace_size / ubt_topk -- SYNC.  Top-k query (Sec. 5, "Adaption
+ * to Top-k Search"): the K triangles of highest balance probability (which =
+ * 1) or highest unbalance probability (which = 2), as records sorted by that
+ * probability (descending), ties by (u, v, w).  Where ties at the K-th value
+ * exceed the candidate buffer, an arbitrary subset of the tied triangles
+ * completes the answer.  The threshold is raised as the search narrows: each
+ * pass counts the triangle products at 64 cut points with pruning at the
+ * level the current range allows, until the candidates fit; the candidates
+ * are then enumerated and sorted on the device.
+ *   K           1 <= K <= 2^26
+ *   d_out       device ubt_tri_rec[K]
+ *   h_n_out     number of records written (min(K, number of triangles))
+ *   d_work      device workspace of ubt_topk_workspace_size(K) bytes
+ */
+ubt_status ubt_topk_workspace_size(int64_t K, size_t* h_bytes);
+ubt_status ubt_topk(ubt_graph* g, int64_t K, int32_t which, ubt_tri_rec* d_out, int64_t* h_n_out, void* d_work,
+                    size_t work_bytes, void* stream);
+
+/*
  * ubt_set_tuning / ubt_get_tuning -- process-wide launch parameters that the
  * autotuner picks (they change speed, never results).  Unknown names return
  * UBT_ERR_INVALID_ARG.  Names:

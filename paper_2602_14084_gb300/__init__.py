@@ -82,6 +82,8 @@ def lib():
             "ubt_graph_export_pairs": (I32, [P, P, P, P]),
             "ubt_graph_export_undirected": (I32, [P, P, P, P, P, P, P, P]),
             "ubt_count_aeo": (I32, [P, P, I32, P, P]),
+            "ubt_topk_workspace_size": (I32, [I64, ctypes.POINTER(SZ)]),
+            "ubt_topk": (I32, [P, I64, I32, P, ctypes.POINTER(I64), P, SZ, P]),
             "ubt_enumerate_aeo": (I32, [P, ctypes.c_double, I32, P, I64, ctypes.POINTER(I64), P]),
             "ubt_edge_local_counts": (I32, [P, P, I64, P, I32, P, P, P, P]),
             "ubt_vertex_local_counts": (I32, [P, P, I64, P, I32, P, P, P, P]),
@@ -344,6 +346,20 @@ class Graph:
         """Vertex sampling (Algs. 3-4): as edge_local_counts, per sampled vertex,
         estimator |V|/3 * mean."""
         return self._local(lib().ubt_vertex_local_counts, vertices, taus, stream)
+
+    def topk(self, K, which=1, stream=None):
+        """The K most balanced (which=1) or most unbalanced (which=2) triangles,
+        as records (TRI_REC_DTYPE) in decreasing order of that probability."""
+        torch = _torch()
+        L = lib()
+        nb = ctypes.c_size_t(0)
+        _check(L.ubt_topk_workspace_size(int(K), ctypes.byref(nb)), "ubt_topk_workspace_size")
+        work = torch.empty(int(nb.value), dtype=torch.uint8, device=self.device)
+        out = torch.empty(int(K) * TRI_REC_DTYPE.itemsize, dtype=torch.uint8, device=self.device)
+        n = ctypes.c_int64(0)
+        _check(L.ubt_topk(self._h, int(K), int(which), _ptr(out), ctypes.byref(n), _ptr(work), work.numel(),
+                          _stream(stream)), "ubt_topk")
+        return out.cpu().numpy()[: int(n.value) * TRI_REC_DTYPE.itemsize].view(TRI_REC_DTYPE)
 
     def export_undirected(self, stream=None):
         """The undirected adjacency in Absolute Edge Order and the AEO edge owners."""

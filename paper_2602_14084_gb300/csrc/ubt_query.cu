@@ -434,12 +434,15 @@ __global__ void k_finish_multi(const unsigned long long* __restrict__ bins, Fini
   }
 }
 
+// balanced records: Blo < P <= B; unbalanced: U < P <= Uhi (top-k uses the
+// extra bounds; the threshold queries pass INT64_MIN / INT64_MAX)
 struct EnumP {
   int64_t B, U;
   int which;
   ubt_tri_rec* out;
   unsigned long long cap;
   unsigned long long* cursor;
+  int64_t Blo = INT64_MIN, Uhi = INT64_MAX;
 };
 struct Enum {
   using P = EnumP;
@@ -456,8 +459,8 @@ struct Enum {
     int64_t P = 0;
     if (hit) {
       P = tri_product(quv, quw, qvw);
-      if ((p.which & 1) && P <= p.B) cls = 1;
-      else if ((p.which & 2) && P > p.U) cls = 2;
+      if ((p.which & 1) && P <= p.B && P > p.Blo) cls = 1;
+      else if ((p.which & 2) && P > p.U && P <= p.Uhi) cls = 2;
     }
     const unsigned m = __ballot_sync(kFull, cls != 0);
     if (!m) return;
@@ -951,6 +954,184 @@ extern "C" ubt_status ubt_graph_export(const ubt_graph* g, uint32_t* h_row_ptr, 
     h_list_sizes[3] = 0;
   }
   UBT_CUDA(cudaStreamSynchronize(s));
+  return UBT_OK;
+}
+
+// ------------------------------------------------------------ top-k
+
+namespace ubt {
+namespace {
+
+// record order of a top-k answer: P_bal descending (balanced) or ascending
+// (unbalanced), then (u, v, w)
+__device__ __forceinline__ bool rec_before(const ubt_tri_rec& a, const ubt_tri_rec& b, bool desc) {
+  if (a.p_bal != b.p_bal) return desc ? a.p_bal > b.p_bal : a.p_bal < b.p_bal;
+  if (a.u != b.u) return a.u < b.u;
+  if (a.v != b.v) return a.v < b.v;
+  return a.w < b.w;
+}
+
+// one step of a bitonic network whose comparators all put the earlier record
+// first (the first step of every merge pairs i with its mirror); positions
+// >= n act as records after every record and are skipped
+__global__ void k_sort_recs_step(ubt_tri_rec* r, uint32_t n, uint32_t kk, uint32_t j, int desc) {
+  for (uint32_t i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
+    const uint32_t ixj = (j == (kk >> 1)) ? (i ^ (kk - 1)) : (i ^ j);
+    if (ixj > i && ixj < n) {
+      const ubt_tri_rec a = r[i], b = r[ixj];
+      if (rec_before(b, a, desc != 0)) {
+        r[i] = b;
+        r[ixj] = a;
+      }
+    }
+  }
+}
+
+ubt_status sort_records(ubt_tri_rec* r, uint32_t n, bool desc, int sms, cudaStream_t s) {
+  uint32_t cap = 2;
+  while (cap < n) cap <<= 1;
+  const int grid = (int)std::min<int64_t>(((int64_t)n + 255) / 256, (int64_t)sms * 8);
+  for (uint32_t kk = 2; kk <= cap; kk <<= 1)
+    for (uint32_t j = kk >> 1; j > 0; j >>= 1)
+      k_sort_recs_step<<<std::max(grid, 1), 256, 0, s>>>(r, n, kk, j, desc ? 1 : 0);
+  UBT_CUDA(cudaGetLastError());
+  return UBT_OK;
+}
+
+// Counts of the triangle products P among up to 128 sorted levels in one
+// pruned traversal: h_bins[r] = #{P : #{levels < P} = r}.
+ubt_status count_levels(const ubt_graph* g, const std::vector<int64_t>& lev, int64_t L, unsigned long long* h_bins,
+                        cudaStream_t s) {
+  CountBinsP p;
+  p.nt = (int)lev.size() / 2;
+  for (size_t i = 0; i < lev.size(); i++) p.S[i] = lev[i];
+  p.out = g->scratch->hist;
+  UBT_CUDA(cudaMemsetAsync(g->scratch->hist, 0, sizeof(g->scratch->hist), s));
+  ubt_status st = launch_traverse<CountBins>(g, p, L, s);
+  if (st != UBT_OK) return st;
+  UBT_CUDA(cudaMemcpyAsync(h_bins, g->scratch->hist, sizeof(unsigned long long) * (lev.size() + 1),
+                           cudaMemcpyDeviceToHost, s));
+  UBT_CUDA(cudaStreamSynchronize(s));
+  return UBT_OK;
+}
+
+// records with P in the given bounds appended to r[at, cap): returns how many
+// exist (all of them, even past cap)
+ubt_status enum_range(const ubt_graph* g, int which, int64_t B, int64_t Blo, int64_t U, int64_t Uhi, int64_t L,
+                      ubt_tri_rec* r, int64_t cap, int64_t* found, cudaStream_t s) {
+  EnumP p{B, U, which, r, (unsigned long long)std::max<int64_t>(cap, 0), &g->scratch->enum_cursor, Blo, Uhi};
+  ubt_status st = launch_traverse<Enum>(g, p, L, s);
+  if (st != UBT_OK) return st;
+  unsigned long long f = 0;
+  UBT_CUDA(cudaMemcpyAsync(&f, &g->scratch->enum_cursor, sizeof(f), cudaMemcpyDeviceToHost, s));
+  UBT_CUDA(cudaStreamSynchronize(s));
+  *found = (int64_t)f;
+  return UBT_OK;
+}
+
+int64_t topk_capacity(int64_t K) {
+  int64_t c = 1;
+  while (c < std::max<int64_t>(2 * K, K + 4096)) c <<= 1;
+  return c;
+}
+
+constexpr int64_t kP1 = 1ll << 45;  // |P| <= 2^45
+
+}  // namespace
+}  // namespace ubt
+
+extern "C" ubt_status ubt_topk_workspace_size(int64_t K, size_t* h_bytes) {
+  if (!h_bytes || K < 1 || K > (1ll << 26)) return UBT_ERR_INVALID_ARG;
+  *h_bytes = (size_t)topk_capacity(K) * sizeof(ubt_tri_rec);
+  return UBT_OK;
+}
+
+extern "C" ubt_status ubt_topk(ubt_graph* g, int64_t K, int32_t which, ubt_tri_rec* d_out, int64_t* h_n_out,
+                               void* d_work, size_t work_bytes, void* stream) {
+  if (!g || !d_out || !h_n_out || !d_work || K < 1 || K > (1ll << 26)) return UBT_ERR_INVALID_ARG;
+  if (which != 1 && which != 2) return UBT_ERR_INVALID_ARG;
+  if (g->kind != UBT_GRAPH_FIXED) return UBT_ERR_UNSUPPORTED;
+  const int64_t cap = topk_capacity(K);
+  if (work_bytes < (size_t)cap * sizeof(ubt_tri_rec)) return UBT_ERR_WORKSPACE_TOO_SMALL;
+  cudaStream_t s = (cudaStream_t)stream;
+  ubt_tri_rec* cand = (ubt_tri_rec*)d_work;
+  const bool bal = which == 1;
+  // Balanced: the K largest P_bal are the K smallest P.  Keep lo < hi with
+  // #{P <= lo} < K <= #{P <= hi}, and narrow (lo, hi] 64-fold per pass by
+  // counting P at 64 cuts, until the triangles up to hi fit the candidate
+  // buffer or hi = lo + 1.  Each pass prunes at the level its interval
+  // allows (the raised threshold of Sec. 5's top-k adaptation): a triangle
+  // with |P| below max(0, -hi) cannot have P <= hi.  Unbalanced mirrors it
+  // with #{P >= x}: keep #{P >= hi} < K <= #{P >= lo}.
+  int64_t lo = bal ? -kP1 - 1 : -kP1, hi = bal ? kP1 : kP1 + 1;
+  int64_t n_in = -1;  // triangles in the final range
+  for (int pass = 0; pass < 16; pass++) {
+    // 64 cuts, non-decreasing (strictly increasing when the range allows):
+    // balanced in (lo, hi] ending at hi, unbalanced in [lo, hi) starting at lo
+    std::vector<int64_t> cuts(64);
+    const __int128 span = (__int128)hi - lo;
+    for (int j = 0; j < 64; j++) cuts[j] = lo + (int64_t)((span * (bal ? j + 1 : j) + 63) / 64);
+    std::vector<int64_t> lev(64);
+    for (int j = 0; j < 64; j++) lev[j] = bal ? cuts[j] : cuts[j] - 1;  // P <= c  |  P >= c  <=>  P > c - 1
+    std::sort(lev.begin(), lev.end());
+    unsigned long long bins[129];
+    const int64_t L = bal ? std::max<int64_t>(0, -hi) : std::max<int64_t>(0, lo);
+    ubt_status st = count_levels(g, lev, L, bins, s);
+    if (st != UBT_OK) return st;
+    int64_t cum[64];
+    if (bal) {
+      int64_t acc = 0;
+      for (int j = 0; j < 64; j++) { acc += (int64_t)bins[j]; cum[j] = acc; }  // #{P <= cuts[j]}
+      int jj = 0;
+      while (jj < 63 && cum[jj] < K) jj++;
+      if (cum[jj] < K) {  // fewer than K triangles in all: take them all
+        n_in = cum[jj];
+        hi = cuts[jj];
+        break;
+      }
+      const int64_t nlo = jj > 0 ? cuts[jj - 1] : lo;
+      hi = cuts[jj];
+      lo = nlo;
+      n_in = cum[jj];
+    } else {
+      int64_t acc = 0;
+      for (int j = 63; j >= 0; j--) { acc += (int64_t)bins[j + 1]; cum[j] = acc; }  // #{P >= cuts[j]}
+      if (cum[0] < K) {  // cuts[0] = lo: fewer than K triangles in all: take them all
+        n_in = cum[0];
+        break;
+      }
+      int jj = 63;
+      while (cum[jj] < K) jj--;
+      hi = jj < 63 ? cuts[jj + 1] : hi;
+      lo = cuts[jj];
+      n_in = cum[jj];
+    }
+    if (n_in <= cap || hi - lo <= 1) break;
+  }
+  // candidates: every triangle strictly inside the answer (fewer than K), then
+  // the triangles of the last range, as many as fit
+  int64_t n1 = 0, n2 = 0;
+  ubt_status st;
+  if (bal) {
+    st = enum_range(g, 1, lo, INT64_MIN, 0, 0, std::max<int64_t>(0, -lo), cand, cap, &n1, s);
+    if (st != UBT_OK) return st;
+    st = enum_range(g, 1, hi, lo, 0, 0, std::max<int64_t>(0, -hi), cand + std::min(n1, cap), cap - std::min(n1, cap),
+                    &n2, s);
+  } else {
+    st = enum_range(g, 2, 0, 0, hi - 1, INT64_MAX, std::max<int64_t>(0, hi), cand, cap, &n1, s);
+    if (st != UBT_OK) return st;
+    st = enum_range(g, 2, 0, 0, lo - 1, hi - 1, std::max<int64_t>(0, lo), cand + std::min(n1, cap),
+                    cap - std::min(n1, cap), &n2, s);
+  }
+  if (st != UBT_OK) return st;
+  const int64_t have = std::min(n1 + n2, cap);
+  st = sort_records(cand, (uint32_t)have, bal, g->sm_count, s);
+  if (st != UBT_OK) return st;
+  const int64_t nout = std::min(have, K);
+  if (nout > 0)
+    UBT_CUDA(cudaMemcpyAsync(d_out, cand, sizeof(ubt_tri_rec) * nout, cudaMemcpyDeviceToDevice, s));
+  UBT_CUDA(cudaStreamSynchronize(s));
+  *h_n_out = nout;
   return UBT_OK;
 }
 

@@ -1,0 +1,86 @@
+"""Top-k query (Sec. 5): the K triangles of highest balance (unbalance)
+probability against the oracle's full enumeration sorted by the same order
+(P_bal descending / ascending, ties by (u, v, w)) -- identical whenever the
+tied triangles at the K-th value fit the candidate buffer; otherwise the
+records above the K-th value are identical and the rest are valid ties."""
+import math
+
+import numpy as np
+import pytest
+
+import oracle
+import synth
+from gpu_util import mixed_graph, require_gpu
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def ubt():
+    return require_gpu()
+
+
+def oracle_topk(n, s, d, k, K, which):
+    uvw, cls, pb = oracle.enumerate_records(n, s, d, k, 0.5, 3)  # every triangle once, exact P_bal
+    key = -pb if which == 1 else pb
+    order = np.lexsort((uvw[:, 2], uvw[:, 1], uvw[:, 0], key))
+    return uvw[order][:K], pb[order][:K]
+
+
+def graphs():
+    g = synth.config_graph("er2k")
+    yield "er2k", g.n, g.src, g.dst, g.k
+    s, d = synth.rmat(12, 16, 0.57, 0.19, 0.19, 3)
+    yield "rmat12", 1 << 12, s, d, synth.quantise(synth.p_beta(s.size, 0.5, 0.5, 4))
+    s, d = mixed_graph(3000, 30000, 5)
+    k = synth.k_uniform(s.size, 6)
+    r = synth.rng(8).random(s.size)
+    k[r < 0.2] = 0          # many certain edges: many exact ties
+    k[(r >= 0.2) & (r < 0.3)] = 65536
+    yield "mixed_ties", 3000, s, d, k
+
+
+@pytest.mark.parametrize("which", [1, 2])
+def test_topk_matches_oracle(ubt, which):
+    for name, n, s, d, k in graphs():
+        G = ubt.Graph(n, s, d, k=k)
+        T = oracle.num_triangles(n, s, d)
+        for K in sorted({1, 7, 100, 1000, max(1, T - 1), T, T + 5}):
+            want_uvw, want_pb = oracle_topk(n, s, d, k, K, which)
+            rec = G.topk(K, which)
+            assert rec.shape[0] == min(K, T), (name, K)
+            got_uvw = np.stack([rec["u"], rec["v"], rec["w"]], axis=1).astype(np.uint32)
+            assert np.array_equal(rec["p_bal"], want_pb), (name, K, which)
+            assert np.array_equal(got_uvw, want_uvw), (name, K, which)
+            assert np.all(rec["cls"] == which)
+        assert G.guard() == 0
+
+
+def test_topk_ties_beyond_the_buffer(ubt):
+    """K_40 with one probability: 9,880 triangles share one value, more than
+    the candidate buffer for K = 10 holds; any 10 distinct triangles answer."""
+    n = 40
+    pairs = [(a, b) for a in range(n) for b in range(a + 1, n)]
+    s = np.array([a for a, _ in pairs], dtype=np.uint32)
+    d = np.array([b for _, b in pairs], dtype=np.uint32)
+    k = np.full(len(pairs), 50000, dtype=np.uint32)
+    G = ubt.Graph(n, s, d, k=k)
+    _, _, pb = oracle.enumerate_records(n, s, d, k, 0.5, 3)
+    for which in (1, 2):
+        rec = G.topk(10, which)
+        assert rec.shape[0] == 10
+        assert np.all(rec["p_bal"] == pb[0])
+        uvw = np.stack([rec["u"], rec["v"], rec["w"]], axis=1)
+        assert np.unique(uvw, axis=0).shape[0] == 10
+        assert np.all((uvw[:, 0] < uvw[:, 1]) & (uvw[:, 1] < uvw[:, 2]) & (uvw[:, 2] < n))
+    assert math.comb(n, 3) == 9880
+
+
+def test_topk_invalid(ubt):
+    s, d = synth.er_graph(100, 500, 3)
+    G = ubt.Graph(100, s, d, k=synth.k_uniform(500, 4))
+    for K, which in [(0, 1), (5, 3)]:
+        with pytest.raises(ubt.UbtError):
+            G.topk(K, which)
+    E = ubt.Graph(5, np.zeros(0, np.uint32), np.zeros(0, np.uint32), k=np.zeros(0, np.uint32))
+    assert E.topk(3, 1).shape[0] == 0

@@ -238,7 +238,8 @@ def main():
     ap.add_argument("--no-extras", dest="extras", action="store_false")
     ap.add_argument("--no-cpu-baseline", dest="cpu", action="store_false", default=True)
     ap.add_argument("--only", default=None,
-                    choices=["count", "count32", "count-unpruned", "worlds", "expected", "backward", "enumerate"],
+                    choices=["count", "count32", "count-unpruned", "worlds", "expected", "backward", "enumerate",
+                             "aeo", "edge-sampling", "vertex-sampling", "topk"],
                     help="profiling driver: build the --workload graph, run one form of the query "
                          "--warmup + --steps times, print its mean time and exit")
     ap.add_argument("--workload", default=WORKLOAD, choices=["cl1m", "rmat22", "rmat20", "cl4m", "er2k"])
@@ -445,7 +446,8 @@ def profile_driver(ubt, args):
             p = g.p if g.p is not None else synth.p_uniform_f32(g.m, 5)
             return ubt.Graph(g.n, g.src, g.dst, p=torch.from_numpy(np.ascontiguousarray(p)).cuda())
         k = g.k if g.k is not None else synth.quantise(g.p)
-        return ubt.Graph(g.n, g.src, g.dst, k=k)
+        return ubt.Graph(g.n, g.src, g.dst, k=k,
+                         undirected=args.only in ("aeo", "edge-sampling", "vertex-sampling"))
 
     # the knobs the benchmark would use (cached tunings only: no search here)
     G = build()
@@ -470,8 +472,23 @@ def profile_driver(ubt, args):
     if args.only == "enumerate":
         nb, nu = G.count_threshold([0.9])
         cap = int(nb[0] + nu[0])
-        rec = torch.empty(max(cap, 1) * ubt.TRI_REC_DTYPE.itemsize, dtype=torch.uint8, device="cuda")
+        recbuf = torch.empty(max(cap, 1) * ubt.TRI_REC_DTYPE.itemsize, dtype=torch.uint8, device="cuda")
         found = ctypes.c_int64(0)
+    if args.only in ("edge-sampling", "vertex-sampling"):
+        top = g.m if args.only == "edge-sampling" else g.n
+        smp = torch.from_numpy(np.random.default_rng(1000).integers(0, top, size=10000).astype(np.int32)).cuda()
+        lb = torch.empty(10000, dtype=torch.int64, device="cuda")
+        lu = torch.empty(10000, dtype=torch.int64, device="cuda")
+        le = torch.empty(2, dtype=torch.float64, device="cuda")
+        lfn = ubt.lib().ubt_edge_local_counts if args.only == "edge-sampling" else ubt.lib().ubt_vertex_local_counts
+        t08 = np.array([0.8])
+    if args.only == "topk":
+        nbytes = ctypes.c_size_t(0)
+        ubt.lib().ubt_topk_workspace_size(1000, ctypes.byref(nbytes))
+        twork = torch.empty(int(nbytes.value), dtype=torch.uint8, device="cuda")
+        tout = torch.empty(1000 * ubt.TRI_REC_DTYPE.itemsize, dtype=torch.uint8, device="cuda")
+        tn = ctypes.c_int64(0)
+    cp = lambda t: ctypes.c_void_p(t.data_ptr())
     fn = {
         "count": lambda: G.count_threshold_(taus, counts, prune=True),
         "count32": lambda: G.count_threshold_(taus, counts, prune=True),
@@ -479,8 +496,15 @@ def profile_driver(ubt, args):
         "worlds": lambda: G.sample_worlds_(7, W, wout, None, wws),
         "expected": lambda: G.expected_counts_(eo),
         "backward": lambda: G.expected_counts_backward_(gout, grad),
-        "enumerate": lambda: ubt.lib().ubt_enumerate(G.handle, 0.9, 3, 1, ctypes.c_void_p(rec.data_ptr()), cap,
-                                                     ctypes.byref(found), None),
+        "enumerate": lambda: ubt.lib().ubt_enumerate(G.handle, 0.9, 3, 1, cp(recbuf), cap, ctypes.byref(found),
+                                                     None),
+        "aeo": lambda: G.count_aeo_([0.8], counts),
+        "edge-sampling": lambda: lfn(G.handle, cp(smp), 10000, t08.ctypes.data_as(ctypes.c_void_p), 1, cp(lb),
+                                     cp(lu), cp(le), None),
+        "vertex-sampling": lambda: lfn(G.handle, cp(smp), 10000, t08.ctypes.data_as(ctypes.c_void_p), 1, cp(lb),
+                                       cp(lu), cp(le), None),
+        "topk": lambda: ubt.lib().ubt_topk(G.handle, 1000, 1, cp(tout), ctypes.byref(tn), cp(twork), twork.numel(),
+                                           None),
     }[args.only]
     times = time_steps(fn, args.steps, args.warmup)
     print(json.dumps({"only": args.only, "workload": args.workload, "ms": 1e3 * float(np.mean(times)),

@@ -335,7 +335,7 @@ def main():
     alg_bytes = alg_bytes_of(st)
     pk, pk_kind = peaks()
     achieved = alg_bytes / t_step / 1e9
-    kname = "k_traverse<CountReg<4>>"
+    kname = "k_traverse<CountBins>" if ubt.get_tuning("count_visitor") == 0 else "k_traverse<CountReg<4>>"
     roofline = {"bound": "hbm", "achieved": achieved, "peak": pk["hbm_gbs"], "unit": "GB/s",
                 "frac": achieved / pk["hbm_gbs"], "traffic": ncu_traffic(kname, WORKLOAD),
                 "kernel": kname, "peak_kind": pk_kind,

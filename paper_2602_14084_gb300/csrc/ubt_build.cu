@@ -46,23 +46,55 @@ __global__ void k_vertex_graph(const int64_t* __restrict__ voff, int64_t ng, int
   }
 }
 
+// Adds 1 to ctr[key] for every lane with `on`, with one atomic per run of
+// equal keys in consecutive lanes (edge lists sorted by source put a
+// vertex's edges together, and one counter then takes every lane's add);
+// returns the lane's slot: the counter's old value plus its rank in the run.
+// All 32 lanes call it.
+__device__ __forceinline__ uint32_t add_by_runs(uint32_t* ctr, uint32_t key, bool on) {
+  const uint32_t lane = lane_id();
+  const unsigned act = __ballot_sync(kFull, on);
+  const uint32_t prev = __shfl_up_sync(kFull, key, 1);
+  const bool head = on && !(lane > 0 && ((act >> (lane - 1)) & 1u) && prev == key);
+  const unsigned heads = __ballot_sync(kFull, head);
+  const unsigned upto = (2u << lane) - 1u;          // lanes 0..lane (all bits for lane 31)
+  const unsigned after = (heads | ~act) & ~upto;     // where runs end, after this lane
+  const uint32_t next = after ? (uint32_t)__ffs(after) - 1u : 32u;
+  uint32_t old = 0;
+  if (head) old = atomicAdd(&ctr[key], next - lane);
+  const unsigned mine = heads & upto;
+  const uint32_t my_head = mine ? 31u - (uint32_t)__clz(mine) : lane;
+  return __shfl_sync(kFull, old, my_head) + (lane - my_head);
+}
+
+// Grid-stride loops over the edges in which every warp takes 32 consecutive
+// edges per step, so that warp-wide runs (add_by_runs) see neighbours.
+#define UBT_FOR_EDGE_WARPS(base, m)                                                                     \
+  for (int64_t base = (int64_t)blockIdx.x * blockDim.x + (threadIdx.x & ~31); base < (m);               \
+       base += (int64_t)gridDim.x * blockDim.x)
+
 __global__ void k_validate_degree(int64_t n, int64_t m, const uint32_t* __restrict__ src,
                                   const uint32_t* __restrict__ dst, const uint32_t* __restrict__ k,
                                   const float* __restrict__ p, const uint32_t* __restrict__ vgraph,
                                   uint32_t* __restrict__ deg, unsigned long long* err) {
-  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < m; i += (int64_t)gridDim.x * blockDim.x) {
-    const uint32_t a = src[i], b = dst[i];
-    if ((int64_t)a >= n || (int64_t)b >= n) { report(err, i, -UBT_ERR_VERTEX_OOB); continue; }
-    if (a == b) { report(err, i, -UBT_ERR_SELF_LOOP); continue; }
-    if (k) {
-      if (k[i] > 65536u) report(err, i, -UBT_ERR_PROB_OOB);
-    } else {
-      const float x = p[i];
-      if (!(x >= 0.0f && x <= 1.0f)) report(err, i, -UBT_ERR_PROB_OOB);
+  const uint32_t lane = lane_id();
+  UBT_FOR_EDGE_WARPS(base, m) {
+    const int64_t i = base + lane;
+    bool ok = i < m;
+    const uint32_t a = ok ? src[i] : 0u, b = ok ? dst[i] : 0u;
+    if (ok && ((int64_t)a >= n || (int64_t)b >= n)) { report(err, i, -UBT_ERR_VERTEX_OOB); ok = false; }
+    if (ok && a == b) { report(err, i, -UBT_ERR_SELF_LOOP); ok = false; }
+    if (ok) {
+      if (k) {
+        if (k[i] > 65536u) report(err, i, -UBT_ERR_PROB_OOB);
+      } else {
+        const float x = p[i];
+        if (!(x >= 0.0f && x <= 1.0f)) report(err, i, -UBT_ERR_PROB_OOB);
+      }
+      if (vgraph && vgraph[a] != vgraph[b]) { report(err, i, -UBT_ERR_INVALID_ARG); ok = false; }
     }
-    if (vgraph && vgraph[a] != vgraph[b]) { report(err, i, -UBT_ERR_INVALID_ARG); continue; }
-    atomicAdd(&deg[a], 1u);
-    atomicAdd(&deg[b], 1u);
+    add_by_runs(deg, a, ok);
+    if (ok) atomicAdd(&deg[b], 1u);
   }
 }
 
@@ -74,9 +106,12 @@ __device__ inline bool node_before(const uint32_t* deg, uint32_t a, uint32_t b) 
 
 __global__ void k_out_degree(int64_t m, const uint32_t* __restrict__ src, const uint32_t* __restrict__ dst,
                              const uint32_t* __restrict__ deg, uint32_t* __restrict__ outdeg) {
-  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < m; i += (int64_t)gridDim.x * blockDim.x) {
-    const uint32_t a = src[i], b = dst[i];
-    atomicAdd(&outdeg[node_before(deg, a, b) ? a : b], 1u);
+  const uint32_t lane = lane_id();
+  UBT_FOR_EDGE_WARPS(base, m) {
+    const int64_t i = base + lane;
+    const bool on = i < m;
+    const uint32_t a = on ? src[i] : 0u, b = on ? dst[i] : 0u;
+    add_by_runs(outdeg, on && node_before(deg, a, b) ? a : b, on);
   }
 }
 
@@ -85,11 +120,16 @@ __global__ void k_scatter(int64_t m, const uint32_t* __restrict__ src, const uin
                           const uint32_t* __restrict__ deg, const uint32_t* __restrict__ row_ptr,
                           uint32_t* __restrict__ fill, uint64_t* __restrict__ adj, uint32_t* __restrict__ eid,
                           const uint32_t* __restrict__ key_in, uint32_t* __restrict__ key_out) {
-  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < m; i += (int64_t)gridDim.x * blockDim.x) {
-    const uint32_t a = src[i], b = dst[i];
-    const bool ab = node_before(deg, a, b);
+  const uint32_t lane = lane_id();
+  UBT_FOR_EDGE_WARPS(base, m) {
+    const int64_t i = base + lane;
+    const bool on = i < m;
+    const uint32_t a = on ? src[i] : 0u, b = on ? dst[i] : 0u;
+    const bool ab = on && node_before(deg, a, b);
     const uint32_t lo = ab ? a : b, hi = ab ? b : a;
-    const uint32_t pos = row_ptr[lo] + atomicAdd(&fill[lo], 1u);
+    const uint32_t slot = add_by_runs(fill, lo, on);
+    if (!on) continue;
+    const uint32_t pos = row_ptr[lo] + slot;
     uint32_t val;
     if (k) {
       val = (uint32_t)(int32_t)(32768 - (int32_t)k[i]);     // q = 32768 - k
@@ -113,17 +153,21 @@ __device__ inline uint64_t key_by_absq(uint64_t e) {
 }
 
 // Lists of <= 32 entries: one warp per list, bitonic network over the lanes.
-__device__ void warp_bitonic(uint64_t& key, uint64_t& e, uint32_t& id, uint32_t& ky, int lane) {
+// Bitonic sort of the values held by each aligned group of W lanes (W = 8,
+// 16 or 32), ascending by key within every group.
+template <int W>
+__device__ __forceinline__ void group_bitonic(uint64_t& key, uint64_t& e, uint32_t& id, uint32_t& ky, int lane) {
+  const int li = lane & (W - 1);
 #pragma unroll
-  for (int kk = 2; kk <= 32; kk <<= 1) {
+  for (int kk = 2; kk <= W; kk <<= 1) {
 #pragma unroll
     for (int j = kk >> 1; j > 0; j >>= 1) {
       const uint64_t ok = __shfl_xor_sync(kFull, key, j);
       const uint64_t oe = __shfl_xor_sync(kFull, e, j);
       const uint32_t oi = __shfl_xor_sync(kFull, id, j);
       const uint32_t oy = __shfl_xor_sync(kFull, ky, j);
-      const bool up = (lane & kk) == 0;
-      const bool lower = (lane & j) == 0;
+      const bool up = (li & kk) == 0;
+      const bool lower = (li & j) == 0;
       const bool take_min = (lower == up);
       const bool sw = take_min ? (ok < key) : (ok > key);
       if (sw) { key = ok; e = oe; id = oi; ky = oy; }
@@ -131,30 +175,137 @@ __device__ void warp_bitonic(uint64_t& key, uint64_t& e, uint32_t& id, uint32_t&
   }
 }
 
+// Sorts the rows of one group of W lanes (row rs..rs+len, len <= W; groups
+// without a row pass in = false everywhere): by neighbour id, reporting
+// duplicates, then (FIXED) by |q| descending.
+template <int W>
+__device__ __forceinline__ void sort_group_row(uint64_t* adj, uint32_t* eid, uint32_t* ekey, uint32_t rs, uint32_t len,
+                                               bool row, int fixed, unsigned long long* err, int lane) {
+  const int li = lane & (W - 1);
+  const bool in = row && (uint32_t)li < len;
+  uint64_t e = in ? adj[rs + li] : ~0ull;
+  uint32_t id = in ? eid[rs + li] : 0u;
+  uint32_t ky = (in && ekey) ? ekey[rs + li] : 0u;
+  uint64_t key = in ? key_by_col(e) : ~0ull;
+  group_bitonic<W>(key, e, id, ky, lane);
+  const uint64_t prev = __shfl_up_sync(kFull, key, 1);
+  if (in && li > 0 && prev == key) report(err, rs + li, -UBT_ERR_DUPLICATE_EDGE);
+  if (fixed) {
+    key = in ? key_by_absq(e) : ~0ull;
+    group_bitonic<W>(key, e, id, ky, lane);
+  }
+  if (in) {
+    adj[rs + li] = e;
+    eid[rs + li] = id;
+    if (ekey) ekey[rs + li] = ky;
+  }
+}
+
+// Rows of 2..32 entries: a warp takes 4 consecutive rows; the rows of at
+// most 8 entries are sorted together, one per 8-lane group, the others one
+// after another by the whole warp.
 __global__ void k_sort_short_rows(int64_t n, const uint32_t* __restrict__ row_ptr, uint64_t* adj, uint32_t* eid,
                                   uint32_t* ekey, int fixed, unsigned long long* err) {
   const int lane = threadIdx.x & 31;
   const int64_t warps = (int64_t)gridDim.x * (blockDim.x >> 5);
-  for (int64_t u = blockIdx.x * (int64_t)(blockDim.x >> 5) + (threadIdx.x >> 5); u < n; u += warps) {
-    const uint32_t rs = row_ptr[u], re = row_ptr[u + 1];
-    const uint32_t len = re - rs;
-    if (len < 2 || len > 32) continue;
-    const bool in = (uint32_t)lane < len;
-    uint64_t e = in ? adj[rs + lane] : ~0ull;
-    uint32_t id = in ? eid[rs + lane] : 0u;
-    uint32_t ky = (in && ekey) ? ekey[rs + lane] : 0u;
-    uint64_t key = in ? key_by_col(e) : ~0ull;
-    warp_bitonic(key, e, id, ky, lane);
-    const uint64_t prev = __shfl_up_sync(kFull, key, 1);
-    if (in && lane > 0 && prev == key) report(err, rs + lane, -UBT_ERR_DUPLICATE_EDGE);
-    if (fixed) {
-      key = in ? key_by_absq(e) : ~0ull;
-      warp_bitonic(key, e, id, ky, lane);
+  for (int64_t u0 = 4 * (blockIdx.x * (int64_t)(blockDim.x >> 5) + (threadIdx.x >> 5)); u0 < n; u0 += 4 * warps) {
+    const int64_t u = u0 + (lane >> 3);
+    uint32_t rs = 0, len = 0;
+    if (u < n) {
+      rs = row_ptr[u];
+      len = row_ptr[u + 1] - rs;
     }
-    if (in) {
-      adj[rs + lane] = e;
-      eid[rs + lane] = id;
-      if (ekey) ekey[rs + lane] = ky;
+    sort_group_row<8>(adj, eid, ekey, rs, len, len >= 2 && len <= 8, fixed, err, lane);
+    unsigned big = __ballot_sync(kFull, (lane & 7) == 0 && len > 8 && len <= 32);
+    while (big) {
+      const int g = __ffs(big) - 1;
+      big &= big - 1;
+      const uint32_t rsg = __shfl_sync(kFull, rs, g), leng = __shfl_sync(kFull, len, g);
+      sort_group_row<32>(adj, eid, ekey, rsg, leng, true, fixed, err, lane);
+    }
+  }
+}
+
+// Rows of 33..128 entries: one warp per row, four entries per lane (entry
+// r * 32 + lane in register r), bitonic network across registers and lanes.
+__device__ __forceinline__ void cswap4(uint64_t (&k)[4], uint64_t (&e)[4], uint32_t (&d)[4], uint32_t (&y)[4], int a,
+                                       int b, bool asc) {
+  const bool sw = asc ? (k[a] > k[b]) : (k[a] < k[b]);
+  if (sw) {
+    uint64_t t = k[a]; k[a] = k[b]; k[b] = t;
+    t = e[a]; e[a] = e[b]; e[b] = t;
+    uint32_t x = d[a]; d[a] = d[b]; d[b] = x;
+    x = y[a]; y[a] = y[b]; y[b] = x;
+  }
+}
+__device__ __forceinline__ void warp_sort128(uint64_t (&k)[4], uint64_t (&e)[4], uint32_t (&d)[4], uint32_t (&y)[4],
+                                             int lane) {
+#pragma unroll
+  for (int kk = 2; kk <= 128; kk <<= 1) {
+#pragma unroll
+    for (int j = kk >> 1; j > 0; j >>= 1) {
+      if (j >= 32) {  // partner in another register of the same lane
+        const int rj = j >> 5;
+#pragma unroll
+        for (int r = 0; r < 4; r++)
+          if ((r & rj) == 0) cswap4(k, e, d, y, r, r | rj, (((r << 5) | lane) & kk) == 0);
+      } else {        // partner in another lane, same register
+#pragma unroll
+        for (int r = 0; r < 4; r++) {
+          const uint64_t ok = __shfl_xor_sync(kFull, k[r], j);
+          const uint64_t oe = __shfl_xor_sync(kFull, e[r], j);
+          const uint32_t od = __shfl_xor_sync(kFull, d[r], j);
+          const uint32_t oy = __shfl_xor_sync(kFull, y[r], j);
+          const bool up = (((r << 5) | lane) & kk) == 0;
+          const bool lower = (lane & j) == 0;
+          const bool sw = (lower == up) ? (ok < k[r]) : (ok > k[r]);
+          if (sw) { k[r] = ok; e[r] = oe; d[r] = od; y[r] = oy; }
+        }
+      }
+    }
+  }
+}
+
+__global__ void k_sort_mid_rows(const uint32_t* __restrict__ rows, uint32_t nrows, const uint32_t* __restrict__ row_ptr,
+                                uint64_t* adj, uint32_t* eid, uint32_t* ekey, int fixed, unsigned long long* err) {
+  const int lane = threadIdx.x & 31;
+  const int64_t warps = (int64_t)gridDim.x * (blockDim.x >> 5);
+  for (int64_t r0 = blockIdx.x * (int64_t)(blockDim.x >> 5) + (threadIdx.x >> 5); r0 < nrows; r0 += warps) {
+    const uint32_t u = rows[r0];
+    const uint32_t rs = row_ptr[u], len = row_ptr[u + 1] - rs;
+    uint64_t k[4], e[4];
+    uint32_t d[4], y[4];
+#pragma unroll
+    for (int r = 0; r < 4; r++) {
+      const uint32_t i = (uint32_t)(r * 32 + lane);
+      const bool in = i < len;
+      e[r] = in ? adj[rs + i] : ~0ull;
+      d[r] = in ? eid[rs + i] : 0u;
+      y[r] = (in && ekey) ? ekey[rs + i] : 0u;
+      k[r] = in ? key_by_col(e[r]) : ~0ull;
+    }
+    warp_sort128(k, e, d, y, lane);
+#pragma unroll
+    for (int r = 0; r < 4; r++) {  // duplicates: equal keys at neighbouring positions
+      const uint64_t up1 = __shfl_up_sync(kFull, k[r], 1);
+      const uint64_t last = r > 0 ? __shfl_sync(kFull, k[r > 0 ? r - 1 : 0], 31) : ~0ull;
+      const uint64_t prev = lane > 0 ? up1 : last;
+      const uint32_t i = (uint32_t)(r * 32 + lane);
+      if (i < len && i > 0 && prev == k[r]) report(err, rs + i, -UBT_ERR_DUPLICATE_EDGE);
+    }
+    if (fixed) {
+#pragma unroll
+      for (int r = 0; r < 4; r++) k[r] = ((uint32_t)(r * 32 + lane) < len) ? key_by_absq(e[r]) : ~0ull;
+      warp_sort128(k, e, d, y, lane);
+    }
+#pragma unroll
+    for (int r = 0; r < 4; r++) {
+      const uint32_t i = (uint32_t)(r * 32 + lane);
+      if (i < len) {
+        adj[rs + i] = e[r];
+        eid[rs + i] = d[r];
+        if (ekey) ekey[rs + i] = y[r];
+      }
     }
   }
 }
@@ -226,12 +377,17 @@ __global__ void k_sort_long_rows(const uint32_t* __restrict__ rows, uint32_t nro
   }
 }
 
+// Rows longer than 32: counts[2] of 33..128 (warp sort, listed from the end of
+// `mid`), counts[0] of 129..smem_max (block sort in shared memory, from the
+// start of `mid`), counts[1] longer (block sort in global memory, `huge`).
 __global__ void k_collect_long(int64_t n, const uint32_t* __restrict__ row_ptr, uint32_t smem_max, uint32_t* mid,
                                uint32_t* huge, unsigned long long* counts) {
   for (int64_t u = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; u < n; u += (int64_t)gridDim.x * blockDim.x) {
     const uint32_t len = row_ptr[u + 1] - row_ptr[u];
-    if (len > 32 && len <= smem_max) mid[atomicAdd(&counts[0], 1ull)] = (uint32_t)u;
-    else if (len > smem_max && len > 32) huge[atomicAdd(&counts[1], 1ull)] = (uint32_t)u;
+    if (len <= 32) continue;
+    if (len <= 128) mid[n - 1 - (int64_t)atomicAdd(&counts[2], 1ull)] = (uint32_t)u;
+    else if (len <= smem_max) mid[atomicAdd(&counts[0], 1ull)] = (uint32_t)u;
+    else huge[atomicAdd(&counts[1], 1ull)] = (uint32_t)u;
   }
 }
 
@@ -245,34 +401,46 @@ __device__ inline uint32_t pair_owner(uint32_t u, uint32_t v, uint32_t du, uint3
   return (pull && dv > du) ? v : u;
 }
 
-// pairs per owner (one warp per row u)
-__global__ void k_pair_count(int64_t n, const uint32_t* __restrict__ row_ptr, const uint64_t* __restrict__ adj,
-                             int pull, uint32_t* __restrict__ pcount) {
-  const int lane = threadIdx.x & 31;
-  const int64_t warps = (int64_t)gridDim.x * (blockDim.x >> 5);
-  for (int64_t u = blockIdx.x * (int64_t)(blockDim.x >> 5) + (threadIdx.x >> 5); u < n; u += warps) {
-    const uint32_t rs = row_ptr[u], re = row_ptr[u + 1];
-    for (uint32_t i = rs + lane; i < re; i += 32) {
-      const uint32_t v = adj_col(adj[i]);
-      atomicAdd(&pcount[pair_owner((uint32_t)u, v, re - rs, row_ptr[v + 1] - row_ptr[v], pull)], 1u);
-    }
-  }
+// rowid[p] = the row that holds CSR position p (one thread per row)
+__global__ void k_row_ids(int64_t n, const uint32_t* __restrict__ row_ptr, uint32_t* __restrict__ rowid) {
+  for (int64_t u = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; u < n; u += (int64_t)gridDim.x * blockDim.x)
+    for (uint32_t p = row_ptr[u]; p < row_ptr[u + 1]; p++) rowid[p] = (uint32_t)u;
 }
 
-// pair words grouped by owner: the streamed vertex and the edge's CSR position
-__global__ void k_pair_fill(int64_t n, const uint32_t* __restrict__ row_ptr, const uint64_t* __restrict__ adj,
-                            int pull, const uint32_t* __restrict__ pair_ptr, uint32_t* __restrict__ pfill,
-                            uint64_t* __restrict__ pairs) {
-  const int lane = threadIdx.x & 31;
-  const int64_t warps = (int64_t)gridDim.x * (blockDim.x >> 5);
-  for (int64_t u = blockIdx.x * (int64_t)(blockDim.x >> 5) + (threadIdx.x >> 5); u < n; u += warps) {
-    const uint32_t rs = row_ptr[u], re = row_ptr[u + 1];
-    for (uint32_t i = rs + lane; i < re; i += 32) {
-      const uint32_t v = adj_col(adj[i]);
-      const uint32_t x = pair_owner((uint32_t)u, v, re - rs, row_ptr[v + 1] - row_ptr[v], pull);
-      const uint32_t streamed = x == (uint32_t)u ? v : (uint32_t)u;
-      pairs[pair_ptr[x] + atomicAdd(&pfill[x], 1u)] = ((uint64_t)i << 32) | streamed;
-    }
+// pairs per owner, one thread per forward entry (rowid: the row of every
+// CSR position); also the oriented wedges sum_u sum_{v in N>(u)} |N>(v)|
+// (Alg. 1's probes), one atomic per block
+__global__ void k_pair_count(int64_t m, const uint32_t* __restrict__ row_ptr, const uint64_t* __restrict__ adj,
+                             const uint32_t* __restrict__ rowid, int pull, uint32_t* __restrict__ pcount,
+                             unsigned long long* wedges) {
+  __shared__ unsigned long long s_w;
+  if (threadIdx.x == 0) s_w = 0;
+  __syncthreads();
+  unsigned long long wsum = 0;
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < m; i += (int64_t)gridDim.x * blockDim.x) {
+    const uint32_t u = rowid[i], v = adj_col(adj[i]);
+    const uint32_t du = row_ptr[u + 1] - row_ptr[u], dv = row_ptr[v + 1] - row_ptr[v];
+    wsum += dv;
+    atomicAdd(&pcount[pair_owner(u, v, du, dv, pull)], 1u);
+  }
+  atomicAdd(&s_w, wsum);
+  __syncthreads();
+  if (threadIdx.x == 0 && s_w) atomicAdd(wedges, s_w);
+}
+
+// pair words grouped by owner: the streamed vertex and the edge's CSR
+// position; work[x] += length of the streamed list (the owner's task size)
+__global__ void k_pair_fill(int64_t m, const uint32_t* __restrict__ row_ptr, const uint64_t* __restrict__ adj,
+                            const uint32_t* __restrict__ rowid, int pull, const uint32_t* __restrict__ pair_ptr,
+                            uint32_t* __restrict__ pfill, uint64_t* __restrict__ pairs,
+                            unsigned long long* __restrict__ work) {
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < m; i += (int64_t)gridDim.x * blockDim.x) {
+    const uint32_t u = rowid[i], v = adj_col(adj[i]);
+    const uint32_t du = row_ptr[u + 1] - row_ptr[u], dv = row_ptr[v + 1] - row_ptr[v];
+    const uint32_t x = pair_owner(u, v, du, dv, pull);
+    const uint32_t streamed = x == u ? v : u;
+    pairs[pair_ptr[x] + atomicAdd(&pfill[x], 1u)] = ((uint64_t)i << 32) | streamed;
+    atomicAdd(&work[x], (unsigned long long)(x == u ? dv : du));
   }
 }
 
@@ -280,61 +448,76 @@ __global__ void k_pair_fill(int64_t n, const uint32_t* __restrict__ row_ptr, con
 enum : uint8_t { kClsMedium = 1, kClsHub = 2, kClsGiant = 3 };
 constexpr uint8_t kNoTask = 0xFF;
 constexpr int kLgMax = 47;  // work buckets 2^0 .. 2^47
+constexpr int kBuckets2 = 4 * (kLgMax + 1);
 
-// Per owner x: streamed work sum over its pairs of |N>(s)|, its log2 bucket
-// and class; bucket[x] = lg * 4 + cls, or kNoTask (fewer than 2 list entries
-// or no pairs: no triangle can be found there).
-// stats: [0] oriented wedges sum_u sum_{v in N>(u)} |N>(v)| (Alg. 1's probes),
-//        [1] longest list, [2] longest list of a block task, [3] streamed
-//        work of all pairs, [4 + lg * 4 + cls] bucket sizes
-__global__ void k_row_stats(int64_t n, const uint32_t* __restrict__ row_ptr, const uint64_t* __restrict__ adj,
-                            const uint32_t* __restrict__ pair_ptr, const uint64_t* __restrict__ pairs,
-                            uint32_t hub_thr, uint32_t giant_thr, unsigned long long block_work,
-                            uint8_t* __restrict__ bucket, unsigned long long* stats) {
-  const int lane = threadIdx.x & 31;
-  const int64_t warps = (int64_t)gridDim.x * (blockDim.x >> 5);
-  for (int64_t x = blockIdx.x * (int64_t)(blockDim.x >> 5) + (threadIdx.x >> 5); x < n; x += warps) {
-    const uint32_t rs = row_ptr[x], re = row_ptr[x + 1];
-    const uint32_t len = re - rs;
-    const uint32_t ps = pair_ptr[x], pe = pair_ptr[x + 1];
-    unsigned long long wedge = 0, w = 0;
-    for (uint32_t i = rs + lane; i < re; i += 32) {
-      const uint32_t v = adj_col(adj[i]);
-      wedge += row_ptr[v + 1] - row_ptr[v];
+// Per owner x (one thread): its streamed work (from k_pair_fill), the log2
+// bucket and class; bucket[x] = lg * 4 + cls, or kNoTask (fewer than 2 list
+// entries or no pairs: no triangle can be found there).  Per-block counts in
+// shared memory, one global atomic per block and bucket.
+// stats: [1] longest list, [2] longest list of a block task, [3] streamed
+//        work of all pairs, [4 + lg * 4 + cls] bucket sizes ([0] is set by
+//        k_pair_count)
+__global__ void k_row_stats(int64_t n, const uint32_t* __restrict__ row_ptr, const uint32_t* __restrict__ pair_ptr,
+                            const unsigned long long* __restrict__ work, uint32_t hub_thr, uint32_t giant_thr,
+                            unsigned long long block_work, uint8_t* __restrict__ bucket,
+                            unsigned long long* stats) {
+  __shared__ uint32_t s_cnt[kBuckets2];
+  __shared__ unsigned long long s_work;
+  __shared__ uint32_t s_max, s_hmax;
+  for (int i = threadIdx.x; i < kBuckets2; i += blockDim.x) s_cnt[i] = 0;
+  if (threadIdx.x == 0) { s_work = 0; s_max = 0; s_hmax = 0; }
+  __syncthreads();
+  unsigned long long wsum = 0;
+  uint32_t mx = 0, hmx = 0;
+  for (int64_t x = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; x < n; x += (int64_t)gridDim.x * blockDim.x) {
+    const uint32_t len = row_ptr[x + 1] - row_ptr[x];
+    const uint32_t np = pair_ptr[x + 1] - pair_ptr[x];
+    const unsigned long long w = np ? work[x] : 0ull;
+    uint8_t b = kNoTask;
+    if (len >= 2 && np > 0) {
+      const int cls = len > giant_thr ? kClsGiant : ((len > hub_thr || w > block_work) ? kClsHub : kClsMedium);
+      int lg = w ? 63 - __clzll(w) : 0;
+      lg = lg > kLgMax ? kLgMax : lg;
+      b = (uint8_t)(lg * 4 + cls);
+      atomicAdd(&s_cnt[b], 1u);
+      if (cls == kClsHub) hmx = max(hmx, len);
     }
-    for (uint32_t i = ps + lane; i < pe; i += 32) {
-      const uint32_t sv = (uint32_t)pairs[i];
-      w += row_ptr[sv + 1] - row_ptr[sv];
-    }
-#pragma unroll
-    for (int d = 16; d > 0; d >>= 1) {
-      wedge += __shfl_xor_sync(kFull, wedge, d);
-      w += __shfl_xor_sync(kFull, w, d);
-    }
-    if (lane == 0) {
-      uint8_t b = kNoTask;
-      if (len >= 2 && pe > ps) {
-        const int cls = len > giant_thr ? kClsGiant : ((len > hub_thr || w > block_work) ? kClsHub : kClsMedium);
-        int lg = w ? 63 - __clzll(w) : 0;
-        lg = lg > kLgMax ? kLgMax : lg;
-        b = (uint8_t)(lg * 4 + cls);
-        atomicAdd(&stats[4 + b], 1ull);
-        if (cls == kClsHub) atomicMax(&stats[2], (unsigned long long)len);
-      }
-      bucket[x] = b;
-      atomicAdd(&stats[0], wedge);
-      atomicAdd(&stats[3], w);
-      atomicMax(&stats[1], (unsigned long long)len);
-    }
+    bucket[x] = b;
+    wsum += w;
+    mx = max(mx, len);
+  }
+  atomicAdd(&s_work, wsum);
+  atomicMax(&s_max, mx);
+  atomicMax(&s_hmax, hmx);
+  __syncthreads();
+  for (int i = threadIdx.x; i < kBuckets2; i += blockDim.x)
+    if (s_cnt[i]) atomicAdd(&stats[4 + i], (unsigned long long)s_cnt[i]);
+  if (threadIdx.x == 0) {
+    atomicAdd(&stats[3], s_work);
+    atomicMax(&stats[1], (unsigned long long)s_max);
+    atomicMax(&stats[2], (unsigned long long)s_hmax);
   }
 }
 
+// Task lists: every block ranks its owners per bucket in shared memory and
+// reserves one range per bucket with a single global atomic.
 __global__ void k_fill_lists(int64_t n, const uint8_t* __restrict__ bucket, unsigned long long* cursor,
                              uint32_t* __restrict__ lists) {
-  for (int64_t u = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; u < n; u += (int64_t)gridDim.x * blockDim.x) {
-    const uint8_t b = bucket[u];
-    if (b == kNoTask) continue;
-    lists[atomicAdd(&cursor[b], 1ull)] = (uint32_t)u;
+  __shared__ uint32_t s_cnt[kBuckets2];
+  __shared__ unsigned long long s_base[kBuckets2];
+  for (int64_t base = (int64_t)blockIdx.x * blockDim.x; base < n; base += (int64_t)gridDim.x * blockDim.x) {
+    for (int i = threadIdx.x; i < kBuckets2; i += blockDim.x) s_cnt[i] = 0;
+    __syncthreads();
+    const int64_t x = base + threadIdx.x;
+    const uint8_t b = x < n ? bucket[x] : kNoTask;
+    uint32_t rank = 0;
+    if (b != kNoTask) rank = atomicAdd(&s_cnt[b], 1u);
+    __syncthreads();
+    for (int i = threadIdx.x; i < kBuckets2; i += blockDim.x)
+      if (s_cnt[i]) s_base[i] = atomicAdd(&cursor[i], (unsigned long long)s_cnt[i]);
+    __syncthreads();
+    if (b != kNoTask) lists[s_base[b] + rank] = (uint32_t)x;
+    __syncthreads();
   }
 }
 
@@ -344,10 +527,15 @@ __global__ void k_fill_lists(int64_t n, const uint8_t* __restrict__ bucket, unsi
 __global__ void k_uscatter(int64_t m, const uint32_t* __restrict__ src, const uint32_t* __restrict__ dst,
                            const uint32_t* __restrict__ k, const uint32_t* __restrict__ uptr,
                            uint32_t* __restrict__ ufill, uint64_t* __restrict__ uadj, uint32_t* __restrict__ ueid) {
-  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < m; i += (int64_t)gridDim.x * blockDim.x) {
-    const uint32_t a = src[i], b = dst[i];
+  const uint32_t lane = lane_id();
+  UBT_FOR_EDGE_WARPS(base, m) {
+    const int64_t i = base + lane;
+    const bool on = i < m;
+    const uint32_t a = on ? src[i] : 0u, b = on ? dst[i] : 0u;
+    const uint32_t sa = add_by_runs(ufill, a, on);
+    if (!on) continue;
     const uint32_t val = (uint32_t)(int32_t)(32768 - (int32_t)k[i]);
-    const uint32_t pa = uptr[a] + atomicAdd(&ufill[a], 1u);
+    const uint32_t pa = uptr[a] + sa;
     const uint32_t pb = uptr[b] + atomicAdd(&ufill[b], 1u);
     uadj[pa] = adj_pack(b, val);
     ueid[pa] = (uint32_t)i;
@@ -508,6 +696,7 @@ struct BuildLayout {
   uint32_t* mid_rows;
   uint32_t* huge_rows;
   uint8_t* bucket;
+  unsigned long long* work;    // streamed work per owner
   unsigned long long* stats;   // 4 + 4*48 counters, 4*48 cursors, 2 counters
   char* sort_tmp;
   size_t total;
@@ -563,7 +752,8 @@ BuildLayout layout(void* ws, size_t cap, int64_t n, int64_t m, const ubt_graph_o
   L.mid_rows = c.take<uint32_t>(n1);
   L.huge_rows = c.take<uint32_t>(n1);
   L.bucket = c.take<uint8_t>(n1);
-  L.stats = c.take<unsigned long long>(2 * kStats + 2);
+  L.work = c.take<unsigned long long>(n1);
+  L.stats = c.take<unsigned long long>(2 * kStats + 4);
   const int64_t lb = list_bound(n, m);
   L.sort_tmp = lb > tuning().sort_smem_max
                    ? c.take<char>((size_t)kSortHugeBlocks * (size_t)pow2_at_least(lb) * 24) : nullptr;
@@ -645,7 +835,7 @@ extern "C" ubt_status ubt_create_graph(int64_t n, int64_t m, const uint32_t* d_s
   UBT_CUDA(cudaMemsetAsync(&L.scratch->err, 0xFF, sizeof(unsigned long long), s));
   UBT_CUDA(cudaMemsetAsync(L.deg, 0, sizeof(uint32_t) * (n + 1), s));
   UBT_CUDA(cudaMemsetAsync(L.fill, 0, sizeof(uint32_t) * (n + 1), s));
-  UBT_CUDA(cudaMemsetAsync(L.stats, 0, sizeof(unsigned long long) * (2 * kStats + 2), s));
+  UBT_CUDA(cudaMemsetAsync(L.stats, 0, sizeof(unsigned long long) * (2 * kStats + 4), s));
   const int thr = 256;
   const int grid_e = (int)std::min<int64_t>(std::max<int64_t>((m + thr - 1) / thr, 1), (int64_t)sms * 32);
   const int grid_v = (int)std::min<int64_t>(std::max<int64_t>((n + thr - 1) / thr, 1), (int64_t)sms * 32);
@@ -676,9 +866,14 @@ extern "C" ubt_status ubt_create_graph(int64_t n, int64_t m, const uint32_t* d_s
     k_sort_short_rows<<<grid_w, thr, 0, s>>>(n, L.row_ptr, L.adj, L.eid, L.ekey, fixed, &L.scratch->err);
     const uint32_t sort_smem = (uint32_t)tuning().sort_smem_max;
     k_collect_long<<<grid_v, thr, 0, s>>>(n, L.row_ptr, sort_smem, L.mid_rows, L.huge_rows, lcount);
-    unsigned long long lc[2] = {0, 0};
+    unsigned long long lc[3] = {0, 0, 0};
     UBT_CUDA(cudaMemcpyAsync(lc, lcount, sizeof(lc), cudaMemcpyDeviceToHost, s));
     UBT_CUDA(cudaStreamSynchronize(s));
+    if (lc[2]) {
+      const int g = (int)std::min<unsigned long long>((lc[2] + 7) / 8, (unsigned long long)sms * 32);
+      k_sort_mid_rows<<<g, thr, 0, s>>>(L.mid_rows + (n - (int64_t)lc[2]), (uint32_t)lc[2], L.row_ptr, L.adj, L.eid,
+                                        L.ekey, fixed, &L.scratch->err);
+    }
     if (lc[0]) {
       const size_t smem = (size_t)std::max<uint32_t>(sort_smem, 64) * 24;
       UBT_CUDA(cudaFuncSetAttribute(k_sort_long_rows<false>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
@@ -702,18 +897,23 @@ extern "C" ubt_status ubt_create_graph(int64_t n, int64_t m, const uint32_t* d_s
   UBT_CUDA(cudaMemsetAsync(L.pair_ptr, 0, sizeof(uint32_t) * (n + 1), s));
   if (n > 0) {
     UBT_CUDA(cudaMemsetAsync(L.fill, 0, sizeof(uint32_t) * (n + 1), s));
-    if (m > 0) k_pair_count<<<grid_w, thr, 0, s>>>(n, L.row_ptr, L.adj, pull, L.fill);
+    // the row of every CSR position, in the (not yet used) adjoint accumulators
+    uint32_t* rowid = (uint32_t*)L.gacc;
+    k_row_ids<<<grid_v, thr, 0, s>>>(n, L.row_ptr, rowid);
+    if (m > 0) k_pair_count<<<grid_e, thr, 0, s>>>(m, L.row_ptr, L.adj, rowid, pull, L.fill, &L.stats[0]);
     UBT_CUDA(exclusive_scan_u32(L.fill, L.pair_ptr, n, L.scan_tmp, s));
     UBT_CUDA(cudaMemsetAsync(L.fill, 0, sizeof(uint32_t) * (n + 1), s));
-    if (m > 0) k_pair_fill<<<grid_w, thr, 0, s>>>(n, L.row_ptr, L.adj, pull, L.pair_ptr, L.fill, L.pairs);
+    UBT_CUDA(cudaMemsetAsync(L.work, 0, sizeof(unsigned long long) * n, s));
+    if (m > 0)
+      k_pair_fill<<<grid_e, thr, 0, s>>>(m, L.row_ptr, L.adj, rowid, pull, L.pair_ptr, L.fill, L.pairs, L.work);
     UBT_CUDA(cudaGetLastError());
   }
   // 5. work lists: giant | hub | medium tasks, each by decreasing work bucket
   unsigned long long stats[kStats];
   memset(stats, 0, sizeof(stats));
   if (n > 0) {
-    k_row_stats<<<grid_w, thr, 0, s>>>(n, L.row_ptr, L.adj, L.pair_ptr, L.pairs, (uint32_t)hub_thr,
-                                      (uint32_t)giant_thr, (unsigned long long)block_work, L.bucket, L.stats);
+    k_row_stats<<<grid_v, thr, 0, s>>>(n, L.row_ptr, L.pair_ptr, L.work, (uint32_t)hub_thr, (uint32_t)giant_thr,
+                                      (unsigned long long)block_work, L.bucket, L.stats);
     UBT_CUDA(cudaMemcpyAsync(stats, L.stats, sizeof(stats), cudaMemcpyDeviceToHost, s));
     UBT_CUDA(cudaStreamSynchronize(s));
   }
@@ -748,11 +948,16 @@ extern "C" ubt_status ubt_create_graph(int64_t n, int64_t m, const uint32_t* d_s
     if (m > 0) k_uscatter<<<grid_e, thr, 0, s>>>(m, d_src, d_dst, d_k, L.uptr, L.fill, L.uadj, L.ueid);
     k_sort_short_rows<<<grid_w, thr, 0, s>>>(n, L.uptr, L.uadj, L.ueid, nullptr, 1, &L.scratch->err);
     const uint32_t sort_smem = (uint32_t)tuning().sort_smem_max;
-    UBT_CUDA(cudaMemsetAsync(lcount, 0, 2 * sizeof(unsigned long long), s));
+    UBT_CUDA(cudaMemsetAsync(lcount, 0, 3 * sizeof(unsigned long long), s));
     k_collect_long<<<grid_v, thr, 0, s>>>(n, L.uptr, sort_smem, L.mid_rows, L.huge_rows, lcount);
-    unsigned long long lc[2] = {0, 0};
+    unsigned long long lc[3] = {0, 0, 0};
     UBT_CUDA(cudaMemcpyAsync(lc, lcount, sizeof(lc), cudaMemcpyDeviceToHost, s));
     UBT_CUDA(cudaStreamSynchronize(s));
+    if (lc[2]) {
+      const int g2 = (int)std::min<unsigned long long>((lc[2] + 7) / 8, (unsigned long long)sms * 32);
+      k_sort_mid_rows<<<g2, thr, 0, s>>>(L.mid_rows + (n - (int64_t)lc[2]), (uint32_t)lc[2], L.uptr, L.uadj, L.ueid,
+                                         nullptr, 1, &L.scratch->err);
+    }
     if (lc[0]) {
       const size_t smem = (size_t)std::max<uint32_t>(sort_smem, 64) * 24;
       UBT_CUDA(cudaFuncSetAttribute(k_sort_long_rows<false>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));

@@ -33,8 +33,10 @@ struct AeoArgs {
   const uint32_t* umir;       // mirror position of every entry
   const uint32_t* apair_ptr;  // edges owned by x: [apair_ptr[x], apair_ptr[x + 1])
   const uint64_t* apairs;     // streamed endpoint | position of the edge in x's row << 32
-  const uint32_t* alist;      // owners
+  const uint32_t* alist;      // owners: block tasks first, then warp tasks
   uint32_t n_owners;
+  uint32_t n_block;           // owners handled by a whole block
+  uint32_t wcap;              // per-warp table slots
   uint32_t n;
   uint32_t m2;                // 2m, the number of row entries
   Scratch* sc;
@@ -51,7 +53,8 @@ struct AeoPair {
   bool ok;
 };
 
-__device__ __forceinline__ AeoPair aeo_pair(const AeoArgs& a, uint32_t x, uint32_t idx, bool in, uint32_t tab_end) {
+__device__ __forceinline__ AeoPair aeo_pair(const AeoArgs& a, uint32_t x, uint32_t idx, bool in, uint32_t tab_begin,
+                                            uint32_t tab_end, uint32_t rs, uint32_t tlen) {
   AeoPair pr;
   pr.x = x;
   pr.ok = in;
@@ -72,6 +75,9 @@ __device__ __forceinline__ AeoPair aeo_pair(const AeoArgs& a, uint32_t x, uint32
   const int64_t aq = qabs(pr.qe);
   pr.cut = aq * aq;
   if (a.L > 0 && aq * (1ll << 30) < a.L) pr.ok = false;  // Lemma 2
+  // the table entries that can pair with e lie in x's row after e and before
+  // Lemma 3's cutoff: skip the chunk when it holds none of them
+  if (pr.ok && a.L > 0 && rs + prune_prefix(a.uadj + rs, tlen, pr.cut, a.L) <= tab_begin) pr.ok = false;
   if (pr.ok) {
     const uint32_t ys = a.uptr[pr.y], ye = a.uptr[pr.y + 1];
     const uint32_t start = a.umir[pr.pe] + 1;
@@ -214,12 +220,49 @@ __device__ void aeo_task(const AeoArgs& a, V& vis, uint32_t x, uint32_t* tab, ui
       c = __shfl_sync(kFull, c, 0);
       cnt = __shfl_sync(kFull, cnt, 0);
       if (cnt == 0) break;
-      aeo_probe<V>(a, vis, t, aeo_pair(a, x, ps + c + lane, (uint32_t)lane < cnt, rs + c1));
+      aeo_probe<V>(a, vis, t, aeo_pair(a, x, ps + c + lane, (uint32_t)lane < cnt, rs + c0, rs + c1, rs, tlen));
     }
     __syncthreads();
   }
   vis.task_end(x);
   __syncthreads();
+}
+
+// One warp handles owner x (a row of at most 128 entries): one table.
+template <class V>
+__device__ void aeo_warp_task(const AeoArgs& a, V& vis, uint32_t x, uint32_t* wtab) {
+  const int lane = (int)lane_id();
+  if (x >= a.n) {
+    if (lane == 0) guard_fail(a.sc, kGuardVertex, x);
+    return;
+  }
+  const uint32_t rs = a.uptr[x], re = a.uptr[x + 1];
+  const uint32_t ps = a.apair_ptr[x], pend = a.apair_ptr[x + 1];
+  if (re < rs || re > a.m2 || pend < ps || pend - ps > re - rs) {
+    if (lane == 0) guard_fail(a.sc, kGuardList, x);
+    return;
+  }
+  const uint32_t np = pend - ps;
+  const uint32_t tlen = a.L > 0 ? prune_prefix(a.uadj + rs, re - rs, 1ll << 30, a.L) : re - rs;  // Lemma 2
+  if (tlen < 2 || np == 0) return;
+  const uint32_t slots = slots_for(tlen);
+  if (slots > a.wcap) {
+    if (lane == 0) guard_fail(a.sc, kGuardTable, x);
+    return;
+  }
+  const Table t = make_table(wtab, a.wcap, slots);
+  for (uint32_t i = lane; i < slots; i += 32) t.key[i] = kEmpty;
+  __syncwarp();
+  for (uint32_t i = lane; i < tlen; i += 32) {
+    const uint64_t e = a.uadj[rs + i];
+    table_insert(t, adj_col(e), adj_valbits(e), rs + i, a.sc);
+  }
+  __syncwarp();
+  vis.task_begin(x);
+  for (uint32_t cs = 0; cs < np; cs += 32)
+    aeo_probe<V>(a, vis, t, aeo_pair(a, x, ps + cs + lane, (uint32_t)lane < np - cs, rs, rs + tlen, rs, tlen));
+  vis.task_end(x);
+  __syncwarp();
 }
 
 template <class V>
@@ -235,8 +278,18 @@ __global__ void __launch_bounds__(512, 2) k_aeo(AeoArgs a, typename V::P p) {
     __syncthreads();
     const uint32_t task = s_misc[2];
     __syncthreads();
-    if (task >= a.n_owners) break;
+    if (task >= a.n_block) break;
     aeo_task(a, vis, a.alist[task], tab, s_misc);
+  }
+  __syncthreads();  // the block tables are free: the region becomes per-warp tables
+  const int lane = threadIdx.x & 31;
+  uint32_t* wtab = tab + (size_t)(threadIdx.x >> 5) * a.wcap * 3;
+  while (true) {
+    unsigned long long t0 = 0;
+    if (lane == 0) t0 = atomicAdd(&a.sc->task[1], 1ull);
+    t0 = __shfl_sync(kFull, t0, 0);
+    if (t0 >= (unsigned long long)(a.n_owners - a.n_block)) break;
+    aeo_warp_task(a, vis, a.alist[a.n_block + (uint32_t)t0], wtab);
   }
   __syncthreads();
   vis.block_end();
@@ -256,6 +309,8 @@ ubt_status launch_aeo(const ubt_graph* g, int64_t L, const typename V::P& p, cud
   a.apairs = g->apairs;
   a.alist = g->alist;
   a.n_owners = (uint32_t)g->n_aowners;
+  a.n_block = (uint32_t)g->n_ablock;
+  a.wcap = (uint32_t)table_slots(std::min<int64_t>(128, std::max<int64_t>(g->max_udeg, 2)));
   a.n = (uint32_t)g->n;
   a.m2 = (uint32_t)(2 * g->m);
   a.sc = g->scratch;
@@ -266,7 +321,8 @@ ubt_status launch_aeo(const ubt_graph* g, int64_t L, const typename V::P& p, cud
   UBT_CUDA(cudaMemsetAsync(a.sc, 0, kScratchHeader / 2, s));
   if (a.n_owners == 0) return UBT_OK;
   const int threads = 512;
-  const size_t smem = (size_t)((V::smem_bytes(threads) + 15) / 16) * 16 + (size_t)a.cap * 3 * 4;
+  const size_t tables = std::max<size_t>((size_t)a.cap, (size_t)(threads / 32) * a.wcap) * 3 * 4;
+  const size_t smem = (size_t)((V::smem_bytes(threads) + 15) / 16) * 16 + tables;
   UBT_CUDA(cudaFuncSetAttribute(k_aeo<V>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
   int per_sm = 0;
   UBT_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_aeo<V>, threads, smem));

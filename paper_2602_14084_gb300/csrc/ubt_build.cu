@@ -647,16 +647,19 @@ __global__ void k_apair_fill(int64_t n, const uint32_t* __restrict__ uptr, const
     if (lane == 0) work[x] = w;
   }
 }
-// owners by decreasing log2 of their streamed work
-__global__ void k_afill_lists(int64_t n, const uint32_t* __restrict__ apair_ptr,
+// owners by decreasing log2 of their streamed work, those with rows longer
+// than kAeoWarpRow (whole-block tasks) first: bucket = lg * 2 + (1 if block)
+constexpr uint32_t kAeoWarpRow = 128;
+__global__ void k_afill_lists(int64_t n, const uint32_t* __restrict__ uptr, const uint32_t* __restrict__ apair_ptr,
                               const unsigned long long* __restrict__ work, unsigned long long* cursor,
                               uint32_t* __restrict__ lists, int count_only) {
   for (int64_t x = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; x < n; x += (int64_t)gridDim.x * blockDim.x) {
     if (apair_ptr[x + 1] == apair_ptr[x]) continue;
     const unsigned long long w = work[x];
     const int lg = w ? 63 - __clzll(w) : 0;
-    if (count_only) atomicAdd(&cursor[lg], 1ull);
-    else lists[atomicAdd(&cursor[lg], 1ull)] = (uint32_t)x;
+    const int b = lg * 2 + (uptr[x + 1] - uptr[x] > kAeoWarpRow ? 1 : 0);
+    if (count_only) atomicAdd(&cursor[b], 1ull);
+    else lists[atomicAdd(&cursor[b], 1ull)] = (uint32_t)x;
   }
 }
 __global__ void k_max_row(int64_t n, const uint32_t* __restrict__ ptr, unsigned long long* out) {
@@ -941,7 +944,7 @@ extern "C" ubt_status ubt_create_graph(int64_t n, int64_t m, const uint32_t* d_s
   (void)ng;
   // 6. undirected adjacency in Absolute Edge Order, its mirror positions and
   //    the AEO pair partition (optional)
-  int64_t n_aowners = 0, max_udeg = 0;
+  int64_t n_aowners = 0, n_ablock = 0, max_udeg = 0;
   if (und && n > 0) {
     UBT_CUDA(exclusive_scan_u32(L.deg, L.uptr, n, L.scan_tmp, s));
     UBT_CUDA(cudaMemsetAsync(L.fill, 0, sizeof(uint32_t) * (n + 1), s));
@@ -975,25 +978,29 @@ extern "C" ubt_status ubt_create_graph(int64_t n, int64_t m, const uint32_t* d_s
     k_apair_count<<<grid_w, thr, 0, s>>>(n, L.uptr, L.uadj, L.fill);
     UBT_CUDA(exclusive_scan_u32(L.fill, L.apair_ptr, n, L.scan_tmp, s));
     k_apair_fill<<<grid_w, thr, 0, s>>>(n, L.uptr, L.uadj, L.apair_ptr, L.apairs, L.awork);
-    unsigned long long* acur = L.stats;  // kLgMax + 1 cursors
-    UBT_CUDA(cudaMemsetAsync(acur, 0, sizeof(unsigned long long) * (kLgMax + 2), s));
-    k_afill_lists<<<grid_v, thr, 0, s>>>(n, L.apair_ptr, L.awork, acur, L.alist, 1);
-    unsigned long long acount[kLgMax + 2];
+    unsigned long long* acur = L.stats;  // 2 (kLgMax + 1) cursors, then the longest row
+    constexpr int kAB = 2 * (kLgMax + 1);
+    UBT_CUDA(cudaMemsetAsync(acur, 0, sizeof(unsigned long long) * (kAB + 1), s));
+    k_afill_lists<<<grid_v, thr, 0, s>>>(n, L.uptr, L.apair_ptr, L.awork, acur, L.alist, 1);
+    unsigned long long acount[kAB + 1];
     UBT_CUDA(cudaMemcpyAsync(acount, acur, sizeof(acount), cudaMemcpyDeviceToHost, s));
     UBT_CUDA(cudaStreamSynchronize(s));
     unsigned long long run = 0;
-    for (int lg = kLgMax; lg >= 0; lg--) {
-      const unsigned long long c = acount[lg];
-      acount[lg] = run;
-      run += c;
+    for (int cls = 1; cls >= 0; cls--) {  // block tasks, then warp tasks
+      for (int lg = kLgMax; lg >= 0; lg--) {
+        const unsigned long long c = acount[lg * 2 + cls];
+        acount[lg * 2 + cls] = run;
+        run += c;
+      }
+      if (cls == 1) n_ablock = (int64_t)run;
     }
     n_aowners = (int64_t)run;
-    acount[kLgMax + 1] = 0;
+    acount[kAB] = 0;
     UBT_CUDA(cudaMemcpyAsync(acur, acount, sizeof(acount), cudaMemcpyHostToDevice, s));
-    k_afill_lists<<<grid_v, thr, 0, s>>>(n, L.apair_ptr, L.awork, acur, L.alist, 0);
-    k_max_row<<<grid_v, thr, 0, s>>>(n, L.uptr, &acur[kLgMax + 1]);
+    k_afill_lists<<<grid_v, thr, 0, s>>>(n, L.uptr, L.apair_ptr, L.awork, acur, L.alist, 0);
+    k_max_row<<<grid_v, thr, 0, s>>>(n, L.uptr, &acur[kAB]);
     unsigned long long mx = 0;
-    UBT_CUDA(cudaMemcpyAsync(&mx, &acur[kLgMax + 1], sizeof(mx), cudaMemcpyDeviceToHost, s));
+    UBT_CUDA(cudaMemcpyAsync(&mx, &acur[kAB], sizeof(mx), cudaMemcpyDeviceToHost, s));
     UBT_CUDA(cudaMemcpyAsync(&err, &L.scratch->err, sizeof(err), cudaMemcpyDeviceToHost, s));
     UBT_CUDA(cudaGetLastError());
     UBT_CUDA(cudaStreamSynchronize(s));
@@ -1030,6 +1037,7 @@ extern "C" ubt_status ubt_create_graph(int64_t n, int64_t m, const uint32_t* d_s
   g->apairs = L.apairs;
   g->alist = L.alist;
   g->n_aowners = n_aowners;
+  g->n_ablock = n_ablock;
   g->max_udeg = max_udeg;
   g->gacc = L.gacc;
   g->bacc = L.bacc;

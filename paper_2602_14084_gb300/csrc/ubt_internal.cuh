@@ -97,7 +97,7 @@ struct ubt_graph {
   uint32_t* apair_ptr = nullptr;    // n + 1: edges owned by x in the AEO traversal
   uint64_t* apairs = nullptr;       // m: streamed endpoint | position of the edge in x's row << 32
   uint32_t* alist = nullptr;        // owners, by decreasing streamed work
-  int64_t n_aowners = 0, max_udeg = 0;
+  int64_t n_aowners = 0, n_ablock = 0, max_udeg = 0;  // owners; the first n_ablock are block tasks
   unsigned long long* gacc = nullptr;   // m: backward accumulators
   unsigned long long* bacc = nullptr;   // batch accumulators
   uint32_t* gtab = nullptr;         // global hash tables for very long lists

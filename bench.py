@@ -767,6 +767,20 @@ def extra_topk(ubt, args, flush):
                 "note": "host wall time of the synchronous call, D2H of the K records included"}
     del G
     _release()
+    # per-vertex top-10 of 100,000 uniformly drawn vertices
+    G = ubt.Graph(g.n, g.src, g.dst, k=g.k, undirected=True)
+    verts = torch.from_numpy(np.random.default_rng(5).integers(0, g.n, size=100000).astype(np.int32)).cuda()
+    G.vertex_topk(verts[:1000], 10, 1)
+    times = []
+    for _ in range(3):
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        G.vertex_topk(verts, 10, 1)
+        times.append(1e3 * (time.perf_counter() - t0))
+    res["vertex_top10_of_100k_vertices"] = {"ms_median": float(np.median(times)),
+                                           "note": "host wall time, D2H of 1M records included"}
+    del G
+    _release()
     return res
 
 

@@ -388,6 +388,22 @@ ubt_status ubt_vertex_local_counts(ubt_graph* g, const uint32_t* d_vertices, int
                                    void* stream);
 
 /*
+ * ubt_vertex_topk -- ASYNC.  Per-vertex top-k (Sec. 5, top-k "locally for
+ * each node"): for each of k listed vertices, its K triangles of highest
+ * balance (which = 1) or unbalance (which = 2) probability, sorted by that
+ * probability (descending), ties by (u, v, w).  Where more than 1,024 - (the
+ * triangles strictly better than the K-th) triangles tie at the K-th value,
+ * an arbitrary subset of the ties completes the vertex's answer.
+ *   d_vertices  device uint32[k], each < n (larger ids set the self-check word)
+ *   K           1..256
+ *   d_out       device ubt_tri_rec[k * K]: vertex i's records at [i K, i K + d_n_out[i])
+ *   d_n_out     device int32[k]: min(K, triangles through the vertex)
+ * Needs UBT_OPT_UNDIRECTED.
+ */
+ubt_status ubt_vertex_topk(ubt_graph* g, const uint32_t* d_vertices, int64_t k, int32_t K, int32_t which,
+                           ubt_tri_rec* d_out, int32_t* d_n_out, void* stream);
+
+/*
  * ubt_graph_export_undirected -- SYNC.  Copies the undirected adjacency of a
  * graph built with UBT_OPT_UNDIRECTED to host memory (any pointer may be
  * NULL; UBT_ERR_UNSUPPORTED without the option).  Row x holds every edge at x,

@@ -83,6 +83,7 @@ def lib():
             "ubt_graph_export_undirected": (I32, [P, P, P, P, P, P, P, P]),
             "ubt_count_aeo": (I32, [P, P, I32, P, P]),
             "ubt_topk_workspace_size": (I32, [I64, ctypes.POINTER(SZ)]),
+            "ubt_vertex_topk": (I32, [P, P, I64, I32, I32, P, P, P]),
             "ubt_topk": (I32, [P, I64, I32, P, ctypes.POINTER(I64), P, SZ, P]),
             "ubt_enumerate_aeo": (I32, [P, ctypes.c_double, I32, P, I64, ctypes.POINTER(I64), P]),
             "ubt_edge_local_counts": (I32, [P, P, I64, P, I32, P, P, P, P]),
@@ -360,6 +361,20 @@ class Graph:
         _check(L.ubt_topk(self._h, int(K), int(which), _ptr(out), ctypes.byref(n), _ptr(work), work.numel(),
                           _stream(stream)), "ubt_topk")
         return out.cpu().numpy()[: int(n.value) * TRI_REC_DTYPE.itemsize].view(TRI_REC_DTYPE)
+
+    def vertex_topk(self, vertices, K, which=1, stream=None):
+        """Per vertex, its K most balanced (which=1) or unbalanced (which=2)
+        triangles: a list of record arrays (TRI_REC_DTYPE), one per vertex."""
+        torch = _torch()
+        it = _dev_u32(vertices, self.device)
+        k = int(it.numel())
+        out = torch.empty(max(k * int(K), 1) * TRI_REC_DTYPE.itemsize, dtype=torch.uint8, device=self.device)
+        cnt = torch.zeros(max(k, 1), dtype=torch.int32, device=self.device)
+        _check(lib().ubt_vertex_topk(self._h, _ptr(it), k, int(K), int(which), _ptr(out), _ptr(cnt), _stream(stream)),
+               "ubt_vertex_topk")
+        rec = out.cpu().numpy()[: k * int(K) * TRI_REC_DTYPE.itemsize].view(TRI_REC_DTYPE).reshape(k, int(K))
+        c = cnt.cpu().numpy()[:k]
+        return [rec[i, : int(c[i])] for i in range(k)]
 
     def export_undirected(self, stream=None):
         """The undirected adjacency in Absolute Edge Order and the AEO edge owners."""

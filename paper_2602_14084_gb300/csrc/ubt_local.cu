@@ -268,6 +268,179 @@ ubt_status local_counts(ubt_graph* g, const uint32_t* d_items, int64_t k, int ve
   return UBT_OK;
 }
 
+// ------------------------------------------------------------ per-vertex top-k
+
+// Per-vertex top-k (Sec. 5: "top-k ... locally for each node"): for every
+// listed vertex, its K triangles of highest balance (which = 1) or unbalance
+// (which = 2) probability.  One block per vertex, two passes over the
+// triangles through it (its row as the table, every neighbour's row
+// streamed, each triangle once): a histogram of the triangles' rank key
+// r = P + 2^45 (balanced) or 2^45 - P (unbalanced; smaller is better) over
+// 2049 slices of 2^35 finds the slice holding the K-th best; the second pass
+// keeps the triangles of better slices (fewer than K) and as many of that
+// slice as fit, and a shared-memory sort by (r, u, v, w) gives the answer.
+constexpr int kTopkSlices = 2049;  // slices of 2^35 over the rank range [0, 2^46]
+constexpr int kTopkCap = 1024;   // candidate buffer per vertex
+constexpr int kTopkMax = 256;    // largest K
+
+struct TopkArgs {
+  const uint32_t* uptr;
+  const uint64_t* uadj;
+  const uint32_t* items;
+  uint32_t n_items, n, m2, K;
+  int which;
+  uint32_t cap;                  // table slots
+  Scratch* sc;
+  ubt_tri_rec* out;              // [item][K]
+  int32_t* n_out;                // [item]
+};
+
+__device__ __forceinline__ uint64_t topk_rank(long long P, int which) {
+  return which == 1 ? (uint64_t)(P + (1ll << 45)) : (uint64_t)((1ll << 45) - P);
+}
+
+__device__ __forceinline__ bool cand_before(uint64_t ra, const uint32_t* ta, uint64_t rb, const uint32_t* tb) {
+  if (ra != rb) return ra < rb;
+  if (ta[0] != tb[0]) return ta[0] < tb[0];
+  if (ta[1] != tb[1]) return ta[1] < tb[1];
+  return ta[2] < tb[2];
+}
+
+__global__ void __launch_bounds__(512, 1) k_vertex_topk(TopkArgs a) {
+  extern __shared__ __align__(16) char smem[];
+  __shared__ uint32_t s_misc[8];
+  uint32_t* hist = (uint32_t*)smem;                                   // 2049 (+pad) slice counts
+  uint64_t* crank = (uint64_t*)(smem + 2064 * 4);                     // candidates: rank
+  uint32_t* ctri = (uint32_t*)(crank + kTopkCap);                     // candidates: sorted triple
+  uint32_t* tab = ctri + 3 * kTopkCap;
+  const int tid = threadIdx.x, lane = tid & 31, wid = tid >> 5, nw = blockDim.x >> 5;
+  while (true) {
+    if (tid == 0) s_misc[0] = (uint32_t)atomicAdd(&a.sc->task[0], 1ull);
+    __syncthreads();
+    const uint32_t item = s_misc[0];
+    if (item >= a.n_items) break;
+    const uint32_t v = a.items[item];
+    const bool ok = v < a.n;
+    if (!ok && tid == 0) guard_fail(a.sc, kGuardVertex, v);
+    const uint32_t rs = ok ? a.uptr[v] : 0u, deg = ok ? a.uptr[v + 1] - rs : 0u;
+    const uint32_t chunk = a.cap / 4;
+    uint32_t sstar = kTopkSlices - 1, below = 0;  // threshold slice, candidates in better slices
+    for (int pass = 0; pass < 2; pass++) {
+      if (pass == 0) {
+        for (int i = tid; i < kTopkSlices; i += blockDim.x) hist[i] = 0;
+      } else if (tid == 0) {
+        s_misc[1] = 0;       // cursor of better slices
+        s_misc[2] = below;   // cursor of the threshold slice
+      }
+      __syncthreads();
+      for (uint32_t c0 = 0; c0 < deg; c0 += chunk) {
+        const uint32_t c1 = min(deg, c0 + chunk);
+        const uint32_t slots = slots_for(c1 - c0);
+        const Table t = make_table(tab, a.cap, slots);
+        for (uint32_t i = tid; i < slots; i += blockDim.x) t.key[i] = kEmpty;
+        __syncthreads();
+        for (uint32_t i = c0 + tid; i < c1; i += blockDim.x) {
+          const uint64_t e = a.uadj[rs + i];
+          table_insert(t, adj_col(e), adj_valbits(e), rs + i, a.sc);
+        }
+        __syncthreads();
+        for (uint32_t j = wid; j < deg; j += nw) {
+          const uint32_t pa = rs + j;
+          if (pa + 1 >= rs + c1) continue;  // b must come after a in v's row
+          const uint64_t ea = a.uadj[pa];
+          const uint32_t av = adj_col(ea);
+          const uint32_t qa = adj_valbits(ea);
+          if (av >= a.n) {
+            if (lane == 0) guard_fail(a.sc, kGuardVertex, av);
+            continue;
+          }
+          const uint32_t s0 = a.uptr[av], s1 = a.uptr[av + 1];
+          for (uint32_t b0 = s0; b0 < s1; b0 += 32) {
+            const uint32_t pos = b0 + lane;
+            const bool act = pos < s1;
+            const uint64_t e = act ? a.uadj[pos] : 0ull;
+            uint32_t qt = 0, pt = 0;
+            const bool hit = act && table_find<true>(t, adj_col(e), qt, pt, a.sc) && pt > pa;
+            if (!hit) continue;
+            const long long P = (long long)((int32_t)qa * (int32_t)qt) * (long long)(int32_t)adj_valbits(e);
+            const uint64_t r = topk_rank(P, a.which);
+            const uint32_t sl = (uint32_t)(r >> 35);
+            if (pass == 0) {
+              atomicAdd(&hist[sl], 1u);
+            } else if (sl <= sstar) {
+              const uint32_t at = sl < sstar ? atomicAdd(&s_misc[1], 1u) : atomicAdd(&s_misc[2], 1u);
+              if (at < kTopkCap) {
+                uint32_t x0 = v, x1 = av, x2 = adj_col(e), tt;
+                if (x0 > x1) { tt = x0; x0 = x1; x1 = tt; }
+                if (x1 > x2) { tt = x1; x1 = x2; x2 = tt; }
+                if (x0 > x1) { tt = x0; x0 = x1; x1 = tt; }
+                crank[at] = r;
+                ctri[3 * at] = x0;
+                ctri[3 * at + 1] = x1;
+                ctri[3 * at + 2] = x2;
+              }
+            }
+          }
+        }
+        __syncthreads();
+      }
+      if (pass == 0) {
+        // the slice of the K-th best: first slice whose running count reaches K
+        if (tid == 0) {  // (fewer than K in all: every slice)
+          uint32_t acc = 0, sel = kTopkSlices - 1;
+          for (uint32_t i = 0; i < (uint32_t)kTopkSlices; i++) {
+            if (acc + hist[i] >= a.K) { sel = i; break; }
+            acc += hist[i];
+          }
+          uint32_t bel = 0;
+          for (uint32_t i = 0; i < sel; i++) bel += hist[i];
+          s_misc[3] = sel;
+          s_misc[4] = bel;
+        }
+        __syncthreads();
+        sstar = s_misc[3];
+        below = s_misc[4];
+      }
+    }
+    __syncthreads();
+    const uint32_t ncand = min((uint32_t)kTopkCap, s_misc[2]);
+    // sort the candidates by (rank, triple): bitonic network, mirror-first merges
+    uint32_t cap2 = 2;
+    while (cap2 < ncand) cap2 <<= 1;
+    for (uint32_t kk = 2; kk <= cap2; kk <<= 1) {
+      for (uint32_t j = kk >> 1; j > 0; j >>= 1) {
+        for (uint32_t i = tid; i < cap2; i += blockDim.x) {
+          const uint32_t ixj = (j == (kk >> 1)) ? (i ^ (kk - 1)) : (i ^ j);
+          if (ixj > i && ixj < ncand && cand_before(crank[ixj], &ctri[3 * ixj], crank[i], &ctri[3 * i])) {
+            const uint64_t r = crank[i];
+            crank[i] = crank[ixj];
+            crank[ixj] = r;
+            for (int q = 0; q < 3; q++) {
+              const uint32_t t2 = ctri[3 * i + q];
+              ctri[3 * i + q] = ctri[3 * ixj + q];
+              ctri[3 * ixj + q] = t2;
+            }
+          }
+        }
+        __syncthreads();
+      }
+    }
+    const uint32_t nout = min(a.K, ncand);
+    for (uint32_t i = tid; i < nout; i += blockDim.x) {
+      ubt_tri_rec rec;
+      rec.u = ctri[3 * i];
+      rec.v = ctri[3 * i + 1];
+      rec.w = ctri[3 * i + 2];
+      rec.cls = (uint32_t)a.which;
+      const long long P = a.which == 1 ? (long long)crank[i] - (1ll << 45) : (1ll << 45) - (long long)crank[i];
+      rec.p_bal = (double)((1ll << 45) - P) * 0x1p-46;
+      a.out[(size_t)item * a.K + i] = rec;
+    }
+    if (tid == 0) a.n_out[item] = (int32_t)nout;
+    __syncthreads();
+  }
+}
+
 }  // namespace
 
 }  // namespace ubt
@@ -284,4 +457,38 @@ extern "C" ubt_status ubt_vertex_local_counts(ubt_graph* g, const uint32_t* d_ve
                                               const double* h_tau, int32_t n_tau, int64_t* d_bal, int64_t* d_unbal,
                                               double* d_estimate, void* stream) {
   return local_counts(g, d_vertices, k, 1, h_tau, n_tau, d_bal, d_unbal, d_estimate, (cudaStream_t)stream);
+}
+
+extern "C" ubt_status ubt_vertex_topk(ubt_graph* g, const uint32_t* d_vertices, int64_t k, int32_t K, int32_t which,
+                                      ubt_tri_rec* d_out, int32_t* d_n_out, void* stream) {
+  if (!g || k < 0 || (k > 0 && (!d_vertices || !d_out || !d_n_out))) return UBT_ERR_INVALID_ARG;
+  if (K < 1 || K > kTopkMax || (which != 1 && which != 2) || k >= 0xFFFFFFFFll) return UBT_ERR_INVALID_ARG;
+  if (g->kind != UBT_GRAPH_FIXED || !g->uptr) return UBT_ERR_UNSUPPORTED;
+  cudaStream_t s = (cudaStream_t)stream;
+  TopkArgs a;
+  a.uptr = g->uptr;
+  a.uadj = g->uadj;
+  a.items = d_vertices;
+  a.n_items = (uint32_t)k;
+  a.n = (uint32_t)g->n;
+  a.m2 = (uint32_t)(2 * g->m);
+  a.K = (uint32_t)K;
+  a.which = which;
+  a.cap = (uint32_t)std::min<int64_t>(table_slots(std::max<int64_t>(g->max_udeg, 2)),
+                                      std::max<int64_t>(64, std::min<int64_t>(tuning().smem_table_max, 4096)));
+  a.sc = g->scratch;
+  a.out = d_out;
+  a.n_out = d_n_out;
+  UBT_CUDA(cudaMemsetAsync(a.sc, 0, kScratchHeader / 2, s));
+  if (k == 0) return UBT_OK;
+  const int threads = 512;
+  const size_t smem = 2064 * 4 + (size_t)kTopkCap * (8 + 12) + (size_t)a.cap * 3 * 4;
+  UBT_CUDA(cudaFuncSetAttribute(k_vertex_topk, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+  int per_sm = 0;
+  UBT_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_vertex_topk, threads, smem));
+  if (per_sm < 1) return UBT_ERR_INVALID_ARG;
+  const int64_t blocks = std::min<int64_t>((int64_t)g->sm_count * per_sm, k);
+  k_vertex_topk<<<(int)blocks, threads, smem, s>>>(a);
+  UBT_CUDA(cudaGetLastError());
+  return UBT_OK;
 }

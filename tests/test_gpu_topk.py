@@ -84,3 +84,51 @@ def test_topk_invalid(ubt):
             G.topk(K, which)
     E = ubt.Graph(5, np.zeros(0, np.uint32), np.zeros(0, np.uint32), k=np.zeros(0, np.uint32))
     assert E.topk(3, 1).shape[0] == 0
+
+
+def oracle_vertex_topk(n, s, d, k, K, which, vertices):
+    uvw, cls, pb = oracle.enumerate_records(n, s, d, k, 0.5, 3)
+    out = []
+    for v in vertices:
+        sel = np.any(uvw == v, axis=1)
+        u, p = uvw[sel], pb[sel]
+        key = -p if which == 1 else p
+        order = np.lexsort((u[:, 2], u[:, 1], u[:, 0], key))
+        out.append((u[order][:K], p[order][:K]))
+    return out
+
+
+@pytest.mark.parametrize("which", [1, 2])
+def test_vertex_topk_matches_oracle(ubt, which):
+    for name, n, s, d, k in graphs():
+        G = ubt.Graph(n, s, d, k=k, undirected=True)
+        verts = np.unique(np.concatenate([synth.rng(3).integers(0, n, size=60), [0, n - 1]])).astype(np.uint32)
+        deg = np.bincount(np.concatenate([s, d]).astype(np.int64), minlength=n)
+        verts = np.unique(np.concatenate([verts, [int(np.argmax(deg))]])).astype(np.uint32)  # the largest hub too
+        for K in (1, 5, 64):
+            got = G.vertex_topk(verts, K, which)
+            want = oracle_vertex_topk(n, s, d, k, K, which, verts)
+            for v, g_rec, (w_uvw, w_pb) in zip(verts, got, want):
+                assert g_rec.shape[0] == w_uvw.shape[0], (name, v, K)
+                assert np.array_equal(g_rec["p_bal"], w_pb), (name, v, K, which)
+                g_uvw = np.stack([g_rec["u"], g_rec["v"], g_rec["w"]], axis=1).astype(np.uint32)
+                assert np.array_equal(g_uvw, w_uvw), (name, v, K, which)
+        assert G.guard() == 0
+
+
+def test_vertex_topk_chunked_tables(ubt):
+    s, d = mixed_graph(3000, 30000, 21)
+    k = synth.k_uniform(s.size, 22)
+    old = ubt.get_tuning("smem_table_max")
+    try:
+        ubt.set_tuning("smem_table_max", 64)
+        G = ubt.Graph(3000, s, d, k=k, undirected=True)
+        deg = np.bincount(np.concatenate([s, d]).astype(np.int64), minlength=3000)
+        verts = np.argsort(-deg)[:8].astype(np.uint32)   # rows far longer than one table
+        got = G.vertex_topk(verts, 16, 1)
+        want = oracle_vertex_topk(3000, s, d, k, 16, 1, verts)
+        for g_rec, (w_uvw, w_pb) in zip(got, want):
+            assert np.array_equal(g_rec["p_bal"], w_pb)
+            assert np.array_equal(np.stack([g_rec["u"], g_rec["v"], g_rec["w"]], axis=1).astype(np.uint32), w_uvw)
+    finally:
+        ubt.set_tuning("smem_table_max", old)

@@ -746,6 +746,41 @@ def extra_sampling(ubt, args, flush):
     return res
 
 
+DIST_TAUS = [0.55, 0.6, 0.7, 0.8, 0.9, 0.95]
+
+
+def dist_p(name, m, seed):
+    import synth
+    return {"uniform": lambda: synth.rng(seed).random(m),
+            "normal": lambda: synth.p_normal(m, seed),
+            "beta_0.5_0.5": lambda: synth.p_beta(m, 0.5, 0.5, seed),
+            "beta_3_1": lambda: synth.p_beta(m, 3.0, 1.0, seed),
+            "beta_1_3": lambda: synth.p_beta(m, 1.0, 3.0, seed)}[name]()
+
+
+def extra_dist(ubt, args, flush):
+    """Pruned counting time against t for five P+ distributions on the same
+    Chung-Lu n=1e6 structure (the paper's Fig. 7 study on one graph)."""
+    import torch
+    import synth
+    g = make_graph("cl1m")
+    out = torch.empty(2, dtype=torch.int64, device="cuda")
+    steps = max(3, args.steps // 4)
+    res = {"workload": "cl1m structure, P+ redrawn per distribution, one threshold per launch"}
+    for i, name in enumerate(("uniform", "normal", "beta_0.5_0.5", "beta_3_1", "beta_1_3")):
+        k = synth.quantise(dist_p(name, g.m, 300 + i))
+        G = ubt.Graph(g.n, g.src, g.dst, k=k)
+        rows = []
+        for t in DIST_TAUS:
+            ms = _events_ms(lambda: G.count_threshold_([t], out, prune=True), steps, 1, flush)
+            c = out.cpu().numpy()
+            rows.append({"t": t, "ms": ms, "balanced": int(c[0]), "unbalanced": int(c[1])})
+        res[name] = rows
+        del G
+        _release()
+    return res
+
+
 def extra_topk(ubt, args, flush):
     """Top-k most balanced / most unbalanced triangles of the Chung-Lu n=1e6
     graph (Sec. 5's top-k adaptation; the whole search, enumeration and sort)."""
@@ -792,7 +827,8 @@ def extras(ubt, G, g, T, args, flush):
                      ("c5_cl4m_grad", extra_grad),
                      ("aeo_vs_degree_cl1m", lambda u, a, f: extra_aeo(u, a, f, "cl1m")),
                      ("aeo_vs_degree_rmat22", lambda u, a, f: extra_aeo(u, a, f, "rmat22")),
-                     ("sampling_cl1m", extra_sampling), ("topk_cl1m", extra_topk)):
+                     ("sampling_cl1m", extra_sampling), ("topk_cl1m", extra_topk),
+                     ("distributions_cl1m", extra_dist)):
         try:
             with at.tuning_scope(args.lib_defaults):  # each workload starts from the library defaults
                 out[name] = fn(ubt, args, flush)

@@ -223,6 +223,12 @@ def p_beta(m: int, alpha: float, beta: float, seed: int) -> np.ndarray:
     return rng(seed).beta(alpha, beta, size=m)
 
 
+def p_normal(m: int, seed: int, mean: float = 0.5, sd: float = 0.15) -> np.ndarray:
+    """Normal(mean, sd) clipped to [0, 1] (the paper's Sec. 6 distribution
+    study names a Normal without its parameters)."""
+    return np.clip(rng(seed).normal(mean, sd, size=m), 0.0, 1.0)
+
+
 def p_beta_mixture(m: int, seed: int, w: float = 0.5,
                    ab1=(8.0, 2.0), ab2=(2.0, 8.0)) -> np.ndarray:
     """w * Beta(ab1) + (1 - w) * Beta(ab2): sign-confident bimodal P+."""

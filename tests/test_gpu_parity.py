@@ -90,6 +90,36 @@ def test_counts_many_thresholds_bit_exact(ubt, case, which):
     assert G.guard() == 0
 
 
+DISTS = {"uniform": lambda m, sd: synth.rng(sd).random(m),
+         "normal": lambda m, sd: synth.p_normal(m, sd),
+         "beta_0.5_0.5": lambda m, sd: synth.p_beta(m, 0.5, 0.5, sd),
+         "beta_3_1": lambda m, sd: synth.p_beta(m, 3.0, 1.0, sd),
+         "beta_1_3": lambda m, sd: synth.p_beta(m, 1.0, 3.0, sd)}
+
+
+@pytest.mark.parametrize("dist", sorted(DISTS))
+def test_counts_across_p_distributions(ubt, dist):
+    """The five P+ distributions of the Sec. 6 distribution study on one
+    structure: pruned counts bit-exact for both counting visitors."""
+    s, d = mixed_graph(3000, 30000, 41)
+    k = synth.quantise(DISTS[dist](s.size, 42))
+    G = ubt.Graph(3000, s, d, k=k)
+    taus = TAUS + SWEEP32
+    ob, ou = oracle.count_threshold(3000, s, d, k, taus)
+    old = ubt.get_tuning("count_visitor")
+    try:
+        for vis in (0, 1):
+            ubt.set_tuning("count_visitor", vis)
+            gb, gu = G.count_threshold(taus, prune=1)
+            assert np.array_equal(gb, ob) and np.array_equal(gu, ou), (dist, vis)
+            for i, t in enumerate(TAUS):
+                b1, u1 = G.count_threshold([t], prune=1)
+                assert (int(b1[0]), int(u1[0])) == (int(ob[i]), int(ou[i])), (dist, vis, t)
+    finally:
+        ubt.set_tuning("count_visitor", old)
+    assert G.guard() == 0
+
+
 @pytest.mark.parametrize("case", PARITY, ids=[c[0] for c in PARITY])
 def test_enumeration_bit_exact(ubt, case):
     name, n, s, d, k = case

@@ -461,6 +461,12 @@ ubt_status ubt_topk(ubt_graph* g, int64_t K, int32_t which, ubt_tri_rec* d_out, 
  *                     longer lists use a table in global scratch
  *   "block_unit"      pairs a warp takes at a time inside a block task (1..32,
  *                     default 16)
+ *   "long_min"        streamed lists at least this long are streamed by the
+ *                     whole warp, up to four entries per lane (default 64);
+ *                     shorter ones are concatenated across the warp's pairs
+ *   "long_tail"       1 (default): the last < 64 entries of a long list are
+ *                     concatenated with the short lists; 0: the warp streams
+ *                     them itself with idle lanes
  *   "world_words_per_pass"  64-world words per traversal of ubt_sample_worlds
  *                     (1, 2, 4, 8, 16, 32 or 64)
  *   "small_batch"     warp tasks taken per grab of a task counter

@@ -53,11 +53,13 @@ RUN_KNOBS: Dict[str, List[int]] = {
     "warp_threads": [64, 128],
     "blocks_per_sm": [1, 2, 4, 32],
     "world_words_per_pass": [1, 2, 4, 8, 16, 32, 64],
+    "long_min": [32, 48, 64, 96, 128],
+    "long_tail": [1, 0],
 }
 # knobs that matter per query kind (others are left as they are)
 QUERY_KNOBS: Dict[str, List[str]] = {
     "count": ["count_visitor", "hub_threshold", "block_work", "block_unit", "small_batch", "blocks_per_sm",
-              "block_threads", "warp_threads", "smem_table_max", "pull"],
+              "block_threads", "warp_threads", "smem_table_max", "pull", "long_min", "long_tail"],
     "expected": ["hub_threshold", "block_work", "block_unit", "small_batch", "blocks_per_sm", "block_threads",
                  "warp_threads", "smem_table_max", "pull"],
     "worlds": ["world_words_per_pass", "hub_threshold", "block_work", "block_unit", "small_batch",

@@ -96,6 +96,12 @@ extern "C" ubt_status ubt_set_tuning(const char* name, int64_t value) {
   } else if (!strcmp(name, "block_unit")) {
     if (value < 1 || value > 32) return UBT_ERR_INVALID_ARG;
     t.block_unit = value;
+  } else if (!strcmp(name, "long_min")) {
+    if (value < 1 || value > (1 << 20)) return UBT_ERR_INVALID_ARG;
+    t.long_min = value;
+  } else if (!strcmp(name, "long_tail")) {
+    if (value < 0 || value > 1) return UBT_ERR_INVALID_ARG;
+    t.long_tail = value;
   } else if (!strcmp(name, "sort_smem_max")) {
     if (value < 64 || value > 4096 || (value & (value - 1))) return UBT_ERR_INVALID_ARG;
     t.sort_smem_max = value;
@@ -120,6 +126,8 @@ extern "C" ubt_status ubt_get_tuning(const char* name, int64_t* h_value) {
   else if (!strcmp(name, "count_visitor")) *h_value = t.count_visitor;
   else if (!strcmp(name, "block_work")) *h_value = t.block_work;
   else if (!strcmp(name, "block_unit")) *h_value = t.block_unit;
+  else if (!strcmp(name, "long_min")) *h_value = t.long_min;
+  else if (!strcmp(name, "long_tail")) *h_value = t.long_tail;
   else return UBT_ERR_INVALID_ARG;
   return UBT_OK;
 }

@@ -127,6 +127,8 @@ struct Tuning {
   int64_t world_words_per_pass = 8;
   int64_t small_batch = 4;        // warp tasks taken per grab
   int64_t block_unit = 16;        // pairs per warp step in block tasks
+  int64_t long_min = 64;          // streamed lists this long are streamed by the whole warp
+  int64_t long_tail = 1;          // 1: the last < 64 entries of such a list join the short lists
   int64_t sort_smem_max = 4096;
 };
 Tuning& tuning();

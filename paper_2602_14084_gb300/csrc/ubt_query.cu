@@ -681,6 +681,8 @@ TravArgs make_trav_args(const ubt_graph* g, int64_t L, bool with_pos) {
   a.warp_slots = (uint32_t)table_slots(g->hub_threshold);
   a.unit = (uint32_t)std::min<int64_t>(32, std::max<int64_t>(1, T.block_unit));
   a.batch = (uint32_t)std::max<int64_t>(1, T.small_batch);
+  a.long_min = (uint32_t)T.long_min;
+  a.long_tail = (uint32_t)T.long_tail;
   a.L = L;
   return a;
 }

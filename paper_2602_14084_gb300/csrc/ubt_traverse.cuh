@@ -77,6 +77,8 @@ struct TravArgs {
   uint32_t warp_slots;      // per-warp table capacity (power of two)
   uint32_t unit;            // pairs per warp step in block tasks
   uint32_t batch;           // warp tasks taken per grab
+  uint32_t long_min;        // streamed lists at least this long take the whole-warp path
+  uint32_t long_tail;       // 1: a long list's last < 64 entries join the concatenated short lists
   int64_t L;                // prune level, 0 = none
 };
 
@@ -265,8 +267,10 @@ __device__ __forceinline__ void probe_pairs(const TravArgs& a, V& vis, const Tab
     }
   }
   // long lists: one at a time, the whole warp streams it, up to four entries per lane
-  constexpr uint32_t kLong = 48;
-  unsigned longm = __ballot_sync(kFull, dv >= kLong);
+  const uint32_t kLong = a.long_min;
+  const bool tail_short = a.long_tail != 0;
+  const bool was_long = dv >= kLong;
+  unsigned longm = __ballot_sync(kFull, was_long);
   while (longm) {
     const int j = __ffs(longm) - 1;
     longm &= longm - 1;
@@ -281,13 +285,25 @@ __device__ __forceinline__ void probe_pairs(const TravArgs& a, V& vis, const Tab
       long_steps<V, 4, true>(adj, sc, vis, t, lane, uj, vj, vsj, dvj, qj, pj, off);
       off += 128;
     }
-    while (off < dvj) {
-      long_steps<V, 2, false>(adj, sc, vis, t, lane, uj, vj, vsj, dvj, qj, pj, off);
-      off += 64;
+    if (tail_short) {
+      // full half-chunk, then the rest (< 64 entries) is streamed with the short lists
+      if (dvj - off >= 64) {
+        long_steps<V, 2, true>(adj, sc, vis, t, lane, uj, vj, vsj, dvj, qj, pj, off);
+        off += 64;
+      }
+      if (lane == j) {
+        vs += off;
+        dv -= off;
+      }
+    } else {
+      while (off < dvj) {
+        long_steps<V, 2, false>(adj, sc, vis, t, lane, uj, vj, vsj, dvj, qj, pj, off);
+        off += 64;
+      }
     }
   }
   // short lists: concatenated so that every lane probes one entry per half-step
-  const uint32_t ds = dv >= kLong ? 0u : dv;
+  const uint32_t ds = (was_long && !tail_short) ? 0u : dv;
   uint32_t incl = ds;
 #pragma unroll
   for (int d = 1; d < 32; d <<= 1) {

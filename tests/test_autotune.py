@@ -17,7 +17,7 @@ def knobs(monkeypatch):
     state = {"hub_threshold": 128, "block_work": 1 << 14, "pull": 1, "count_visitor": 0, "block_unit": 16,
              "small_batch": 4,
              "blocks_per_sm": 32, "block_threads": 512, "warp_threads": 128, "smem_table_max": 8192,
-             "world_words_per_pass": 8}
+             "world_words_per_pass": 8, "long_min": 64, "long_tail": 1}
 
     def get(name):
         return state[name]
@@ -161,7 +161,8 @@ def test_candidate_values_are_within_the_library_limits():
     lim = {"hub_threshold": (2, 4096), "block_work": (1, 1 << 40), "pull": (0, 1), "count_visitor": (0, 1), "block_unit": (1, 32),
            "small_batch": (1, 1024),
            "block_threads": (64, 512), "warp_threads": (64, 512), "blocks_per_sm": (1, 32),
-           "smem_table_max": (64, 1 << 20), "world_words_per_pass": (1, 64)}
+           "smem_table_max": (64, 1 << 20), "world_words_per_pass": (1, 64), "long_min": (1, 1 << 20),
+           "long_tail": (0, 1)}
     for k, vals in at.ALL_KNOBS.items():
         lo, hi = lim[k]
         assert all(lo <= v <= hi for v in vals), k

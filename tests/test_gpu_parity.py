@@ -315,7 +315,10 @@ def test_giant_lists_use_global_tables(ubt):
 @pytest.mark.parametrize("knobs", [{"hub_threshold": 2}, {"hub_threshold": 200}, {"pull": 0},
                                    {"block_work": 1}, {"block_work": 1 << 30, "hub_threshold": 32},
                                    {"block_unit": 1}, {"block_unit": 32}, {"count_visitor": 1},
-                                   {"small_batch": 1, "warp_threads": 64, "block_threads": 64}, {"warp_threads": 512, "block_threads": 128}])
+                                   {"small_batch": 1, "warp_threads": 64, "block_threads": 64}, {"warp_threads": 512, "block_threads": 128},
+                                   {"long_min": 1}, {"long_min": 1 << 20}, {"long_tail": 1},
+                                   {"long_tail": 1, "long_min": 1}, {"long_tail": 1, "long_min": 64, "count_visitor": 1},
+                                   {"long_tail": 1, "long_min": 130, "pull": 0}])
 def test_task_split_variants(ubt, knobs):
     """Every way of partitioning the pairs and splitting the work into block /
     warp tasks gives the same bit-exact counts and expected-count sums."""
@@ -333,6 +336,9 @@ def test_task_split_variants(ubt, knobs):
         T, S = oracle.expected_fixed(2000, s, d, k)
         _, _, T2, sumP = G.expected_counts(with_exact=True)
         assert T2 == T and S == T * (1 << 47) - 4 * sumP
+        ouvw, ocls, opb = oracle.enumerate_records(2000, s, d, k, 0.75, 3)
+        uvw, cls, pb = sort_records(G.enumerate(0.75, 3))
+        assert np.array_equal(uvw, ouvw) and np.array_equal(cls, ocls) and np.array_equal(pb, opb)
         assert G.guard() == 0
     finally:
         for k, v in old.items():

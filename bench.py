@@ -447,7 +447,8 @@ def profile_driver(ubt, args):
             return ubt.Graph(g.n, g.src, g.dst, p=torch.from_numpy(np.ascontiguousarray(p)).cuda())
         k = g.k if g.k is not None else synth.quantise(g.p)
         return ubt.Graph(g.n, g.src, g.dst, k=k,
-                         undirected=args.only in ("aeo", "edge-sampling", "vertex-sampling"))
+                         undirected=args.only in ("aeo", "edge-sampling", "vertex-sampling"),
+                         edge_index=args.only == "vertex-sampling")
 
     # the knobs the benchmark would use (cached tunings only: no search here)
     G = build()
@@ -714,7 +715,7 @@ def extra_sampling(ubt, args, flush):
     mean absolute percentage error over 10 seeds against the exact counts."""
     import torch
     g = make_graph("cl1m")
-    G = ubt.Graph(g.n, g.src, g.dst, k=g.k, undirected=True)
+    G = ubt.Graph(g.n, g.src, g.dst, k=g.k, undirected=True, edge_index=True)
     tau = [0.8]
     exact_b, exact_u = G.count_threshold(tau)
     K = 10000
@@ -741,6 +742,24 @@ def extra_sampling(ubt, args, flush):
         res[kind] = {"ms_per_estimate_median": float(np.median(times)), "mape_balanced": float(ape_b.mean()),
                      "mape_unbalanced": float(ape_u.mean()),
                      "note": "time includes the D2H of the per-sample counts"}
+    # vertex sampling without the edge index (every neighbour's row streamed)
+    old = ubt.get_tuning("edge_index")
+    ubt.set_tuning("edge_index", 0)
+    try:
+        smp = torch.from_numpy(np.random.default_rng(1000).integers(0, g.n, size=K).astype(np.int32)).cuda()
+        times = []
+        for _ in range(3):
+            torch.cuda.synchronize()
+            a = torch.cuda.Event(enable_timing=True)
+            b = torch.cuda.Event(enable_timing=True)
+            a.record()
+            G.vertex_local_counts(smp, tau)
+            b.record()
+            b.synchronize()
+            times.append(a.elapsed_time(b))
+        res["vertex"]["ms_per_estimate_without_edge_index"] = float(np.median(times))
+    finally:
+        ubt.set_tuning("edge_index", old)
     del G
     _release()
     return res
@@ -802,18 +821,26 @@ def extra_topk(ubt, args, flush):
                 "note": "host wall time of the synchronous call, D2H of the K records included"}
     del G
     _release()
-    # per-vertex top-10 of 100,000 uniformly drawn vertices
-    G = ubt.Graph(g.n, g.src, g.dst, k=g.k, undirected=True)
+    # per-vertex top-10 of 100,000 uniformly drawn vertices, with and without
+    # the edge index
+    G = ubt.Graph(g.n, g.src, g.dst, k=g.k, undirected=True, edge_index=True)
     verts = torch.from_numpy(np.random.default_rng(5).integers(0, g.n, size=100000).astype(np.int32)).cuda()
     G.vertex_topk(verts[:1000], 10, 1)
-    times = []
-    for _ in range(3):
-        torch.cuda.synchronize()
-        t0 = time.perf_counter()
-        G.vertex_topk(verts, 10, 1)
-        times.append(1e3 * (time.perf_counter() - t0))
-    res["vertex_top10_of_100k_vertices"] = {"ms_median": float(np.median(times)),
-                                           "note": "host wall time, D2H of 1M records included"}
+    old = ubt.get_tuning("edge_index")
+    out = {}
+    try:
+        for mode in (old, 0):
+            ubt.set_tuning("edge_index", mode)
+            times = []
+            for _ in range(3):
+                torch.cuda.synchronize()
+                t0 = time.perf_counter()
+                G.vertex_topk(verts, 10, 1)
+                times.append(1e3 * (time.perf_counter() - t0))
+            out["ms_median" if mode else "ms_median_without_edge_index"] = float(np.median(times))
+    finally:
+        ubt.set_tuning("edge_index", old)
+    res["vertex_top10_of_100k_vertices"] = dict(out, note="host wall time, D2H of 1M records included")
     del G
     _release()
     return res

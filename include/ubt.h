@@ -100,11 +100,17 @@ typedef struct {
     int64_t n_graphs;
     /* UBT_OPT_UNDIRECTED: also build the undirected adjacency in Absolute
      * Edge Order (FIXED graphs only), which ubt_count_aeo, ubt_enumerate_aeo,
-     * ubt_edge_local_counts and ubt_vertex_local_counts need. */
+     * ubt_edge_local_counts and ubt_vertex_local_counts need.
+     * UBT_OPT_EDGE_INDEX (with UBT_OPT_UNDIRECTED): also build a hash index
+     * of the edges ({u, w} -> edge value; 12 bytes per slot, the power of two
+     * >= 2m slots).  ubt_vertex_local_counts and ubt_vertex_topk then look a
+     * neighbour pair up in it instead of streaming a neighbour's row when that
+     * row is much longer than the pairs left to check (same results). */
     int64_t flags;
 } ubt_graph_opts;
 
 #define UBT_OPT_UNDIRECTED 1
+#define UBT_OPT_EDGE_INDEX 2
 
 /* Human-readable name of a status code (static string). */
 const char* ubt_status_str(ubt_status s);
@@ -467,6 +473,14 @@ ubt_status ubt_topk(ubt_graph* g, int64_t K, int32_t which, ubt_tri_rec* d_out, 
  *   "long_tail"       1 (default): the last < 64 entries of a long list are
  *                     concatenated with the short lists; 0: the warp streams
  *                     them itself with idle lanes
+ *   "edge_index"      vertex local counts / per-vertex top-k on a graph with
+ *                     UBT_OPT_EDGE_INDEX: 0 never use the index, 1 (default)
+ *                     use it for a neighbour whose row is more than 8 times
+ *                     longer than the pairs left to check, 2 always
+ *   "vertex_split"    ubt_vertex_local_counts on a graph with the edge index:
+ *                     samples whose pruned row is longer (default 1024) are
+ *                     spread over all blocks by a second launch (at most 64
+ *                     per call; the rest are counted by one block each)
  *   "world_words_per_pass"  64-world words per traversal of ubt_sample_worlds
  *                     (1, 2, 4, 8, 16, 32 or 64)
  *   "small_batch"     warp tasks taken per grab of a task counter

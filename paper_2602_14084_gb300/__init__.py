@@ -25,6 +25,7 @@ _HERE = os.path.dirname(os.path.abspath(__file__))
 LIB_PATH = os.path.join(_HERE, "libubt.so")
 FIXED, REAL = 0, 1
 UBT_OPT_UNDIRECTED = 1
+UBT_OPT_EDGE_INDEX = 2
 
 # ubt_tri_rec: {uint32 u, v, w, cls; double p_bal}
 TRI_REC_DTYPE = np.dtype([("u", "<u4"), ("v", "<u4"), ("w", "<u4"), ("cls", "<u4"), ("p_bal", "<f8")])
@@ -146,12 +147,15 @@ class Graph:
     n: number of vertices; src, dst: endpoints (uint32, numpy or torch);
     exactly one of k (uint32 in [0, 65536], P+ = k/65536) or p (float32 in
     [0, 1]).  edge_key: optional Philox key per edge; vertex_offsets: int64
-    [n_graphs + 1] for a batch of disjoint graphs.  Device memory (the
-    workspace) is a torch tensor owned by this object.
+    [n_graphs + 1] for a batch of disjoint graphs.  undirected: also build
+    the rows in Absolute Edge Order (AEO iteration, samplers, per-vertex
+    top-k); edge_index (with undirected): also build the hash index of the
+    edges that the vertex queries use for neighbours with long rows.  Device
+    memory (the workspace) is a torch tensor owned by this object.
     """
 
     def __init__(self, n, src, dst, k=None, p=None, edge_key=None, vertex_offsets=None, device="cuda",
-                 stream=None, undirected=False):
+                 stream=None, undirected=False, edge_index=False):
         torch = _torch()
         if (k is None) == (p is None):
             raise ValueError("give exactly one of k or p")
@@ -170,9 +174,10 @@ class Graph:
         opts = None
         self._keep = []
         self.undirected = bool(undirected)
-        if edge_key is not None or vertex_offsets is not None or undirected:
+        self.edge_index = bool(edge_index)
+        if edge_key is not None or vertex_offsets is not None or undirected or edge_index:
             opts = _GraphOpts()
-            opts.flags = UBT_OPT_UNDIRECTED if undirected else 0
+            opts.flags = (UBT_OPT_UNDIRECTED if undirected else 0) | (UBT_OPT_EDGE_INDEX if edge_index else 0)
             if edge_key is not None:
                 ek = _dev_u32(edge_key, self.device)
                 self._keep.append(ek)

@@ -102,6 +102,12 @@ extern "C" ubt_status ubt_set_tuning(const char* name, int64_t value) {
   } else if (!strcmp(name, "long_tail")) {
     if (value < 0 || value > 1) return UBT_ERR_INVALID_ARG;
     t.long_tail = value;
+  } else if (!strcmp(name, "vertex_split")) {
+    if (value < 1 || value > (1ll << 32)) return UBT_ERR_INVALID_ARG;
+    t.vertex_split = value;
+  } else if (!strcmp(name, "edge_index")) {
+    if (value < 0 || value > 2) return UBT_ERR_INVALID_ARG;
+    t.edge_index = value;
   } else if (!strcmp(name, "sort_smem_max")) {
     if (value < 64 || value > 4096 || (value & (value - 1))) return UBT_ERR_INVALID_ARG;
     t.sort_smem_max = value;
@@ -128,6 +134,8 @@ extern "C" ubt_status ubt_get_tuning(const char* name, int64_t* h_value) {
   else if (!strcmp(name, "block_unit")) *h_value = t.block_unit;
   else if (!strcmp(name, "long_min")) *h_value = t.long_min;
   else if (!strcmp(name, "long_tail")) *h_value = t.long_tail;
+  else if (!strcmp(name, "edge_index")) *h_value = t.edge_index;
+  else if (!strcmp(name, "vertex_split")) *h_value = t.vertex_split;
   else return UBT_ERR_INVALID_ARG;
   return UBT_OK;
 }

@@ -597,6 +597,32 @@ __global__ void k_umirror(int64_t n, const uint32_t* __restrict__ uptr, const ui
       umir[p] = epos[2 * (size_t)ueid[p] + ((uint32_t)x > adj_col(uadj[p]) ? 0 : 1)];
 }
 
+// Edge index: every edge once, from the row of its smaller endpoint.  The
+// table has at least twice as many slots as edges, so every insert finds a
+// free slot; the loop bound is a self-check.
+__global__ void k_edge_index(int64_t n, const uint32_t* __restrict__ uptr, const uint64_t* __restrict__ uadj,
+                             unsigned long long* __restrict__ ehkey, uint32_t* __restrict__ ehval, uint64_t slots,
+                             int shift, unsigned long long* err) {
+  const int lane = threadIdx.x & 31;
+  const int64_t warps = (int64_t)gridDim.x * (blockDim.x >> 5);
+  for (int64_t x = blockIdx.x * (int64_t)(blockDim.x >> 5) + (threadIdx.x >> 5); x < n; x += warps)
+    for (uint32_t p = uptr[x] + lane; p < uptr[x + 1]; p += 32) {
+      const uint64_t e = uadj[p];
+      if ((uint32_t)x > adj_col(e)) continue;
+      const uint64_t key = edge_index_key((uint32_t)x, adj_col(e));
+      uint64_t h = edge_index_home(key, shift);
+      uint64_t it = 0;
+      for (; it < slots; it++) {
+        if (atomicCAS(&ehkey[h], (unsigned long long)kEdgeIndexEmpty, (unsigned long long)key) == kEdgeIndexEmpty) {
+          ehval[h] = adj_valbits(e);
+          break;
+        }
+        h = (h + 1) & (slots - 1);
+      }
+      if (it == slots) report(err, p, -UBT_ERR_INVALID_ARG);
+    }
+}
+
 // AEO traversal: edge x-y is handled by x, the endpoint with the longer list
 // (ties: the larger id), which holds the hash table; y's list is streamed.
 __device__ inline bool aeo_owns(uint32_t x, uint32_t y, uint32_t dx, uint32_t dy) {
@@ -689,6 +715,9 @@ struct BuildLayout {
   uint64_t* apairs;
   uint32_t* alist;
   unsigned long long* awork;
+  unsigned long long* ehkey;   // edge index (optional)
+  uint32_t* ehval;
+  int64_t eh_slots;
   unsigned long long* gacc;
   unsigned long long* bacc;
   uint32_t* gtab;
@@ -744,6 +773,10 @@ BuildLayout layout(void* ws, size_t cap, int64_t n, int64_t m, const ubt_graph_o
   L.apairs = und ? c.take<uint64_t>(std::max<int64_t>(m, 1)) : nullptr;
   L.alist = und ? c.take<uint32_t>(n1) : nullptr;
   L.awork = und ? c.take<unsigned long long>(n1) : nullptr;
+  const bool eidx = und && (opts->flags & UBT_OPT_EDGE_INDEX);
+  L.eh_slots = eidx ? pow2_at_least(std::max<int64_t>(2 * m, 64)) : 0;
+  L.ehkey = eidx ? c.take<unsigned long long>(L.eh_slots) : nullptr;
+  L.ehval = eidx ? c.take<uint32_t>(L.eh_slots) : nullptr;
   L.gacc = c.take<unsigned long long>(std::max<int64_t>(m, 1));
   // per graph: T, sum_lo, sum_hi (expected counts) of a batch
   L.bacc = c.take<unsigned long long>(3 * std::max<int64_t>(ng, 1));
@@ -817,7 +850,8 @@ extern "C" ubt_status ubt_create_graph(int64_t n, int64_t m, const uint32_t* d_s
   }
   if (m > 0 && (!d_src || !d_dst)) return UBT_ERR_INVALID_ARG;
   const bool und = opts && (opts->flags & UBT_OPT_UNDIRECTED);
-  if (opts && (opts->flags & ~(int64_t)UBT_OPT_UNDIRECTED)) return UBT_ERR_INVALID_ARG;
+  if (opts && (opts->flags & ~(int64_t)(UBT_OPT_UNDIRECTED | UBT_OPT_EDGE_INDEX))) return UBT_ERR_INVALID_ARG;
+  if (opts && (opts->flags & UBT_OPT_EDGE_INDEX) && !und) return UBT_ERR_INVALID_ARG;
   if (und && flags != UBT_GRAPH_FIXED) return UBT_ERR_UNSUPPORTED;
   if (!d_workspace || ((uintptr_t)d_workspace & 255)) return UBT_ERR_INVALID_ARG;
   const bool batch = opts && opts->d_vertex_offsets;
@@ -974,6 +1008,13 @@ extern "C" ubt_status ubt_create_graph(int64_t n, int64_t m, const uint32_t* d_s
     }
     k_uepos<<<grid_w, thr, 0, s>>>(n, L.uptr, L.uadj, L.ueid, L.uepos);
     k_umirror<<<grid_w, thr, 0, s>>>(n, L.uptr, L.uadj, L.ueid, L.uepos, L.umir);
+    if (L.ehkey) {
+      UBT_CUDA(cudaMemsetAsync(L.ehkey, 0xFF, sizeof(unsigned long long) * (size_t)L.eh_slots, s));
+      int lg = 0;
+      while ((1ll << lg) < L.eh_slots) lg++;
+      k_edge_index<<<grid_w, thr, 0, s>>>(n, L.uptr, L.uadj, L.ehkey, L.ehval, (uint64_t)L.eh_slots, 64 - lg,
+                                          &L.scratch->err);
+    }
     UBT_CUDA(cudaMemsetAsync(L.fill, 0, sizeof(uint32_t) * (n + 1), s));
     k_apair_count<<<grid_w, thr, 0, s>>>(n, L.uptr, L.uadj, L.fill);
     UBT_CUDA(exclusive_scan_u32(L.fill, L.apair_ptr, n, L.scan_tmp, s));
@@ -1039,6 +1080,14 @@ extern "C" ubt_status ubt_create_graph(int64_t n, int64_t m, const uint32_t* d_s
   g->n_aowners = n_aowners;
   g->n_ablock = n_ablock;
   g->max_udeg = max_udeg;
+  g->ehkey = (uint64_t*)L.ehkey;
+  g->ehval = L.ehval;
+  g->eh_slots = L.eh_slots;
+  {
+    int lg = 0;
+    while ((1ll << lg) < L.eh_slots) lg++;
+    g->eh_shift = 64 - lg;
+  }
   g->gacc = L.gacc;
   g->bacc = L.bacc;
   g->gtab = L.gtab;

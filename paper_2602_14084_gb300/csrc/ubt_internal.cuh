@@ -53,6 +53,17 @@ __host__ __device__ inline uint64_t adj_pack(uint32_t col, uint32_t valbits) {
   return ((uint64_t)valbits << 32) | col;
 }
 
+// Edge index (UBT_OPT_EDGE_INDEX): open addressing with linear probing over
+// a power-of-two number of slots (at least 2m, so at most half are used);
+// key min(u, w) << 32 | max(u, w), empty slots hold ~0.
+constexpr uint64_t kEdgeIndexEmpty = ~0ull;
+__host__ __device__ inline uint64_t edge_index_key(uint32_t a, uint32_t b) {
+  return a < b ? ((uint64_t)a << 32) | b : ((uint64_t)b << 32) | a;
+}
+__host__ __device__ inline uint64_t edge_index_home(uint64_t key, int shift) {
+  return (key * 0x9E3779B97F4A7C15ull) >> shift;  // Fibonacci hashing: the top bits
+}
+
 // Query scratch carved from the graph workspace (one per graph).
 struct Scratch {
   unsigned long long task[4];       // next giant / hub / small task, spare
@@ -98,6 +109,10 @@ struct ubt_graph {
   uint64_t* apairs = nullptr;       // m: streamed endpoint | position of the edge in x's row << 32
   uint32_t* alist = nullptr;        // owners, by decreasing streamed work
   int64_t n_aowners = 0, n_ablock = 0, max_udeg = 0;  // owners; the first n_ablock are block tasks
+  uint64_t* ehkey = nullptr;        // edge index (UBT_OPT_EDGE_INDEX; else null): eh_slots keys
+  uint32_t* ehval = nullptr;        // eh_slots edge values (valbits)
+  int64_t eh_slots = 0;             // power of two >= max(2m, 64)
+  int eh_shift = 64;                // 64 - log2(eh_slots)
   unsigned long long* gacc = nullptr;   // m: backward accumulators
   unsigned long long* bacc = nullptr;   // batch accumulators
   uint32_t* gtab = nullptr;         // global hash tables for very long lists
@@ -129,6 +144,8 @@ struct Tuning {
   int64_t block_unit = 16;        // pairs per warp step in block tasks
   int64_t long_min = 64;          // streamed lists this long are streamed by the whole warp
   int64_t long_tail = 1;          // 1: the last < 64 entries of such a list join the short lists
+  int64_t edge_index = 1;         // vertex queries: 0 never look pairs up in the edge index, 1 when cheaper, 2 always
+  int64_t vertex_split = 1024;    // vertex samples with longer pruned rows are spread over all blocks (edge index)
   int64_t sort_smem_max = 4096;
 };
 Tuning& tuning();

@@ -41,9 +41,108 @@ struct LocalP {
   int perm[kLocalTau];          // caller index of the i-th smallest t
 };
 
+// Edge index lookup (UBT_OPT_EDGE_INDEX): the value of edge a-b, if present.
+// Probes end at the key or an empty slot (at most half the slots are used);
+// the bound is a self-check.
+struct EdgeIndex {
+  const uint64_t* key;
+  const uint32_t* val;
+  uint64_t mask;   // slots - 1
+  int shift;
+  int mode;        // 0 unused, 1 where cheaper than streaming, 2 always
+};
+
+__device__ __forceinline__ bool edge_index_find(const EdgeIndex& ix, uint32_t a, uint32_t b, uint32_t& val,
+                                                Scratch* sc) {
+  const uint64_t k = edge_index_key(a, b);
+  uint64_t h = edge_index_home(k, ix.shift);
+  for (uint64_t it = 0; it <= ix.mask; it++) {
+    const uint64_t x = ix.key[h];
+    if (x == k) {
+      val = ix.val[h];
+      return true;
+    }
+    if (x == kEdgeIndexEmpty) return false;
+    h = (h + 1) & ix.mask;
+  }
+  guard_fail(sc, kGuardFind, a);
+  return false;
+}
+
+// Vertex queries: the triangles v-a-b with b among `cand` positions of v's
+// row are found either by streaming a's row (`len` entries) through v's
+// table or by looking every candidate pair a-b up in the edge index; a
+// lookup costs a few dependent random reads, a streamed entry one coalesced
+// read and a shared-memory probe.
+constexpr uint32_t kIndexCost = 8;
+__device__ __forceinline__ bool use_index(const EdgeIndex& ix, uint32_t cand, uint32_t len) {
+  return ix.mode == 2 || (ix.mode == 1 && (uint64_t)cand * kIndexCost < len);
+}
+
+// Triangles v-a-w with w after a in v's row (positions pa + 1 .. rend), from
+// the edge index alone (rows longer than one shared-memory table): the
+// smaller of
+//   every b after a in v's row, looked up as a-b, and
+//   every w among the first `len` entries of a's row (from s0), looked up
+//   as v-w and kept when w comes after a in v's row -- the rows are in
+//   Absolute Edge Order, so that is |q_vw| < |q_va|, or equal and w > a --
+//   and lies in v's Lemma 2 prefix (|q_vw| 2^30 >= L, L = 0: all).
+// found(P, w) receives every triangle.
+template <class F>
+__device__ __forceinline__ void index_pairs(const EdgeIndex& ix, const uint64_t* __restrict__ uadj, uint32_t v,
+                                            uint32_t av, uint32_t qa, uint32_t pa, uint32_t rend, uint32_t s0,
+                                            uint32_t len, int64_t L, int lane, Scratch* sc, F&& found) {
+  if (rend - (pa + 1) <= len) {
+    for (uint32_t b0 = pa + 1; b0 < rend; b0 += 32) {
+      const uint32_t pos = b0 + lane;
+      const bool act = pos < rend;
+      const uint64_t eb = act ? uadj[pos] : 0ull;
+      uint32_t qab = 0;
+      if (act && edge_index_find(ix, av, adj_col(eb), qab, sc))
+        found((long long)((int32_t)qa * (int32_t)adj_valbits(eb)) * (long long)(int32_t)qab, adj_col(eb));
+    }
+  } else {
+    const int64_t aq = qabs(qa);
+    for (uint32_t b0 = s0; b0 < s0 + len; b0 += 32) {
+      const uint32_t pos = b0 + lane;
+      const bool act = pos < s0 + len;
+      const uint64_t ew = act ? uadj[pos] : 0ull;
+      const uint32_t w = adj_col(ew);
+      uint32_t qvw = 0;
+      if (act && w != v && edge_index_find(ix, v, w, qvw, sc)) {
+        const int64_t wq = qabs(qvw);
+        if ((wq < aq || (wq == aq && w > av)) && (L == 0 || wq * (1ll << 30) >= L))
+          found((long long)((int32_t)qa * (int32_t)qvw) * (long long)(int32_t)adj_valbits(ew), w);
+      }
+    }
+  }
+}
+
+EdgeIndex edge_index_of(const ubt_graph* g) {
+  EdgeIndex ix;
+  ix.key = g->ehkey;
+  ix.val = g->ehval;
+  ix.mask = g->eh_slots ? (uint64_t)g->eh_slots - 1 : 0;
+  ix.shift = g->eh_shift;
+  ix.mode = g->ehkey ? (int)tuning().edge_index : 0;
+  return ix;
+}
+
+// Vertex samples whose pruned row is longer than `split` (with the edge
+// index) are not counted by one block: the sampling kernel queues them (at
+// most kLongCap per query; more are counted in place) and a second launch
+// spreads their neighbours, kPart at a time, over all blocks.  Queue in the
+// query scratch: [0] queued, [1] next part, [2 + i] entry i = row length << 32
+// | sample index.
+constexpr int kLongCap = 64;
+constexpr uint32_t kPart = 256;
+
 struct LocalArgs {
   const uint32_t* uptr;
   const uint64_t* uadj;
+  EdgeIndex ix;
+  uint32_t split;               // pruned rows longer than this are split across blocks
+  unsigned long long* lq;       // the queue (query scratch)
   const uint32_t* uepos;        // 2m: positions of every edge in its endpoints' rows
   const uint32_t* items;        // sampled edges (input index) or vertices
   uint32_t n_items;
@@ -62,6 +161,27 @@ __device__ __forceinline__ int level_of(const long long* S, int half, long long 
   for (int b = half; b > 0; b >>= 1)
     if (S[r + b - 1] < P) r += b;
   return r;
+}
+
+// Neighbours j0, j0 + step, ... < j1 of vertex x (row at rs, Lemma 2 prefix
+// tlen, largest |q| qmax), every pair from the edge index, each triangle
+// once (the other vertex after the neighbour in x's row) and binned.
+__device__ __forceinline__ void index_neighbours(const LocalArgs& a, const LocalP& p, const long long* S,
+                                                 unsigned long long* bins, uint32_t x, uint32_t rs, uint32_t tlen,
+                                                 int64_t qmax, uint32_t j0, uint32_t j1, uint32_t step, int lane) {
+  for (uint32_t j = j0; j < j1; j += step) {
+    const uint64_t ea = a.uadj[rs + j];
+    const uint32_t av = adj_col(ea), qp = adj_valbits(ea);
+    if (av >= a.n) {
+      if (lane == 0) guard_fail(a.sc, kGuardVertex, av);
+      continue;
+    }
+    const uint32_t s0 = a.uptr[av];
+    uint32_t len = a.uptr[av + 1] - s0;
+    if (a.L > 0) len = prune_prefix(a.uadj + s0, len, qabs(qp) * qmax, a.L);
+    index_pairs(a.ix, a.uadj, x, av, qp, rs + j, rs + tlen, s0, len, a.L, lane, a.sc,
+                [&](long long P, uint32_t) { atomicAdd(&bins[level_of(S, p.half, P)], 1ull); });
+  }
 }
 
 __global__ void __launch_bounds__(512, 2) k_local(LocalArgs a, LocalP p) {
@@ -122,6 +242,24 @@ __global__ void __launch_bounds__(512, 2) k_local(LocalArgs a, LocalP p) {
     }
     const uint32_t rs = a.uptr[x];
     const uint32_t chunk = a.cap / 4;
+    if (ok && a.vertex_mode && a.ix.mode != 0 && (tlen > chunk || tlen > a.split)) {
+      // a long row: no table, every pair from the edge index -- counted by the
+      // split launch when the queue has room (its counts here stay 0), else here
+      if (tid == 0) {
+        uint32_t queued = 0;
+        if (tlen > a.split) {
+          const unsigned long long slot = atomicAdd(&a.lq[0], 1ull);
+          if (slot < (unsigned long long)kLongCap) {
+            a.lq[2 + slot] = ((unsigned long long)tlen << 32) | item;
+            queued = 1;
+          }
+        }
+        s_misc[1] = queued;
+      }
+      __syncthreads();
+      if (!s_misc[1]) index_neighbours(a, p, S, bins, x, rs, tlen, qmax, wid, tlen ? tlen - 1 : 0, nw, lane);
+      ok = false;  // skip the table chunks
+    }
     for (uint32_t c0 = 0; ok && c0 < tlen; c0 += chunk) {
       const uint32_t c1 = min(tlen, c0 + chunk);
       const uint32_t slots = slots_for(c1 - c0);
@@ -154,6 +292,23 @@ __global__ void __launch_bounds__(512, 2) k_local(LocalArgs a, LocalP p) {
           uint32_t len = a.uptr[av + 1] - s0;
           if (a.L > 0) len = prune_prefix(a.uadj + s0, len, qabs(qp) * qmax, a.L);
           s1 = s0 + len;
+          // the same triangles from v's side: b after a in this chunk of v's
+          // row, each pair a-b looked up in the edge index
+          const uint32_t b_lo = max(pp + 1, rs + c0), b_hi = rs + c1;
+          if (use_index(a.ix, b_hi - b_lo, len)) {
+            for (uint32_t b0 = b_lo; b0 < b_hi; b0 += 32) {
+              const uint32_t pos = b0 + lane;
+              const bool act = pos < b_hi;
+              const uint64_t eb = act ? a.uadj[pos] : 0ull;
+              uint32_t qab = 0;
+              const bool hit = act && edge_index_find(a.ix, av, adj_col(eb), qab, a.sc);
+              if (hit) {
+                const long long P = (long long)((int32_t)qp * (int32_t)adj_valbits(eb)) * (long long)(int32_t)qab;
+                atomicAdd(&bins[level_of(S, p.half, P)], 1ull);
+              }
+            }
+            continue;
+          }
         }
         for (uint32_t b0 = s0; b0 < s1; b0 += 32) {
           const uint32_t pos = b0 + lane;
@@ -180,6 +335,55 @@ __global__ void __launch_bounds__(512, 2) k_local(LocalArgs a, LocalP p) {
       for (int r = p.nt + i + 1; r <= 2 * p.nt; r++) u += bins[r];
       a.bal[(size_t)item * p.nt + p.perm[i]] = b;
       a.unbal[(size_t)item * p.nt + p.perm[i]] = u;
+    }
+    __syncthreads();
+  }
+}
+
+// The split launch: the queued vertex samples' neighbours, kPart per block
+// task; each task adds its per-threshold counts to the sample's outputs
+// (zero after the sampling kernel).
+__global__ void __launch_bounds__(512, 2) k_local_split(LocalArgs a, LocalP p) {
+  __shared__ long long S[256];
+  __shared__ unsigned long long bins[144];
+  __shared__ uint32_t pref[kLongCap + 1];
+  __shared__ uint32_t s_part;
+  const int tid = threadIdx.x, lane = tid & 31, wid = tid >> 5, nw = blockDim.x >> 5;
+  for (int i = tid; i < 256; i += blockDim.x) S[i] = i < 2 * p.nt ? p.S[i] : INT64_MAX;
+  const uint32_t nq = (uint32_t)min(a.lq[0], (unsigned long long)kLongCap);
+  if (tid == 0) {
+    uint32_t acc = 0;
+    for (uint32_t i = 0; i < nq; i++) {
+      pref[i] = acc;
+      const uint32_t tlen = (uint32_t)(a.lq[2 + i] >> 32);
+      acc += (tlen - 1 + kPart - 1) / kPart;  // neighbours 0 .. tlen - 2 have a later one
+    }
+    pref[nq] = acc;
+  }
+  __syncthreads();
+  const uint32_t total = pref[nq];
+  while (true) {
+    if (tid == 0) s_part = (uint32_t)atomicAdd(&a.lq[1], 1ull);
+    for (int i = tid; i <= 2 * p.nt; i += blockDim.x) bins[i] = 0;
+    __syncthreads();
+    const uint32_t part = s_part;
+    if (part >= total) break;
+    uint32_t e = 0;
+    while (e + 1 < nq && pref[e + 1] <= part) e++;
+    const unsigned long long ent = a.lq[2 + e];
+    const uint32_t item = (uint32_t)ent, tlen = (uint32_t)(ent >> 32);
+    const uint32_t x = a.items[item], rs = a.uptr[x];
+    const int64_t qmax = a.L > 0 ? qabs(adj_valbits(a.uadj[rs])) : 0;
+    const uint32_t j0 = (part - pref[e]) * kPart, j1 = min(j0 + kPart, tlen - 1);
+    index_neighbours(a, p, S, bins, x, rs, tlen, qmax, j0 + wid, j1, nw, lane);
+    __syncthreads();
+    if (tid < p.nt) {
+      const int i = tid;
+      unsigned long long b = 0, u = 0;
+      for (int r = 0; r <= p.nt - 1 - i; r++) b += bins[r];
+      for (int r = p.nt + i + 1; r <= 2 * p.nt; r++) u += bins[r];
+      if (b) atomicAdd((unsigned long long*)&a.bal[(size_t)item * p.nt + p.perm[i]], b);
+      if (u) atomicAdd((unsigned long long*)&a.unbal[(size_t)item * p.nt + p.perm[i]], u);
     }
     __syncthreads();
   }
@@ -235,6 +439,9 @@ ubt_status local_counts(ubt_graph* g, const uint32_t* d_items, int64_t k, int ve
   LocalArgs a;
   a.uptr = g->uptr;
   a.uadj = g->uadj;
+  a.ix = edge_index_of(g);
+  a.split = (uint32_t)std::min<int64_t>(T.vertex_split, 0xFFFFFFFFll);
+  a.lq = &g->scratch->hist[0];
   a.uepos = g->uepos;
   a.items = d_items;
   a.n_items = (uint32_t)k;
@@ -249,6 +456,7 @@ ubt_status local_counts(ubt_graph* g, const uint32_t* d_items, int64_t k, int ve
   a.bal = d_bal;
   a.unbal = d_unbal;
   UBT_CUDA(cudaMemsetAsync(a.sc, 0, kScratchHeader / 2, s));
+  UBT_CUDA(cudaMemsetAsync(a.lq, 0, 2 * sizeof(unsigned long long), s));
   if (k > 0) {
     const int threads = 512;
     const size_t smem = 256 * 8 + 144 * 8 + (size_t)a.cap * 3 * 4;
@@ -259,6 +467,10 @@ ubt_status local_counts(ubt_graph* g, const uint32_t* d_items, int64_t k, int ve
     const int64_t blocks = std::min<int64_t>((int64_t)g->sm_count * per_sm, k);
     k_local<<<(int)blocks, threads, smem, s>>>(a, p);
     UBT_CUDA(cudaGetLastError());
+    if (vertex_mode && a.ix.mode != 0) {
+      k_local_split<<<(int)(g->sm_count * 2), threads, 0, s>>>(a, p);
+      UBT_CUDA(cudaGetLastError());
+    }
   }
   if (d_est) {
     const double scale = (vertex_mode ? (double)g->n : (double)g->m) / 3.0;
@@ -286,6 +498,7 @@ constexpr int kTopkMax = 256;    // largest K
 struct TopkArgs {
   const uint32_t* uptr;
   const uint64_t* uadj;
+  EdgeIndex ix;
   const uint32_t* items;
   uint32_t n_items, n, m2, K;
   int which;
@@ -333,15 +546,18 @@ __global__ void __launch_bounds__(512, 1) k_vertex_topk(TopkArgs a) {
         s_misc[2] = below;   // cursor of the threshold slice
       }
       __syncthreads();
-      for (uint32_t c0 = 0; c0 < deg; c0 += chunk) {
-        const uint32_t c1 = min(deg, c0 + chunk);
+      const bool index_only = a.ix.mode != 0 && deg > chunk;  // a row longer than one table
+      for (uint32_t c0 = 0; c0 < deg; c0 = index_only ? deg : c0 + chunk) {  // index_only: one pass
+        const uint32_t c1 = index_only ? deg : min(deg, c0 + chunk);
         const uint32_t slots = slots_for(c1 - c0);
-        const Table t = make_table(tab, a.cap, slots);
-        for (uint32_t i = tid; i < slots; i += blockDim.x) t.key[i] = kEmpty;
-        __syncthreads();
-        for (uint32_t i = c0 + tid; i < c1; i += blockDim.x) {
-          const uint64_t e = a.uadj[rs + i];
-          table_insert(t, adj_col(e), adj_valbits(e), rs + i, a.sc);
+        const Table t = make_table(tab, a.cap, index_only ? 32u : slots);
+        if (!index_only) {
+          for (uint32_t i = tid; i < slots; i += blockDim.x) t.key[i] = kEmpty;
+          __syncthreads();
+          for (uint32_t i = c0 + tid; i < c1; i += blockDim.x) {
+            const uint64_t e = a.uadj[rs + i];
+            table_insert(t, adj_col(e), adj_valbits(e), rs + i, a.sc);
+          }
         }
         __syncthreads();
         for (uint32_t j = wid; j < deg; j += nw) {
@@ -354,15 +570,8 @@ __global__ void __launch_bounds__(512, 1) k_vertex_topk(TopkArgs a) {
             if (lane == 0) guard_fail(a.sc, kGuardVertex, av);
             continue;
           }
-          const uint32_t s0 = a.uptr[av], s1 = a.uptr[av + 1];
-          for (uint32_t b0 = s0; b0 < s1; b0 += 32) {
-            const uint32_t pos = b0 + lane;
-            const bool act = pos < s1;
-            const uint64_t e = act ? a.uadj[pos] : 0ull;
-            uint32_t qt = 0, pt = 0;
-            const bool hit = act && table_find<true>(t, adj_col(e), qt, pt, a.sc) && pt > pa;
-            if (!hit) continue;
-            const long long P = (long long)((int32_t)qa * (int32_t)qt) * (long long)(int32_t)adj_valbits(e);
+          // triangle v-av-w with P found: histogram (pass 0) or candidate (pass 1)
+          auto found = [&](long long P, uint32_t w) {
             const uint64_t r = topk_rank(P, a.which);
             const uint32_t sl = (uint32_t)(r >> 35);
             if (pass == 0) {
@@ -370,7 +579,7 @@ __global__ void __launch_bounds__(512, 1) k_vertex_topk(TopkArgs a) {
             } else if (sl <= sstar) {
               const uint32_t at = sl < sstar ? atomicAdd(&s_misc[1], 1u) : atomicAdd(&s_misc[2], 1u);
               if (at < kTopkCap) {
-                uint32_t x0 = v, x1 = av, x2 = adj_col(e), tt;
+                uint32_t x0 = v, x1 = av, x2 = w, tt;
                 if (x0 > x1) { tt = x0; x0 = x1; x1 = tt; }
                 if (x1 > x2) { tt = x1; x1 = x2; x2 = tt; }
                 if (x0 > x1) { tt = x0; x0 = x1; x1 = tt; }
@@ -380,6 +589,32 @@ __global__ void __launch_bounds__(512, 1) k_vertex_topk(TopkArgs a) {
                 ctri[3 * at + 2] = x2;
               }
             }
+          };
+          const uint32_t s0 = a.uptr[av], s1 = a.uptr[av + 1];
+          if (index_only) {
+            index_pairs(a.ix, a.uadj, v, av, qa, pa, rs + deg, s0, s1 - s0, 0, lane, a.sc, found);
+            continue;
+          }
+          const uint32_t b_lo = max(pa + 1, rs + c0), b_hi = rs + c1;
+          if (use_index(a.ix, b_hi - b_lo, s1 - s0)) {
+            // from v's side: b after a in this chunk, each pair looked up
+            for (uint32_t b0 = b_lo; b0 < b_hi; b0 += 32) {
+              const uint32_t pos = b0 + lane;
+              const bool act = pos < b_hi;
+              const uint64_t eb = act ? a.uadj[pos] : 0ull;
+              uint32_t qab = 0;
+              if (act && edge_index_find(a.ix, av, adj_col(eb), qab, a.sc))
+                found((long long)((int32_t)qa * (int32_t)adj_valbits(eb)) * (long long)(int32_t)qab, adj_col(eb));
+            }
+            continue;
+          }
+          for (uint32_t b0 = s0; b0 < s1; b0 += 32) {
+            const uint32_t pos = b0 + lane;
+            const bool act = pos < s1;
+            const uint64_t e = act ? a.uadj[pos] : 0ull;
+            uint32_t qt = 0, pt = 0;
+            const bool hit = act && table_find<true>(t, adj_col(e), qt, pt, a.sc) && pt > pa;
+            if (hit) found((long long)((int32_t)qa * (int32_t)qt) * (long long)(int32_t)adj_valbits(e), adj_col(e));
           }
         }
         __syncthreads();
@@ -468,6 +703,7 @@ extern "C" ubt_status ubt_vertex_topk(ubt_graph* g, const uint32_t* d_vertices, 
   TopkArgs a;
   a.uptr = g->uptr;
   a.uadj = g->uadj;
+  a.ix = edge_index_of(g);
   a.items = d_vertices;
   a.n_items = (uint32_t)k;
   a.n = (uint32_t)g->n;

@@ -199,3 +199,73 @@ def test_undirected_rows_sorted_in_global_memory(ubt):
         ob, ou = oracle.count_threshold(3000, s, d, k, TAUS)
         gb, gu = G.count_aeo(TAUS)
         assert np.array_equal(gb, ob) and np.array_equal(gu, ou)
+
+
+@pytest.mark.parametrize("mode", [0, 1, 2])
+@pytest.mark.parametrize("case", CASES, ids=[c[0] for c in CASES])
+def test_vertex_local_counts_with_edge_index(ubt, case, mode):
+    """Vertex local counts on a graph with the edge index: neighbour pairs
+    looked up in it (mode 1 where cheaper, mode 2 always, mode 0 never) give
+    the oracle's counts bit for bit; so do edge local counts and the AEO
+    count on the same graph."""
+    name, n, s, d, k = case
+    taus = [0.5, 0.6, 0.8, 0.95]
+    eb, eu, vb, vu = oracle.local_counts(n, s, d, k, taus)
+    with with_knobs(ubt, {"edge_index": mode}):
+        G = ubt.Graph(n, s, d, k=k, undirected=True, edge_index=True)
+        vs = synth.rng(17).integers(0, n, size=500).astype(np.uint32)
+        gb, gu, _ = G.vertex_local_counts(vs, taus)
+        assert np.array_equal(gb, vb[vs]) and np.array_equal(gu, vu[vs]), (name, mode)
+        gb, gu, _ = G.vertex_local_counts(np.arange(n, dtype=np.uint32), taus)
+        assert np.array_equal(gb, vb) and np.array_equal(gu, vu), (name, mode)
+        es = synth.rng(18).integers(0, s.size, size=300).astype(np.uint32)
+        gb, gu, _ = G.edge_local_counts(es, taus)
+        assert np.array_equal(gb, eb[es]) and np.array_equal(gu, eu[es]), (name, mode)
+        ob, ou = oracle.count_threshold(n, s, d, k, taus)
+        gb, gu = G.count_aeo(taus)
+        assert np.array_equal(gb, ob) and np.array_equal(gu, ou)
+        assert G.guard() == 0
+
+
+def test_edge_index_chunked_tables_and_options(ubt):
+    s, d = mixed_graph(3000, 30000, 21)
+    k = synth.k_uniform(s.size, 22)
+    taus = [0.5, 0.7, 0.9]
+    _, _, vb, vu = oracle.local_counts(3000, s, d, k, taus)
+    for mode in (1, 2):
+        with with_knobs(ubt, {"smem_table_max": 64, "edge_index": mode}):
+            G = ubt.Graph(3000, s, d, k=k, undirected=True, edge_index=True)
+            gb, gu, _ = G.vertex_local_counts(np.arange(3000, dtype=np.uint32), taus)
+            assert np.array_equal(gb, vb) and np.array_equal(gu, vu), mode
+            assert G.guard() == 0
+    # the index needs the undirected rows
+    with pytest.raises(ubt.UbtError):
+        ubt.Graph(3000, s, d, k=k, edge_index=True)
+    # empty graph
+    z = np.zeros(0, np.uint32)
+    E = ubt.Graph(10, z, z, k=z, undirected=True, edge_index=True)
+    gb, gu, _ = E.vertex_local_counts(np.arange(10, dtype=np.uint32), [0.6])
+    assert np.all(gb == 0) and np.all(gu == 0)
+
+
+@pytest.mark.parametrize("split", [1, 8, 200])
+@pytest.mark.parametrize("case", CASES, ids=[c[0] for c in CASES])
+def test_vertex_samples_split_across_blocks(ubt, case, split):
+    """Vertex samples with long rows are queued (64 per call) and their
+    neighbours spread over all blocks by a second launch; the rest of the
+    long ones are counted in place.  Repeats of one long vertex each get its
+    full counts."""
+    name, n, s, d, k = case
+    taus = [0.5, 0.65, 0.8, 0.95]
+    _, _, vb, vu = oracle.local_counts(n, s, d, k, taus)
+    deg = np.bincount(np.concatenate([s, d]).astype(np.int64), minlength=n)
+    hubs = np.argsort(-deg)[:5]
+    vs = np.concatenate([np.repeat(hubs, 3), synth.rng(23).integers(0, n, size=400)]).astype(np.uint32)
+    with with_knobs(ubt, {"vertex_split": split, "edge_index": 1}):
+        G = ubt.Graph(n, s, d, k=k, undirected=True, edge_index=True)
+        gb, gu, est = G.vertex_local_counts(vs, taus)
+        assert np.array_equal(gb, vb[vs]) and np.array_equal(gu, vu[vs]), (name, split)
+        assert np.allclose(est[0], n / 3.0 * vb[vs].mean(0), rtol=1e-12)
+        gb, gu, _ = G.vertex_local_counts(np.arange(n, dtype=np.uint32), taus)
+        assert np.array_equal(gb, vb) and np.array_equal(gu, vu), (name, split)
+        assert G.guard() == 0

@@ -132,3 +132,54 @@ def test_vertex_topk_chunked_tables(ubt):
             assert np.array_equal(np.stack([g_rec["u"], g_rec["v"], g_rec["w"]], axis=1).astype(np.uint32), w_uvw)
     finally:
         ubt.set_tuning("smem_table_max", old)
+
+
+@pytest.mark.parametrize("mode", [1, 2])
+def test_vertex_topk_with_edge_index(ubt, mode):
+    """Neighbour pairs looked up in the edge index (where cheaper: mode 1;
+    for every neighbour: mode 2) give the same answers."""
+    old = ubt.get_tuning("edge_index")
+    try:
+        ubt.set_tuning("edge_index", mode)
+        for name, n, s, d, k in graphs():
+            G = ubt.Graph(n, s, d, k=k, undirected=True, edge_index=True)
+            deg = np.bincount(np.concatenate([s, d]).astype(np.int64), minlength=n)
+            verts = np.unique(np.concatenate([synth.rng(4).integers(0, n, size=40), np.argsort(-deg)[:4],
+                                              [0, n - 1]])).astype(np.uint32)
+            for which in (1, 2):
+                for K in (1, 64):
+                    got = G.vertex_topk(verts, K, which)
+                    want = oracle_vertex_topk(n, s, d, k, K, which, verts)
+                    for v, g_rec, (w_uvw, w_pb) in zip(verts, got, want):
+                        assert np.array_equal(g_rec["p_bal"], w_pb), (name, v, K, which)
+                        g_uvw = np.stack([g_rec["u"], g_rec["v"], g_rec["w"]], axis=1).astype(np.uint32)
+                        assert np.array_equal(g_uvw, w_uvw), (name, v, K, which)
+            assert G.guard() == 0
+    finally:
+        ubt.set_tuning("edge_index", old)
+
+
+@pytest.mark.parametrize("mode", [0, 1, 2])
+def test_vertex_topk_chunked_tables_with_edge_index(ubt, mode):
+    """Rows longer than one table: with the index every pair is looked up in
+    it (modes 1, 2), without (mode 0) the table is built chunk by chunk."""
+    s, d = mixed_graph(3000, 30000, 21)
+    k = synth.k_uniform(s.size, 22)
+    old = {x: ubt.get_tuning(x) for x in ("smem_table_max", "edge_index")}
+    try:
+        ubt.set_tuning("smem_table_max", 64)
+        ubt.set_tuning("edge_index", mode)
+        G = ubt.Graph(3000, s, d, k=k, undirected=True, edge_index=True)
+        deg = np.bincount(np.concatenate([s, d]).astype(np.int64), minlength=3000)
+        verts = np.concatenate([np.argsort(-deg)[:8], synth.rng(6).integers(0, 3000, size=24)]).astype(np.uint32)
+        for which in (1, 2):
+            got = G.vertex_topk(verts, 16, which)
+            want = oracle_vertex_topk(3000, s, d, k, 16, which, verts)
+            for g_rec, (w_uvw, w_pb) in zip(got, want):
+                assert np.array_equal(g_rec["p_bal"], w_pb)
+                assert np.array_equal(np.stack([g_rec["u"], g_rec["v"], g_rec["w"]], axis=1).astype(np.uint32),
+                                      w_uvw)
+        assert G.guard() == 0
+    finally:
+        for x, v in old.items():
+            ubt.set_tuning(x, v)

@@ -145,7 +145,7 @@ struct Tuning {
   int64_t long_min = 64;          // streamed lists this long are streamed by the whole warp
   int64_t long_tail = 1;          // 1: the last < 64 entries of such a list join the short lists
   int64_t edge_index = 1;         // vertex queries: 0 never look pairs up in the edge index, 1 when cheaper, 2 always
-  int64_t vertex_split = 1024;    // vertex samples with longer pruned rows are spread over all blocks (edge index)
+  int64_t vertex_split = 256;     // vertex samples with longer pruned rows are spread over all blocks (edge index)
   int64_t sort_smem_max = 4096;
 };
 Tuning& tuning();

@@ -233,3 +233,47 @@ def test_cl4m_full_expected_counts_and_gradient(ubt):
     bad = np.abs(got - want) > tol + 1e-12
     assert not bad.any(), (int(bad.sum()), float(np.max(np.abs(got - want) / (tol + 1e-30))))
     assert G.guard() == 0
+
+
+def test_cl1m_full_aeo_sampling_and_topk(ubt):
+    """Chung-Lu n=1e6 with the undirected rows and the edge index, as the
+    benchmark builds it for the Alg. 2 iteration, the samplers and top-k:
+    AEO counts on the whole graph; local counts of 5,000 sampled edges and of
+    5,000 sampled vertices plus the 16 largest hubs (repeated, so the split
+    launch's queue overflows and both of its paths run), with the index in
+    every mode; the top 1,000 most balanced / unbalanced triangles against
+    the oracle's enumeration above t = 0.999."""
+    g = synth.config_graph("cl1m")
+    G = ubt.Graph(g.n, g.src, g.dst, k=g.k, undirected=True, edge_index=True)
+    try:
+        ob, ou = oracle.count_threshold(g.n, g.src, g.dst, g.k, TAUS)
+        gb, gu = G.count_aeo(TAUS)
+        assert np.array_equal(gb, ob) and np.array_equal(gu, ou)
+        eb, eu, vb, vu = oracle.local_counts(g.n, g.src, g.dst, g.k, TAUS)
+        es = synth.rng(31).integers(0, g.m, size=5000).astype(np.uint32)
+        gb, gu, _ = G.edge_local_counts(es, TAUS)
+        assert np.array_equal(gb, eb[es]) and np.array_equal(gu, eu[es])
+        deg = np.bincount(np.concatenate([g.src, g.dst]).astype(np.int64), minlength=g.n)
+        hubs = np.argsort(-deg)[:16]
+        vs = np.concatenate([synth.rng(32).integers(0, g.n, size=5000), np.repeat(hubs, 5)]).astype(np.uint32)
+        old = ubt.get_tuning("edge_index")
+        try:
+            for mode in (1, 0, 2):
+                ubt.set_tuning("edge_index", mode)
+                gb, gu, est = G.vertex_local_counts(vs, TAUS)
+                assert np.array_equal(gb, vb[vs]) and np.array_equal(gu, vu[vs]), mode
+                assert np.allclose(est[0], g.n / 3.0 * vb[vs].mean(0), rtol=1e-12)
+        finally:
+            ubt.set_tuning("edge_index", old)
+        for which in (1, 2):
+            ouvw, _, opb = oracle.enumerate_records(g.n, g.src, g.dst, g.k, 0.999, which)
+            key = -opb if which == 1 else opb
+            order = np.lexsort((ouvw[:, 2], ouvw[:, 1], ouvw[:, 0], key))
+            assert order.size > 1000
+            rec = G.topk(1000, which)
+            assert np.array_equal(rec["p_bal"], opb[order][:1000]), which
+            got = np.stack([rec["u"], rec["v"], rec["w"]], axis=1).astype(np.uint32)
+            assert np.array_equal(got, ouvw[order][:1000]), which
+        assert G.guard() == 0
+    finally:
+        G.close()

@@ -478,9 +478,10 @@ ubt_status ubt_topk(ubt_graph* g, int64_t K, int32_t which, ubt_tri_rec* d_out, 
  *                     use it for a neighbour whose row is more than 8 times
  *                     longer than the pairs left to check, 2 always
  *   "vertex_split"    ubt_vertex_local_counts on a graph with the edge index:
- *                     samples whose pruned row is longer (default 256) are
- *                     spread over all blocks by a second launch (at most 64
- *                     per call; the rest are counted by one block each)
+ *                     samples whose pruned row is longer (default 64) are
+ *                     spread over the warps of all blocks by a second launch
+ *                     (at most 1,024 per call; the rest are counted by one
+ *                     block each)
  *   "world_words_per_pass"  64-world words per traversal of ubt_sample_worlds
  *                     (1, 2, 4, 8, 16, 32 or 64)
  *   "small_batch"     warp tasks taken per grab of a task counter

@@ -715,6 +715,7 @@ struct BuildLayout {
   uint64_t* apairs;
   uint32_t* alist;
   unsigned long long* awork;
+  unsigned long long* lqueue;  // long vertex samples of a local-count call (with the undirected rows)
   unsigned long long* ehkey;   // edge index (optional)
   uint32_t* ehval;
   int64_t eh_slots;
@@ -773,6 +774,7 @@ BuildLayout layout(void* ws, size_t cap, int64_t n, int64_t m, const ubt_graph_o
   L.apairs = und ? c.take<uint64_t>(std::max<int64_t>(m, 1)) : nullptr;
   L.alist = und ? c.take<uint32_t>(n1) : nullptr;
   L.awork = und ? c.take<unsigned long long>(n1) : nullptr;
+  L.lqueue = und ? c.take<unsigned long long>(2 + kLongQueue) : nullptr;
   const bool eidx = und && (opts->flags & UBT_OPT_EDGE_INDEX);
   L.eh_slots = eidx ? pow2_at_least(std::max<int64_t>(2 * m, 64)) : 0;
   L.ehkey = eidx ? c.take<unsigned long long>(L.eh_slots) : nullptr;
@@ -1080,6 +1082,7 @@ extern "C" ubt_status ubt_create_graph(int64_t n, int64_t m, const uint32_t* d_s
   g->n_aowners = n_aowners;
   g->n_ablock = n_ablock;
   g->max_udeg = max_udeg;
+  g->lqueue = L.lqueue;
   g->ehkey = (uint64_t*)L.ehkey;
   g->ehval = L.ehval;
   g->eh_slots = L.eh_slots;

@@ -64,6 +64,9 @@ __host__ __device__ inline uint64_t edge_index_home(uint64_t key, int shift) {
   return (key * 0x9E3779B97F4A7C15ull) >> shift;  // Fibonacci hashing: the top bits
 }
 
+// Entries of the queue of long vertex samples (ubt_graph::lqueue).
+constexpr int kLongQueue = 1024;
+
 // Query scratch carved from the graph workspace (one per graph).
 struct Scratch {
   unsigned long long task[4];       // next giant / hub / small task, spare
@@ -109,6 +112,8 @@ struct ubt_graph {
   uint64_t* apairs = nullptr;       // m: streamed endpoint | position of the edge in x's row << 32
   uint32_t* alist = nullptr;        // owners, by decreasing streamed work
   int64_t n_aowners = 0, n_ablock = 0, max_udeg = 0;  // owners; the first n_ablock are block tasks
+  unsigned long long* lqueue = nullptr;  // with the undirected rows: 2 + kLongQueue words, the vertex
+                                         // samples a local-count call spreads over all blocks
   uint64_t* ehkey = nullptr;        // edge index (UBT_OPT_EDGE_INDEX; else null): eh_slots keys
   uint32_t* ehval = nullptr;        // eh_slots edge values (valbits)
   int64_t eh_slots = 0;             // power of two >= max(2m, 64)
@@ -145,7 +150,7 @@ struct Tuning {
   int64_t long_min = 64;          // streamed lists this long are streamed by the whole warp
   int64_t long_tail = 1;          // 1: the last < 64 entries of such a list join the short lists
   int64_t edge_index = 1;         // vertex queries: 0 never look pairs up in the edge index, 1 when cheaper, 2 always
-  int64_t vertex_split = 256;     // vertex samples with longer pruned rows are spread over all blocks (edge index)
+  int64_t vertex_split = 64;      // vertex samples with longer pruned rows are spread over all blocks (edge index)
   int64_t sort_smem_max = 4096;
 };
 Tuning& tuning();

@@ -131,18 +131,17 @@ EdgeIndex edge_index_of(const ubt_graph* g) {
 // Vertex samples whose pruned row is longer than `split` (with the edge
 // index) are not counted by one block: the sampling kernel queues them (at
 // most kLongCap per query; more are counted in place) and a second launch
-// spreads their neighbours, kPart at a time, over all blocks.  Queue in the
-// query scratch: [0] queued, [1] next part, [2 + i] entry i = row length << 32
-// | sample index.
-constexpr int kLongCap = 64;
-constexpr uint32_t kPart = 256;
+// spreads their neighbours over the warps of all blocks.  The queue
+// (ubt_graph::lqueue): [0] queued, [1] next warp task, [2 + i] entry i =
+// row length << 32 | sample index.
+constexpr int kLongCap = kLongQueue;
 
 struct LocalArgs {
   const uint32_t* uptr;
   const uint64_t* uadj;
   EdgeIndex ix;
   uint32_t split;               // pruned rows longer than this are split across blocks
-  unsigned long long* lq;       // the queue (query scratch)
+  unsigned long long* lq;       // the queue of long samples (ubt_graph::lqueue)
   const uint32_t* uepos;        // 2m: positions of every edge in its endpoints' rows
   const uint32_t* items;        // sampled edges (input index) or vertices
   uint32_t n_items;
@@ -340,53 +339,85 @@ __global__ void __launch_bounds__(512, 2) k_local(LocalArgs a, LocalP p) {
   }
 }
 
-// The split launch: the queued vertex samples' neighbours, kPart per block
-// task; each task adds its per-threshold counts to the sample's outputs
-// (zero after the sampling kernel).
+// The split launch: the queued vertex samples' neighbours, kWarpNb per warp
+// task from one counter over all queued samples, no block barriers.  Each
+// warp bins into its own shared histogram and adds its per-threshold counts
+// to the sample's outputs (zero after the sampling kernel) when it moves on
+// to another sample or runs out of tasks.
+constexpr uint32_t kWarpNb = 4;
+
+__device__ __forceinline__ void flush_bins(const LocalArgs& a, const LocalP& p, unsigned long long* wb,
+                                           uint32_t item, int lane) {
+  __syncwarp();
+  for (int i = lane; i < p.nt; i += 32) {
+    unsigned long long b = 0, u = 0;
+    for (int r = 0; r <= p.nt - 1 - i; r++) b += wb[r];
+    for (int r = p.nt + i + 1; r <= 2 * p.nt; r++) u += wb[r];
+    if (b) atomicAdd((unsigned long long*)&a.bal[(size_t)item * p.nt + p.perm[i]], b);
+    if (u) atomicAdd((unsigned long long*)&a.unbal[(size_t)item * p.nt + p.perm[i]], u);
+  }
+  __syncwarp();
+  for (int r = lane; r <= 2 * p.nt; r += 32) wb[r] = 0;
+  __syncwarp();
+}
+
 __global__ void __launch_bounds__(512, 2) k_local_split(LocalArgs a, LocalP p) {
+  extern __shared__ __align__(16) char smem[];
   __shared__ long long S[256];
-  __shared__ unsigned long long bins[144];
   __shared__ uint32_t pref[kLongCap + 1];
-  __shared__ uint32_t s_part;
-  const int tid = threadIdx.x, lane = tid & 31, wid = tid >> 5, nw = blockDim.x >> 5;
+  const int tid = threadIdx.x, lane = tid & 31, wid = tid >> 5;
+  unsigned long long* wb = (unsigned long long*)smem + (size_t)wid * (2 * p.nt + 1);  // this warp's bins
   for (int i = tid; i < 256; i += blockDim.x) S[i] = i < 2 * p.nt ? p.S[i] : INT64_MAX;
+  for (int r = lane; r <= 2 * p.nt; r += 32) wb[r] = 0;
   const uint32_t nq = (uint32_t)min(a.lq[0], (unsigned long long)kLongCap);
-  if (tid == 0) {
-    uint32_t acc = 0;
-    for (uint32_t i = 0; i < nq; i++) {
-      pref[i] = acc;
-      const uint32_t tlen = (uint32_t)(a.lq[2 + i] >> 32);
-      acc += (tlen - 1 + kPart - 1) / kPart;  // neighbours 0 .. tlen - 2 have a later one
+  if (wid == 0) {
+    // first warp task of every entry: lane l sums entries [l * seg, (l + 1) * seg),
+    // a warp scan gives each lane its segment's start
+    constexpr uint32_t seg = (kLongCap + 31) / 32;
+    const uint32_t b0 = lane * seg, b1 = min(nq, b0 + seg);
+    uint32_t mine = 0;
+    for (uint32_t i = b0; i < b1; i++)
+      mine += ((uint32_t)(a.lq[2 + i] >> 32) - 1 + kWarpNb - 1) / kWarpNb;  // neighbours 0 .. tlen - 2
+    uint32_t incl = mine;
+#pragma unroll
+    for (int d = 1; d < 32; d <<= 1) {
+      const uint32_t y = __shfl_up_sync(kFull, incl, d);
+      if (lane >= d) incl += y;
     }
-    pref[nq] = acc;
+    uint32_t acc = incl - mine;
+    for (uint32_t i = b0; i < b1; i++) {
+      pref[i] = acc;
+      acc += ((uint32_t)(a.lq[2 + i] >> 32) - 1 + kWarpNb - 1) / kWarpNb;
+    }
+    if (lane == 31) pref[nq] = incl;
   }
   __syncthreads();
   const uint32_t total = pref[nq];
+  uint32_t cur = 0xFFFFFFFFu;  // entry whose counts this warp's bins hold
+  uint32_t cur_item = 0;
   while (true) {
-    if (tid == 0) s_part = (uint32_t)atomicAdd(&a.lq[1], 1ull);
-    for (int i = tid; i <= 2 * p.nt; i += blockDim.x) bins[i] = 0;
-    __syncthreads();
-    const uint32_t part = s_part;
-    if (part >= total) break;
-    uint32_t e = 0;
-    while (e + 1 < nq && pref[e + 1] <= part) e++;
+    uint32_t task = 0;
+    if (lane == 0) task = (uint32_t)atomicAdd(&a.lq[1], 1ull);
+    task = __shfl_sync(kFull, task, 0);
+    if (task >= total) break;
+    uint32_t e = 0, hi = nq - 1;  // the last entry whose first task is <= task
+    while (e < hi) {
+      const uint32_t mid = (e + hi + 1) >> 1;
+      if (pref[mid] <= task) e = mid; else hi = mid - 1;
+    }
     const unsigned long long ent = a.lq[2 + e];
     const uint32_t item = (uint32_t)ent, tlen = (uint32_t)(ent >> 32);
+    if (e != cur) {
+      if (cur != 0xFFFFFFFFu) flush_bins(a, p, wb, cur_item, lane);
+      cur = e;
+      cur_item = item;
+    }
     const uint32_t x = a.items[item], rs = a.uptr[x];
     const int64_t qmax = a.L > 0 ? qabs(adj_valbits(a.uadj[rs])) : 0;
-    const uint32_t j0 = (part - pref[e]) * kPart, j1 = min(j0 + kPart, tlen - 1);
-    index_neighbours(a, p, S, bins, x, rs, tlen, qmax, j0 + wid, j1, nw, lane);
-    __syncthreads();
-    if (tid < p.nt) {
-      const int i = tid;
-      unsigned long long b = 0, u = 0;
-      for (int r = 0; r <= p.nt - 1 - i; r++) b += bins[r];
-      for (int r = p.nt + i + 1; r <= 2 * p.nt; r++) u += bins[r];
-      if (b) atomicAdd((unsigned long long*)&a.bal[(size_t)item * p.nt + p.perm[i]], b);
-      if (u) atomicAdd((unsigned long long*)&a.unbal[(size_t)item * p.nt + p.perm[i]], u);
-    }
-    __syncthreads();
+    const uint32_t j0 = (task - pref[e]) * kWarpNb, j1 = min(j0 + kWarpNb, tlen - 1);
+    index_neighbours(a, p, S, wb, x, rs, tlen, qmax, j0, j1, 1, lane);
   }
+  if (cur != 0xFFFFFFFFu) flush_bins(a, p, wb, cur_item, lane);
 }
 
 // estimate[t] = scale / k * sum over samples of the local count
@@ -441,7 +472,7 @@ ubt_status local_counts(ubt_graph* g, const uint32_t* d_items, int64_t k, int ve
   a.uadj = g->uadj;
   a.ix = edge_index_of(g);
   a.split = (uint32_t)std::min<int64_t>(T.vertex_split, 0xFFFFFFFFll);
-  a.lq = &g->scratch->hist[0];
+  a.lq = g->lqueue;
   a.uepos = g->uepos;
   a.items = d_items;
   a.n_items = (uint32_t)k;
@@ -468,7 +499,8 @@ ubt_status local_counts(ubt_graph* g, const uint32_t* d_items, int64_t k, int ve
     k_local<<<(int)blocks, threads, smem, s>>>(a, p);
     UBT_CUDA(cudaGetLastError());
     if (vertex_mode && a.ix.mode != 0) {
-      k_local_split<<<(int)(g->sm_count * 2), threads, 0, s>>>(a, p);
+      const size_t wbytes = (size_t)(threads / 32) * (2 * n_tau + 1) * 8;  // per-warp bins
+      k_local_split<<<(int)(g->sm_count * 2), threads, wbytes, s>>>(a, p);
       UBT_CUDA(cudaGetLastError());
     }
   }

@@ -554,6 +554,7 @@ __device__ __forceinline__ bool cand_before(uint64_t ra, const uint32_t* ta, uin
 __global__ void __launch_bounds__(512, 1) k_vertex_topk(TopkArgs a) {
   extern __shared__ __align__(16) char smem[];
   __shared__ uint32_t s_misc[8];
+  __shared__ uint32_t s_scan[32];
   uint32_t* hist = (uint32_t*)smem;                                   // 2049 (+pad) slice counts
   uint64_t* crank = (uint64_t*)(smem + 2064 * 4);                     // candidates: rank
   uint32_t* ctri = (uint32_t*)(crank + kTopkCap);                     // candidates: sorted triple
@@ -573,6 +574,7 @@ __global__ void __launch_bounds__(512, 1) k_vertex_topk(TopkArgs a) {
     for (int pass = 0; pass < 2; pass++) {
       if (pass == 0) {
         for (int i = tid; i < kTopkSlices; i += blockDim.x) hist[i] = 0;
+        if (tid == 0) s_misc[2] = 0;  // pass 0 also keeps every triangle while they fit
       } else if (tid == 0) {
         s_misc[1] = 0;       // cursor of better slices
         s_misc[2] = below;   // cursor of the threshold slice
@@ -602,14 +604,14 @@ __global__ void __launch_bounds__(512, 1) k_vertex_topk(TopkArgs a) {
             if (lane == 0) guard_fail(a.sc, kGuardVertex, av);
             continue;
           }
-          // triangle v-av-w with P found: histogram (pass 0) or candidate (pass 1)
+          // triangle v-av-w with P found: histogram and candidate while the
+          // buffer has room (pass 0), or candidate of a slice up to the K-th's (pass 1)
           auto found = [&](long long P, uint32_t w) {
             const uint64_t r = topk_rank(P, a.which);
             const uint32_t sl = (uint32_t)(r >> 35);
-            if (pass == 0) {
-              atomicAdd(&hist[sl], 1u);
-            } else if (sl <= sstar) {
-              const uint32_t at = sl < sstar ? atomicAdd(&s_misc[1], 1u) : atomicAdd(&s_misc[2], 1u);
+            if (pass == 0) atomicAdd(&hist[sl], 1u);
+            if (pass == 0 || sl <= sstar) {
+              const uint32_t at = (pass == 0 || sl == sstar) ? atomicAdd(&s_misc[2], 1u) : atomicAdd(&s_misc[1], 1u);
               if (at < kTopkCap) {
                 uint32_t x0 = v, x1 = av, x2 = w, tt;
                 if (x0 > x1) { tt = x0; x0 = x1; x1 = tt; }
@@ -652,17 +654,44 @@ __global__ void __launch_bounds__(512, 1) k_vertex_topk(TopkArgs a) {
         __syncthreads();
       }
       if (pass == 0) {
-        // the slice of the K-th best: first slice whose running count reaches K
-        if (tid == 0) {  // (fewer than K in all: every slice)
-          uint32_t acc = 0, sel = kTopkSlices - 1;
-          for (uint32_t i = 0; i < (uint32_t)kTopkSlices; i++) {
-            if (acc + hist[i] >= a.K) { sel = i; break; }
+        // every triangle fitted the buffer: they are the candidates
+        if (s_misc[2] <= (uint32_t)kTopkCap) break;
+        // else the slice of the K-th best (more than kTopkCap >= K triangles,
+        // so it exists): the first slice whose running count reaches K, by a
+        // block-wide scan over contiguous runs of slices
+        const uint32_t per = (kTopkSlices + blockDim.x - 1) / blockDim.x;
+        const uint32_t i0 = min((uint32_t)kTopkSlices, tid * per), i1 = min((uint32_t)kTopkSlices, i0 + per);
+        uint32_t mine = 0;
+        for (uint32_t i = i0; i < i1; i++) mine += hist[i];
+        uint32_t incl = mine;
+#pragma unroll
+        for (int d = 1; d < 32; d <<= 1) {
+          const uint32_t y = __shfl_up_sync(kFull, incl, d);
+          if (lane >= d) incl += y;
+        }
+        if (lane == 31) s_scan[wid] = incl;
+        __syncthreads();
+        if (wid == 0) {
+          const uint32_t w0 = lane < nw ? s_scan[lane] : 0u;
+          uint32_t wi = w0;
+#pragma unroll
+          for (int d = 1; d < 32; d <<= 1) {
+            const uint32_t y = __shfl_up_sync(kFull, wi, d);
+            if (lane >= d) wi += y;
+          }
+          if (lane < nw) s_scan[lane] = wi - w0;  // exclusive offset of each warp
+        }
+        __syncthreads();
+        uint32_t acc = incl - mine + s_scan[wid];
+        if (acc < a.K && acc + mine >= a.K) {
+          for (uint32_t i = i0; i < i1; i++) {
+            if (acc + hist[i] >= a.K) {
+              s_misc[3] = i;
+              s_misc[4] = acc;
+              break;
+            }
             acc += hist[i];
           }
-          uint32_t bel = 0;
-          for (uint32_t i = 0; i < sel; i++) bel += hist[i];
-          s_misc[3] = sel;
-          s_misc[4] = bel;
         }
         __syncthreads();
         sstar = s_misc[3];

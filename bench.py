@@ -690,20 +690,31 @@ def extra_aeo(ubt, args, flush, name):
     g = make_graph(name)
     k = g.k if g.k is not None else __import__("synth").quantise(g.p)
     t0 = time.perf_counter()
-    G = ubt.Graph(g.n, g.src, g.dst, k=k, undirected=True)
+    G = ubt.Graph(g.n, g.src, g.dst, k=k, undirected=True, edge_index=True)
     torch.cuda.synchronize()
     build_s = time.perf_counter() - t0
     out = torch.empty(2, dtype=torch.int64, device="cuda")
     steps = max(3, args.steps // 4)
     rows = []
-    for t in AEO_TAUS:
-        ms_deg = _events_ms(lambda: G.count_threshold_([t], out, prune=True), steps, 1, flush)
-        a = out.cpu().numpy().copy()
-        ms_aeo = _events_ms(lambda: G.count_aeo_([t], out), steps, 1, flush)
-        b = out.cpu().numpy().copy()
-        assert np.array_equal(a, b), "AEO and degree-ordered counts differ"
-        rows.append({"t": t, "degree_ms": ms_deg, "aeo_ms": ms_aeo, "balanced": int(a[0]), "unbalanced": int(a[1])})
-    res = {"workload": name, "n": g.n, "m": g.m, "build_with_undirected_s": build_s, "per_t": rows}
+    old = ubt.get_tuning("edge_index")
+    try:
+        for t in AEO_TAUS:
+            ms_deg = _events_ms(lambda: G.count_threshold_([t], out, prune=True), steps, 1, flush)
+            a = out.cpu().numpy().copy()
+            ubt.set_tuning("edge_index", 1)
+            ms_aeo = _events_ms(lambda: G.count_aeo_([t], out), steps, 1, flush)
+            b = out.cpu().numpy().copy()
+            ubt.set_tuning("edge_index", 0)
+            ms_tab = _events_ms(lambda: G.count_aeo_([t], out), steps, 1, flush)
+            c = out.cpu().numpy().copy()
+            assert np.array_equal(a, b) and np.array_equal(a, c), "AEO and degree-ordered counts differ"
+            rows.append({"t": t, "degree_ms": ms_deg, "aeo_ms": ms_aeo, "aeo_tables_ms": ms_tab,
+                         "balanced": int(a[0]), "unbalanced": int(a[1])})
+    finally:
+        ubt.set_tuning("edge_index", old)
+    res = {"workload": name, "n": g.n, "m": g.m, "build_with_undirected_and_index_s": build_s, "per_t": rows,
+           "note": "aeo_ms: edge-index form (each edge streams the shorter Lemma 3 window); "
+                   "aeo_tables_ms: owner tables in shared memory"}
     del G
     _release()
     return res

@@ -102,8 +102,8 @@ typedef struct {
      * Edge Order (FIXED graphs only), which ubt_count_aeo, ubt_enumerate_aeo,
      * ubt_edge_local_counts and ubt_vertex_local_counts need.
      * UBT_OPT_EDGE_INDEX (with UBT_OPT_UNDIRECTED): also build a hash index
-     * of the edges ({u, w} -> edge value; 12 bytes per slot, the power of two
-     * >= 2m slots).  ubt_vertex_local_counts and ubt_vertex_topk then look a
+     * of the edges ({u, w} -> edge value; 16 bytes per slot, the power of two
+     * >= 4m slots).  ubt_vertex_local_counts and ubt_vertex_topk then look a
      * neighbour pair up in it instead of streaming a neighbour's row when that
      * row is much longer than the pairs left to check (same results). */
     int64_t flags;

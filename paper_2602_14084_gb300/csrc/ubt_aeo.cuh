@@ -295,12 +295,172 @@ __global__ void __launch_bounds__(512, 2) k_aeo(AeoArgs a, typename V::P p) {
   vis.block_end();
 }
 
+// The same iteration on a graph with the edge index (UBT_OPT_EDGE_INDEX):
+// no owner tables.  Edge e = u-v has two windows of candidate partners, u's
+// row after e and v's row after e, each up to Lemma 3's cutoff; the shorter
+// one is streamed and, for each entry s-w of it, the closing edge o-w (o the
+// other endpoint) is looked up in the index.  It counts when o-w lies after
+// e in o's row -- |q_ow| < |q_e|, or equal and w > s, the row order being
+// Absolute Edge Order -- and passes the cutoff, exactly the conditions the
+// table form tests through row positions.  Warps take 32 edges at a time;
+// long windows are streamed by the whole warp, short ones concatenated.
+// Visitors without CSR positions only (the positions of o-w are not known).
+struct AeoIxArgs {
+  const uint32_t* uptr;
+  const uint64_t* uadj;
+  const uint32_t* uepos;      // 2m: [2e + side] position of edge e in its endpoints' rows
+  const uint4* eslots;        // edge index
+  uint64_t emask;
+  int eshift;
+  uint32_t n, m, m2;
+  Scratch* sc;
+  int64_t L;
+};
+
+__device__ __forceinline__ bool aeo_ix_find(const AeoIxArgs& a, uint32_t o, uint32_t w, uint32_t& val) {
+  const int r = edge_index_lookup(a.eslots, a.emask, a.eshift, o, w, val);
+  if (r < 0) guard_fail(a.sc, kGuardFind, o);
+  return r > 0;
+}
+
+// entry s-w of the streamed window: the closing edge o-w, if it exists, lies
+// after e in o's row and passes Lemma 3
+__device__ __forceinline__ bool aeo_ix_hit(const AeoIxArgs& a, uint32_t o, uint32_t s, uint32_t w, int64_t aq,
+                                           int64_t cut, uint32_t& qow) {
+  if (w == o || !aeo_ix_find(a, o, w, qow)) return false;
+  const int64_t oq = qabs(qow);
+  return (oq < aq || (oq == aq && w > s)) && (a.L == 0 || oq * cut >= a.L);
+}
+
+template <class V>
+__global__ void __launch_bounds__(512, 2) k_aeo_index(AeoIxArgs a, typename V::P p) {
+  static_assert(!V::kPos, "the index form knows no CSR position of the closing edge");
+  extern __shared__ __align__(16) char smem[];
+  V vis(p, smem);
+  vis.block_init();
+  __syncthreads();
+  const int lane = (int)lane_id();
+  while (true) {
+    unsigned long long e0 = 0;
+    if (lane == 0) e0 = atomicAdd(&a.sc->task[0], 32ull);
+    e0 = __shfl_sync(kFull, e0, 0);
+    if (e0 >= a.m) break;
+    const uint64_t e = e0 + (uint64_t)lane;
+    bool ok = e < a.m;
+    uint32_t o = 0, sv = 0, qe = 0, vs = 0, dv = 0;
+    int64_t aq = 0, cut = 0;
+    if (ok) {
+      const uint32_t p0 = a.uepos[2 * e], p1 = a.uepos[2 * e + 1];
+      if (p0 >= a.m2 || p1 >= a.m2) {
+        guard_fail(a.sc, kGuardList, (uint32_t)e);
+        ok = false;
+      } else {
+        const uint64_t ea = a.uadj[p0];
+        const uint32_t u = adj_col(a.uadj[p1]), v = adj_col(ea);  // p0 lies in u's row, p1 in v's
+        qe = adj_valbits(ea);
+        aq = qabs(qe);
+        cut = aq * aq;
+        if (u >= a.n || v >= a.n || (a.L > 0 && aq * (1ll << 30) < a.L)) {  // Lemma 2 on e
+          if (u >= a.n || v >= a.n) guard_fail(a.sc, kGuardVertex, (uint32_t)e);
+          ok = false;
+        } else {
+          const uint32_t ue = a.uptr[u + 1], ve = a.uptr[v + 1];
+          const uint32_t cu = a.L > 0 ? a.uptr[u] + prune_prefix(a.uadj + a.uptr[u], ue - a.uptr[u], cut, a.L) : ue;
+          const uint32_t cv = a.L > 0 ? a.uptr[v] + prune_prefix(a.uadj + a.uptr[v], ve - a.uptr[v], cut, a.L) : ve;
+          const uint32_t lu = cu > p0 + 1 ? cu - (p0 + 1) : 0u, lv = cv > p1 + 1 ? cv - (p1 + 1) : 0u;
+          if (lu <= lv) { sv = u; o = v; vs = p0 + 1; dv = lu; }
+          else { sv = v; o = u; vs = p1 + 1; dv = lv; }
+        }
+      }
+    }
+    if (!ok) dv = 0;
+    // long windows: the whole warp, one window at a time
+    constexpr uint32_t kLong = 48;
+    unsigned longm = __ballot_sync(kFull, dv >= kLong);
+    while (longm) {
+      const int j = __ffs(longm) - 1;
+      longm &= longm - 1;
+      const uint32_t oj = __shfl_sync(kFull, o, j), sj = __shfl_sync(kFull, sv, j);
+      const uint32_t vsj = __shfl_sync(kFull, vs, j), dvj = __shfl_sync(kFull, dv, j);
+      const uint32_t qj = __shfl_sync(kFull, qe, j);
+      const long long aqj = __shfl_sync(kFull, (long long)aq, j), cj = __shfl_sync(kFull, (long long)cut, j);
+      for (uint32_t off = 0; off < dvj; off += 32) {
+        const uint32_t i = off + lane;
+        const uint64_t ew = i < dvj ? a.uadj[vsj + i] : 0ull;
+        uint32_t qow = 0;
+        const bool hit = i < dvj && aeo_ix_hit(a, oj, sj, adj_col(ew), aqj, cj, qow);
+        vis.step(hit, oj, sj, adj_col(ew), qj, qow, adj_valbits(ew), 0u, 0u, vsj + i);
+      }
+    }
+    // short windows: concatenated, one entry per lane per step
+    const uint32_t ds = dv >= kLong ? 0u : dv;
+    uint32_t incl = ds;
+#pragma unroll
+    for (int d = 1; d < 32; d <<= 1) {
+      const uint32_t y = __shfl_up_sync(kFull, incl, d);
+      if (lane >= d) incl += y;
+    }
+    const uint32_t total = __shfl_sync(kFull, incl, 31);
+    const uint32_t excl = incl - ds;
+    for (uint32_t base = 0; base < total; base += 32) {
+      const uint32_t f = base + lane;
+      const bool act = f < total;
+      int j = 0;
+#pragma unroll
+      for (int b = 16; b > 0; b >>= 1) {
+        const uint32_t tj = __shfl_sync(kFull, incl, j + b - 1);
+        if (tj <= f) j += b;
+      }
+      j = j > 31 ? 31 : j;
+      const uint32_t vsj = __shfl_sync(kFull, vs, j), exj = __shfl_sync(kFull, excl, j);
+      const uint32_t oj = __shfl_sync(kFull, o, j), sj = __shfl_sync(kFull, sv, j);
+      const uint32_t qj = __shfl_sync(kFull, qe, j);
+      const long long aqj = __shfl_sync(kFull, (long long)aq, j), cj = __shfl_sync(kFull, (long long)cut, j);
+      const uint32_t pos = vsj + (f - exj);
+      const uint64_t ew = act ? a.uadj[pos] : 0ull;
+      uint32_t qow = 0;
+      const bool hit = act && aeo_ix_hit(a, oj, sj, adj_col(ew), aqj, cj, qow);
+      vis.step(hit, oj, sj, adj_col(ew), qj, qow, adj_valbits(ew), 0u, 0u, pos);
+    }
+  }
+  __syncthreads();
+  vis.block_end();
+}
+
 namespace {
 
 template <class V>
 ubt_status launch_aeo(const ubt_graph* g, int64_t L, const typename V::P& p, cudaStream_t s) {
   if (!g->uptr) return UBT_ERR_UNSUPPORTED;
   const Tuning& T = tuning();
+  if constexpr (!V::kPos) {
+    if (g->eslots && T.edge_index != 0) {
+      AeoIxArgs a;
+      a.uptr = g->uptr;
+      a.uadj = g->uadj;
+      a.uepos = g->uepos;
+      a.eslots = g->eslots;
+      a.emask = (uint64_t)g->eh_slots - 1;
+      a.eshift = g->eh_shift;
+      a.n = (uint32_t)g->n;
+      a.m = (uint32_t)g->m;
+      a.m2 = (uint32_t)(2 * g->m);
+      a.sc = g->scratch;
+      a.L = L;
+      UBT_CUDA(cudaMemsetAsync(a.sc, 0, kScratchHeader / 2, s));
+      if (g->m == 0) return UBT_OK;
+      const int threads = 512;
+      const size_t smem = (size_t)((V::smem_bytes(threads) + 15) / 16) * 16;
+      UBT_CUDA(cudaFuncSetAttribute(k_aeo_index<V>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+      int per_sm = 0;
+      UBT_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_aeo_index<V>, threads, smem));
+      if (per_sm < 1) return UBT_ERR_INVALID_ARG;
+      per_sm = (int)std::min<int64_t>(per_sm, std::max<int64_t>(1, T.blocks_per_sm));
+      k_aeo_index<V><<<g->sm_count * per_sm, threads, smem, s>>>(a, p);
+      UBT_CUDA(cudaGetLastError());
+      return UBT_OK;
+    }
+  }
   AeoArgs a;
   a.uptr = g->uptr;
   a.uadj = g->uadj;

@@ -598,10 +598,10 @@ __global__ void k_umirror(int64_t n, const uint32_t* __restrict__ uptr, const ui
 }
 
 // Edge index: every edge once, from the row of its smaller endpoint.  The
-// table has at least twice as many slots as edges, so every insert finds a
-// free slot; the loop bound is a self-check.
+// table has at least four times as many slots as edges, so every insert
+// finds a free slot; the loop bound is a self-check.
 __global__ void k_edge_index(int64_t n, const uint32_t* __restrict__ uptr, const uint64_t* __restrict__ uadj,
-                             unsigned long long* __restrict__ ehkey, uint32_t* __restrict__ ehval, uint64_t slots,
+                             uint4* __restrict__ eslots, uint64_t slots,
                              int shift, unsigned long long* err) {
   const int lane = threadIdx.x & 31;
   const int64_t warps = (int64_t)gridDim.x * (blockDim.x >> 5);
@@ -613,8 +613,9 @@ __global__ void k_edge_index(int64_t n, const uint32_t* __restrict__ uptr, const
       uint64_t h = edge_index_home(key, shift);
       uint64_t it = 0;
       for (; it < slots; it++) {
-        if (atomicCAS(&ehkey[h], (unsigned long long)kEdgeIndexEmpty, (unsigned long long)key) == kEdgeIndexEmpty) {
-          ehval[h] = adj_valbits(e);
+        unsigned long long* slot_key = reinterpret_cast<unsigned long long*>(&eslots[h]);
+        if (atomicCAS(slot_key, (unsigned long long)kEdgeIndexEmpty, (unsigned long long)key) == kEdgeIndexEmpty) {
+          eslots[h].z = adj_valbits(e);
           break;
         }
         h = (h + 1) & (slots - 1);
@@ -716,8 +717,7 @@ struct BuildLayout {
   uint32_t* alist;
   unsigned long long* awork;
   unsigned long long* lqueue;  // long vertex samples of a local-count call (with the undirected rows)
-  unsigned long long* ehkey;   // edge index (optional)
-  uint32_t* ehval;
+  uint4* eslots;               // edge index (optional)
   int64_t eh_slots;
   unsigned long long* gacc;
   unsigned long long* bacc;
@@ -776,9 +776,8 @@ BuildLayout layout(void* ws, size_t cap, int64_t n, int64_t m, const ubt_graph_o
   L.awork = und ? c.take<unsigned long long>(n1) : nullptr;
   L.lqueue = und ? c.take<unsigned long long>(2 + kLongQueue) : nullptr;
   const bool eidx = und && (opts->flags & UBT_OPT_EDGE_INDEX);
-  L.eh_slots = eidx ? pow2_at_least(std::max<int64_t>(2 * m, 64)) : 0;
-  L.ehkey = eidx ? c.take<unsigned long long>(L.eh_slots) : nullptr;
-  L.ehval = eidx ? c.take<uint32_t>(L.eh_slots) : nullptr;
+  L.eh_slots = eidx ? pow2_at_least(std::max<int64_t>(4 * m, 64)) : 0;
+  L.eslots = eidx ? c.take<uint4>(L.eh_slots) : nullptr;
   L.gacc = c.take<unsigned long long>(std::max<int64_t>(m, 1));
   // per graph: T, sum_lo, sum_hi (expected counts) of a batch
   L.bacc = c.take<unsigned long long>(3 * std::max<int64_t>(ng, 1));
@@ -1010,11 +1009,11 @@ extern "C" ubt_status ubt_create_graph(int64_t n, int64_t m, const uint32_t* d_s
     }
     k_uepos<<<grid_w, thr, 0, s>>>(n, L.uptr, L.uadj, L.ueid, L.uepos);
     k_umirror<<<grid_w, thr, 0, s>>>(n, L.uptr, L.uadj, L.ueid, L.uepos, L.umir);
-    if (L.ehkey) {
-      UBT_CUDA(cudaMemsetAsync(L.ehkey, 0xFF, sizeof(unsigned long long) * (size_t)L.eh_slots, s));
+    if (L.eslots) {
+      UBT_CUDA(cudaMemsetAsync(L.eslots, 0xFF, sizeof(uint4) * (size_t)L.eh_slots, s));
       int lg = 0;
       while ((1ll << lg) < L.eh_slots) lg++;
-      k_edge_index<<<grid_w, thr, 0, s>>>(n, L.uptr, L.uadj, L.ehkey, L.ehval, (uint64_t)L.eh_slots, 64 - lg,
+      k_edge_index<<<grid_w, thr, 0, s>>>(n, L.uptr, L.uadj, L.eslots, (uint64_t)L.eh_slots, 64 - lg,
                                           &L.scratch->err);
     }
     UBT_CUDA(cudaMemsetAsync(L.fill, 0, sizeof(uint32_t) * (n + 1), s));
@@ -1083,8 +1082,7 @@ extern "C" ubt_status ubt_create_graph(int64_t n, int64_t m, const uint32_t* d_s
   g->n_ablock = n_ablock;
   g->max_udeg = max_udeg;
   g->lqueue = L.lqueue;
-  g->ehkey = (uint64_t*)L.ehkey;
-  g->ehval = L.ehval;
+  g->eslots = L.eslots;
   g->eh_slots = L.eh_slots;
   {
     int lg = 0;

@@ -54,8 +54,10 @@ __host__ __device__ inline uint64_t adj_pack(uint32_t col, uint32_t valbits) {
 }
 
 // Edge index (UBT_OPT_EDGE_INDEX): open addressing with linear probing over
-// a power-of-two number of slots (at least 2m, so at most half are used);
-// key min(u, w) << 32 | max(u, w), empty slots hold ~0.
+// a power-of-two number of 16-byte slots (at least 4m, so at most a quarter
+// are used and a miss rarely leaves its first 32-byte sector) -- key min(u, w) << 32 | max(u, w) in the first 8 bytes, the edge
+// value in the next 4, so that one 16-byte load reads both; empty slots hold
+// the key ~0.
 constexpr uint64_t kEdgeIndexEmpty = ~0ull;
 __host__ __device__ inline uint64_t edge_index_key(uint32_t a, uint32_t b) {
   return a < b ? ((uint64_t)a << 32) | b : ((uint64_t)b << 32) | a;
@@ -63,6 +65,26 @@ __host__ __device__ inline uint64_t edge_index_key(uint32_t a, uint32_t b) {
 __host__ __device__ inline uint64_t edge_index_home(uint64_t key, int shift) {
   return (key * 0x9E3779B97F4A7C15ull) >> shift;  // Fibonacci hashing: the top bits
 }
+#ifdef __CUDACC__
+// 1: edge a-b found (its value in val); 0: absent; -1: the probe bound was
+// reached (a self-check: a table at most a quarter full never reaches it)
+__device__ __forceinline__ int edge_index_lookup(const uint4* __restrict__ slots, uint64_t mask, int shift, uint32_t a,
+                                                 uint32_t b, uint32_t& val) {
+  const uint64_t k = edge_index_key(a, b);
+  uint64_t h = edge_index_home(k, shift);
+  for (uint64_t it = 0; it <= mask; it++) {
+    const uint4 sl = slots[h];
+    const uint64_t key = ((uint64_t)sl.y << 32) | sl.x;
+    if (key == k) {
+      val = sl.z;
+      return 1;
+    }
+    if (key == kEdgeIndexEmpty) return 0;
+    h = (h + 1) & mask;
+  }
+  return -1;
+}
+#endif
 
 // Entries of the queue of long vertex samples (ubt_graph::lqueue).
 constexpr int kLongQueue = 1024;
@@ -114,9 +136,9 @@ struct ubt_graph {
   int64_t n_aowners = 0, n_ablock = 0, max_udeg = 0;  // owners; the first n_ablock are block tasks
   unsigned long long* lqueue = nullptr;  // with the undirected rows: 2 + kLongQueue words, the vertex
                                          // samples a local-count call spreads over all blocks
-  uint64_t* ehkey = nullptr;        // edge index (UBT_OPT_EDGE_INDEX; else null): eh_slots keys
-  uint32_t* ehval = nullptr;        // eh_slots edge values (valbits)
-  int64_t eh_slots = 0;             // power of two >= max(2m, 64)
+  uint4* eslots = nullptr;          // edge index (UBT_OPT_EDGE_INDEX; else null): eh_slots slots of
+                                    // 16 bytes, key in the first 8, edge value (valbits) in the next 4
+  int64_t eh_slots = 0;             // power of two >= max(4m, 64)
   int eh_shift = 64;                // 64 - log2(eh_slots)
   unsigned long long* gacc = nullptr;   // m: backward accumulators
   unsigned long long* bacc = nullptr;   // batch accumulators

@@ -42,11 +42,10 @@ struct LocalP {
 };
 
 // Edge index lookup (UBT_OPT_EDGE_INDEX): the value of edge a-b, if present.
-// Probes end at the key or an empty slot (at most half the slots are used);
-// the bound is a self-check.
+// Probes end at the key or an empty slot (at most a quarter of the slots are
+// used); the bound is a self-check.
 struct EdgeIndex {
-  const uint64_t* key;
-  const uint32_t* val;
+  const uint4* slots;
   uint64_t mask;   // slots - 1
   int shift;
   int mode;        // 0 unused, 1 where cheaper than streaming, 2 always
@@ -54,19 +53,9 @@ struct EdgeIndex {
 
 __device__ __forceinline__ bool edge_index_find(const EdgeIndex& ix, uint32_t a, uint32_t b, uint32_t& val,
                                                 Scratch* sc) {
-  const uint64_t k = edge_index_key(a, b);
-  uint64_t h = edge_index_home(k, ix.shift);
-  for (uint64_t it = 0; it <= ix.mask; it++) {
-    const uint64_t x = ix.key[h];
-    if (x == k) {
-      val = ix.val[h];
-      return true;
-    }
-    if (x == kEdgeIndexEmpty) return false;
-    h = (h + 1) & ix.mask;
-  }
-  guard_fail(sc, kGuardFind, a);
-  return false;
+  const int r = edge_index_lookup(ix.slots, ix.mask, ix.shift, a, b, val);
+  if (r < 0) guard_fail(sc, kGuardFind, a);
+  return r > 0;
 }
 
 // Vertex queries: the triangles v-a-b with b among `cand` positions of v's
@@ -120,11 +109,10 @@ __device__ __forceinline__ void index_pairs(const EdgeIndex& ix, const uint64_t*
 
 EdgeIndex edge_index_of(const ubt_graph* g) {
   EdgeIndex ix;
-  ix.key = g->ehkey;
-  ix.val = g->ehval;
+  ix.slots = g->eslots;
   ix.mask = g->eh_slots ? (uint64_t)g->eh_slots - 1 : 0;
   ix.shift = g->eh_shift;
-  ix.mode = g->ehkey ? (int)tuning().edge_index : 0;
+  ix.mode = g->eslots ? (int)tuning().edge_index : 0;
   return ix;
 }
 

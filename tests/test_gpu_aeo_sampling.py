@@ -269,3 +269,27 @@ def test_vertex_samples_split_across_blocks(ubt, case, split):
         gb, gu, _ = G.vertex_local_counts(np.arange(n, dtype=np.uint32), taus)
         assert np.array_equal(gb, vb) and np.array_equal(gu, vu), (name, split)
         assert G.guard() == 0
+
+
+@pytest.mark.parametrize("case", CASES, ids=[c[0] for c in CASES])
+def test_aeo_edge_index_form(ubt, case):
+    """The Alg. 2 iteration on a graph with the edge index (each edge streams
+    the shorter of its two Lemma 3 windows and looks the closing edge up):
+    counts for 1 / 6 / 32 thresholds with both counting visitors and records
+    bit-exact against the oracle, and equal to the table form's."""
+    name, n, s, d, k = case
+    G = ubt.Graph(n, s, d, k=k, undirected=True, edge_index=True)
+    for taus in (TAUS, SWEEP32, [0.7], [0.5]):
+        ob, ou = oracle.count_threshold(n, s, d, k, taus)
+        for vis in (0, 1):
+            with with_knobs(ubt, {"count_visitor": vis}):
+                gb, gu = G.count_aeo(taus)
+            assert np.array_equal(gb, ob) and np.array_equal(gu, ou), (name, len(taus), vis)
+        with with_knobs(ubt, {"edge_index": 0}):  # the table form on the same graph
+            gb, gu = G.count_aeo(taus)
+        assert np.array_equal(gb, ob) and np.array_equal(gu, ou), (name, len(taus), "tables")
+    for tau, which in [(0.5, 3), (0.75, 3), (0.9, 1), (0.9, 2)]:
+        ouvw, ocls, opb = oracle.enumerate_records(n, s, d, k, tau, which)
+        uvw, cls, pb = sort_records(G.enumerate_aeo(tau, which))
+        assert np.array_equal(uvw, ouvw) and np.array_equal(cls, ocls) and np.array_equal(pb, opb), (name, tau)
+    assert G.guard() == 0

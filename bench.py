@@ -239,7 +239,7 @@ def main():
     ap.add_argument("--no-cpu-baseline", dest="cpu", action="store_false", default=True)
     ap.add_argument("--only", default=None,
                     choices=["count", "count32", "count-unpruned", "worlds", "expected", "backward", "enumerate",
-                             "aeo", "edge-sampling", "vertex-sampling", "topk"],
+                             "aeo", "aeo-tables", "edge-sampling", "vertex-sampling", "topk"],
                     help="profiling driver: build the --workload graph, run one form of the query "
                          "--warmup + --steps times, print its mean time and exit")
     ap.add_argument("--workload", default=WORKLOAD, choices=["cl1m", "rmat22", "rmat20", "cl4m", "er2k"])
@@ -447,8 +447,8 @@ def profile_driver(ubt, args):
             return ubt.Graph(g.n, g.src, g.dst, p=torch.from_numpy(np.ascontiguousarray(p)).cuda())
         k = g.k if g.k is not None else synth.quantise(g.p)
         return ubt.Graph(g.n, g.src, g.dst, k=k,
-                         undirected=args.only in ("aeo", "edge-sampling", "vertex-sampling"),
-                         edge_index=args.only == "vertex-sampling")
+                         undirected=args.only in ("aeo", "aeo-tables", "edge-sampling", "vertex-sampling"),
+                         edge_index=args.only in ("aeo", "vertex-sampling"))
 
     # the knobs the benchmark would use (cached tunings only: no search here)
     G = build()
@@ -499,7 +499,8 @@ def profile_driver(ubt, args):
         "backward": lambda: G.expected_counts_backward_(gout, grad),
         "enumerate": lambda: ubt.lib().ubt_enumerate(G.handle, 0.9, 3, 1, cp(recbuf), cap, ctypes.byref(found),
                                                      None),
-        "aeo": lambda: G.count_aeo_([0.8], counts),
+        "aeo": lambda: G.count_aeo_([0.8], counts),          # edge-index form (graph built with the index)
+        "aeo-tables": lambda: G.count_aeo_([0.8], counts),   # owner-table form (no index)
         "edge-sampling": lambda: lfn(G.handle, cp(smp), 10000, t08.ctypes.data_as(ctypes.c_void_p), 1, cp(lb),
                                      cp(lu), cp(le), None),
         "vertex-sampling": lambda: lfn(G.handle, cp(smp), 10000, t08.ctypes.data_as(ctypes.c_void_p), 1, cp(lb),

@@ -63,7 +63,7 @@ QUERY_KNOBS: Dict[str, List[str]] = {
     "expected": ["hub_threshold", "block_work", "block_unit", "small_batch", "blocks_per_sm", "block_threads",
                  "warp_threads", "smem_table_max", "pull"],
     "worlds": ["world_words_per_pass", "hub_threshold", "block_work", "block_unit", "small_batch",
-               "blocks_per_sm"],
+               "blocks_per_sm", "long_tail", "long_min"],
     "batch": ["block_work", "small_batch", "warp_threads", "blocks_per_sm"],
 }
 ALL_KNOBS = {**BUILD_KNOBS, **RUN_KNOBS}

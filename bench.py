@@ -187,6 +187,14 @@ def make_graph(name):
     return synth.config_graph(name, seed=1)
 
 
+def workload_config(g, T, ws):
+    """The `config` of the benchmark line (both arms time this workload)."""
+    return {"workload": "cl1m: Chung-Lu n=1,000,000 gamma=2.1 mean-deg 20 cap 50,000, "
+                        "P+ ~ Beta(0.5,0.5) -> k/65536, 4 thresholds, pruned, one traversal",
+            "n": g.n, "m": g.m, "triangles": T, "taus": TAUS, "l2": "flushed between steps (512 MB write)",
+            "parallelism": "replicas" if ws > 1 else "single GPU"}
+
+
 def time_steps(fn, steps, warmup, flush=None):
     """W untimed warm-up calls, then `steps` calls each bracketed by CUDA
     events on the current stream, with an L2 flush before each (untimed)."""
@@ -215,18 +223,17 @@ def reference_arm(args):
     if rank != 0:
         return 0
     import oracle
-    import synth
-    # bounded sample of the workload: the same Chung-Lu recipe at n = 250,000
-    n = 250_000
-    s, d = synth.chung_lu(n, 2.1, 20.0, 50_000.0, 1)
-    k = synth.quantise(synth.p_beta(s.size, 0.5, 0.5, 1001))
-    T = oracle.num_triangles(n, s, d)
+    # the benchmark's own workload: one step is one oracle pass over the whole
+    # cl1m graph (about 4.5 s on one core, so the default 3 + 20 steps take
+    # under two minutes)
+    g = make_graph(WORKLOAD)
+    T = oracle.num_triangles(g.n, g.src, g.dst)
     for _ in range(args.warmup):
-        oracle.count_threshold(n, s, d, k, TAUS)
+        oracle.count_threshold(g.n, g.src, g.dst, g.k, TAUS)
     times = []
     for _ in range(args.steps):
         t0 = time.perf_counter()
-        oracle.count_threshold(n, s, d, k, TAUS)
+        oracle.count_threshold(g.n, g.src, g.dst, g.k, TAUS)
         times.append(time.perf_counter() - t0)
     ms = 1e3 * float(np.mean(times))
     v = T / (ms / 1e3)
@@ -234,11 +241,9 @@ def reference_arm(args):
         "impl": "reference", "metric": METRIC, "value": v, "unit": UNIT, "n_gpus": args.gpus,
         "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True,
         "scaling": "weak", "vs_baseline": None, "dtype": "int64", "data": "synthetic",
-        "config": {"workload": "cl250k (Chung-Lu n=250,000 sample of the cl1m recipe)", "taus": TAUS,
-                   "triangles": T, "m": int(s.size)},
+        "config": workload_config(g, T, 1),
         "cpu_baseline": {"value": v, "unit": UNIT, "cores": 1, "kind": "oracle",
-                         "sample": "Chung-Lu n=250,000 (same gamma/mean/cap/P+ recipe), 4 thresholds, "
-                                   "full graph per step"},
+                         "sample": "the whole cl1m graph per step (4 thresholds, one forward-listing pass)"},
         "e2e": {"value": v, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
     }
     print(json.dumps(line))
@@ -390,10 +395,7 @@ def main():
         "metric": METRIC, "value": job_throughput(T, t_step, ws), "unit": UNIT, "n_gpus": ws, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": 1e3 * t_step, "higher_is_better": True, "scaling": "weak",
         "vs_baseline": None, "dtype": "int64", "data": "synthetic",
-        "config": {"workload": "cl1m: Chung-Lu n=1,000,000 gamma=2.1 mean-deg 20 cap 50,000, "
-                               "P+ ~ Beta(0.5,0.5) -> k/65536, 4 thresholds, pruned, one traversal",
-                   "n": g.n, "m": g.m, "triangles": T, "taus": TAUS, "l2": "flushed between steps (512 MB write)",
-                   "parallelism": "replicas" if ws > 1 else "single GPU"},
+        "config": workload_config(g, T, ws),
         "roofline": roofline,
         "e2e": {"value": job_throughput(T, e2e_t, ws), "unit": UNIT, "h2d_bytes_per_step": 12 * g.m,
                 "d2h_bytes_per_step": 16 * len(TAUS), "ms_per_step": 1e3 * e2e_t,

@@ -101,13 +101,21 @@ class Clocks:
                 "reasons": sorted(reasons), "samples": len(sm)}
 
 
-def csrc_digest():
-    """Digest of the CUDA sources: ncu counters apply only to the kernels they were taken on."""
+# the sources the counting traversal (k_traverse) and the graph layout it
+# reads are built from; the AEO, sampling, world and no-allocation kernels
+# live in the others
+COUNT_SOURCES = ("ubt_api.cu", "ubt_build.cu", "ubt_internal.cuh", "ubt_query.cu", "ubt_scan.cu",
+                 "ubt_traverse.cuh")
+
+
+def csrc_digest(files=None):
+    """Digest of the CUDA sources (all, or the named files): ncu counters
+    apply only to the kernels they were taken on."""
     import hashlib
     h = hashlib.sha256()
     d = os.path.join(ROOT, "paper_2602_14084_gb300", "csrc")
     for f in sorted(os.listdir(d)):
-        if f.endswith((".cu", ".cuh")):
+        if f.endswith((".cu", ".cuh")) and (files is None or f in files):
             with open(os.path.join(d, f), "rb") as fh:
                 h.update(f.encode() + fh.read())
     return h.hexdigest()[:16]
@@ -153,7 +161,7 @@ def ncu_traffic(kernel, workload):
             rec = json.load(f).get("%s %s" % (kernel, workload))
     except Exception:
         return None
-    if not rec or rec.get("csrc_digest") != csrc_digest():
+    if not rec or rec.get("count_sources_digest") != csrc_digest(COUNT_SOURCES):
         return None
     return rec["dram_bytes_per_launch"]
 

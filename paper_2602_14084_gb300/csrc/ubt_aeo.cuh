@@ -325,11 +325,40 @@ __device__ __forceinline__ bool aeo_ix_find(const AeoIxArgs& a, uint32_t o, uint
 
 // entry s-w of the streamed window: the closing edge o-w, if it exists, lies
 // after e in o's row and passes Lemma 3
-__device__ __forceinline__ bool aeo_ix_hit(const AeoIxArgs& a, uint32_t o, uint32_t s, uint32_t w, int64_t aq,
-                                           int64_t cut, uint32_t& qow) {
-  if (w == o || !aeo_ix_find(a, o, w, qow)) return false;
+__device__ __forceinline__ bool aeo_ix_keep(const AeoIxArgs& a, uint32_t s, uint32_t w, uint32_t qow, int64_t aq,
+                                            int64_t cut) {
   const int64_t oq = qabs(qow);
   return (oq < aq || (oq == aq && w > s)) && (a.L == 0 || oq * cut >= a.L);
+}
+
+// Two lanes' worth of lookups at once: both home slots are read before
+// either is examined (at most a quarter of the slots are used, so nearly
+// every lookup ends there); the rare longer probe continues alone.
+__device__ __forceinline__ void aeo_ix_hit2(const AeoIxArgs& a, const bool (&act)[2], const uint32_t (&o)[2],
+                                            const uint32_t (&s)[2], const uint32_t (&w)[2], const int64_t (&aq)[2],
+                                            const int64_t (&cut)[2], bool (&hit)[2], uint32_t (&qow)[2]) {
+  uint64_t k[2], h[2];
+  uint4 sl[2];
+#pragma unroll
+  for (int i = 0; i < 2; i++) {
+    k[i] = edge_index_key(o[i], w[i]);
+    h[i] = edge_index_home(k[i], a.eshift);
+    sl[i] = (act[i] && w[i] != o[i]) ? a.eslots[h[i]] : make_uint4(0xFFFFFFFFu, 0xFFFFFFFFu, 0u, 0u);
+  }
+#pragma unroll
+  for (int i = 0; i < 2; i++) {
+    hit[i] = false;
+    qow[i] = 0;
+    if (!act[i] || w[i] == o[i]) continue;
+    const uint64_t key = ((uint64_t)sl[i].y << 32) | sl[i].x;
+    bool found = key == k[i];
+    if (found) {
+      qow[i] = sl[i].z;
+    } else if (key != kEdgeIndexEmpty) {  // the home slot holds another edge: probe on
+      found = aeo_ix_find(a, o[i], w[i], qow[i]);
+    }
+    hit[i] = found && aeo_ix_keep(a, s[i], w[i], qow[i], aq[i], cut[i]);
+  }
 }
 
 template <class V>
@@ -384,12 +413,27 @@ __global__ void __launch_bounds__(512, 2) k_aeo_index(AeoIxArgs a, typename V::P
       const uint32_t vsj = __shfl_sync(kFull, vs, j), dvj = __shfl_sync(kFull, dv, j);
       const uint32_t qj = __shfl_sync(kFull, qe, j);
       const long long aqj = __shfl_sync(kFull, (long long)aq, j), cj = __shfl_sync(kFull, (long long)cut, j);
-      for (uint32_t off = 0; off < dvj; off += 32) {
-        const uint32_t i = off + lane;
-        const uint64_t ew = i < dvj ? a.uadj[vsj + i] : 0ull;
-        uint32_t qow = 0;
-        const bool hit = i < dvj && aeo_ix_hit(a, oj, sj, adj_col(ew), aqj, cj, qow);
-        vis.step(hit, oj, sj, adj_col(ew), qj, qow, adj_valbits(ew), 0u, 0u, vsj + i);
+      for (uint32_t off = 0; off < dvj; off += 64) {
+        bool act[2], hit[2];
+        uint32_t oo[2], ss[2], ww[2], qow[2];
+        int64_t aa[2], cc[2];
+        uint64_t ew[2];
+#pragma unroll
+        for (int u = 0; u < 2; u++) {
+          const uint32_t i = off + 32 * u + lane;
+          act[u] = i < dvj;
+          ew[u] = act[u] ? a.uadj[vsj + i] : 0ull;
+          oo[u] = oj;
+          ss[u] = sj;
+          ww[u] = adj_col(ew[u]);
+          aa[u] = aqj;
+          cc[u] = cj;
+        }
+        aeo_ix_hit2(a, act, oo, ss, ww, aa, cc, hit, qow);
+#pragma unroll
+        for (int u = 0; u < 2; u++)
+          if (u == 0 || off + 32 < dvj)
+            vis.step(hit[u], oj, sj, ww[u], qj, qow[u], adj_valbits(ew[u]), 0u, 0u, vsj + off + 32 * u + lane);
       }
     }
     // short windows: concatenated, one entry per lane per step
@@ -402,25 +446,37 @@ __global__ void __launch_bounds__(512, 2) k_aeo_index(AeoIxArgs a, typename V::P
     }
     const uint32_t total = __shfl_sync(kFull, incl, 31);
     const uint32_t excl = incl - ds;
-    for (uint32_t base = 0; base < total; base += 32) {
-      const uint32_t f = base + lane;
-      const bool act = f < total;
-      int j = 0;
+    for (uint32_t base = 0; base < total; base += 64) {
+      bool act[2], hit[2];
+      uint32_t oo[2], ss[2], ww[2], qq[2], pos[2], qow[2];
+      int64_t aa[2], cc[2];
+      uint64_t ew[2];
 #pragma unroll
-      for (int b = 16; b > 0; b >>= 1) {
-        const uint32_t tj = __shfl_sync(kFull, incl, j + b - 1);
-        if (tj <= f) j += b;
+      for (int u = 0; u < 2; u++) {
+        const uint32_t f = base + 32 * u + lane;
+        act[u] = f < total;
+        int j = 0;
+#pragma unroll
+        for (int b = 16; b > 0; b >>= 1) {
+          const uint32_t tj = __shfl_sync(kFull, incl, j + b - 1);
+          if (tj <= f) j += b;
+        }
+        j = j > 31 ? 31 : j;
+        const uint32_t vsj = __shfl_sync(kFull, vs, j), exj = __shfl_sync(kFull, excl, j);
+        oo[u] = __shfl_sync(kFull, o, j);
+        ss[u] = __shfl_sync(kFull, sv, j);
+        qq[u] = __shfl_sync(kFull, qe, j);
+        aa[u] = __shfl_sync(kFull, (long long)aq, j);
+        cc[u] = __shfl_sync(kFull, (long long)cut, j);
+        pos[u] = vsj + (f - exj);
+        ew[u] = act[u] ? a.uadj[pos[u]] : 0ull;
+        ww[u] = adj_col(ew[u]);
       }
-      j = j > 31 ? 31 : j;
-      const uint32_t vsj = __shfl_sync(kFull, vs, j), exj = __shfl_sync(kFull, excl, j);
-      const uint32_t oj = __shfl_sync(kFull, o, j), sj = __shfl_sync(kFull, sv, j);
-      const uint32_t qj = __shfl_sync(kFull, qe, j);
-      const long long aqj = __shfl_sync(kFull, (long long)aq, j), cj = __shfl_sync(kFull, (long long)cut, j);
-      const uint32_t pos = vsj + (f - exj);
-      const uint64_t ew = act ? a.uadj[pos] : 0ull;
-      uint32_t qow = 0;
-      const bool hit = act && aeo_ix_hit(a, oj, sj, adj_col(ew), aqj, cj, qow);
-      vis.step(hit, oj, sj, adj_col(ew), qj, qow, adj_valbits(ew), 0u, 0u, pos);
+      aeo_ix_hit2(a, act, oo, ss, ww, aa, cc, hit, qow);
+#pragma unroll
+      for (int u = 0; u < 2; u++)
+        if (u == 0 || base + 32 < total)
+          vis.step(hit[u], oo[u], ss[u], ww[u], qq[u], qow[u], adj_valbits(ew[u]), 0u, 0u, pos[u]);
     }
   }
   __syncthreads();

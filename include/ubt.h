@@ -103,9 +103,12 @@ typedef struct {
      * ubt_edge_local_counts and ubt_vertex_local_counts need.
      * UBT_OPT_EDGE_INDEX (with UBT_OPT_UNDIRECTED): also build a hash index
      * of the edges ({u, w} -> edge value; 16 bytes per slot, the power of two
-     * >= 4m slots).  ubt_vertex_local_counts and ubt_vertex_topk then look a
-     * neighbour pair up in it instead of streaming a neighbour's row when that
-     * row is much longer than the pairs left to check (same results). */
+     * >= 4m slots).  Same results, different work: ubt_vertex_local_counts
+     * and ubt_vertex_topk look a neighbour pair up in it instead of streaming
+     * a neighbour's row when that row is much longer than the pairs left to
+     * check; ubt_count_aeo and ubt_enumerate_aeo stream, for each edge, the
+     * shorter of its two Lemma 3 windows and look the closing edge up, with
+     * no owner tables (knob "edge_index" = 0 keeps the table forms). */
     int64_t flags;
 } ubt_graph_opts;
 
@@ -356,7 +359,9 @@ ubt_status ubt_graph_export_pairs(const ubt_graph* g, uint32_t* h_pair_ptr, uint
  * edge below a(t) (Lemma 2) and every partner edge below Lemma 3's cutoff for
  * the smallest t; each triangle is found from its first edge in that order.
  * Same arguments and results as ubt_count_threshold with prune = 1.  Needs a
- * graph built with UBT_OPT_UNDIRECTED (else UBT_ERR_UNSUPPORTED).
+ * graph built with UBT_OPT_UNDIRECTED (else UBT_ERR_UNSUPPORTED); with
+ * UBT_OPT_EDGE_INDEX each edge's partners come from the shorter of its two
+ * windows and the edge index, else from the owner's table.
  */
 ubt_status ubt_count_aeo(ubt_graph* g, const double* h_tau, int32_t n_tau, int64_t* d_counts, void* stream);
 
@@ -473,10 +478,12 @@ ubt_status ubt_topk(ubt_graph* g, int64_t K, int32_t which, ubt_tri_rec* d_out, 
  *   "long_tail"       1 (default): the last < 64 entries of a long list are
  *                     concatenated with the short lists; 0: the warp streams
  *                     them itself with idle lanes
- *   "edge_index"      vertex local counts / per-vertex top-k on a graph with
- *                     UBT_OPT_EDGE_INDEX: 0 never use the index, 1 (default)
- *                     use it for a neighbour whose row is more than 8 times
- *                     longer than the pairs left to check, 2 always
+ *   "edge_index"      on a graph with UBT_OPT_EDGE_INDEX: 0 never use the
+ *                     index; 1 (default) vertex local counts / per-vertex
+ *                     top-k use it for a neighbour whose row is more than 8
+ *                     times longer than the pairs left to check, and the AEO
+ *                     calls use its form; 2 as 1, the vertex queries for every
+ *                     neighbour
  *   "vertex_split"    ubt_vertex_local_counts on a graph with the edge index:
  *                     samples whose pruned row is longer (default 64) are
  *                     spread over the warps of all blocks by a second launch

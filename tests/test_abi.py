@@ -75,3 +75,46 @@ def test_workspace_size_argument_checks(L):
     assert L.ubt_create_graph(10, 5, 256, 256, 256, 256, 0, None, 256, 1 << 20, None, ctypes.byref(h)) == -1
     assert L.ubt_count_threshold(None, None, 1, 0, None, None) == -1
     assert L.ubt_destroy_graph(None) == -1
+
+
+def test_traversal_and_index_knobs(L):
+    import paper_2602_14084_gb300 as ubt
+    knobs = {"long_min": (1, 1 << 20, [0, (1 << 20) + 1]), "long_tail": (0, 1, [-1, 2]),
+             "edge_index": (0, 2, [-1, 3]), "vertex_split": (1, 1 << 32, [0, (1 << 32) + 1])}
+    for name, (lo, hi, bad) in knobs.items():
+        old = ubt.get_tuning(name)
+        try:
+            for v in (lo, hi):
+                ubt.set_tuning(name, v)
+                assert ubt.get_tuning(name) == v, name
+            for v in bad:
+                with pytest.raises(ubt.UbtError):
+                    ubt.set_tuning(name, v)
+                assert ubt.get_tuning(name) == hi, name  # a rejected value leaves the knob as it was
+        finally:
+            ubt.set_tuning(name, old)
+
+
+def test_workspace_grows_with_the_options(L):
+    """The undirected rows add the AEO adjacency; the edge index adds 16
+    bytes per slot for the power of two >= 4m slots."""
+    import paper_2602_14084_gb300 as ubt
+    n, m = 100000, 1000000
+
+    def size(flags):
+        opts = ubt._GraphOpts()
+        opts.flags = flags
+        sz = ctypes.c_size_t(0)
+        assert L.ubt_graph_workspace_size(n, m, 0, ctypes.byref(opts), ctypes.byref(sz)) == 0
+        return sz.value
+
+    plain, und, idx = size(0), size(ubt.UBT_OPT_UNDIRECTED), size(ubt.UBT_OPT_UNDIRECTED | ubt.UBT_OPT_EDGE_INDEX)
+    slots = 1 << (4 * m - 1).bit_length()
+    assert und > plain + 2 * m * (8 + 4 + 4 + 4)   # uadj, ueid, umir, uepos at least
+    assert idx - und >= 16 * slots and idx - und < 16 * slots + 4096
+    # the index without the undirected rows is refused when the graph is created
+    opts = ubt._GraphOpts()
+    opts.flags = ubt.UBT_OPT_EDGE_INDEX
+    h = ctypes.c_void_p(0)
+    assert L.ubt_create_graph(10, 0, None, None, None, None, 0, ctypes.byref(opts), 256, 1 << 20, None,
+                              ctypes.byref(h)) == -1

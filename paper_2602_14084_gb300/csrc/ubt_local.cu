@@ -77,31 +77,78 @@ __device__ __forceinline__ bool use_index(const EdgeIndex& ix, uint32_t cand, ui
 //   Absolute Edge Order, so that is |q_vw| < |q_va|, or equal and w > a --
 //   and lies in v's Lemma 2 prefix (|q_vw| 2^30 >= L, L = 0: all).
 // found(P, w) receives every triangle.
+// Two lookups of one lane at once: both home slots are read before either
+// is examined (at most a quarter of the slots are used, so nearly every
+// lookup ends there); the rare longer probe continues alone.
+__device__ __forceinline__ void edge_index_find2(const EdgeIndex& ix, const bool (&act)[2], const uint32_t (&a)[2],
+                                                 const uint32_t (&b)[2], bool (&hit)[2], uint32_t (&val)[2],
+                                                 Scratch* sc) {
+  uint64_t k[2];
+  uint4 sl[2];
+#pragma unroll
+  for (int i = 0; i < 2; i++) {
+    k[i] = edge_index_key(a[i], b[i]);
+    sl[i] = act[i] ? ix.slots[edge_index_home(k[i], ix.shift)] : make_uint4(0xFFFFFFFFu, 0xFFFFFFFFu, 0u, 0u);
+  }
+#pragma unroll
+  for (int i = 0; i < 2; i++) {
+    hit[i] = false;
+    val[i] = 0;
+    if (!act[i]) continue;
+    const uint64_t key = ((uint64_t)sl[i].y << 32) | sl[i].x;
+    if (key == k[i]) {
+      hit[i] = true;
+      val[i] = sl[i].z;
+    } else if (key != kEdgeIndexEmpty) {  // the home slot holds another edge: probe on
+      hit[i] = edge_index_find(ix, a[i], b[i], val[i], sc);
+    }
+  }
+}
+
 template <class F>
 __device__ __forceinline__ void index_pairs(const EdgeIndex& ix, const uint64_t* __restrict__ uadj, uint32_t v,
                                             uint32_t av, uint32_t qa, uint32_t pa, uint32_t rend, uint32_t s0,
                                             uint32_t len, int64_t L, int lane, Scratch* sc, F&& found) {
   if (rend - (pa + 1) <= len) {
-    for (uint32_t b0 = pa + 1; b0 < rend; b0 += 32) {
-      const uint32_t pos = b0 + lane;
-      const bool act = pos < rend;
-      const uint64_t eb = act ? uadj[pos] : 0ull;
-      uint32_t qab = 0;
-      if (act && edge_index_find(ix, av, adj_col(eb), qab, sc))
-        found((long long)((int32_t)qa * (int32_t)adj_valbits(eb)) * (long long)(int32_t)qab, adj_col(eb));
+    for (uint32_t b0 = pa + 1; b0 < rend; b0 += 64) {
+      bool act[2], hit[2];
+      uint32_t oo[2], ww[2], qab[2];
+      uint64_t eb[2];
+#pragma unroll
+      for (int u = 0; u < 2; u++) {
+        const uint32_t pos = b0 + 32 * u + lane;
+        act[u] = pos < rend;
+        eb[u] = act[u] ? uadj[pos] : 0ull;
+        oo[u] = av;
+        ww[u] = adj_col(eb[u]);
+      }
+      edge_index_find2(ix, act, oo, ww, hit, qab, sc);
+#pragma unroll
+      for (int u = 0; u < 2; u++)
+        if (hit[u])
+          found((long long)((int32_t)qa * (int32_t)adj_valbits(eb[u])) * (long long)(int32_t)qab[u], ww[u]);
     }
   } else {
     const int64_t aq = qabs(qa);
-    for (uint32_t b0 = s0; b0 < s0 + len; b0 += 32) {
-      const uint32_t pos = b0 + lane;
-      const bool act = pos < s0 + len;
-      const uint64_t ew = act ? uadj[pos] : 0ull;
-      const uint32_t w = adj_col(ew);
-      uint32_t qvw = 0;
-      if (act && w != v && edge_index_find(ix, v, w, qvw, sc)) {
-        const int64_t wq = qabs(qvw);
-        if ((wq < aq || (wq == aq && w > av)) && (L == 0 || wq * (1ll << 30) >= L))
-          found((long long)((int32_t)qa * (int32_t)qvw) * (long long)(int32_t)adj_valbits(ew), w);
+    for (uint32_t b0 = s0; b0 < s0 + len; b0 += 64) {
+      bool act[2], hit[2];
+      uint32_t oo[2], ww[2], qvw[2];
+      uint64_t ew[2];
+#pragma unroll
+      for (int u = 0; u < 2; u++) {
+        const uint32_t pos = b0 + 32 * u + lane;
+        ew[u] = pos < s0 + len ? uadj[pos] : 0ull;
+        ww[u] = adj_col(ew[u]);
+        act[u] = pos < s0 + len && ww[u] != v;
+        oo[u] = v;
+      }
+      edge_index_find2(ix, act, oo, ww, hit, qvw, sc);
+#pragma unroll
+      for (int u = 0; u < 2; u++) {
+        if (!hit[u]) continue;
+        const int64_t wq = qabs(qvw[u]);
+        if ((wq < aq || (wq == aq && ww[u] > av)) && (L == 0 || wq * (1ll << 30) >= L))
+          found((long long)((int32_t)qa * (int32_t)qvw[u]) * (long long)(int32_t)adj_valbits(ew[u]), ww[u]);
       }
     }
   }

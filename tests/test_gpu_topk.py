@@ -183,3 +183,26 @@ def test_vertex_topk_chunked_tables_with_edge_index(ubt, mode):
     finally:
         for x, v in old.items():
             ubt.set_tuning(x, v)
+
+
+@pytest.mark.parametrize("table_max, n_list", [(64, 3000), (4096, 3000), (64, 200)])
+def test_vertex_topk_every_vertex(ubt, table_max, n_list):
+    """Every vertex of the graph (or 200 drawn with repeats), with tables of
+    64 slots (most rows longer than one table, pairs from the edge index) and
+    of 4,096: the answers equal the oracle's for each vertex."""
+    s, d = mixed_graph(3000, 30000, 21)
+    k = synth.k_uniform(s.size, 22)
+    old = ubt.get_tuning("smem_table_max")
+    try:
+        ubt.set_tuning("smem_table_max", table_max)
+        G = ubt.Graph(3000, s, d, k=k, undirected=True, edge_index=True)
+        verts = np.arange(3000, dtype=np.uint32) if n_list == 3000 else \
+            synth.rng(9).integers(0, 3000, size=n_list).astype(np.uint32)
+        got = G.vertex_topk(verts, 8, 1)
+        want = oracle_vertex_topk(3000, s, d, k, 8, 1, verts)
+        for v, g_rec, (w_uvw, w_pb) in zip(verts, got, want):
+            assert np.array_equal(g_rec["p_bal"], w_pb), v
+            assert np.array_equal(np.stack([g_rec["u"], g_rec["v"], g_rec["w"]], axis=1).astype(np.uint32), w_uvw), v
+        assert G.guard() == 0
+    finally:
+        ubt.set_tuning("smem_table_max", old)

@@ -408,7 +408,10 @@ def main():
         "e2e": {"value": job_throughput(T, e2e_t, ws), "unit": UNIT, "h2d_bytes_per_step": 12 * g.m,
                 "d2h_bytes_per_step": 16 * len(TAUS), "ms_per_step": 1e3 * e2e_t,
                 "includes": "H2D of src/dst/k, graph build (validate, orient, CSR, sort), query, D2H"},
-        "gpu_launches": 2 * args.steps,
+        # per query: the block-task traversal (giant / hub owners), the
+        # warp-task traversal (medium owners; this workload has both) and the
+        # kernel that turns the bins into counts
+        "gpu_launches": args.steps * ((1 if info["hub_vertices"] > 0 else 0) + 1 + 1),
         "clocks": clk,
         "build_ms": build_ms,
         "tuning": {k: tuning[k] for k in ("source", "config", "key") if k in tuning},

@@ -17,6 +17,8 @@ Parity status of each function (what pins it, in the tests under
   expected_fixed / expected_real -- the same brute force (exact rationals).
   grad_real                      -- central finite differences (exact: the
       expected count is affine in each p_e); closed form on K_n.
+  ResidentGraph.count            -- equals count_threshold (the serial pass) on
+      several graphs for any thread count; its samples partition the counts.
   philox4x64_10                  -- numpy's Philox bit generator.
   local_counts                   -- sums over edges / vertices = 3 x the counts;
       brute-force classification in exact rationals; closed forms on K_n.
@@ -48,11 +50,15 @@ class OracleError(RuntimeError):
 
 
 def build(force: bool = False) -> str:
-    """Compile the oracle (plain C, -O2) into liboracle.so; returns its path."""
+    """Compile the oracle (plain C, -O2, with OpenMP where the compiler has
+    it, else single-threaded) into liboracle.so; returns its path."""
     if force or not os.path.exists(_LIB) or os.path.getmtime(_LIB) < os.path.getmtime(_SRC):
         tmp = _LIB + ".%d.tmp" % os.getpid()
         cc = os.environ.get("CC", "gcc")
-        subprocess.check_call([cc, "-O2", "-std=c11", "-fPIC", "-shared", "-o", tmp, _SRC, "-lm"])
+        base = [cc, "-O2", "-std=c11", "-fPIC", "-shared", "-o", tmp, _SRC, "-lm"]
+        r = subprocess.run(base[:1] + ["-fopenmp"] + base[1:], capture_output=True)
+        if r.returncode != 0:
+            subprocess.check_call(base)
         os.replace(tmp, _LIB)
     return _LIB
 
@@ -84,6 +90,16 @@ def _L():
         lib.ubto_world_word.argtypes = [ctypes.c_uint64, ctypes.c_uint32, ctypes.c_uint32, ctypes.c_uint32]
         lib.ubto_local_counts.restype = ctypes.c_int
         lib.ubto_local_counts.argtypes = [I64, I64, P, P, P, ctypes.c_int, P, P, P, P, P]
+        lib.ubto_sample_class.restype = I64
+        lib.ubto_sample_class.argtypes = [I64, I64]
+        lib.ubto_threads.restype = ctypes.c_int
+        lib.ubto_threads.argtypes = []
+        lib.ubto_graph_new.restype = P
+        lib.ubto_graph_new.argtypes = [I64, I64, P, P, ctypes.POINTER(ctypes.c_int)]
+        lib.ubto_graph_free.restype = None
+        lib.ubto_graph_free.argtypes = [P]
+        lib.ubto_graph_count.restype = I64
+        lib.ubto_graph_count.argtypes = [P, P, ctypes.c_int, P, I64, I64, ctypes.c_int, P, P]
         lib.ubto_world_counts.restype = ctypes.c_int
         lib.ubto_world_counts.argtypes = [I64, I64, P, P, P, P, ctypes.c_uint64, ctypes.c_int, P, P]
         _lib = lib
@@ -131,6 +147,53 @@ def count_threshold(n, src, dst, k, taus):
     _check(_L().ubto_count_threshold(n, s.size, _ptr(s), _ptr(d), _ptr(kk), t.size, _ptr(t),
                                      _ptr(bal), _ptr(unbal)))
     return bal, unbal
+
+
+def threads() -> int:
+    """Threads the oracle's multi-threaded count can use (1 without OpenMP)."""
+    return int(_L().ubto_threads())
+
+
+def sample_class(u, sample_mod) -> int:
+    """The sample a vertex u belongs to in ResidentGraph.count (a hash of u mod sample_mod)."""
+    return int(_L().ubto_sample_class(int(u), int(sample_mod)))
+
+
+class ResidentGraph:
+    """The oracle's forward lists built once, for repeated counting queries
+    (the CPU baseline times queries on a built graph, as the GPU side does).
+    count() runs Alg. 1's outer loop over `threads` threads; with sample_mod
+    > 1 it visits only the u with sample_class(u, sample_mod) == sample_rem
+    (the triangles whose earliest vertex in Node Order is such a u)."""
+
+    def __init__(self, n, src, dst):
+        s, d = _u32(src), _u32(dst)
+        st = ctypes.c_int(0)
+        self.m = s.size
+        self._g = _L().ubto_graph_new(n, s.size, _ptr(s), _ptr(d), ctypes.byref(st))
+        _check(st.value)
+
+    def count(self, k, taus, threads=1, sample_mod=1, sample_rem=0):
+        """(bal[n_tau], unbal[n_tau], triangles visited)."""
+        kk = _u32(k)
+        assert kk.size == self.m
+        t = np.ascontiguousarray(np.atleast_1d(np.asarray(taus, dtype=np.float64)))
+        bal = np.zeros(t.size, dtype=np.int64)
+        unbal = np.zeros(t.size, dtype=np.int64)
+        tri = _check(_L().ubto_graph_count(self._g, _ptr(kk), t.size, _ptr(t), int(sample_mod), int(sample_rem),
+                                           int(threads), _ptr(bal), _ptr(unbal)))
+        return bal, unbal, int(tri)
+
+    def close(self):
+        if getattr(self, "_g", None):
+            _L().ubto_graph_free(self._g)
+            self._g = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
 
 
 def enumerate_records(n, src, dst, k, tau, which=3):

@@ -144,40 +144,46 @@ static int fgraph_build(fgraph* g, int64_t n, int64_t m, const uint32_t* src, co
 typedef struct { uint32_t a, b, c, e_ab, e_ac, e_bc; } tri_t;
 typedef void (*tri_visit)(void* ctx, const tri_t* t);
 
-/* Alg. 1 framework: for u, for v in N>(u), for w in N>(u) n N>(v) (merge of
- * the two id-sorted lists).  Returns the number of triangles. */
-static int64_t for_each_triangle(const fgraph* g, tri_visit fn, void* ctx) {
+/* Alg. 1's inner loops for one u: for v in N>(u), for w in N>(u) n N>(v)
+ * (merge of the two id-sorted lists).  Returns the number of triangles. */
+static int64_t triangles_from(const fgraph* g, int64_t u, tri_visit fn, void* ctx) {
     int64_t count = 0;
-    for (int64_t u = 0; u < g->n; u++) {
-        int64_t us = g->off[u], ue = g->off[u + 1];
-        for (int64_t iv = us; iv < ue; iv++) {
-            uint32_t v = g->nbr[iv];
-            uint32_t e_uv = g->eix[iv];
-            int64_t i = us, j = g->off[v], je = g->off[v + 1];
-            while (i < ue && j < je) {
-                if (g->nbr[i] < g->nbr[j]) i++;
-                else if (g->nbr[i] > g->nbr[j]) j++;
-                else {
-                    uint32_t w = g->nbr[i];
-                    uint32_t e_uw = g->eix[i], e_vw = g->eix[j];
-                    if (fn) {
-                        /* sort (u, v, w) by id, carrying the opposite-edge labels */
-                        uint32_t x[3] = {(uint32_t)u, v, w};
-                        /* edge between x[p] and x[q] for p<q */
-                        uint32_t e01 = e_uv, e02 = e_uw, e12 = e_vw;
-                        /* bubble sort of three with edge relabelling */
-                        if (x[0] > x[1]) { uint32_t t = x[0]; x[0] = x[1]; x[1] = t; t = e02; e02 = e12; e12 = t; }
-                        if (x[1] > x[2]) { uint32_t t = x[1]; x[1] = x[2]; x[2] = t; t = e01; e01 = e02; e02 = t; }
-                        if (x[0] > x[1]) { uint32_t t = x[0]; x[0] = x[1]; x[1] = t; t = e02; e02 = e12; e12 = t; }
-                        tri_t tr = {x[0], x[1], x[2], e01, e02, e12};
-                        fn(ctx, &tr);
-                    }
-                    count++;
-                    i++; j++;
+    int64_t us = g->off[u], ue = g->off[u + 1];
+    for (int64_t iv = us; iv < ue; iv++) {
+        uint32_t v = g->nbr[iv];
+        uint32_t e_uv = g->eix[iv];
+        int64_t i = us, j = g->off[v], je = g->off[v + 1];
+        while (i < ue && j < je) {
+            if (g->nbr[i] < g->nbr[j]) i++;
+            else if (g->nbr[i] > g->nbr[j]) j++;
+            else {
+                uint32_t w = g->nbr[i];
+                uint32_t e_uw = g->eix[i], e_vw = g->eix[j];
+                if (fn) {
+                    /* sort (u, v, w) by id, carrying the opposite-edge labels */
+                    uint32_t x[3] = {(uint32_t)u, v, w};
+                    /* edge between x[p] and x[q] for p<q */
+                    uint32_t e01 = e_uv, e02 = e_uw, e12 = e_vw;
+                    /* bubble sort of three with edge relabelling */
+                    if (x[0] > x[1]) { uint32_t t = x[0]; x[0] = x[1]; x[1] = t; t = e02; e02 = e12; e12 = t; }
+                    if (x[1] > x[2]) { uint32_t t = x[1]; x[1] = x[2]; x[2] = t; t = e01; e01 = e02; e02 = t; }
+                    if (x[0] > x[1]) { uint32_t t = x[0]; x[0] = x[1]; x[1] = t; t = e02; e02 = e12; e12 = t; }
+                    tri_t tr = {x[0], x[1], x[2], e01, e02, e12};
+                    fn(ctx, &tr);
                 }
+                count++;
+                i++; j++;
             }
         }
     }
+    return count;
+}
+
+/* Alg. 1 framework: for u (every vertex), the loops above.  Returns the
+ * number of triangles. */
+static int64_t for_each_triangle(const fgraph* g, tri_visit fn, void* ctx) {
+    int64_t count = 0;
+    for (int64_t u = 0; u < g->n; u++) count += triangles_from(g, u, fn, ctx);
     return count;
 }
 
@@ -288,6 +294,88 @@ int ubto_count_threshold(int64_t n, int64_t m, const uint32_t* src, const uint32
     }
     free(tb); free(tu);
     return rc;
+}
+
+/* ------------------------------------------------------------------------ */
+/* A built graph kept between queries, counted by several threads            */
+/* ------------------------------------------------------------------------ */
+
+/* The benchmark's CPU arm times queries on a graph already built, as the GPU
+ * arm does: ubto_graph_new builds the forward lists once (validating the
+ * edge list as fgraph_build does) and ubto_graph_count answers the counting
+ * problem (Def. UBTC) on it.  The outer loop of Alg. 1 (over u) is split
+ * among OpenMP threads; each thread counts into its own arrays, which are
+ * added at the end, so the counts do not depend on the thread count.  With
+ * sample_mod > 1 only the u with h(u) % sample_mod == sample_rem are visited,
+ * h(u) = bits 40..63 of u * 0x9E3779B97F4A7C15 (a multiplicative hash, so that
+ * a sample is spread over the id range): exactly the triangles whose earliest
+ * vertex in Node Order is such a u (the samples rem = 0 .. mod-1 partition
+ * the triangles). */
+#ifdef _OPENMP
+#include <omp.h>
+#endif
+
+int64_t ubto_sample_class(int64_t u, int64_t sample_mod) {
+    return (int64_t)((((uint64_t)u * 0x9E3779B97F4A7C15ULL) >> 40) % (uint64_t)sample_mod);
+}
+
+int ubto_threads(void) {
+#ifdef _OPENMP
+    return omp_get_max_threads();
+#else
+    return 1;
+#endif
+}
+
+void* ubto_graph_new(int64_t n, int64_t m, const uint32_t* src, const uint32_t* dst, int* status) {
+    fgraph* g = (fgraph*)malloc(sizeof(fgraph));
+    if (!g) { *status = OR_NOMEM; return NULL; }
+    *status = fgraph_build(g, n, m, src, dst);
+    if (*status != OR_OK) { free(g); return NULL; }
+    return g;
+}
+
+void ubto_graph_free(void* g) {
+    if (!g) return;
+    fgraph_free((fgraph*)g);
+    free(g);
+}
+
+/* Returns the number of triangles visited (or -status); bal / unbal as in
+ * ubto_count_threshold, over the sampled u only. */
+int64_t ubto_graph_count(void* gp, const uint32_t* k, int n_tau, const double* tau, int64_t sample_mod,
+                         int64_t sample_rem, int threads, int64_t* bal, int64_t* unbal) {
+    const fgraph* g = (const fgraph*)gp;
+    int rc = check_k(g->m, k);
+    if (rc != OR_OK) return rc;
+    if (n_tau < 1 || sample_mod < 1 || sample_rem < 0 || sample_rem >= sample_mod) return OR_BAD_TAU;
+    uint64_t* tb = (uint64_t*)malloc(sizeof(uint64_t) * (size_t)n_tau);
+    uint64_t* tu = (uint64_t*)malloc(sizeof(uint64_t) * (size_t)n_tau);
+    if (!tb || !tu) { free(tb); free(tu); return OR_NOMEM; }
+    for (int i = 0; i < n_tau && rc == OR_OK; i++) rc = tau_levels(tau[i], &tb[i], &tu[i]);
+    if (rc != OR_OK) { free(tb); free(tu); return rc; }
+    for (int i = 0; i < n_tau; i++) { bal[i] = 0; unbal[i] = 0; }
+    int64_t total = 0;
+    if (threads < 1) threads = 1;
+#pragma omp parallel num_threads(threads) reduction(+ : total)
+    {
+        int64_t* b = (int64_t*)calloc((size_t)n_tau, sizeof(int64_t));
+        int64_t* u = (int64_t*)calloc((size_t)n_tau, sizeof(int64_t));
+        count_ctx c = {k, n_tau, tb, tu, b, u};
+        if (b && u) {
+#pragma omp for schedule(dynamic, 64)
+            for (int64_t x = 0; x < g->n; x++)
+                if (ubto_sample_class(x, sample_mod) == sample_rem) total += triangles_from(g, x, visit_count, &c);
+#pragma omp critical
+            for (int i = 0; i < n_tau; i++) { bal[i] += b[i]; unbal[i] += u[i]; }
+        } else {
+#pragma omp critical
+            rc = OR_NOMEM;
+        }
+        free(b); free(u);
+    }
+    free(tb); free(tu);
+    return rc != OR_OK ? rc : total;
 }
 
 typedef struct {

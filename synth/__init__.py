@@ -484,8 +484,9 @@ def config_graph(name: str, seed: int = 1) -> Graph:
     rmat20    -- R-MAT scale 20, edge factor 16, k ~ U{0..65536}.
     cl4m      -- Chung-Lu n=4e6, gamma=2.3, mean degree 20, max 50,000,
                  p ~ U[0,1] float32.
-    Small variants for tests: ``rmat<s>`` for any scale s, ``cl<n>`` is not
-    provided (use chung_lu directly).
+    Small variants for tests and profiling: ``rmat<s>`` for any scale s
+    (k ~ U{0..65536}, as rmat20), ``rmat<s>m`` with rmat22's Beta mixture;
+    ``cl<n>`` is not provided (use chung_lu directly).
     """
     if name == "er2k":
         n = 2000
@@ -501,9 +502,10 @@ def config_graph(name: str, seed: int = 1) -> Graph:
         s, d = chung_lu(n, 2.3, 20.0, 50_000.0, seed)
         return Graph(name, n, s, d, p=p_uniform_f32(s.size, seed + 1000))
     if name.startswith("rmat"):
-        scale = int(name[4:])
+        mixture = name.endswith("m")
+        scale = int(name[4:-1] if mixture else name[4:])
         s, d = rmat(scale, 16, 0.57, 0.19, 0.19, seed)
-        if scale == 22:
+        if scale == 22 or mixture:
             k = quantise(p_beta_mixture(s.size, seed + 1000))
         else:
             k = k_uniform(s.size, seed + 1000)

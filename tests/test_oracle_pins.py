@@ -458,3 +458,61 @@ def test_local_counts_complete_graph(n, k):
         isb, isu = pbal >= Fraction(t), 1 - pbal > Fraction(t)
         assert np.all(eb[:, i] == (n - 2) * isb) and np.all(eu[:, i] == (n - 2) * isu)
         assert np.all(vb[:, i] == math.comb(n - 1, 2) * isb) and np.all(vu[:, i] == math.comb(n - 1, 2) * isu)
+
+
+# ------------------------------------------- the multi-threaded resident count
+
+@pytest.mark.parametrize("name", ["er2k", "mixed", "rmat12", "cl"])
+def test_resident_count_equals_serial_pass(name):
+    """ResidentGraph.count (Alg. 1's outer loop split over threads) gives the
+    serial oracle's counts for every thread count, and its samples partition
+    them."""
+    if name == "er2k":
+        g = synth.config_graph("er2k")
+        n, s, d, k = g.n, g.src, g.dst, g.k
+    elif name == "mixed":
+        n = 400
+        s, d = synth.er_graph(n, 6000, 71)
+        k = special_k(s.size, 72)
+    elif name == "rmat12":
+        g = synth.config_graph("rmat12")
+        n, s, d, k = g.n, g.src, g.dst, g.k
+    else:
+        n = 20000
+        s, d = synth.chung_lu(n, 2.1, 20.0, 2000.0, 73)
+        k = synth.quantise(synth.p_beta_mixture(s.size, 74))
+    taus = [0.51 + i * (0.48 / 31) for i in range(32)]
+    b, u = oracle.count_threshold(n, s, d, k, taus)
+    T = oracle.num_triangles(n, s, d)
+    R = oracle.ResidentGraph(n, s, d)
+    for th in (1, 2, 7):
+        b2, u2, t2 = R.count(k, taus, threads=th)
+        assert np.array_equal(b2, b) and np.array_equal(u2, u) and t2 == T, th
+    sb, su, st = np.zeros(32, np.int64), np.zeros(32, np.int64), 0
+    for r in range(3):
+        b3, u3, t3 = R.count(k, taus, threads=3, sample_mod=3, sample_rem=r)
+        sb, su, st = sb + b3, su + u3, st + t3
+    assert np.array_equal(sb, b) and np.array_equal(su, u) and st == T
+    R.close()
+
+
+def test_resident_count_sample_is_the_triangles_of_the_sampled_earliest_vertices():
+    """A sample (class(u) == rem) counts exactly the triangles whose earliest
+    vertex in Node Order (degree, then id) is such a u: checked against the
+    O(n^3) listing with Node Order computed here."""
+    n = 70
+    s, d = synth.er_graph(n, 900, 81)
+    k = special_k(s.size, 82)
+    tri, _ = brute_triangles(n, s, d)
+    deg = np.bincount(np.concatenate([s, d]).astype(np.int64), minlength=n)
+    rank = np.lexsort((np.arange(n), deg))  # vertices in Node Order
+    pos = np.empty(n, np.int64)
+    pos[rank] = np.arange(n)
+    first = tri[np.arange(tri.shape[0]), np.argmin(pos[tri], axis=1)]
+    R = oracle.ResidentGraph(n, s, d)
+    for mod in (2, 5):
+        cls = np.array([oracle.sample_class(x, mod) for x in range(n)])
+        assert np.all((cls >= 0) & (cls < mod))
+        for rem in range(mod):
+            _, _, t = R.count(k, [0.5], threads=2, sample_mod=mod, sample_rem=rem)
+            assert t == int(np.count_nonzero(cls[first] == rem)), (mod, rem)

@@ -201,10 +201,13 @@ ubt_status ubt_count_threshold(ubt_graph* g, const double* h_tau, int32_t n_tau,
  *   library call); the array is cleared on `stream` at every call.
  *   The first call on a device looks up the array's device address (once per
  *   device, with that device current); make that first call before any
- *   stream capture.
+ *   stream capture.  The current device must be the one the graph was built
+ *   on (else UBT_ERR_INVALID_ARG): the array used is that device's.
  *   All calls share the one array: calls that overlap on the GPU (on
  *   different streams, or on different graphs at the same time) race and
  *   give wrong counts.  Issue them one after another on one stream.
+ *   A failed self-check of the traversal is copied into the graph's own
+ *   self-check word at the end of the call, so ubt_query_guard sees it.
  */
 ubt_status ubt_count_threshold_noalloc(ubt_graph* g, const double* h_tau, int32_t n_tau, int32_t prune,
                                        int64_t* d_counts, void* stream);
@@ -252,9 +255,30 @@ ubt_status ubt_expected_counts(ubt_graph* g, double* d_out, int64_t* d_exact, vo
  * Arithmetic: FIXED graphs exact in int64 before the final scaling; REAL
  * graphs exact int64 products of the 2^-30 fixed-point s values, rounded to
  * 2^-40 and accumulated in 64-bit integers, scaled to float at the end.
+ * Limit: an edge's accumulator is a signed 64-bit integer and every triangle
+ * adds a term of magnitude at most 2^30 (FIXED, units of 2^-30) or 2^40
+ * (REAL, units of 2^-40), so the sum is exact while an edge lies in fewer
+ * than 2^33 (FIXED) or 2^23 = 8,388,608 (REAL) triangles.  The sum of a REAL
+ * edge in more triangles than that can wrap; no check is made.
  */
 ubt_status ubt_expected_counts_backward(ubt_graph* g, const double* d_gout, float* d_grad_p,
                                         void* stream);
+
+/*
+ * ubt_set_edge_values -- ASYNC.  Replaces the probabilities of a REAL graph
+ * with d_p (device float[m], input edge order, each in [0, 1]) without
+ * rebuilding it: every stored s = 1 - 2p is recomputed from the new p, in the
+ * arithmetic of ubt_create_graph.  Structure, orientation and work lists are
+ * unchanged (REAL rows are ordered by neighbour id, which p does not affect),
+ * so expected counts and their adjoint then answer for the new p (Sec. 3's
+ * P_bal equation, with the new P+).  This is what a gradient step on p needs.
+ * An entry outside [0, 1] or NaN keeps its old value, and the first such
+ * input index is recorded in the self-check word (ubt_query_guard, code 6).
+ * Graph kind: REAL only (UBT_ERR_UNSUPPORTED for FIXED: their rows are
+ * ordered by |q|, which a new k would change).
+ * Errors: UBT_ERR_INVALID_ARG, UBT_ERR_UNSUPPORTED, UBT_ERR_CUDA.
+ */
+ubt_status ubt_set_edge_values(ubt_graph* g, const float* d_p, void* stream);
 
 /*
  * ubt_sample_worlds_workspace_size / ubt_sample_worlds -- ASYNC.  Monte-Carlo
@@ -320,7 +344,9 @@ ubt_status ubt_traversal_stats(ubt_graph* g, const double* h_tau, int32_t n_tau,
  * graph's traversals: 0 when every check since the last call passed, else
  * (code << 56 | detail) of the first failure (1/2 hash-table probe limit in
  * find/insert, 3 neighbour id >= n, 4 list offsets out of range, 5 table
- * larger than its region).  A failed check skips the access it guards.
+ * larger than its region, 6 an edge value outside [0, 1] given to
+ * ubt_set_edge_values, detail = its input index).  A failed check skips the
+ * access it guards.  ubt_count_threshold_noalloc reports here too.
  */
 ubt_status ubt_query_guard(ubt_graph* g, int64_t* h_word, void* stream);
 

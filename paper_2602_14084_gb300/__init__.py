@@ -72,6 +72,7 @@ def lib():
             "ubt_enumerate": (I32, [P, ctypes.c_double, I32, I32, P, I64, ctypes.POINTER(I64), P]),
             "ubt_expected_counts": (I32, [P, P, P, P]),
             "ubt_expected_counts_backward": (I32, [P, P, P, P]),
+            "ubt_set_edge_values": (I32, [P, P, P]),
             "ubt_sample_worlds_workspace_size": (I32, [P, I64, ctypes.POINTER(SZ)]),
             "ubt_sample_worlds": (I32, [P, ctypes.c_uint64, I64, P, P, P, SZ, P]),
             "ubt_batch_query": (I32, [P, P, I32, ctypes.c_uint64, P, P, P, P]),
@@ -160,6 +161,8 @@ class Graph:
         if (k is None) == (p is None):
             raise ValueError("give exactly one of k or p")
         self.device = torch.device(device)
+        if self.device.type == "cuda" and self.device.index is None:
+            self.device = torch.device("cuda", torch.cuda.current_device())
         self.n = int(n)
         L = lib()
         s_dev = _dev_u32(src, self.device)
@@ -416,6 +419,16 @@ class Graph:
             s -= 1 << 128
         return float(o[0]), float(o[1]), int(e[0]), s
 
+    def set_edge_values_(self, p, stream=None):
+        """ASYNC: new probabilities of a REAL graph (float32 [m], input edge
+        order, on this graph's device) without a rebuild (ubt_set_edge_values).
+        An entry outside [0, 1] keeps its old value and is reported by guard()."""
+        torch = _torch()
+        if not isinstance(p, torch.Tensor) or p.dtype != torch.float32 or p.device != self.device \
+                or p.numel() != self.m or not p.is_contiguous():
+            raise ValueError("p must be a contiguous float32 tensor of %d entries on %s" % (self.m, self.device))
+        _check(lib().ubt_set_edge_values(self._h, _ptr(p), _stream(stream)), "ubt_set_edge_values")
+
     def expected_counts_backward_(self, gout, grad, stream=None):
         _check(lib().ubt_expected_counts_backward(self._h, _ptr(gout), _ptr(grad), _stream(stream)),
                "ubt_expected_counts_backward")
@@ -470,19 +483,27 @@ class _ExpectedCountsFn:
             torch = _torch()
 
             class ExpectedCounts(torch.autograd.Function):
-                """(E_bal, E_unbal) of a REAL graph; backward is the hand-written adjoint kernel."""
+                """(E_bal, E_unbal) of a REAL graph at probabilities p; backward is
+                the hand-written adjoint kernel.  Both load p into the graph first
+                (ubt_set_edge_values), so they answer for the p they are given."""
 
                 @staticmethod
                 def forward(ctx, p, graph):
+                    p32 = _p_for(graph, p)
+                    graph.set_edge_values_(p32)
                     out = torch.empty(2, dtype=torch.float64, device=graph.device)
                     graph.expected_counts_(out)
                     ctx.graph = graph
                     ctx.p_dtype = p.dtype
+                    ctx.save_for_backward(p)
                     return out[0].clone(), out[1].clone()
 
                 @staticmethod
                 def backward(ctx, g_bal, g_unbal):
                     graph = ctx.graph
+                    (p,) = ctx.saved_tensors
+                    # another forward on this graph may have loaded other values since
+                    graph.set_edge_values_(_p_for(graph, p))
                     gout = torch.stack([g_bal.to(torch.float64).reshape(()), g_unbal.to(torch.float64).reshape(())])
                     grad = torch.empty(graph.m, dtype=torch.float32, device=graph.device)
                     graph.expected_counts_backward_(gout.contiguous(), grad)
@@ -492,10 +513,22 @@ class _ExpectedCountsFn:
         return cls._cls
 
 
+def _p_for(graph, p):
+    """p as the contiguous float32 device tensor ubt_set_edge_values takes."""
+    torch = _torch()
+    if graph.kind != REAL:
+        raise ValueError("expected_counts(graph, p) needs a REAL graph (built with p=...)")
+    if p.numel() != graph.m:
+        raise ValueError("p has %d entries, the graph %d edges" % (p.numel(), graph.m))
+    return p.detach().to(device=graph.device, dtype=torch.float32).contiguous().reshape(-1)
+
+
 def expected_counts(graph: Graph, p):
-    """Differentiable (E_bal, E_unbal) of `graph`, which must have been built
-    from exactly these probabilities `p` (REAL graph, or FIXED with p = k/65536).
-    Gradients flow to `p` through the adjoint kernel."""
+    """Differentiable (E_bal, E_unbal) of the REAL graph `graph` at the edge
+    probabilities `p` (one per input edge, in input order): p is loaded into
+    the graph (no rebuild) before the forward traversal and again before the
+    adjoint, so updating p between calls is enough.  Gradients flow to `p`
+    through the adjoint kernel."""
     return _ExpectedCountsFn.get().apply(p, graph)
 
 

@@ -134,9 +134,7 @@ __global__ void k_scatter(int64_t m, const uint32_t* __restrict__ src, const uin
     if (k) {
       val = (uint32_t)(int32_t)(32768 - (int32_t)k[i]);     // q = 32768 - k
     } else {
-      // s = 1 - 2p as a 2^-30 fixed-point integer: 1 - 2p is exact in double for
-      // float32 p >= 2^-29, and the rounding to the 2^-30 grid is exact for p >= 2^-7
-      val = (uint32_t)(int32_t)__double2ll_rn((1.0 - 2.0 * (double)p[i]) * 1073741824.0);
+      val = real_valbits(p[i]);
     }
     adj[pos] = adj_pack(hi, val);
     eid[pos] = (uint32_t)i;
@@ -1124,5 +1122,39 @@ extern "C" ubt_status ubt_graph_get_info(const ubt_graph* g, ubt_graph_info* h_i
   h_info->wedges = g->wedges;
   h_info->kind = g->kind;
   h_info->probes = g->probes;
+  return UBT_OK;
+}
+
+namespace ubt {
+namespace {
+
+// New edge values of a REAL graph: CSR position pos holds input edge eid[pos],
+// so its value becomes s(p[eid[pos]]); the rows stay sorted (by neighbour id).
+// A p outside [0, 1] (or NaN) leaves the entry as it was and records the
+// first such input index in the self-check word (code 6).
+__global__ void k_set_edge_values(int64_t m, const float* __restrict__ p, const uint32_t* __restrict__ eid,
+                                  uint64_t* __restrict__ adj, unsigned long long* guard) {
+  for (int64_t pos = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; pos < m; pos += (int64_t)gridDim.x * blockDim.x) {
+    const uint32_t e = eid[pos];
+    const float x = p[e];
+    if (!(x >= 0.0f && x <= 1.0f)) {
+      atomicCAS(guard, 0ull, (6ull << 56) | (unsigned long long)e);
+      continue;
+    }
+    adj[pos] = adj_pack(adj_col(adj[pos]), real_valbits(x));
+  }
+}
+
+}  // namespace
+}  // namespace ubt
+
+extern "C" ubt_status ubt_set_edge_values(ubt_graph* g, const float* d_p, void* stream) {
+  if (!g || (!d_p && g->m > 0)) return UBT_ERR_INVALID_ARG;
+  if (g->kind != UBT_GRAPH_REAL) return UBT_ERR_UNSUPPORTED;
+  if (g->m == 0) return UBT_OK;
+  cudaStream_t s = (cudaStream_t)stream;
+  const int grid = (int)std::min<int64_t>((g->m + 255) / 256, (int64_t)g->sm_count * 8);
+  k_set_edge_values<<<grid, 256, 0, s>>>(g->m, d_p, g->eid, g->adj, &g->scratch->guard);
+  UBT_CUDA(cudaGetLastError());
   return UBT_OK;
 }

@@ -86,6 +86,15 @@ __device__ __forceinline__ int edge_index_lookup(const uint4* __restrict__ slots
 }
 #endif
 
+#ifdef __CUDACC__
+// The stored value of a REAL edge: s = 1 - 2p as a 2^-30 fixed-point int32.
+// 1 - 2p is exact in double for float32 p >= 2^-29, and the rounding to the
+// 2^-30 grid is exact for p >= 2^-7.
+__device__ __forceinline__ uint32_t real_valbits(float p) {
+  return (uint32_t)(int32_t)__double2ll_rn((1.0 - 2.0 * (double)p) * 1073741824.0);
+}
+#endif
+
 // Entries of the queue of long vertex samples (ubt_graph::lqueue).
 constexpr int kLongQueue = 1024;
 

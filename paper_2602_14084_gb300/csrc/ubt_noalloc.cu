@@ -38,10 +38,12 @@ constexpr int kMaxDevices = 64;
 std::mutex g_mu;
 void* g_addr[kMaxDevices];
 
-ubt_status scratch_address(void** out) {
+// The array of the graph's device; that device must be the current one, as
+// every launch of the call goes to the current device.
+ubt_status scratch_address(const ubt_graph* g, void** out) {
   int dev = 0;
   UBT_CUDA(cudaGetDevice(&dev));
-  if (dev < 0 || dev >= kMaxDevices) return UBT_ERR_INVALID_ARG;
+  if (dev != g->device || dev < 0 || dev >= kMaxDevices) return UBT_ERR_INVALID_ARG;
   std::lock_guard<std::mutex> lock(g_mu);
   if (!g_addr[dev]) {
     void* p = nullptr;
@@ -52,6 +54,14 @@ ubt_status scratch_address(void** out) {
   return UBT_OK;
 }
 
+// The fixed array's self-check word goes to the graph's own (first failure
+// wins there too), so that ubt_query_guard reports a failed check of this
+// call although the next call clears the array.
+__global__ void k_merge_guard(const Scratch* from, Scratch* to) {
+  const unsigned long long w = from->guard;
+  if (w) atomicCAS(&to->guard, 0ull, w);
+}
+
 }  // namespace
 
 extern "C" ubt_status ubt_count_threshold_noalloc(ubt_graph* g, const double* h_tau, int32_t n_tau, int32_t prune,
@@ -59,12 +69,16 @@ extern "C" ubt_status ubt_count_threshold_noalloc(ubt_graph* g, const double* h_
   if (!g || !d_counts || !h_tau) return UBT_ERR_INVALID_ARG;
   if (n_tau < 1 || n_tau > kNoallocMaxTau) return UBT_ERR_SCRATCH_LIMIT;
   void* base = nullptr;
-  const ubt_status st = scratch_address(&base);
+  ubt_status st = scratch_address(g, &base);
   if (st != UBT_OK) return st;
   cudaStream_t s = (cudaStream_t)stream;
   // the array keeps the previous call's contents: clear counters and accumulators
   UBT_CUDA(cudaMemsetAsync(base, 0, kNoallocBytes, s));
   Scratch* sc = (Scratch*)base;
   unsigned long long* acc = (unsigned long long*)((char*)base + sizeof(Scratch));
-  return count_reg_at(g, h_tau, n_tau, prune, d_counts, sc, acc, s);
+  st = count_reg_at(g, h_tau, n_tau, prune, d_counts, sc, acc, s);
+  if (st != UBT_OK) return st;
+  k_merge_guard<<<1, 1, 0, s>>>(sc, g->scratch);
+  UBT_CUDA(cudaGetLastError());
+  return UBT_OK;
 }

@@ -35,3 +35,32 @@ def mixed_graph(n, m, seed):
     key = np.unique(lo * n + hi)
     src, dst = (key // n).astype(np.uint32), (key % n).astype(np.uint32)
     return synth.random_orientation(src, dst, seed + 9)
+
+
+def grad_report(got, want, gabs):
+    """(ok mask, plain relative error per edge, edges where the floor applied)."""
+    floor = 1e-3 * gabs
+    tol = 1e-5 * np.maximum(np.abs(want), floor)
+    ok = np.abs(got - want) <= tol + 1e-12
+    rel = np.abs(got - want) / np.maximum(np.abs(want), 1e-300)
+    return ok, rel, int(np.count_nonzero(floor > np.abs(want)))
+
+
+def difference_quotients(ubt, G, p, edges):
+    """(E_bal(p_e = 1) - E_bal(p_e = 0)) for each listed edge, from the GPU
+    forward, in float64."""
+    import torch
+    base = torch.from_numpy(p.copy()).cuda()
+    out = torch.empty(2, dtype=torch.float64, device="cuda")
+    fd = np.zeros(len(edges))
+    for i, e in enumerate(edges):
+        vals = []
+        for x in (1.0, 0.0):
+            q = base.clone()
+            q[int(e)] = x
+            G.set_edge_values_(q)
+            G.expected_counts_(out)
+            vals.append(out[0].item())
+        fd[i] = vals[0] - vals[1]
+    G.set_edge_values_(base)
+    return fd

@@ -402,3 +402,52 @@ def test_count_host_end_to_end(ubt, er2k):
     b, u = ubt.count_host(g.n, g.src, g.dst, g.k, [0.6, 0.75, 0.9])
     ob, ou = oracle.count_threshold(g.n, g.src, g.dst, g.k, [0.6, 0.75, 0.9])
     assert np.array_equal(b, ob) and np.array_equal(u, ou)
+
+
+def test_workspace_one_byte_short_is_refused_before_any_kernel(ubt, er2k):
+    """A workspace one byte below the queried size: ubt_create_graph,
+    ubt_sample_worlds, ubt_topk and ubt_count_host return
+    UBT_ERR_WORKSPACE_TOO_SMALL and leave their outputs untouched."""
+    import ctypes
+    import torch
+    g = er2k
+    L = ubt.lib()
+    cp = lambda t: ctypes.c_void_p(t.data_ptr())
+    stream = ctypes.c_void_p(torch.cuda.current_stream().cuda_stream)
+    src = torch.from_numpy(g.src.view(np.int32)).cuda()
+    dst = torch.from_numpy(g.dst.view(np.int32)).cuda()
+    kk = torch.from_numpy(g.k.view(np.int32)).cuda()
+    nb = ctypes.c_size_t(0)
+    assert L.ubt_graph_workspace_size(g.n, g.m, 0, None, ctypes.byref(nb)) == 0
+    ws = torch.empty(int(nb.value), dtype=torch.uint8, device="cuda")
+    h = ctypes.c_void_p(0)
+    st = L.ubt_create_graph(g.n, g.m, cp(src), cp(dst), cp(kk), None, 0, None, cp(ws), int(nb.value) - 1, stream,
+                            ctypes.byref(h))
+    assert st == -8 and not h.value
+    G = ubt.Graph(g.n, g.src, g.dst, k=g.k)
+    W = 128
+    need = G.sample_worlds_workspace(W)
+    wws = torch.empty(need, dtype=torch.uint8, device="cuda")
+    out = torch.full((W,), -1, dtype=torch.int64, device="cuda")
+    st = L.ubt_sample_worlds(G.handle, ctypes.c_uint64(7), W, cp(out), None, cp(wws), need - 1, stream)
+    assert st == -8
+    torch.cuda.synchronize()
+    assert bool((out == -1).all())
+    K = 100
+    L.ubt_topk_workspace_size(K, ctypes.byref(nb))
+    tw = torch.empty(int(nb.value), dtype=torch.uint8, device="cuda")
+    tout = torch.full((K * ubt.TRI_REC_DTYPE.itemsize,), 0xAB, dtype=torch.uint8, device="cuda")
+    nout = ctypes.c_int64(-1)
+    st = L.ubt_topk(G.handle, K, 1, cp(tout), ctypes.byref(nout), cp(tw), int(nb.value) - 1, stream)
+    assert st == -8 and nout.value == -1
+    torch.cuda.synchronize()
+    assert bool((tout == 0xAB).all())
+    L.ubt_count_host_workspace_size(g.n, g.m, ctypes.byref(nb))
+    hws = torch.empty(int(nb.value), dtype=torch.uint8, device="cuda")
+    taus = np.array([0.6, 0.9])
+    hout = np.full(4, -1, dtype=np.int64)
+    st = L.ubt_count_host(g.n, g.m, g.src.ctypes.data_as(ctypes.c_void_p), g.dst.ctypes.data_as(ctypes.c_void_p),
+                          g.k.ctypes.data_as(ctypes.c_void_p), taus.ctypes.data_as(ctypes.c_void_p), 2, 1,
+                          hout.ctypes.data_as(ctypes.c_void_p), cp(hws), int(nb.value) - 1, stream)
+    assert st == -8 and (hout == -1).all()
+    assert G.guard() == 0

@@ -2,17 +2,20 @@
 allocate device memory where they query (code that may only use the buffers
 it is handed): its per-call scratch is a fixed array inside the library.
 
-Called through the C ABI and compared with ubt_count_threshold, twice in a
-row on each graph (the fixed array keeps the previous call's contents, so the
-second call checks that it is cleared).  Counts are integers: the comparison
-is exact.  This file sorts last so that a run stopping at the first failure
-has already run every other test.
+Called through the C ABI and compared with ubt_count_threshold and with the
+oracle, twice in a row on each graph (the fixed array keeps the previous
+call's contents, so the second call checks that it is cleared).  Counts are
+integers: the comparison is exact.  The traversal's self-checks of these
+calls reach the graph's own self-check word, which must read 0 afterwards.
+This file sorts last so that a run stopping at the first failure has already
+run every other test.
 """
 import ctypes
 
 import numpy as np
 import pytest
 
+import oracle
 import synth
 from gpu_util import mixed_graph, require_gpu
 
@@ -41,14 +44,17 @@ def test_noalloc_matches_count_threshold_twice(taus):
     import torch
     for n, s, d, k in graphs():
         G = ubt.Graph(n, s, d, k=k)
+        ob, ou = oracle.count_threshold(n, s, d, k, taus)
         for prune in (0, 1):
             want_b, want_u = G.count_threshold(taus, prune=prune)
             want = np.concatenate([want_b, want_u])
+            assert np.array_equal(want, np.concatenate([ob, ou]))
             for _ in range(2):
                 out = torch.full((2 * len(taus),), -1, dtype=torch.int64, device="cuda")
                 assert call_noalloc(ubt, G, taus, prune, out) == 0
                 torch.cuda.synchronize()
                 assert np.array_equal(out.cpu().numpy(), want), (n, taus, prune)
+        assert G.guard() == 0
 
 
 def test_noalloc_rejects_more_thresholds_than_its_scratch_holds():

@@ -85,7 +85,7 @@ extern "C" ubt_status ubt_set_tuning(const char* name, int64_t value) {
     if (value < 1 || value > 1024) return UBT_ERR_INVALID_ARG;
     t.small_batch = value;
   } else if (!strcmp(name, "count_visitor")) {
-    if (value < 0 || value > 1) return UBT_ERR_INVALID_ARG;
+    if (value < 0 || value > 2) return UBT_ERR_INVALID_ARG;
     t.count_visitor = value;
   } else if (!strcmp(name, "pull")) {
     if (value < 0 || value > 1) return UBT_ERR_INVALID_ARG;

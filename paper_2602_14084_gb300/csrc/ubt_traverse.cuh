@@ -56,6 +56,10 @@
 #ifndef UBT_LB_MINB
 #define UBT_LB_MINB 1
 #endif
+// entries per lane of a full chunk of a long list (4 or 8)
+#ifndef UBT_LONG_U
+#define UBT_LONG_U 4
+#endif
 
 namespace ubt {
 
@@ -143,6 +147,7 @@ __device__ __forceinline__ uint32_t slots_for(uint32_t entries) {
 // A bucket with a free slot ends every probe sequence, and there are more
 // buckets than entries, so both loops end within bmask + 1 buckets; the limit
 // is a self-check.  Slots of a bucket are taken in order (first free slot).
+template <bool kPos = true>
 __device__ __forceinline__ void table_insert(const Table& t, uint32_t w, uint32_t val, uint32_t pos, Scratch* sc) {
   uint32_t b = hash_slot(w, t.shift);
   for (uint32_t it = 0; it <= t.bmask; it++) {
@@ -150,7 +155,7 @@ __device__ __forceinline__ void table_insert(const Table& t, uint32_t w, uint32_
     for (int i = 0; i < 4; i++) {
       if (atomicCAS(&t.key[4 * b + i], kEmpty, w) == kEmpty) {
         t.val[4 * b + i] = val;
-        t.pos[4 * b + i] = pos;
+        if (kPos) t.pos[4 * b + i] = pos;
         return;
       }
     }
@@ -199,6 +204,55 @@ __device__ __forceinline__ bool table_find(const Table& t, uint32_t w, uint32_t&
   return hit;
 }
 
+// Words of table memory per slot: visitors that need no CSR position keep
+// only keys and values (8 bytes a slot), which lets more warp tables share
+// an SM's shared memory.
+template <bool kPos>
+struct TableWords {
+  static constexpr uint32_t kWords = kPos ? 3u : 2u;
+};
+
+// table_find for the 32 converged lanes of a warp (every lane calls it; a
+// lane without an entry passes any key and ignores the result): the search
+// past a full home bucket -- rare, at most 1/4 of the slots are used -- is
+// entered by the whole warp only when some lane needs it, and the value is
+// read from the slot the bucket search ends at, hit or not, so that the
+// common case runs without a divergent branch.
+template <bool kPos>
+__device__ __forceinline__ bool table_find_warp(const Table& t, uint32_t w, uint32_t& val, uint32_t& pos,
+                                                Scratch* sc) {
+  uint32_t b = hash_slot(w, t.shift);
+  const uint4 k = reinterpret_cast<const uint4*>(t.key)[b];
+  const bool m0 = k.x == w, m1 = k.y == w, m2 = k.z == w, m3 = k.w == w;
+  bool hit = m0 | m1 | m2 | m3;
+  uint32_t s = 4 * b + (m0 ? 0u : (m1 ? 1u : (m2 ? 2u : 3u)));
+  const bool more = !hit && k.w != kEmpty;
+  if (__any_sync(kFull, more)) {
+    if (more) {  // the home bucket is full: continue in the next ones
+      bool ended = false;
+      for (uint32_t it = 1; it <= t.bmask; it++) {
+        b = (b + 1) & t.bmask;
+        const uint4 kk = reinterpret_cast<const uint4*>(t.key)[b];
+        const bool n0 = kk.x == w, n1 = kk.y == w, n2 = kk.z == w, n3 = kk.w == w;
+        if (n0 | n1 | n2 | n3) {
+          hit = true;
+          s = 4 * b + (n0 ? 0u : (n1 ? 1u : (n2 ? 2u : 3u)));
+          ended = true;
+          break;
+        }
+        if (kk.w == kEmpty) {
+          ended = true;
+          break;
+        }
+      }
+      if (!ended) guard_fail(sc, kGuardFind, w);
+    }
+  }
+  val = t.val[s];
+  if (kPos) pos = t.pos[s];
+  return hit;
+}
+
 // Per-lane description of one pair handed to probe_pairs: owner x (its list
 // is the table), streamed vertex s, CSR position and value of the x-s edge.
 struct Pair {
@@ -215,22 +269,19 @@ __device__ __forceinline__ void long_steps(const uint64_t* __restrict__ adj, Scr
                                            int lane, uint32_t uj, uint32_t vj, uint32_t vsj, uint32_t dvj,
                                            uint32_t qj, uint32_t pj, uint32_t off) {
   uint64_t e[U];
+  const uint64_t* __restrict__ row = adj + vsj + off + lane;
 #pragma unroll
-  for (int s = 0; s < U; s++) {
-    const uint32_t i = off + 32 * s + lane;
-    e[s] = (kAll || i < dvj) ? adj[vsj + i] : 0ull;
-  }
+  for (int s = 0; s < U; s++) e[s] = (kAll || off + 32 * s + lane < dvj) ? row[32 * s] : 0ull;
   if constexpr (V::kBatched) {
     // all U probes first, then the visitor takes their hits together
     bool hit[U];
     uint32_t quw[U], qvw[U];
 #pragma unroll
     for (int s = 0; s < U; s++) {
-      const uint32_t i = off + 32 * s + lane;
       uint32_t puw = 0;
-      quw[s] = 0;
       qvw[s] = adj_valbits(e[s]);
-      hit[s] = (kAll || i < dvj) && table_find<false>(t, adj_col(e[s]), quw[s], puw, sc);
+      const bool f = table_find_warp<false>(t, adj_col(e[s]), quw[s], puw, sc);
+      hit[s] = (kAll || off + 32 * s + lane < dvj) && f;
     }
     vis.template steps<U>(hit, qj, quw, qvw);
   } else {
@@ -238,7 +289,8 @@ __device__ __forceinline__ void long_steps(const uint64_t* __restrict__ adj, Scr
     for (int s = 0; s < U; s++) {
       const uint32_t i = off + 32 * s + lane;
       uint32_t quw = 0, puw = 0;
-      const bool hit = (kAll || i < dvj) && table_find<V::kPos>(t, adj_col(e[s]), quw, puw, sc);
+      const bool f = table_find_warp<V::kPos>(t, adj_col(e[s]), quw, puw, sc);
+      const bool hit = (kAll || i < dvj) && f;
       if (kAll || off + 32 * s < dvj)
         vis.step(hit, uj, vj, adj_col(e[s]), qj, quw, adj_valbits(e[s]), pj, puw, vsj + i);
     }
@@ -281,7 +333,11 @@ __device__ __forceinline__ void probe_pairs(const TravArgs& a, V& vis, const Tab
     const uint32_t qj = __shfl_sync(kFull, pr.qe, j);
     const uint32_t pj = __shfl_sync(kFull, pr.pe, j);
     uint32_t off = 0;
-    while (dvj - off >= 128) {
+    while (dvj - off >= 32 * UBT_LONG_U) {
+      long_steps<V, UBT_LONG_U, true>(adj, sc, vis, t, lane, uj, vj, vsj, dvj, qj, pj, off);
+      off += 32 * UBT_LONG_U;
+    }
+    if (UBT_LONG_U > 4 && dvj - off >= 128) {
       long_steps<V, 4, true>(adj, sc, vis, t, lane, uj, vj, vsj, dvj, qj, pj, off);
       off += 128;
     }
@@ -337,7 +393,8 @@ __device__ __forceinline__ void probe_pairs(const TravArgs& a, V& vis, const Tab
     for (int s = 0; s < 2; s++) {
       const int j = (int)jj[s];
       uint32_t quw = 0, puw = 0;
-      const bool hit = act[s] && table_find<V::kPos>(t, adj_col(e[s]), quw, puw, sc);
+      const bool found = table_find_warp<V::kPos>(t, adj_col(e[s]), quw, puw, sc);
+      const bool hit = act[s] && found;
       const uint32_t uj = __shfl_sync(kFull, pr.x, j);
       const uint32_t vj = __shfl_sync(kFull, pr.s, j);
       const uint32_t qj = __shfl_sync(kFull, pr.qe, j);
@@ -422,7 +479,7 @@ __device__ __forceinline__ void block_task(const TravArgs& a, V& vis, uint32_t x
   __syncthreads();
   for (uint32_t i = tid; i < len; i += blockDim.x) {
     const uint64_t e = a.adj[rs + i];
-    table_insert(t, adj_col(e), adj_valbits(e), rs + i, a.sc);
+    table_insert<V::kPos>(t, adj_col(e), adj_valbits(e), rs + i, a.sc);
   }
   __syncthreads();
   vis.task_begin(x);
@@ -474,7 +531,7 @@ __device__ __forceinline__ void warp_task(const TravArgs& a, V& vis, uint32_t x,
   __syncwarp();
   for (uint32_t i = lane; i < len; i += 32) {
     const uint64_t e = a.adj[rs + i];
-    table_insert(t, adj_col(e), adj_valbits(e), rs + i, a.sc);
+    table_insert<V::kPos>(t, adj_col(e), adj_valbits(e), rs + i, a.sc);
   }
   __syncwarp();
   vis.task_begin(x);
@@ -520,7 +577,7 @@ __device__ void traverse(const TravArgs& a, V& vis, char* smem_tables) {
     }
   }
   if (kPhases & kWarpTasks) {
-    uint32_t* wtab = tab + (size_t)wid * a.warp_slots * 3;
+    uint32_t* wtab = tab + (size_t)wid * a.warp_slots * TableWords<V::kPos>::kWords;
     // medium tasks, one warp each
     while (true) {
       unsigned long long t0 = 0;
@@ -535,12 +592,13 @@ __device__ void traverse(const TravArgs& a, V& vis, char* smem_tables) {
   vis.block_end();
 }
 
-// Shared memory of one block of a traversal kernel: visitor bytes + tables.
-inline size_t traverse_smem_bytes(const TravArgs& a, int phases, int threads, int vis_smem) {
+// Shared memory of one block of a traversal kernel: visitor bytes + tables
+// (words 32-bit words per table slot).
+inline size_t traverse_smem_bytes(const TravArgs& a, int phases, int threads, int vis_smem, uint32_t words) {
   const size_t vis_bytes = (size_t)((vis_smem + 15) / 16) * 16;
   size_t tables = 0;
-  if (phases & kBlockTasks) tables = std::max(tables, (size_t)a.hub_slots * 3 * 4);
-  if (phases & kWarpTasks) tables = std::max(tables, (size_t)(threads / 32) * a.warp_slots * 3 * 4);
+  if (phases & kBlockTasks) tables = std::max(tables, (size_t)a.hub_slots * words * 4);
+  if (phases & kWarpTasks) tables = std::max(tables, (size_t)(threads / 32) * a.warp_slots * words * 4);
   return vis_bytes + tables;
 }
 
@@ -569,7 +627,7 @@ template <class V, int kPhases>
 ubt_status launch_phase(const ubt_graph* g, const TravArgs& a, const typename V::P& p, int threads, cudaStream_t s) {
   const Tuning& T = tuning();
   threads = (int)std::min<int64_t>(Bounds<V, kPhases>::kThreads, std::max<int64_t>(64, threads / 32 * 32));
-  const size_t smem = traverse_smem_bytes(a, kPhases, threads, V::smem_bytes(threads));
+  const size_t smem = traverse_smem_bytes(a, kPhases, threads, V::smem_bytes(threads), TableWords<V::kPos>::kWords);
   UBT_CUDA(cudaFuncSetAttribute(k_traverse<V, kPhases>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
   int per_sm = 0;
   UBT_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_traverse<V, kPhases>, threads, smem));

@@ -176,25 +176,45 @@ struct Worlds {
     }
     since = 0;
   }
+  // The queued triangles one after another, with the next triangle's sign
+  // words loaded before the current one's counters are updated, so that a
+  // warp's loads overlap its counter updates.
   __device__ void drain() {
     __syncwarp();
     const int lane = (int)lane_id();
     const unsigned long long* X = p.X;
     const uint32_t wp = p.wp;
     if (SLOTS == 2) {
+      unsigned long long n0 = 0, n1 = 0;  // the next triangle's XOR words
+      if (qn) {
+        const size_t a = (size_t)q[0] * 64, b = (size_t)q[kQueue] * 64, c = (size_t)q[2 * kQueue] * 64;
+        n0 = X[a + lane] ^ X[b + lane] ^ X[c + lane];
+        n1 = X[a + lane + 32] ^ X[b + lane + 32] ^ X[c + lane + 32];
+      }
       for (uint32_t t = 0; t < qn; t++) {
-        const size_t a = (size_t)q[t] * 64, b = (size_t)q[kQueue + t] * 64, c = (size_t)q[2 * kQueue + t] * 64;
-        pl[0].inc(X[a + lane] ^ X[b + lane] ^ X[c + lane]);
-        pl[1].inc(X[a + lane + 32] ^ X[b + lane + 32] ^ X[c + lane + 32]);
+        const unsigned long long c0 = n0, c1 = n1;
+        if (t + 1 < qn) {  // the same for every lane (qn is)
+          const size_t a = (size_t)q[t + 1] * 64, b = (size_t)q[kQueue + t + 1] * 64,
+                       c = (size_t)q[2 * kQueue + t + 1] * 64;
+          n0 = X[a + lane] ^ X[b + lane] ^ X[c + lane];
+          n1 = X[a + lane + 32] ^ X[b + lane + 32] ^ X[c + lane + 32];
+        }
+        pl[0].inc(c0);
+        pl[1].inc(c1);
         if (++since == kLimit) flush();
       }
     } else {
       const uint32_t per = 32 / wp;  // triangles per iteration
       const uint32_t grp = (uint32_t)lane / wp, w = (uint32_t)lane % wp;
+      auto word = [&](uint32_t t) -> unsigned long long {
+        return t < qn ? X[(size_t)q[t] * wp + w] ^ X[(size_t)q[kQueue + t] * wp + w] ^
+                            X[(size_t)q[2 * kQueue + t] * wp + w]
+                      : 0ull;
+      };
+      unsigned long long nb = word(grp);
       for (uint32_t t0 = 0; t0 < qn; t0 += per) {
-        const uint32_t t = t0 + grp;
-        unsigned long long bw = 0;
-        if (t < qn) bw = X[(size_t)q[t] * wp + w] ^ X[(size_t)q[kQueue + t] * wp + w] ^ X[(size_t)q[2 * kQueue + t] * wp + w];
+        const unsigned long long bw = nb;
+        nb = word(t0 + per + grp);
         pl[0].inc(bw);
         if (++since == kLimit) flush();
       }
@@ -384,6 +404,9 @@ size_t worlds_table_words(const ubt_graph* g, int64_t W) {
   return (size_t)std::max<int64_t>(g->m, 1) * (size_t)wp;
 }
 
+// the workspace ubt_sample_worlds_workspace_size reports and ubt_sample_worlds requires
+size_t worlds_workspace_bytes(const ubt_graph* g, int64_t W) { return worlds_table_words(g, W) * 8 + 256; }
+
 }  // namespace
 }  // namespace ubt
 
@@ -391,7 +414,7 @@ using namespace ubt;
 
 extern "C" ubt_status ubt_sample_worlds_workspace_size(const ubt_graph* g, int64_t W, size_t* h_bytes) {
   if (!g || !h_bytes || W < 64 || W % 64) return UBT_ERR_INVALID_ARG;
-  *h_bytes = worlds_table_words(g, W) * 8 + 256;
+  *h_bytes = worlds_workspace_bytes(g, W);
   return UBT_OK;
 }
 
@@ -400,7 +423,7 @@ extern "C" ubt_status ubt_sample_worlds(ubt_graph* g, uint64_t seed, int64_t W, 
   if (!g || !d_bal_per_world || W < 64 || W % 64 || W / 64 > 0xFFFFFFFFll) return UBT_ERR_INVALID_ARG;
   if (g->kind != UBT_GRAPH_FIXED) return UBT_ERR_UNSUPPORTED;
   if (!d_workspace || ((uintptr_t)d_workspace & 255)) return UBT_ERR_INVALID_ARG;
-  if (ws_bytes < worlds_table_words(g, W) * 8) return UBT_ERR_WORKSPACE_TOO_SMALL;
+  if (ws_bytes < worlds_workspace_bytes(g, W)) return UBT_ERR_WORKSPACE_TOO_SMALL;
   cudaStream_t s = (cudaStream_t)stream;
   const int64_t words = W / 64;
   int64_t wp = std::min<int64_t>(words, tuning().world_words_per_pass);

@@ -1,23 +1,27 @@
 """Benchmark of the exact t-count path on one GB300 (or N replicas).
 
 Workload (one "step" = one threshold-count query over the whole graph):
-  cl1m: Chung-Lu power-law graph, n = 1,000,000, gamma = 2.1, mean degree 20,
-  expected degrees capped at 50,000 (about 9.1M undirected edges after
-  deduplication), P+ ~ Beta(0.5, 0.5) quantised to k/65536, thresholds
-  t in {0.55, 0.70, 0.85, 0.95} answered in one traversal with probability
-  pruning.  The unpruned query runs too (not timed as the headline) and must
-  give identical counts.
+  rmat22: R-MAT scale 22, edge factor 16, (a, b, c) = (0.57, 0.19, 0.19),
+  symmetrised and deduplicated (4,194,304 vertices, 64.2M edges, 2.11e9
+  triangles), P+ ~ 0.5 Beta(8,2) + 0.5 Beta(2,8) quantised to k/65536; the 32
+  thresholds t_i = 0.51 + i 0.48/31 (i = 0..31) answered in one traversal
+  with probability pruning.  The unpruned query runs too (not timed as the
+  headline) and must give identical counts.
 
 value  = triangles of the graph / query time (triangles per second), the
          graph already built and resident in HBM (the paper pre-sorts its data
          and times queries, Sec. 7.2).  L2 is flushed between timed steps.
 e2e    = the same metric through ubt_count_host from pinned host buffers:
          H2D copy of (src, dst, k), graph build, query, D2H of the counts.
-extras = MC sign worlds, expected counts forward + backward, the 32-threshold
-         sweep with enumeration (--extras, on by default; --no-extras skips).
+extras = the t = 0.9 enumeration on the same graph, the Chung-Lu n=1e6
+         4-threshold query, MC sign worlds, the ego-net batch, expected counts
+         forward + backward, Alg. 2, the samplers, top-k and the distribution
+         study (--extras, on by default; --no-extras skips).
 
---impl reference runs the CPU oracle (plain C, one core) on a bounded sample
-of the same workload as the comparison arm.
+cpu_baseline / --impl reference: the CPU oracle (plain C, Alg. 1's outer
+loop over all host cores) on a bounded sample of the same workload: the
+triangles whose earliest vertex in Node Order falls in one of 16 hash classes
+of the vertices.
 """
 from __future__ import annotations
 
@@ -34,10 +38,13 @@ import numpy as np
 ROOT = os.path.dirname(os.path.abspath(__file__))
 sys.path.insert(0, ROOT)
 
-TAUS = [0.55, 0.70, 0.85, 0.95]
-WORKLOAD = "cl1m"
-METRIC = "exact t-count triangles/s (Chung-Lu n=1e6, 4 thresholds, pruned)"
+SWEEP32 = [0.51 + i * (0.48 / 31) for i in range(32)]   # 32 thresholds in [0.51, 0.99]
+TAUS = SWEEP32
+WORKLOAD = "rmat22"
+METRIC = "exact t-count triangles/s (R-MAT scale 22, 32 thresholds in one launch, pruned)"
 UNIT = "triangles/s"
+CL1M_TAUS = [0.55, 0.70, 0.85, 0.95]
+CPU_SAMPLE_MOD = 16   # the CPU arms count one of 16 hash classes of the vertices per pass
 
 
 def peaks():
@@ -197,10 +204,42 @@ def make_graph(name):
 
 def workload_config(g, T, ws):
     """The `config` of the benchmark line (both arms time this workload)."""
-    return {"workload": "cl1m: Chung-Lu n=1,000,000 gamma=2.1 mean-deg 20 cap 50,000, "
-                        "P+ ~ Beta(0.5,0.5) -> k/65536, 4 thresholds, pruned, one traversal",
-            "n": g.n, "m": g.m, "triangles": T, "taus": TAUS, "l2": "flushed between steps (512 MB write)",
+    return {"workload": "rmat22: R-MAT scale 22, edge factor 16, (0.57,0.19,0.19,0.05), symmetrised and "
+                        "deduplicated, P+ ~ 0.5 Beta(8,2) + 0.5 Beta(2,8) -> k/65536; 32 thresholds "
+                        "t_i = 0.51 + i 0.48/31 in one traversal, pruned",
+            "n": g.n, "m": g.m, "triangles": T, "n_taus": len(TAUS), "taus": "0.51 + i*0.48/31, i = 0..31",
+            "l2": "inputs larger than L2 (513 MB of forward lists) and L2 flushed between steps (512 MB write)",
             "parallelism": "replicas" if ws > 1 else "single GPU"}
+
+
+def golden_sweep(g):
+    """The oracle's stored counts of the headline workload (written by
+    tests/golden/make_fullsize_golden.py), if they were made for this input."""
+    try:
+        with open(os.path.join(ROOT, "tests", "golden", "rmat22_sweep32.json")) as f:
+            rec = json.load(f)
+    except Exception:
+        return None
+    import hashlib
+    h = hashlib.sha256()
+    for a in (g.src, g.dst, g.k):
+        h.update(np.ascontiguousarray(a, dtype=np.uint32).tobytes())
+    return rec if rec.get("input_digest") == h.hexdigest()[:24] else None
+
+
+def count_kernel_name(ubt, n_tau):
+    """The counting traversal the current tuning launches."""
+    v = ubt.get_tuning("count_visitor")
+    if v == 1:
+        return "k_traverse<CountReg<%d>>" % (1 if n_tau <= 1 else 2 if n_tau <= 2 else 4 if n_tau <= 4 else 8) \
+            if n_tau <= 8 else "k_traverse<CountMulti>"
+    return "k_traverse<CountBins>"
+
+
+def cpu_sample_desc(tri, mod=CPU_SAMPLE_MOD):
+    return ("R-MAT scale 22, 32 thresholds: the %d triangles whose earliest vertex in Node Order falls in one of "
+            "%d hash classes of the vertices (Alg. 1's outer loop over that class), graph built beforehand"
+            % (tri, mod))
 
 
 def time_steps(fn, steps, warmup, flush=None):
@@ -226,36 +265,56 @@ def time_steps(fn, steps, warmup, flush=None):
 
 
 def reference_arm(args):
-    """CPU oracle as the comparison arm (rank 0 only)."""
+    """CPU oracle as the comparison arm (rank 0 only): each step counts one
+    hash class of 16 of the workload's vertices (Alg. 1 from those vertices,
+    all host cores), on the graph built beforehand."""
     ws, rank, local = dist_env()
     if rank != 0:
         return 0
     import oracle
-    # the benchmark's own workload: one step is one oracle pass over the whole
-    # cl1m graph (about 4.5 s on one core, so the default 3 + 20 steps take
-    # under two minutes)
+    oracle.build()
     g = make_graph(WORKLOAD)
-    T = oracle.num_triangles(g.n, g.src, g.dst)
-    for _ in range(args.warmup):
-        oracle.count_threshold(g.n, g.src, g.dst, g.k, TAUS)
-    times = []
-    for _ in range(args.steps):
+    R = oracle.ResidentGraph(g.n, g.src, g.dst)
+    th = oracle.threads()
+    for i in range(args.warmup):
+        R.count(g.k, TAUS, threads=th, sample_mod=CPU_SAMPLE_MOD, sample_rem=i % CPU_SAMPLE_MOD)
+    times, tris = [], []
+    for i in range(args.steps):
         t0 = time.perf_counter()
-        oracle.count_threshold(g.n, g.src, g.dst, g.k, TAUS)
+        _, _, tri = R.count(g.k, TAUS, threads=th, sample_mod=CPU_SAMPLE_MOD, sample_rem=i % CPU_SAMPLE_MOD)
         times.append(time.perf_counter() - t0)
+        tris.append(tri)
+    R.close()
+    v = float(np.sum(tris)) / float(np.sum(times))
     ms = 1e3 * float(np.mean(times))
-    v = T / (ms / 1e3)
+    T = None
+    try:
+        with open(os.path.join(ROOT, "tests", "golden", "rmat22_sweep32.json")) as f:
+            T = json.load(f)["triangles"]
+    except Exception:
+        pass
     line = {
         "impl": "reference", "metric": METRIC, "value": v, "unit": UNIT, "n_gpus": args.gpus,
         "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True,
         "scaling": "weak", "vs_baseline": None, "dtype": "int64", "data": "synthetic",
         "config": workload_config(g, T, 1),
-        "cpu_baseline": {"value": v, "unit": UNIT, "cores": 1, "kind": "oracle",
-                         "sample": "the whole cl1m graph per step (4 thresholds, one forward-listing pass)"},
+        "cpu_baseline": {"value": v, "unit": UNIT, "cores": th, "kind": "oracle", "cpu": cpu_model(),
+                         "sample": "per step " + cpu_sample_desc(int(np.mean(tris)))},
         "e2e": {"value": v, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
     }
     print(json.dumps(line))
     return 0
+
+
+def cpu_model():
+    try:
+        for line in open("/proc/cpuinfo"):
+            if line.lower().startswith(("model name", "cpu part")):
+                return line.split(":", 1)[1].strip()
+    except OSError:
+        pass
+    import platform
+    return platform.machine()
 
 
 def main():
@@ -269,10 +328,14 @@ def main():
     ap.add_argument("--no-cpu-baseline", dest="cpu", action="store_false", default=True)
     ap.add_argument("--only", default=None,
                     choices=["count", "count32", "count-unpruned", "worlds", "expected", "backward", "enumerate",
-                             "aeo", "aeo-tables", "edge-sampling", "vertex-sampling", "topk"],
+                             "aeo", "aeo-tables", "edge-sampling", "vertex-sampling", "topk", "build", "batch"],
                     help="profiling driver: build the --workload graph, run one form of the query "
                          "--warmup + --steps times, print its mean time and exit")
-    ap.add_argument("--workload", default=WORKLOAD, choices=["cl1m", "rmat22", "rmat20", "cl4m", "er2k"])
+    ap.add_argument("--workload", default=WORKLOAD,
+                    help="graph of the profiling driver: cl1m, rmat22, rmat20, cl4m, er2k, or a smaller "
+                         "rmat<s> (k uniform) / rmat<s>m (rmat22's probability mixture)")
+    ap.add_argument("--knob", action="append", default=[], metavar="NAME=VALUE",
+                    help="profiling driver: set a tuning knob after the shipped tuning is applied (repeatable)")
     ap.add_argument("--digest", action="store_true", help="print the CUDA-source digest and exit")
     ap.add_argument("--tune", action="store_true",
                     help="search the knobs of every benchmark query (no cache) and store the results in the "
@@ -361,7 +424,7 @@ def main():
     alg_bytes = alg_bytes_of(st)
     pk, pk_kind = peaks()
     achieved = alg_bytes / t_step / 1e9
-    kname = "k_traverse<CountBins>" if ubt.get_tuning("count_visitor") == 0 else "k_traverse<CountReg<4>>"
+    kname = count_kernel_name(ubt, len(TAUS))
     roofline = {"bound": "hbm", "achieved": achieved, "peak": pk["hbm_gbs"], "unit": "GB/s",
                 "frac": achieved / pk["hbm_gbs"], "traffic": ncu_traffic(kname, WORKLOAD),
                 "kernel": kname, "peak_kind": pk_kind,
@@ -369,6 +432,26 @@ def main():
                 "table_entries": st["table_entries"], "pairs": st["pairs"],
                 "alg1_probes": info["wedges"]}
     st0 = G.traversal_stats(TAUS, prune=False)
+    golden = golden_sweep(g)
+    if golden is not None:
+        assert np.array_equal(cb, golden["balanced"]) and np.array_equal(cu, golden["unbalanced"]), \
+            "GPU counts differ from the oracle's stored counts"
+        assert T == golden["triangles"]
+
+    # the enumeration of C3 (t = 0.9, both classes) on the same graph
+    nb9, nu9 = G.count_threshold([0.9])
+    cap = int(nb9[0] + nu9[0])
+    recbuf = torch.empty(max(cap, 1) * ubt.TRI_REC_DTYPE.itemsize, dtype=torch.uint8, device="cuda")
+    found = ctypes.c_int64(0)
+
+    def enum():
+        r = ubt.lib().ubt_enumerate(G.handle, 0.9, 3, 1, ctypes.c_void_p(recbuf.data_ptr()), cap,
+                                    ctypes.byref(found), ctypes.c_void_p(torch.cuda.current_stream().cuda_stream))
+        assert r == 0, r
+
+    enum_ms = _events_ms(enum, max(3, args.steps // 4), 1, flush)
+    assert found.value == cap
+    del recbuf
 
     # end to end through the C ABI from pinned host buffers
     hs = torch.from_numpy(g.src.view(np.int32)).pin_memory()
@@ -418,6 +501,10 @@ def main():
         "unpruned": {"ms_per_step": 1e3 * float(np.mean(times_unpruned)),
                      "value": T / float(np.mean(times_unpruned)), "streamed_entries": st0["streamed"],
                      "alg_bytes": alg_bytes_of(st0)},
+        "counts_match_oracle": ("equal to the oracle's stored counts (tests/golden/rmat22_sweep32.json)"
+                                if golden is not None else "stored oracle counts are for another input"),
+        "enumerate_0.9": {"ms": enum_ms, "records": cap, "record_bytes": 24 * cap,
+                          "triangles_per_s": T / (enum_ms / 1e3)},
         "graph": info,
     }
 
@@ -426,15 +513,18 @@ def main():
         _release()
         line["extras"] = extras(ubt, None, g, T, args, flush)
     if args.cpu and rank == 0:
+        # the oracle as it stands, on all host cores, one hash class of 16 of
+        # the vertices (about 1/16 of the work), the graph built beforehand
         import oracle
         oracle.build()
+        R = oracle.ResidentGraph(g.n, g.src, g.dst)
+        th = oracle.threads()
         t1 = time.perf_counter()
-        ob, ou = oracle.count_threshold(g.n, g.src, g.dst, g.k, TAUS)
+        _, _, tri = R.count(g.k, TAUS, threads=th, sample_mod=CPU_SAMPLE_MOD, sample_rem=0)
         dt = time.perf_counter() - t1
-        assert np.array_equal(ob, cb) and np.array_equal(ou, cu), "GPU counts differ from the oracle"
-        line["cpu_baseline"] = {"value": T / dt, "unit": UNIT, "cores": 1, "kind": "oracle",
-                                "sample": "the full cl1m graph, 4 thresholds, one pass (%.1f s)" % dt,
-                                "matches_gpu": True}
+        R.close()
+        line["cpu_baseline"] = {"value": tri / dt, "unit": UNIT, "cores": th, "kind": "oracle", "cpu": cpu_model(),
+                                "sample": cpu_sample_desc(tri) + " (%.1f s)" % dt}
     if ws > 1:
         torch.distributed.barrier()
     if rank == 0:
@@ -442,9 +532,6 @@ def main():
     if ws > 1:
         torch.distributed.destroy_process_group()
     return 0
-
-
-SWEEP32 = [0.51 + i * (0.48 / 31) for i in range(32)]   # 32 thresholds in [0.51, 0.99]
 
 
 def _events_ms(fn, steps, warmup, flush=None):
@@ -465,7 +552,7 @@ def profile_driver(ubt, args):
     import synth
     from paper_2602_14084_gb300 import autotune as at
     g = make_graph(args.workload)
-    taus = SWEEP32 if args.only == "count32" else TAUS
+    taus = SWEEP32 if args.only == "count32" else CL1M_TAUS
 
     def build():
         if args.only in ("expected", "backward"):
@@ -481,13 +568,15 @@ def profile_driver(ubt, args):
     q = {"count": "count", "count32": "count", "count-unpruned": "count", "worlds": "worlds"}.get(args.only)
     rec = None
     if q and not args.no_tune:
-        var = {"count": at.count_variant(len(TAUS), True), "count32": at.count_variant(32, True),
-               "count-unpruned": at.count_variant(len(TAUS), False), "worlds": "W4096"}[args.only]
+        var = {"count": at.count_variant(len(CL1M_TAUS), True), "count32": at.count_variant(32, True),
+               "count-unpruned": at.count_variant(len(CL1M_TAUS), False), "worlds": "W4096"}[args.only]
         rec = at.lookup(q, G.info(), var)
         if rec:
             at.apply(rec["config"])
-            G.close()
-            G = build()
+    if rec or args.knob:
+        at.apply({kv.split("=")[0]: int(kv.split("=")[1]) for kv in args.knob})
+        G.close()
+        G = build()
     counts = torch.empty(2 * len(taus), dtype=torch.int64, device="cuda")
     eo = torch.empty(2, dtype=torch.float64, device="cuda")
     gout = torch.tensor([1.0, 0.0], dtype=torch.float64, device="cuda")
@@ -516,7 +605,29 @@ def profile_driver(ubt, args):
         tout = torch.empty(1000 * ubt.TRI_REC_DTYPE.itemsize, dtype=torch.uint8, device="cuda")
         tn = ctypes.c_int64(0)
     cp = lambda t: ctypes.c_void_p(t.data_ptr())
+    if args.only == "build":
+        src_d = torch.from_numpy(g.src.view(np.int32)).cuda()
+        dst_d = torch.from_numpy(g.dst.view(np.int32)).cuda()
+        k_d = torch.from_numpy((g.k if g.k is not None else synth.quantise(g.p)).view(np.int32)).cuda()
+        keep = []
+
+        def build_once():  # the build kernels of ubt_create_graph (the graph itself is dropped)
+            keep.clear()
+            keep.append(ubt.Graph(g.n, src_d, dst_d, k=k_d))
+    if args.only == "batch":
+        # 500 ego nets (50..5,000 vertices, log-uniform) of the workload graph
+        sel = synth.ego_select(g.n, g.src, g.dst, 500, 50, 5000, 1)
+        eg = synth.ego_induce_torch(g.n, g.src, g.dst, sel, device="cuda")
+        kp = torch.from_numpy(g.k.view(np.int32)).cuda()
+        Gb = ubt.Graph(int(eg["v_off"][-1].item()), eg["src"], eg["dst"], k=kp[eg["eid"].long()], edge_key=eg["eid"],
+                       vertex_offsets=eg["v_off"])
+        ng = Gb.n_graphs
+        bcounts = torch.empty(ng * 6, dtype=torch.int64, device="cuda")
+        bexp = torch.empty(ng * 2, dtype=torch.float64, device="cuda")
+        bworlds = torch.empty(ng * 64, dtype=torch.int64, device="cuda")
     fn = {
+        "build": lambda: build_once() if args.only == "build" else None,
+        "batch": lambda: Gb.batch_query_([0.6, 0.75, 0.9], 11, bcounts, bexp, bworlds) if args.only == "batch" else None,
         "count": lambda: G.count_threshold_(taus, counts, prune=True),
         "count32": lambda: G.count_threshold_(taus, counts, prune=True),
         "count-unpruned": lambda: G.count_threshold_(taus, counts, prune=False),
@@ -536,56 +647,50 @@ def profile_driver(ubt, args):
     }[args.only]
     times = time_steps(fn, args.steps, args.warmup)
     print(json.dumps({"only": args.only, "workload": args.workload, "ms": 1e3 * float(np.mean(times)),
-                      "guard": G.guard(), "tuning": rec["config"] if rec else "defaults"}))
+                      "guard": G.guard(), "tuning": at.current(at.QUERY_KNOBS.get(q or "count", []))}))
     return 0
 
 
-def extra_rmat22(ubt, args, flush):
-    """R-MAT scale 22: the 32-threshold sweep in one traversal, and
-    enumeration at t = 0.9 into a device buffer."""
+def extra_cl1m(ubt, args, flush):
+    """Chung-Lu n = 1e6 (gamma 2.1, mean degree 20, cap 50,000), P+ ~
+    Beta(0.5, 0.5): the 4-threshold query (t = 0.55, 0.70, 0.85, 0.95) pruned
+    and unpruned, its roofline and end to end through ubt_count_host (the
+    counts are checked against the oracle in tests/test_gpu_fullsize.py)."""
     import torch
     from paper_2602_14084_gb300 import autotune as at
-    g = make_graph("rmat22")
-    out = torch.empty(2 * len(SWEEP32), dtype=torch.int64, device="cuda")
-    tuning = tuned(ubt, "count", at.count_variant(len(SWEEP32), True), lambda: ubt.Graph(g.n, g.src, g.dst, k=g.k),
-                   lambda G_: G_.count_threshold_(SWEEP32, out, prune=True), args)
-    t0 = time.perf_counter()
+    g = make_graph("cl1m")
+    out = torch.empty(2 * len(CL1M_TAUS), dtype=torch.int64, device="cuda")
+    tuning = tuned(ubt, "count", at.count_variant(len(CL1M_TAUS), True), lambda: ubt.Graph(g.n, g.src, g.dst, k=g.k),
+                   lambda G_: G_.count_threshold_(CL1M_TAUS, out, prune=True), args)
     G = ubt.Graph(g.n, g.src, g.dst, k=g.k)
-    torch.cuda.synchronize()
-    build_s = time.perf_counter() - t0
     _, _, T, _ = G.expected_counts(with_exact=True)
-    steps = max(3, args.steps // 4)
-    ms = _events_ms(lambda: G.count_threshold_(SWEEP32, out, prune=True), steps, 1, flush)
-    b, u = out.cpu().numpy()[:32], out.cpu().numpy()[32:]
-    b0, u0 = G.count_threshold(SWEEP32, prune=False)
-    assert np.array_equal(b, b0) and np.array_equal(u, u0), "pruned and unpruned sweeps differ"
-    assert np.all(np.diff(b) <= 0) and np.all(np.diff(u) <= 0), "counts not monotone in t"
-    st = G.traversal_stats(SWEEP32, prune=True)
+    steps = max(3, args.steps // 2)
+    ms = _events_ms(lambda: G.count_threshold_(CL1M_TAUS, out, prune=True), steps, 3, flush)
+    b, u = out.cpu().numpy()[:4], out.cpu().numpy()[4:]
+    ms0 = _events_ms(lambda: G.count_threshold_(CL1M_TAUS, out, prune=False), steps, 1, flush)
+    b0, u0 = out.cpu().numpy()[:4], out.cpu().numpy()[4:]
+    assert np.array_equal(b, b0) and np.array_equal(u, u0), "pruned and unpruned counts differ"
+    st = G.traversal_stats(CL1M_TAUS, prune=True)
     alg = alg_bytes_of(st)
     pk, pk_kind = peaks()
-    nb9, nu9 = G.count_threshold([0.9])
-    cap = int(nb9[0] + nu9[0])
-    rec = torch.empty(max(cap, 1) * ubt.TRI_REC_DTYPE.itemsize, dtype=torch.uint8, device="cuda")
-    found = ctypes.c_int64(0)
-
-    def enum():
-        r = ubt.lib().ubt_enumerate(G.handle, 0.9, 3, 1, ctypes.c_void_p(rec.data_ptr()), cap, ctypes.byref(found),
-                                    ctypes.c_void_p(torch.cuda.current_stream().cuda_stream))
-        assert r == 0, r
-
-    ems = _events_ms(enum, steps, 1, flush)
-    assert found.value == cap
-    res = {"workload": "R-MAT scale 22, edge factor 16, (0.57,0.19,0.19,0.05), P+ ~ 0.5 Beta(8,2) + 0.5 Beta(2,8)",
-           "n": g.n, "m": g.m, "triangles": T, "build_s": build_s,
-           "sweep32": {"ms": ms, "triangles_per_s": T / (ms / 1e3), "alg_bytes": alg,
-                       "streamed_entries": st["streamed"], "achieved_gbs": alg / (ms / 1e3) / 1e9,
-                       "frac_hbm": alg / (ms / 1e3) / 1e9 / pk["hbm_gbs"], "peak_kind": pk_kind,
-                       "bal_at_0.51": int(b[0]), "bal_at_0.99": int(b[-1])},
-           "enumerate_0.9": {"ms": ems, "records": cap, "record_bytes": 24 * cap,
-                             "triangles_per_s": T / (ems / 1e3)},
-           "tuning": {k: tuning[k] for k in ("source", "config") if k in tuning}}
-    del G, rec
+    del G
     _release()
+    e2e_ms = []
+    for i in range(4):
+        torch.cuda.synchronize()
+        t1 = time.perf_counter()
+        ubt.count_host(g.n, g.src, g.dst, g.k, CL1M_TAUS)
+        if i:
+            e2e_ms.append(1e3 * (time.perf_counter() - t1))
+    res = {"workload": "Chung-Lu n=1,000,000 gamma=2.1 mean-deg 20 cap 50,000, P+ ~ Beta(0.5,0.5) -> k/65536, "
+                       "4 thresholds in one traversal",
+           "n": g.n, "m": g.m, "triangles": T, "ms": ms, "triangles_per_s": T / (ms / 1e3), "unpruned_ms": ms0,
+           "alg_bytes": alg, "streamed_entries": st["streamed"], "achieved_gbs": alg / (ms / 1e3) / 1e9,
+           "frac_hbm": alg / (ms / 1e3) / 1e9 / pk["hbm_gbs"], "peak_kind": pk_kind,
+           "kernel": count_kernel_name(ubt, 4), "e2e_ms": float(np.mean(e2e_ms)),
+           "e2e_note": "ubt_count_host from pageable numpy arrays (H2D, build, query, D2H), host wall time",
+           "balanced": b.tolist(), "unbalanced": u.tolist(),
+           "tuning": {k: tuning[k] for k in ("source", "config") if k in tuning}}
     return res
 
 
@@ -701,8 +806,60 @@ def extra_grad(ubt, args, flush):
     eb, eu = ubt.expected_counts(G, pt)
     res = {"workload": "Chung-Lu n=4,000,000 gamma=2.3 mean-deg 20 cap 50,000, p ~ U[0,1] float32",
            "n": g.n, "m": g.m, "triangles": int(round(eb.item() + eu.item())), "fwd_ms": fms, "fwd_bwd_ms": fbms,
-           "via": "torch.autograd.Function -> ubt_expected_counts / ubt_expected_counts_backward"}
+           "via": "torch.autograd.Function -> ubt_set_edge_values + ubt_expected_counts / "
+                  "ubt_expected_counts_backward"}
     del G, pt
+    _release()
+    res["subgraph_gradient_check"] = grad_check_subgraph(ubt, g)
+    return res
+
+
+def grad_check_subgraph(ubt, g):
+    """The adjoint's gradient on the subgraph induced by a BFS from a seeded
+    vertex (>= 1,000 edges) against float64 difference quotients of the GPU
+    forward: E is affine in each p_e, so E(p_e = 1) - E(p_e = 0) is dE/dp_e
+    exactly up to the forward's rounding.  Tolerance per edge 1e-5 max(|g|,
+    1e-3 A_e) with A_e = sum over the edge's triangles of |(1-2p_f)(1-2p_g)|,
+    which is the gradient at p' = min(p, 1 - p) (there every factor is |1-2p|)."""
+    import torch
+    import synth
+    deg = np.bincount(np.concatenate([g.src, g.dst]).astype(np.int64), minlength=g.n)
+    start = int(synth.rng(61).choice(np.nonzero(deg >= 10)[0]))
+    verts, ls, ld, eid = synth.bfs_induced(g.n, g.src, g.dst, start, 1000)
+    p = np.ascontiguousarray(g.p[eid])
+    base = torch.from_numpy(p.copy()).cuda()
+    G = ubt.Graph(verts.size, ls, ld, p=base)
+    gout = torch.tensor([1.0, 0.0], dtype=torch.float64, device="cuda")
+    grad = torch.empty(ls.size, dtype=torch.float32, device="cuda")
+
+    def backward_at(q):
+        G.set_edge_values_(q)
+        G.expected_counts_backward_(gout, grad)
+        return grad.double().cpu().numpy()
+
+    got = backward_at(base)
+    A = backward_at(torch.minimum(base, 1.0 - base).contiguous())
+    out = torch.empty(2, dtype=torch.float64, device="cuda")
+    fd = np.zeros(ls.size)
+    for e in range(ls.size):
+        vals = []
+        for x in (1.0, 0.0):
+            q = base.clone()
+            q[e] = x
+            G.set_edge_values_(q)
+            G.expected_counts_(out)
+            vals.append(out[0].item())
+        fd[e] = vals[0] - vals[1]
+    floor = 1e-3 * A
+    tol = 1e-5 * np.maximum(np.abs(fd), floor)
+    nz = np.abs(fd) > 0
+    rel = np.abs(got - fd)[nz] / np.abs(fd)[nz]
+    res = {"vertices": int(verts.size), "edges": int(ls.size), "max_plain_relative_error": float(rel.max()),
+           "median_plain_relative_error": float(np.median(rel)),
+           "edges_using_the_floor": int(np.count_nonzero(floor > np.abs(fd))),
+           "edges_outside_tolerance": int(np.count_nonzero(np.abs(got - fd) > tol + 1e-12)),
+           "guard": G.guard()}
+    del G
     _release()
     return res
 
@@ -888,7 +1045,7 @@ def extras(ubt, G, g, T, args, flush):
     """The other workloads of the path, each on its own graph."""
     from paper_2602_14084_gb300 import autotune as at
     out = {}
-    for name, fn in (("c3_rmat22", extra_rmat22), ("c4_rmat20_worlds", extra_worlds), ("c4_ego10k", extra_ego),
+    for name, fn in (("c2_cl1m", extra_cl1m), ("c4_rmat20_worlds", extra_worlds), ("c4_ego10k", extra_ego),
                      ("c5_cl4m_grad", extra_grad),
                      ("aeo_vs_degree_cl1m", lambda u, a, f: extra_aeo(u, a, f, "cl1m")),
                      ("aeo_vs_degree_rmat22", lambda u, a, f: extra_aeo(u, a, f, "rmat22")),

@@ -481,6 +481,8 @@ ubt_status ubt_topk(ubt_graph* g, int64_t K, int32_t which, ubt_tri_rec* d_out, 
  *   "count_visitor"   threshold counts: 0 (default) classify each triangle
  *                     in the lane that finds it (binned by a slice table);
  *                     1 queue products per warp and classify 32 at a time
+ *                     (by binary search over the levels, or compared with
+ *                     every threshold for at most 8)
  *   "pull"            1 (default): a pair is owned by the endpoint whose
  *                     list is longer, so the shorter list is streamed; 0:
  *                     always by the earlier vertex (Alg. 1 as written)

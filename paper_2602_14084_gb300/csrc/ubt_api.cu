@@ -85,7 +85,7 @@ extern "C" ubt_status ubt_set_tuning(const char* name, int64_t value) {
     if (value < 1 || value > 1024) return UBT_ERR_INVALID_ARG;
     t.small_batch = value;
   } else if (!strcmp(name, "count_visitor")) {
-    if (value < 0 || value > 2) return UBT_ERR_INVALID_ARG;
+    if (value < 0 || value > 1) return UBT_ERR_INVALID_ARG;
     t.count_visitor = value;
   } else if (!strcmp(name, "pull")) {
     if (value < 0 || value > 1) return UBT_ERR_INVALID_ARG;
@@ -179,6 +179,7 @@ extern "C" ubt_status ubt_count_host_workspace_size(int64_t n, int64_t m, size_t
 extern "C" ubt_status ubt_count_host(int64_t n, int64_t m, const uint32_t* h_src, const uint32_t* h_dst,
                                      const uint32_t* h_k, const double* h_tau, int32_t n_tau, int32_t prune,
                                      int64_t* h_counts, void* d_workspace, size_t ws_bytes, void* stream) {
+  UBT_RANGE("ubt_count_host");
   if (!h_counts || !d_workspace || ((uintptr_t)d_workspace & 255)) return UBT_ERR_INVALID_ARG;
   if (m > 0 && (!h_src || !h_dst || !h_k)) return UBT_ERR_INVALID_ARG;
   if (n_tau < 1 || n_tau > 64) return UBT_ERR_INVALID_ARG;

@@ -837,6 +837,7 @@ extern "C" ubt_status ubt_create_graph(int64_t n, int64_t m, const uint32_t* d_s
                                        const uint32_t* d_k, const float* d_p, int32_t flags,
                                        const ubt_graph_opts* opts, void* d_workspace, size_t ws_bytes,
                                        void* stream, ubt_graph** h_out) {
+  UBT_RANGE("ubt_create_graph");
   if (!h_out) return UBT_ERR_INVALID_ARG;
   *h_out = nullptr;
   if (n < 0 || m < 0 || n >= 0xFFFFFFFFll || m >= 0xFFFFFFFFll) return UBT_ERR_INVALID_ARG;
@@ -881,6 +882,8 @@ extern "C" ubt_status ubt_create_graph(int64_t n, int64_t m, const uint32_t* d_s
     k_vertex_graph<<<grid_v, thr, 0, s>>>(opts->d_vertex_offsets, opts->n_graphs, n, L.vgraph);
   }
   // 1. validate + degree
+  NvtxPhases phase;
+  phase.next("build: validate and degree");
   if (m > 0)
     k_validate_degree<<<grid_e, thr, 0, s>>>(n, m, d_src, d_dst, d_k, d_p, L.vgraph, L.deg, &L.scratch->err);
   unsigned long long err = 0;
@@ -889,6 +892,7 @@ extern "C" ubt_status ubt_create_graph(int64_t n, int64_t m, const uint32_t* d_s
   ubt_status st = status_from_err(err);
   if (st != UBT_OK) return st;
   // 2. orientation + CSR offsets
+  phase.next("build: orient, scatter, sort");
   if (m > 0) k_out_degree<<<grid_e, thr, 0, s>>>(m, d_src, d_dst, L.deg, L.fill);
   UBT_CUDA(exclusive_scan_u32(L.fill, L.row_ptr, n, L.scan_tmp, s));
   UBT_CUDA(cudaMemsetAsync(L.fill, 0, sizeof(uint32_t) * (n + 1), s));
@@ -930,6 +934,7 @@ extern "C" ubt_status ubt_create_graph(int64_t n, int64_t m, const uint32_t* d_s
   st = status_from_err(err);
   if (st != UBT_OK) return st;
   // 4. pairs grouped by owner
+  phase.next("build: pairs and work lists");
   UBT_CUDA(cudaMemsetAsync(L.pair_ptr, 0, sizeof(uint32_t) * (n + 1), s));
   if (n > 0) {
     UBT_CUDA(cudaMemsetAsync(L.fill, 0, sizeof(uint32_t) * (n + 1), s));
@@ -979,6 +984,7 @@ extern "C" ubt_status ubt_create_graph(int64_t n, int64_t m, const uint32_t* d_s
   //    the AEO pair partition (optional)
   int64_t n_aowners = 0, n_ablock = 0, max_udeg = 0;
   if (und && n > 0) {
+    phase.next("build: undirected rows in Absolute Edge Order");
     UBT_CUDA(exclusive_scan_u32(L.deg, L.uptr, n, L.scan_tmp, s));
     UBT_CUDA(cudaMemsetAsync(L.fill, 0, sizeof(uint32_t) * (n + 1), s));
     if (m > 0) k_uscatter<<<grid_e, thr, 0, s>>>(m, d_src, d_dst, d_k, L.uptr, L.fill, L.uadj, L.ueid);
@@ -1149,6 +1155,7 @@ __global__ void k_set_edge_values(int64_t m, const float* __restrict__ p, const 
 }  // namespace ubt
 
 extern "C" ubt_status ubt_set_edge_values(ubt_graph* g, const float* d_p, void* stream) {
+  UBT_RANGE("ubt_set_edge_values");
   if (!g || (!d_p && g->m > 0)) return UBT_ERR_INVALID_ARG;
   if (g->kind != UBT_GRAPH_REAL) return UBT_ERR_UNSUPPORTED;
   if (g->m == 0) return UBT_OK;

@@ -3,6 +3,7 @@
 #pragma once
 
 #include <cuda_runtime.h>
+#include <nvtx3/nvToolsExt.h>
 #include <stdint.h>
 
 #include "../../include/ubt.h"
@@ -198,6 +199,32 @@ Tuning& tuning();
   } while (0)
 
 void set_last_cuda_error(cudaError_t e, const char* what, const char* file, int line);
+
+// An NVTX range over a host scope (the build's phases, each query's launch
+// and finish), so that a timeline profiler shows where the library's calls
+// begin and end.  Costs nothing measurable when no profiler is attached.
+struct NvtxRange {
+  explicit NvtxRange(const char* name) { nvtxRangePushA(name); }
+  ~NvtxRange() { nvtxRangePop(); }
+  NvtxRange(const NvtxRange&) = delete;
+  NvtxRange& operator=(const NvtxRange&) = delete;
+};
+// Consecutive phases of one scope: next() closes the open range and opens
+// the next; the last closes with the scope.
+struct NvtxPhases {
+  bool open = false;
+  void next(const char* name) {
+    if (open) nvtxRangePop();
+    nvtxRangePushA(name);
+    open = true;
+  }
+  ~NvtxPhases() {
+    if (open) nvtxRangePop();
+  }
+};
+#define UBT_RANGE_CAT2(a, b) a##b
+#define UBT_RANGE_CAT(a, b) UBT_RANGE_CAT2(a, b)
+#define UBT_RANGE(name) ::ubt::NvtxRange UBT_RANGE_CAT(ubt_range_, __LINE__)(name)
 
 inline size_t align_up(size_t x, size_t a) { return (x + a - 1) / a * a; }
 

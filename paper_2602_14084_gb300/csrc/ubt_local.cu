@@ -781,17 +781,20 @@ using namespace ubt;
 extern "C" ubt_status ubt_edge_local_counts(ubt_graph* g, const uint32_t* d_edges, int64_t k, const double* h_tau,
                                             int32_t n_tau, int64_t* d_bal, int64_t* d_unbal, double* d_estimate,
                                             void* stream) {
+  UBT_RANGE("ubt_edge_local_counts");
   return local_counts(g, d_edges, k, 0, h_tau, n_tau, d_bal, d_unbal, d_estimate, (cudaStream_t)stream);
 }
 
 extern "C" ubt_status ubt_vertex_local_counts(ubt_graph* g, const uint32_t* d_vertices, int64_t k,
                                               const double* h_tau, int32_t n_tau, int64_t* d_bal, int64_t* d_unbal,
                                               double* d_estimate, void* stream) {
+  UBT_RANGE("ubt_vertex_local_counts");
   return local_counts(g, d_vertices, k, 1, h_tau, n_tau, d_bal, d_unbal, d_estimate, (cudaStream_t)stream);
 }
 
 extern "C" ubt_status ubt_vertex_topk(ubt_graph* g, const uint32_t* d_vertices, int64_t k, int32_t K, int32_t which,
                                       ubt_tri_rec* d_out, int32_t* d_n_out, void* stream) {
+  UBT_RANGE("ubt_vertex_topk");
   if (!g || k < 0 || (k > 0 && (!d_vertices || !d_out || !d_n_out))) return UBT_ERR_INVALID_ARG;
   if (K < 1 || K > kTopkMax || (which != 1 && which != 2) || k >= 0xFFFFFFFFll) return UBT_ERR_INVALID_ARG;
   if (g->kind != UBT_GRAPH_FIXED || !g->uptr) return UBT_ERR_UNSUPPORTED;

@@ -66,6 +66,7 @@ __global__ void k_merge_guard(const Scratch* from, Scratch* to) {
 
 extern "C" ubt_status ubt_count_threshold_noalloc(ubt_graph* g, const double* h_tau, int32_t n_tau, int32_t prune,
                                                   int64_t* d_counts, void* stream) {
+  UBT_RANGE("ubt_count_threshold_noalloc");
   if (!g || !d_counts || !h_tau) return UBT_ERR_INVALID_ARG;
   if (n_tau < 1 || n_tau > kNoallocMaxTau) return UBT_ERR_SCRATCH_LIMIT;
   void* base = nullptr;

@@ -416,128 +416,6 @@ struct CountBins {
   }
 };
 
-// CountBins' classification of products queued per warp and classified 32
-// at a time (full warps), into private bins per warp (a warp's shared
-// atomics collide only with its own lanes).  Bins 0 and 2 nt (a product
-// classified at every threshold, or at none) are per-lane registers.  Bins
-// are 32-bit; a warp flushes its bins to the global counters once it has
-// binned 2^30 products, so none can wrap.
-constexpr int kWarpBins = 132;  // >= 2 kMaxTau + 1, a multiple of 4
-struct CountWarpBins {
-  using P = CountBinsP;
-  static constexpr bool kPos = false;
-  static constexpr bool kBatched = true;
-  static constexpr int kRegCap = UBT_COUNT_REGCAP;
-  static constexpr int kTabBytes = CountBins::kTabBytes;
-  static __host__ __device__ int smem_bytes(int threads) {
-    return kTabBytes + 2 * kMaxTau * 8 + (threads / 32) * (kWarpBins * 4 + kHitQueue * 8);
-  }
-  const uint16_t* tab;  // shared: slice table, b0 | c << 8
-  const long long* S;   // shared: levels
-  uint32_t* wb;         // shared: this warp's bins
-  long long* q;         // shared: this warp's queue of products
-  unsigned long long* out;
-  uint32_t qn = 0;
-  uint32_t since = 0;   // products binned by this warp since its last flush
-  uint32_t first = 0, last = 0;  // bins 0 and 2 nt of this lane (< since / 32 + 1 each)
-  int top;
-  __device__ CountWarpBins(const P& p, char* smem) : out(p.out), top(2 * p.nt) {
-    uint16_t* t = (uint16_t*)smem;
-    long long* sv = (long long*)(smem + kTabBytes);
-    char* per = smem + kTabBytes + 2 * kMaxTau * 8;
-    const int warps = blockDim.x >> 5, wid = threadIdx.x >> 5;
-    tab = t;
-    S = sv;
-    wb = (uint32_t*)per + wid * kWarpBins;
-    q = (long long*)(per + warps * kWarpBins * 4) + wid * kHitQueue;
-    for (int i = threadIdx.x; i < 2 * p.nt; i += blockDim.x) sv[i] = p.S[i];
-    for (int i = threadIdx.x; i < warps * kWarpBins; i += blockDim.x) ((uint32_t*)per)[i] = 0;
-    for (int i = threadIdx.x; i < kSlices; i += blockDim.x) {
-      const long long start = (long long)i * (1ll << 35) - (1ll << 45);
-      const long long end = start + (1ll << 35);
-      int b0 = 0, b1 = 0;  // #{S < start}, #{S < end}
-      for (int j = 0; j < 2 * p.nt; j++) {
-        b0 += p.S[j] < start ? 1 : 0;
-        b1 += p.S[j] < end ? 1 : 0;
-      }
-      t[i] = (uint16_t)(b0 | ((b1 - b0) << 8));
-    }
-  }
-  __device__ void block_init() {}
-  // all 32 lanes, converged; `valid` lanes bin their product P
-  __device__ __forceinline__ void count(long long P, bool valid) {
-    const uint32_t e = tab[(uint32_t)((unsigned long long)(P + (1ll << 45)) >> 35)];
-    int r = (int)(e & 0xFFu);
-    const int c = (int)(e >> 8);
-    if (__any_sync(kFull, c != 0)) {  // a level inside the product's slice (rare)
-      const int b0 = r;
-      for (int j = 0; j < c; j++) r += S[b0 + j] < P ? 1 : 0;
-    }
-    const bool f = valid && r == 0, l = valid && r == top;
-    first += f ? 1u : 0u;
-    last += l ? 1u : 0u;
-    if (valid && !f && !l) atomicAdd(&wb[r], 1u);
-  }
-  // adds this warp's bins to the global counters and clears them (all lanes)
-  __device__ void flush() {
-    __syncwarp();
-    for (int i = (int)lane_id() + 1; i < top; i += 32) {
-      const uint32_t v = wb[i];
-      if (v) atomicAdd(&out[i], (unsigned long long)v);
-      wb[i] = 0;
-    }
-    const uint32_t f = __reduce_add_sync(kFull, first), l = __reduce_add_sync(kFull, last);
-    if (lane_id() == 0) {
-      if (f) atomicAdd(&out[0], (unsigned long long)f);
-      if (l) atomicAdd(&out[top], (unsigned long long)l);
-    }
-    first = last = 0;
-    since = 0;
-    __syncwarp();
-  }
-  __device__ void drain32() {
-    __syncwarp();
-    const long long mine = q[lane_id()];
-    queue_shift32(q, qn);
-    count(mine, true);
-    since += 32;
-    if (since >= (1u << 26)) flush();  // the 32 lanes' first / last sum below 2^32
-  }
-  __device__ void drain_all() {
-    __syncwarp();
-    const bool valid = lane_id() < qn;
-    count(valid ? q[lane_id()] : 0ll, valid);
-    qn = 0;
-    __syncwarp();
-  }
-  __device__ __forceinline__ void step(bool hit, uint32_t, uint32_t, uint32_t, uint32_t quv, uint32_t quw,
-                                       uint32_t qvw, uint32_t, uint32_t, uint32_t) {
-    const unsigned m = __ballot_sync(kFull, hit);
-    if (!m) return;
-    if (hit) q[qn + __popc(m & lanemask_lt())] = tri_product(quv, quw, qvw);
-    qn += __popc(m);
-    if (qn >= 32) drain32();
-  }
-  template <int U>
-  __device__ __forceinline__ void steps(const bool (&hit)[U], uint32_t quv, const uint32_t (&quw)[U],
-                                        const uint32_t (&qvw)[U]) {
-    static_assert(U % 2 == 0, "steps come in pairs");
-#pragma unroll
-    for (int s = 0; s < U; s += 2) {
-      if (__any_sync(kFull, hit[s] || hit[s + 1])) {
-        enqueue_pair(q, qn, hit[s], hit[s + 1], quv, quw[s], qvw[s], quw[s + 1], qvw[s + 1]);
-        while (qn >= 32) drain32();
-      }
-    }
-  }
-  __device__ void task_begin(uint32_t) {}
-  __device__ void task_end(uint32_t) {}
-  __device__ void block_end() {
-    drain_all();
-    flush();
-  }
-};
-
 struct FinishMulti {
   int nt;
   int perm[kMaxTau];  // caller index of the i-th smallest threshold
@@ -890,7 +768,7 @@ ubt_status count_impl(ubt_graph* g, const double* h_tau, int32_t n_tau, int32_t 
   std::stable_sort(order.begin(), order.end(), [&](int x, int y) { return lv[x].L < lv[y].L; });
   const int64_t L = prune ? lv[order[0]].L : 0;
   const int64_t visitor = tuning().count_visitor;
-  if (visitor == 0 || visitor == 2) {
+  if (visitor == 0) {
     CountBinsP p;
     p.nt = n_tau;
     for (int i = 0; i < n_tau; i++) {
@@ -899,8 +777,7 @@ ubt_status count_impl(ubt_graph* g, const double* h_tau, int32_t n_tau, int32_t 
     }
     p.out = g->scratch->hist;
     UBT_CUDA(cudaMemsetAsync(g->scratch->hist, 0, sizeof(g->scratch->hist), s));
-    if (visitor == 2) st = launch_count<CountWarpBins>(g, p, L, aeo, s);
-    else st = launch_count<CountBins>(g, p, L, aeo, s);
+    st = launch_count<CountBins>(g, p, L, aeo, s);
     if (st != UBT_OK) return st;
     FinishMulti f;
     f.nt = n_tau;
@@ -954,11 +831,13 @@ ubt_status count_impl(ubt_graph* g, const double* h_tau, int32_t n_tau, int32_t 
 
 extern "C" ubt_status ubt_count_threshold(ubt_graph* g, const double* h_tau, int32_t n_tau, int32_t prune,
                                           int64_t* d_counts, void* stream) {
+  UBT_RANGE("ubt_count_threshold");
   return count_impl(g, h_tau, n_tau, prune, d_counts, false, (cudaStream_t)stream);
 }
 
 extern "C" ubt_status ubt_count_aeo(ubt_graph* g, const double* h_tau, int32_t n_tau, int64_t* d_counts,
                                     void* stream) {
+  UBT_RANGE("ubt_count_aeo");
   return count_impl(g, h_tau, n_tau, 1, d_counts, true, (cudaStream_t)stream);
 }
 
@@ -986,15 +865,18 @@ ubt_status enumerate_impl(ubt_graph* g, double tau, int32_t which, int32_t prune
 
 extern "C" ubt_status ubt_enumerate(ubt_graph* g, double tau, int32_t which, int32_t prune, ubt_tri_rec* d_out,
                                     int64_t capacity, int64_t* h_n_found, void* stream) {
+  UBT_RANGE("ubt_enumerate");
   return enumerate_impl(g, tau, which, prune, d_out, capacity, h_n_found, false, (cudaStream_t)stream);
 }
 
 extern "C" ubt_status ubt_enumerate_aeo(ubt_graph* g, double tau, int32_t which, ubt_tri_rec* d_out,
                                         int64_t capacity, int64_t* h_n_found, void* stream) {
+  UBT_RANGE("ubt_enumerate_aeo");
   return enumerate_impl(g, tau, which, 1, d_out, capacity, h_n_found, true, (cudaStream_t)stream);
 }
 
 extern "C" ubt_status ubt_expected_counts(ubt_graph* g, double* d_out, int64_t* d_exact, void* stream) {
+  UBT_RANGE("ubt_expected_counts");
   if (!g || (!d_out && !d_exact)) return UBT_ERR_INVALID_ARG;
   cudaStream_t s = (cudaStream_t)stream;
   ExpectP p{&g->scratch->tri_count, &g->scratch->sum_lo, &g->scratch->sum_hi};
@@ -1008,6 +890,7 @@ extern "C" ubt_status ubt_expected_counts(ubt_graph* g, double* d_out, int64_t* 
 
 extern "C" ubt_status ubt_expected_counts_backward(ubt_graph* g, const double* d_gout, float* d_grad_p,
                                                    void* stream) {
+  UBT_RANGE("ubt_expected_counts_backward");
   if (!g || !d_gout || (!d_grad_p && g->m > 0)) return UBT_ERR_INVALID_ARG;
   cudaStream_t s = (cudaStream_t)stream;
   if (g->m == 0) return UBT_OK;
@@ -1174,6 +1057,7 @@ extern "C" ubt_status ubt_topk_workspace_size(int64_t K, size_t* h_bytes) {
 
 extern "C" ubt_status ubt_topk(ubt_graph* g, int64_t K, int32_t which, ubt_tri_rec* d_out, int64_t* h_n_out,
                                void* d_work, size_t work_bytes, void* stream) {
+  UBT_RANGE("ubt_topk");
   if (!g || !d_out || !h_n_out || !d_work || K < 1 || K > (1ll << 26)) return UBT_ERR_INVALID_ARG;
   if (which != 1 && which != 2) return UBT_ERR_INVALID_ARG;
   if (g->kind != UBT_GRAPH_FIXED) return UBT_ERR_UNSUPPORTED;

@@ -211,6 +211,11 @@ template <bool kPos>
 struct TableWords {
   static constexpr uint32_t kWords = kPos ? 3u : 2u;
 };
+// 32-bit words of shared memory a table of `slots` slots takes for visitor V
+template <class V>
+__host__ __device__ constexpr uint32_t table_words(uint32_t slots) {
+  return slots * TableWords<V::kPos>::kWords;
+}
 
 // table_find for the 32 converged lanes of a warp (every lane calls it; a
 // lane without an entry passes any key and ignores the result): the search
@@ -577,7 +582,7 @@ __device__ void traverse(const TravArgs& a, V& vis, char* smem_tables) {
     }
   }
   if (kPhases & kWarpTasks) {
-    uint32_t* wtab = tab + (size_t)wid * a.warp_slots * TableWords<V::kPos>::kWords;
+    uint32_t* wtab = tab + (size_t)wid * table_words<V>(a.warp_slots);
     // medium tasks, one warp each
     while (true) {
       unsigned long long t0 = 0;
@@ -594,11 +599,12 @@ __device__ void traverse(const TravArgs& a, V& vis, char* smem_tables) {
 
 // Shared memory of one block of a traversal kernel: visitor bytes + tables
 // (words 32-bit words per table slot).
-inline size_t traverse_smem_bytes(const TravArgs& a, int phases, int threads, int vis_smem, uint32_t words) {
-  const size_t vis_bytes = (size_t)((vis_smem + 15) / 16) * 16;
+template <class V>
+inline size_t traverse_smem_bytes(const TravArgs& a, int phases, int threads) {
+  const size_t vis_bytes = (size_t)((V::smem_bytes(threads) + 15) / 16) * 16;
   size_t tables = 0;
-  if (phases & kBlockTasks) tables = std::max(tables, (size_t)a.hub_slots * words * 4);
-  if (phases & kWarpTasks) tables = std::max(tables, (size_t)(threads / 32) * a.warp_slots * words * 4);
+  if (phases & kBlockTasks) tables = std::max(tables, (size_t)table_words<V>(a.hub_slots) * 4);
+  if (phases & kWarpTasks) tables = std::max(tables, (size_t)(threads / 32) * table_words<V>(a.warp_slots) * 4);
   return vis_bytes + tables;
 }
 
@@ -627,7 +633,7 @@ template <class V, int kPhases>
 ubt_status launch_phase(const ubt_graph* g, const TravArgs& a, const typename V::P& p, int threads, cudaStream_t s) {
   const Tuning& T = tuning();
   threads = (int)std::min<int64_t>(Bounds<V, kPhases>::kThreads, std::max<int64_t>(64, threads / 32 * 32));
-  const size_t smem = traverse_smem_bytes(a, kPhases, threads, V::smem_bytes(threads), TableWords<V::kPos>::kWords);
+  const size_t smem = traverse_smem_bytes<V>(a, kPhases, threads);
   UBT_CUDA(cudaFuncSetAttribute(k_traverse<V, kPhases>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
   int per_sm = 0;
   UBT_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_traverse<V, kPhases>, threads, smem));
@@ -643,6 +649,7 @@ ubt_status launch_phase(const ubt_graph* g, const TravArgs& a, const typename V:
 // tasks) run one after the other on `s`.
 template <class V>
 ubt_status launch_traversal(const ubt_graph* g, const TravArgs& a, const typename V::P& p, cudaStream_t s) {
+  UBT_RANGE("traversal launch");
   const Tuning& T = tuning();
   UBT_CUDA(cudaMemsetAsync(a.sc, 0, kScratchHeader / 2, s));
   if (a.n_giant + a.n_hub > 0) {

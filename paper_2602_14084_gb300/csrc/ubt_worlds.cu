@@ -420,6 +420,7 @@ extern "C" ubt_status ubt_sample_worlds_workspace_size(const ubt_graph* g, int64
 
 extern "C" ubt_status ubt_sample_worlds(ubt_graph* g, uint64_t seed, int64_t W, int64_t* d_bal_per_world,
                                         int64_t* d_total, void* d_workspace, size_t ws_bytes, void* stream) {
+  UBT_RANGE("ubt_sample_worlds");
   if (!g || !d_bal_per_world || W < 64 || W % 64 || W / 64 > 0xFFFFFFFFll) return UBT_ERR_INVALID_ARG;
   if (g->kind != UBT_GRAPH_FIXED) return UBT_ERR_UNSUPPORTED;
   if (!d_workspace || ((uintptr_t)d_workspace & 255)) return UBT_ERR_INVALID_ARG;
@@ -449,6 +450,7 @@ extern "C" ubt_status ubt_sample_worlds(ubt_graph* g, uint64_t seed, int64_t W, 
 
 extern "C" ubt_status ubt_batch_query(ubt_graph* g, const double* h_tau, int32_t n_tau, uint64_t seed,
                                       int64_t* d_counts, double* d_expect, int64_t* d_worlds, void* stream) {
+  UBT_RANGE("ubt_batch_query");
   if (!g || !h_tau || !d_counts || n_tau < 1 || n_tau > kBatchTau) return UBT_ERR_INVALID_ARG;
   if (!g->vgraph) return UBT_ERR_INVALID_ARG;
   if (g->kind != UBT_GRAPH_FIXED) return UBT_ERR_UNSUPPORTED;

@@ -3,29 +3,51 @@ times (the package's shipped tunings applied the same way).
 
 Where the oracle finishes in seconds it runs on the whole graph (Chung-Lu
 n=1e6: counts, exact expected-count sums, enumeration; Chung-Lu n=4e6:
-expected counts and the whole gradient).  Where it does not (R-MAT scale 22
-and 20, tens of millions of edges), the GPU outputs are checked through
-outputs the oracle can compute one by one -- every enumeration record is a
-triangle of the input with the right class and P_bal, and for sampled
-vertices the records through that vertex equal the oracle's enumeration of
-its ego net -- and through properties that hold at any size (pruned ==
+expected counts and the whole gradient).  Where it needs minutes (R-MAT
+scale 22 and 20, tens of millions of edges), its values were written once by
+tests/golden/make_fullsize_golden.py (which calls only the oracle) and are
+compared exactly: R-MAT 22's triangle count and 32-threshold counts, R-MAT
+20's balanced counts in every world of four seeded world words and their sum
+over all 4,096 worlds.  Each stored file carries a digest of its input, which
+the test checks first.  On top: every enumeration record is a triangle of
+the input with the class and P_bal of the paper's four-term sum, and for
+sampled vertices the records through that vertex equal the oracle's
+enumeration of its ego net; properties that hold at any size (pruned ==
 unpruned, both pair directions agree, monotonicity in t, the t = 0.5
 partition, words-per-pass invariance of the sign worlds, the Monte-Carlo
 mean against the exact expectation).  Counts and records are compared
 exactly; floating-point values within the tolerances of the other parity
 tests.
 """
+import hashlib
+import json
+import os
+
 import numpy as np
 import pytest
 
 import oracle
 import synth
-from gpu_util import require_gpu, sort_records
+from gpu_util import difference_quotients, grad_report, require_gpu, sort_records
 
 pytestmark = pytest.mark.gpu
 
 TAUS = [0.55, 0.70, 0.85, 0.95]
 SWEEP32 = [0.51 + i * (0.48 / 31) for i in range(32)]
+GOLDEN = os.path.join(os.path.dirname(os.path.abspath(__file__)), "golden")
+
+
+def stored(name, g):
+    """The oracle's stored values for graph g, after checking they were made
+    from the same input arrays."""
+    with open(os.path.join(GOLDEN, name)) as f:
+        rec = json.load(f)
+    h = hashlib.sha256()
+    for a in (g.src, g.dst, g.k):
+        h.update(np.ascontiguousarray(a, dtype=np.uint32).tobytes())
+    assert rec["input_digest"] == h.hexdigest()[:24], "the generator produced another graph than the stored one"
+    assert rec["n"] == g.n and rec["m"] == g.m
+    return rec
 
 
 @pytest.fixture(scope="module")
@@ -86,17 +108,22 @@ def test_cl1m_full_counts_expected_and_enumeration(ubt):
 
 
 def test_rmat22_full_sweep_and_enumeration(ubt):
-    """R-MAT scale 22 (64.2M edges): the 32-threshold sweep and the t = 0.9
-    enumeration, by properties and sampled oracle checks."""
+    """R-MAT scale 22 (64.2M edges): the 32-threshold sweep against the
+    oracle's stored counts, and the t = 0.9 enumeration by the four-term sum
+    per record and sampled oracle enumerations."""
     from paper_2602_14084_gb300 import autotune as at
     g = synth.config_graph("rmat22")
+    want = stored("rmat22_sweep32.json", g)
+    assert want["taus"] == SWEEP32
     G, saved = bench_graph(ubt, g, "count", at.count_variant(32, True), k=g.k)
     try:
         b, u = G.count_threshold(SWEEP32, prune=1)
+        assert np.array_equal(b, want["balanced"]) and np.array_equal(u, want["unbalanced"])
         b0, u0 = G.count_threshold(SWEEP32, prune=0)
         assert np.array_equal(b, b0) and np.array_equal(u, u0)
         assert np.all(np.diff(b) <= 0) and np.all(np.diff(u) <= 0)
         _, _, T, _ = G.expected_counts(with_exact=True)
+        assert T == want["triangles"]
         hb, hu = G.count_threshold([0.5], prune=1)
         assert int(hb[0]) + int(hu[0]) == T  # at t = 0.5 every triangle is classified once
         assert b[0] + u[0] <= T
@@ -116,16 +143,19 @@ def test_rmat22_full_sweep_and_enumeration(ubt):
         G.close()
     finally:
         at.apply(saved)
-    # every record: a triangle of the input, classified and valued as the oracle does
+    # every record: a triangle of the input, classified and valued by the
+    # paper's four-term sum (Sec. 3) in exact integers, as the oracle does:
+    # N = 2^48 P_bal = k1 k2 k3 + k1 k2' k3' + k1' k2 k3' + k1' k2' k3, k' = 2^16 - k
     keys, ks = edge_k_lookup(g.n, g.src, g.dst, g.k)
     uvw, cls, pb = sort_records(rec)
     assert np.all((uvw[:, 0] < uvw[:, 1]) & (uvw[:, 1] < uvw[:, 2]))
     assert np.unique(uvw, axis=0).shape[0] == uvw.shape[0]
-    q = [32768 - k_of(g.n, keys, ks, uvw[:, i], uvw[:, j]) for i, j in ((0, 1), (0, 2), (1, 2))]
-    P = q[0] * q[1] * q[2]
-    assert np.array_equal(pb, ((1 << 45) - P).astype(np.float64) * 2.0 ** -46)
-    X = (2 * 0.9 - 1) * 2.0 ** 45
-    want_cls = np.where(P <= -np.ceil(X), 1, np.where(P > np.floor(X), 2, 0))
+    k1, k2, k3 = [k_of(g.n, keys, ks, uvw[:, i], uvw[:, j]) for i, j in ((0, 1), (0, 2), (1, 2))]
+    c1, c2, c3 = 65536 - k1, 65536 - k2, 65536 - k3
+    N = k1 * k2 * k3 + k1 * c2 * c3 + c1 * k2 * c3 + c1 * c2 * k3
+    assert np.array_equal(pb, N.astype(np.float64) * 2.0 ** -48)
+    tb, tu = int(np.ceil(0.9 * 2.0 ** 48)), int(np.floor(0.9 * 2.0 ** 48))
+    want_cls = np.where(N >= tb, 1, np.where((1 << 48) - N > tu, 2, 0))
     assert np.array_equal(cls, want_cls)
     # completeness on sampled vertices: all records through v = the oracle's
     # enumeration of v's ego net (v and all its neighbours) restricted to v
@@ -154,20 +184,28 @@ def test_rmat22_full_sweep_and_enumeration(ubt):
 
 
 def test_rmat20_worlds_full(ubt):
-    """R-MAT scale 20 (15.7M edges), W = 4096 sign worlds: words per pass do
+    """R-MAT scale 20 (15.7M edges), W = 4096 sign worlds: the oracle's counts
+    of four seeded world words and its sum over all worlds; words per pass do
     not change a count, totals agree, and the Monte-Carlo mean of the
     balanced count lies within 5 standard errors of its exact expectation."""
     import torch
     from paper_2602_14084_gb300 import autotune as at
     g = synth.config_graph("rmat20")
+    want = stored("rmat20_worlds.json", g)
     G, saved = bench_graph(ubt, g, "worlds", "W4096", k=g.k)
     try:
         W = 4096
+        assert want["W"] == W and want["world_seed"] == 7
         eb, _, T, _ = G.expected_counts(with_exact=True)
         out = torch.empty(W, dtype=torch.int64, device="cuda")
         tot = torch.empty(1, dtype=torch.int64, device="cuda")
         G.sample_worlds_(7, W, out, tot)
         a = out.cpu().numpy()
+        # the oracle's per-world counts of the stored words, and their sum over all worlds
+        for w, counts in want["per_world"].items():
+            w = int(w)
+            assert np.array_equal(a[64 * w:64 * (w + 1)], counts), w
+        assert int(a.sum()) == want["balanced_sum_over_all_worlds"]
         wpp = ubt.get_tuning("world_words_per_pass")
         ubt.set_tuning("world_words_per_pass", 8 if wpp != 8 else 64)
         G.sample_worlds_(7, W, out, tot)
@@ -277,3 +315,40 @@ def test_cl1m_full_aeo_sampling_and_topk(ubt):
         assert G.guard() == 0
     finally:
         G.close()
+
+
+def test_cl4m_subgraph_gradient_against_difference_quotients(ubt):
+    """Chung-Lu n=4e6, p ~ U[0,1] float32: on the subgraph induced by a BFS
+    from a seeded vertex, grown until it holds >= 1,000 edges, the adjoint's
+    gradient of every edge against float64 difference quotients of the GPU
+    forward and against the oracle's analytic gradient.  E is affine in each
+    p_e, so the central difference at p_e = 1/2 with h = 1/2, E(p_e = 1) -
+    E(p_e = 0), is exact up to the forward's rounding (endpoints stored
+    exactly).  Tolerance per edge: 1e-5 max(|g|, 1e-3 sum |terms|); the plain
+    relative error and the number of edges where the floor applied are
+    printed."""
+    import torch
+    g = synth.config_graph("cl4m")
+    deg = np.bincount(np.concatenate([g.src, g.dst]).astype(np.int64), minlength=g.n)
+    start = int(synth.rng(61).choice(np.nonzero(deg >= 10)[0]))
+    verts, ls, ld, eid = synth.bfs_induced(g.n, g.src, g.dst, start, 1000)
+    assert ls.size >= 1000
+    p = np.ascontiguousarray(g.p[eid])
+    pt = torch.from_numpy(p.copy()).cuda().requires_grad_(True)
+    G = ubt.Graph(verts.size, ls, ld, p=pt.detach())
+    eb, _ = ubt.expected_counts(G, pt)
+    eb.backward()
+    got = pt.grad.double().cpu().numpy()
+    fd = difference_quotients(ubt, G, p, np.arange(ls.size))
+    og, ga = oracle.grad_real(verts.size, ls, ld, p, with_abs=True)
+    for name, ref in (("difference quotients", fd), ("oracle analytic", og)):
+        ok, rel, floored = grad_report(got, ref, ga)
+        nz = np.abs(ref) > 0
+        print("C5 subgraph (%d vertices, %d edges) vs %s: max plain relative error %.3e over %d edges with "
+              "a nonzero gradient, floor used on %d edges, %d outside tolerance"
+              % (verts.size, ls.size, name, float(rel[nz].max()) if nz.any() else 0.0, int(nz.sum()), floored,
+                 int((~ok).sum())))
+        assert ok.all(), name
+    # the two references agree with each other as well
+    assert np.allclose(fd, og, rtol=1e-6, atol=1e-8)
+    assert G.guard() == 0

@@ -609,7 +609,7 @@ __global__ void k_finish_adjoint(int64_t m, const unsigned long long* __restrict
 // entries, [3] tasks
 __global__ void k_trav_stats(int64_t n, const uint32_t* __restrict__ row_ptr, const uint64_t* __restrict__ adj,
                              const uint32_t* __restrict__ pair_ptr, const uint64_t* __restrict__ pairs, int64_t L,
-                             unsigned long long* out) {
+                             uint32_t light, unsigned long long* out) {
   const int lane = (int)lane_id();
   const int64_t warps = (int64_t)gridDim.x * (blockDim.x >> 5);
   unsigned long long tab = 0, npairs = 0, str = 0, tasks = 0;
@@ -635,7 +635,7 @@ __global__ void k_trav_stats(int64_t n, const uint32_t* __restrict__ row_ptr, co
       if (L > 0 && qe * (1ll << 30) < L) continue;
       const uint32_t vs = row_ptr[sv];
       uint32_t dv = row_ptr[sv + 1] - vs;
-      if (L > 0) dv = prune_prefix(adj + vs, dv, qe * qmax, L);
+      if (L > 0) dv = light ? stream_prefix(adj + vs, dv, qe * qmax, L) : prune_prefix(adj + vs, dv, qe * qmax, L);
       npairs += 1;
       str += dv;
     }
@@ -684,6 +684,7 @@ TravArgs make_trav_args(const ubt_graph* g, int64_t L, bool with_pos) {
   a.long_min = (uint32_t)T.long_min;
   a.long_tail = (uint32_t)T.long_tail;
   a.L = L;
+  a.light_prune = light_prune_for(L);
   return a;
 }
 
@@ -922,7 +923,7 @@ extern "C" ubt_status ubt_traversal_stats(ubt_graph* g, const double* h_tau, int
   UBT_CUDA(cudaMemsetAsync(d, 0, 4 * sizeof(unsigned long long), s));
   if (g->n > 0) {
     const int grid = (int)std::min<int64_t>((g->n + 7) / 8, (int64_t)g->sm_count * 16);
-    k_trav_stats<<<grid, 256, 0, s>>>(g->n, g->row_ptr, g->adj, g->pair_ptr, g->pairs, L, d);
+    k_trav_stats<<<grid, 256, 0, s>>>(g->n, g->row_ptr, g->adj, g->pair_ptr, g->pairs, L, light_prune_for(L), d);
     UBT_CUDA(cudaGetLastError());
   }
   unsigned long long h[4];

@@ -308,8 +308,90 @@ __global__ void k_sort_mid_rows(const uint32_t* __restrict__ rows, uint32_t nrow
   }
 }
 
-// Longer lists: one block per list, bitonic network in shared memory (or in a
-// per-block global slice for lists longer than the "sort_smem_max" tuning).
+// Lists of 129..4096 entries (at most the "sort_smem_max" tuning): one block
+// per list sorts 64-bit words (sort key << 12 | position in the list) in
+// shared memory; the keys are distinct by construction, so the network only
+// moves one word per comparator, and the entries are gathered by position
+// once at the end.
+constexpr int kPackedSortThreads = 512;
+constexpr int kPackedPerThread = 8;                  // 4096 entries / 512 threads
+constexpr uint32_t kPackedMax = kPackedSortThreads * kPackedPerThread;
+
+// ascending bitonic network over pk[0..cap), cap a power of two
+__device__ __forceinline__ void bitonic_packed(unsigned long long* pk, uint32_t cap) {
+  for (uint32_t kk = 2; kk <= cap; kk <<= 1) {
+    for (uint32_t j = kk >> 1; j > 0; j >>= 1) {
+      for (uint32_t t = threadIdx.x; t < (cap >> 1); t += blockDim.x) {
+        const uint32_t i = ((t & ~(j - 1)) << 1) | (t & (j - 1));  // the comparator's lower index
+        const uint32_t ixj = i | j;
+        const unsigned long long a = pk[i], b = pk[ixj];
+        const unsigned long long lo = a < b ? a : b, hi = a < b ? b : a;
+        const bool asc = (i & kk) == 0;
+        pk[i] = asc ? lo : hi;
+        pk[ixj] = asc ? hi : lo;
+      }
+      __syncthreads();
+    }
+  }
+}
+
+__global__ void __launch_bounds__(kPackedSortThreads)
+k_sort_long_rows_packed(const uint32_t* __restrict__ rows, uint32_t nrows, const uint32_t* __restrict__ row_ptr,
+                        uint64_t* adj, uint32_t* eid, uint32_t* ekey, int fixed, unsigned long long* err) {
+  extern __shared__ __align__(16) unsigned long long pk[];
+  for (uint32_t r = blockIdx.x; r < nrows; r += gridDim.x) {
+    const uint32_t u = rows[r];
+    const uint32_t rs = row_ptr[u], len = row_ptr[u + 1] - rs;
+    if (len > kPackedMax) {  // the collector never lists such a row here
+      if (threadIdx.x == 0) report(err, rs, -UBT_ERR_INVALID_ARG);
+      continue;
+    }
+    uint32_t cap = 64;
+    while (cap < len) cap <<= 1;
+    for (uint32_t i = threadIdx.x; i < cap; i += blockDim.x)
+      pk[i] = i < len ? (key_by_col(adj[rs + i]) << 12) | i : ~0ull;
+    __syncthreads();
+    bitonic_packed(pk, cap);
+    for (uint32_t i = threadIdx.x + 1; i < len; i += blockDim.x)
+      if ((pk[i] >> 12) == (pk[i - 1] >> 12)) report(err, rs + i, -UBT_ERR_DUPLICATE_EDGE);
+    if (fixed) {
+      __syncthreads();
+      for (uint32_t i = threadIdx.x; i < len; i += blockDim.x) {
+        const uint32_t w = (uint32_t)(pk[i] & 0xFFFu);
+        pk[i] = (key_by_absq(adj[rs + w]) << 12) | w;
+      }
+      __syncthreads();
+      bitonic_packed(pk, cap);
+    }
+    // gather every entry's sources before any thread overwrites the list
+    uint64_t e[kPackedPerThread];
+    uint32_t d[kPackedPerThread], y[kPackedPerThread];
+#pragma unroll
+    for (int c = 0; c < kPackedPerThread; c++) {
+      const uint32_t i = threadIdx.x + c * kPackedSortThreads;
+      if (i < len) {
+        const uint32_t w = (uint32_t)(pk[i] & 0xFFFu);
+        e[c] = adj[rs + w];
+        d[c] = eid[rs + w];
+        y[c] = ekey ? ekey[rs + w] : 0u;
+      }
+    }
+    __syncthreads();
+#pragma unroll
+    for (int c = 0; c < kPackedPerThread; c++) {
+      const uint32_t i = threadIdx.x + c * kPackedSortThreads;
+      if (i < len) {
+        adj[rs + i] = e[c];
+        eid[rs + i] = d[c];
+        if (ekey) ekey[rs + i] = y[c];
+      }
+    }
+    __syncthreads();
+  }
+}
+
+// Longer lists: one block per list, bitonic network in a per-block global
+// slice (lists longer than the "sort_smem_max" tuning).
 template <bool kGlobal>
 __global__ void k_sort_long_rows(const uint32_t* __restrict__ rows, uint32_t nrows, const uint32_t* __restrict__ row_ptr,
                                  uint64_t* adj, uint32_t* eid, uint32_t* ekey, int fixed, unsigned long long* err,
@@ -915,11 +997,11 @@ extern "C" ubt_status ubt_create_graph(int64_t n, int64_t m, const uint32_t* d_s
                                         L.ekey, fixed, &L.scratch->err);
     }
     if (lc[0]) {
-      const size_t smem = (size_t)std::max<uint32_t>(sort_smem, 64) * 24;
-      UBT_CUDA(cudaFuncSetAttribute(k_sort_long_rows<false>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
-      const int g = (int)std::min<unsigned long long>(lc[0], (unsigned long long)sms * 8);
-      k_sort_long_rows<false><<<g, 512, smem, s>>>(L.mid_rows, (uint32_t)lc[0], L.row_ptr, L.adj, L.eid, L.ekey,
-                                                   fixed, &L.scratch->err, nullptr, 0);
+      const size_t smem = (size_t)std::max<uint32_t>(sort_smem, 64) * 8;
+      UBT_CUDA(cudaFuncSetAttribute(k_sort_long_rows_packed, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+      const int g = (int)std::min<unsigned long long>(lc[0], (unsigned long long)sms * 4);
+      k_sort_long_rows_packed<<<g, kPackedSortThreads, smem, s>>>(L.mid_rows, (uint32_t)lc[0], L.row_ptr, L.adj,
+                                                                  L.eid, L.ekey, fixed, &L.scratch->err);
     }
     if (lc[1]) {
       const int64_t cap = pow2_at_least(list_bound(n, m));
@@ -1001,11 +1083,11 @@ extern "C" ubt_status ubt_create_graph(int64_t n, int64_t m, const uint32_t* d_s
                                          nullptr, 1, &L.scratch->err);
     }
     if (lc[0]) {
-      const size_t smem = (size_t)std::max<uint32_t>(sort_smem, 64) * 24;
-      UBT_CUDA(cudaFuncSetAttribute(k_sort_long_rows<false>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
-      const int g2 = (int)std::min<unsigned long long>(lc[0], (unsigned long long)sms * 8);
-      k_sort_long_rows<false><<<g2, 512, smem, s>>>(L.mid_rows, (uint32_t)lc[0], L.uptr, L.uadj, L.ueid, nullptr,
-                                                    1, &L.scratch->err, nullptr, 0);
+      const size_t smem = (size_t)std::max<uint32_t>(sort_smem, 64) * 8;
+      UBT_CUDA(cudaFuncSetAttribute(k_sort_long_rows_packed, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+      const int g2 = (int)std::min<unsigned long long>(lc[0], (unsigned long long)sms * 4);
+      k_sort_long_rows_packed<<<g2, kPackedSortThreads, smem, s>>>(L.mid_rows, (uint32_t)lc[0], L.uptr, L.uadj,
+                                                                   L.ueid, nullptr, 1, &L.scratch->err);
     }
     if (lc[1]) {
       const int g2 = (int)std::min<unsigned long long>(lc[1], (unsigned long long)sms * 2);

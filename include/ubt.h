@@ -523,8 +523,12 @@ ubt_status ubt_topk(ubt_graph* g, int64_t K, int32_t which, ubt_tri_rec* d_out, 
  *   "sort_smem_max"   longest forward list sorted in shared memory during the
  *                     build (power of two, 64..4096); longer lists are sorted
  *                     in a global-memory slice
+ *   "warp_sort_max"   longest forward list sorted by one warp in registers
+ *                     during the build (128, 256 or 512; at most
+ *                     sort_smem_max unless 128); longer lists up to
+ *                     sort_smem_max are sorted by one block in shared memory
  * Build-time knobs (pull, hub_threshold, block_work, smem_table_max,
- * sort_smem_max) apply to graphs created afterwards; query the workspace size
+ * sort_smem_max, warp_sort_max) apply to graphs created afterwards; query the workspace size
  * after setting them.
  */
 ubt_status ubt_set_tuning(const char* name, int64_t value);

@@ -111,6 +111,9 @@ extern "C" ubt_status ubt_set_tuning(const char* name, int64_t value) {
   } else if (!strcmp(name, "sort_smem_max")) {
     if (value < 64 || value > 4096 || (value & (value - 1))) return UBT_ERR_INVALID_ARG;
     t.sort_smem_max = value;
+  } else if (!strcmp(name, "warp_sort_max")) {
+    if (value != 128 && value != 256 && value != 512) return UBT_ERR_INVALID_ARG;
+    t.warp_sort_max = value;
   } else {
     return UBT_ERR_INVALID_ARG;
   }
@@ -128,6 +131,7 @@ extern "C" ubt_status ubt_get_tuning(const char* name, int64_t* h_value) {
   else if (!strcmp(name, "world_words_per_pass")) *h_value = t.world_words_per_pass;
   else if (!strcmp(name, "small_batch")) *h_value = t.small_batch;
   else if (!strcmp(name, "sort_smem_max")) *h_value = t.sort_smem_max;
+  else if (!strcmp(name, "warp_sort_max")) *h_value = t.warp_sort_max;
   else if (!strcmp(name, "pull")) *h_value = t.pull;
   else if (!strcmp(name, "count_visitor")) *h_value = t.count_visitor;
   else if (!strcmp(name, "block_work")) *h_value = t.block_work;

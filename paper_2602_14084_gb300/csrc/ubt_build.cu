@@ -28,7 +28,6 @@ namespace ubt {
 namespace {
 
 constexpr int kSortHugeBlocks = 16;  // blocks sorting lists longer than that
-constexpr int kBuckets = 64;
 
 // error word: lowest (edge index << 8 | code) wins, so the report is deterministic
 __device__ inline void report(unsigned long long* err, uint64_t index, int code) {
@@ -224,46 +223,105 @@ __global__ void k_sort_short_rows(int64_t n, const uint32_t* __restrict__ row_pt
   }
 }
 
-// Rows of 33..128 entries: one warp per row, four entries per lane (entry
-// r * 32 + lane in register r), bitonic network across registers and lanes.
-__device__ __forceinline__ void cswap4(uint64_t (&k)[4], uint64_t (&e)[4], uint32_t (&d)[4], uint32_t (&y)[4], int a,
-                                       int b, bool asc) {
-  const bool sw = asc ? (k[a] > k[b]) : (k[a] < k[b]);
-  if (sw) {
-    uint64_t t = k[a]; k[a] = k[b]; k[b] = t;
-    t = e[a]; e[a] = e[b]; e[b] = t;
-    uint32_t x = d[a]; d[a] = d[b]; d[b] = x;
-    x = y[a]; y[a] = y[b]; y[b] = x;
-  }
-}
-__device__ __forceinline__ void warp_sort128(uint64_t (&k)[4], uint64_t (&e)[4], uint32_t (&d)[4], uint32_t (&y)[4],
-                                             int lane) {
+// Rows of 33..512 entries: one warp per row, R = 4, 8 or 16 words per lane
+// (entry r * 32 + lane in register r).  A word is the sort key << 12 | the
+// entry's position in the row; the words are distinct, so a bitonic network
+// over registers and lanes moves one word per comparator, and the entries are
+// gathered by position once at the end.
+template <int R>
+__device__ __forceinline__ void warp_bitonic(unsigned long long (&k)[R], int lane) {
 #pragma unroll
-  for (int kk = 2; kk <= 128; kk <<= 1) {
+  for (int kk = 2; kk <= 32 * R; kk <<= 1) {
 #pragma unroll
     for (int j = kk >> 1; j > 0; j >>= 1) {
       if (j >= 32) {  // partner in another register of the same lane
         const int rj = j >> 5;
 #pragma unroll
-        for (int r = 0; r < 4; r++)
-          if ((r & rj) == 0) cswap4(k, e, d, y, r, r | rj, (((r << 5) | lane) & kk) == 0);
+        for (int r = 0; r < R; r++) {
+          if ((r & rj) == 0) {
+            const unsigned long long a = k[r], b = k[r | rj];
+            const bool asc = (((r << 5) | lane) & kk) == 0;
+            k[r] = (a < b) == asc ? a : b;
+            k[r | rj] = (a < b) == asc ? b : a;
+          }
+        }
       } else {        // partner in another lane, same register
 #pragma unroll
-        for (int r = 0; r < 4; r++) {
-          const uint64_t ok = __shfl_xor_sync(kFull, k[r], j);
-          const uint64_t oe = __shfl_xor_sync(kFull, e[r], j);
-          const uint32_t od = __shfl_xor_sync(kFull, d[r], j);
-          const uint32_t oy = __shfl_xor_sync(kFull, y[r], j);
+        for (int r = 0; r < R; r++) {
+          const unsigned long long o = __shfl_xor_sync(kFull, k[r], j);
           const bool up = (((r << 5) | lane) & kk) == 0;
-          const bool lower = (lane & j) == 0;
-          const bool sw = (lower == up) ? (ok < k[r]) : (ok > k[r]);
-          if (sw) { k[r] = ok; e[r] = oe; d[r] = od; y[r] = oy; }
+          const bool take_min = ((lane & j) == 0) == up;
+          k[r] = take_min ? (o < k[r] ? o : k[r]) : (o > k[r] ? o : k[r]);
         }
       }
     }
   }
 }
 
+template <int R>
+__device__ __forceinline__ void sort_row_warp(uint64_t* adj, uint32_t* eid, uint32_t* ekey, uint32_t rs, uint32_t len,
+                                              int fixed, unsigned long long* err, int lane) {
+  unsigned long long k[R];
+#pragma unroll
+  for (int r = 0; r < R; r++) {
+    const uint32_t i = (uint32_t)(r * 32 + lane);
+    k[r] = i < len ? (key_by_col(adj[rs + i]) << 12) | i : ~0ull;
+  }
+  warp_bitonic<R>(k, lane);
+#pragma unroll
+  for (int r = 0; r < R; r++) {  // duplicates: equal neighbours at adjacent sorted positions
+    const unsigned long long up1 = __shfl_up_sync(kFull, k[r], 1);
+    const unsigned long long last = __shfl_sync(kFull, k[r > 0 ? r - 1 : 0], 31);
+    const unsigned long long prev = lane > 0 ? up1 : last;
+    const uint32_t i = (uint32_t)(r * 32 + lane);
+    if (i < len && i > 0 && (prev >> 12) == (k[r] >> 12)) report(err, rs + i, -UBT_ERR_DUPLICATE_EDGE);
+  }
+  if (fixed) {
+#pragma unroll
+    for (int r = 0; r < R; r++) {
+      const uint32_t i = (uint32_t)(r * 32 + lane);
+      const uint32_t w = (uint32_t)(k[r] & 0xFFFu);
+      k[r] = i < len ? (key_by_absq(adj[rs + w]) << 12) | w : ~0ull;
+    }
+    warp_bitonic<R>(k, lane);
+  }
+  // gather by position, one array at a time: every lane reads its entries'
+  // sources before any lane of the warp overwrites that array
+  uint32_t pw[(R + 1) / 2];  // two 12-bit positions per register
+#pragma unroll
+  for (int r = 0; r < R; r += 2)
+    pw[r / 2] = (uint32_t)(k[r] & 0xFFFu) | (r + 1 < R ? (uint32_t)(k[r + 1] & 0xFFFu) << 16 : 0u);
+#define UBT_POS(r) ((r) & 1 ? pw[(r) / 2] >> 16 : pw[(r) / 2] & 0xFFFFu)
+#pragma unroll
+  for (int r = 0; r < R; r++)
+    if ((uint32_t)(r * 32 + lane) < len) k[r] = adj[rs + UBT_POS(r)];
+  __syncwarp();
+#pragma unroll
+  for (int r = 0; r < R; r++)
+    if ((uint32_t)(r * 32 + lane) < len) adj[rs + r * 32 + lane] = k[r];
+  uint32_t v[R];
+#pragma unroll
+  for (int r = 0; r < R; r++)
+    if ((uint32_t)(r * 32 + lane) < len) v[r] = eid[rs + UBT_POS(r)];
+  __syncwarp();
+#pragma unroll
+  for (int r = 0; r < R; r++)
+    if ((uint32_t)(r * 32 + lane) < len) eid[rs + r * 32 + lane] = v[r];
+  if (ekey) {
+#pragma unroll
+    for (int r = 0; r < R; r++)
+      if ((uint32_t)(r * 32 + lane) < len) v[r] = ekey[rs + UBT_POS(r)];
+    __syncwarp();
+#pragma unroll
+    for (int r = 0; r < R; r++)
+      if ((uint32_t)(r * 32 + lane) < len) ekey[rs + r * 32 + lane] = v[r];
+  }
+#undef UBT_POS
+}
+
+// One launch per R takes the rows of the list with 16 R < len <= 32 R (R = 4:
+// every row up to 128 entries) and leaves the others to the other launches.
+template <int R>
 __global__ void k_sort_mid_rows(const uint32_t* __restrict__ rows, uint32_t nrows, const uint32_t* __restrict__ row_ptr,
                                 uint64_t* adj, uint32_t* eid, uint32_t* ekey, int fixed, unsigned long long* err) {
   const int lane = threadIdx.x & 31;
@@ -271,44 +329,22 @@ __global__ void k_sort_mid_rows(const uint32_t* __restrict__ rows, uint32_t nrow
   for (int64_t r0 = blockIdx.x * (int64_t)(blockDim.x >> 5) + (threadIdx.x >> 5); r0 < nrows; r0 += warps) {
     const uint32_t u = rows[r0];
     const uint32_t rs = row_ptr[u], len = row_ptr[u + 1] - rs;
-    uint64_t k[4], e[4];
-    uint32_t d[4], y[4];
-#pragma unroll
-    for (int r = 0; r < 4; r++) {
-      const uint32_t i = (uint32_t)(r * 32 + lane);
-      const bool in = i < len;
-      e[r] = in ? adj[rs + i] : ~0ull;
-      d[r] = in ? eid[rs + i] : 0u;
-      y[r] = (in && ekey) ? ekey[rs + i] : 0u;
-      k[r] = in ? key_by_col(e[r]) : ~0ull;
-    }
-    warp_sort128(k, e, d, y, lane);
-#pragma unroll
-    for (int r = 0; r < 4; r++) {  // duplicates: equal keys at neighbouring positions
-      const uint64_t up1 = __shfl_up_sync(kFull, k[r], 1);
-      const uint64_t last = r > 0 ? __shfl_sync(kFull, k[r > 0 ? r - 1 : 0], 31) : ~0ull;
-      const uint64_t prev = lane > 0 ? up1 : last;
-      const uint32_t i = (uint32_t)(r * 32 + lane);
-      if (i < len && i > 0 && prev == k[r]) report(err, rs + i, -UBT_ERR_DUPLICATE_EDGE);
-    }
-    if (fixed) {
-#pragma unroll
-      for (int r = 0; r < 4; r++) k[r] = ((uint32_t)(r * 32 + lane) < len) ? key_by_absq(e[r]) : ~0ull;
-      warp_sort128(k, e, d, y, lane);
-    }
-#pragma unroll
-    for (int r = 0; r < 4; r++) {
-      const uint32_t i = (uint32_t)(r * 32 + lane);
-      if (i < len) {
-        adj[rs + i] = e[r];
-        eid[rs + i] = d[r];
-        if (ekey) ekey[rs + i] = y[r];
-      }
-    }
+    if (len > 32u * R || (R > 4 && len <= 16u * R)) continue;
+    sort_row_warp<R>(adj, eid, ekey, rs, len, fixed, err, lane);
   }
 }
 
-// Lists of 129..4096 entries (at most the "sort_smem_max" tuning): one block
+// the warp sorts of every row of the list (lengths 33..warp_max)
+void launch_mid_sorts(const uint32_t* rows, uint32_t nrows, const uint32_t* row_ptr, uint64_t* adj, uint32_t* eid,
+                      uint32_t* ekey, int fixed, unsigned long long* err, uint32_t warp_max, int sms, int thr,
+                      cudaStream_t s) {
+  const int g = (int)std::min<unsigned long long>((nrows + 7) / 8, (unsigned long long)sms * 32);
+  k_sort_mid_rows<4><<<g, thr, 0, s>>>(rows, nrows, row_ptr, adj, eid, ekey, fixed, err);
+  if (warp_max >= 256) k_sort_mid_rows<8><<<g, thr, 0, s>>>(rows, nrows, row_ptr, adj, eid, ekey, fixed, err);
+  if (warp_max >= 512) k_sort_mid_rows<16><<<g, thr, 0, s>>>(rows, nrows, row_ptr, adj, eid, ekey, fixed, err);
+}
+
+// Lists of 513..4096 entries (at most the "sort_smem_max" tuning): one block
 // per list sorts 64-bit words (sort key << 12 | position in the list) in
 // shared memory; the keys are distinct by construction, so the network only
 // moves one word per comparator, and the entries are gathered by position
@@ -335,14 +371,18 @@ __device__ __forceinline__ void bitonic_packed(unsigned long long* pk, uint32_t 
   }
 }
 
+// One launch per class takes the rows of the list with lo < len <= hi, with
+// hi / 2 threads (at most 512): every thread has a comparator at every stage.
 __global__ void __launch_bounds__(kPackedSortThreads)
 k_sort_long_rows_packed(const uint32_t* __restrict__ rows, uint32_t nrows, const uint32_t* __restrict__ row_ptr,
-                        uint64_t* adj, uint32_t* eid, uint32_t* ekey, int fixed, unsigned long long* err) {
+                        uint64_t* adj, uint32_t* eid, uint32_t* ekey, int fixed, unsigned long long* err,
+                        uint32_t lo, uint32_t hi) {
   extern __shared__ __align__(16) unsigned long long pk[];
   for (uint32_t r = blockIdx.x; r < nrows; r += gridDim.x) {
     const uint32_t u = rows[r];
     const uint32_t rs = row_ptr[u], len = row_ptr[u + 1] - rs;
-    if (len > kPackedMax) {  // the collector never lists such a row here
+    if (len <= lo || len > hi) continue;
+    if (len > kPackedMax || len > kPackedPerThread * blockDim.x) {  // the launches never give such a row here
       if (threadIdx.x == 0) report(err, rs, -UBT_ERR_INVALID_ARG);
       continue;
     }
@@ -368,7 +408,7 @@ k_sort_long_rows_packed(const uint32_t* __restrict__ rows, uint32_t nrows, const
     uint32_t d[kPackedPerThread], y[kPackedPerThread];
 #pragma unroll
     for (int c = 0; c < kPackedPerThread; c++) {
-      const uint32_t i = threadIdx.x + c * kPackedSortThreads;
+      const uint32_t i = threadIdx.x + c * blockDim.x;
       if (i < len) {
         const uint32_t w = (uint32_t)(pk[i] & 0xFFFu);
         e[c] = adj[rs + w];
@@ -379,7 +419,7 @@ k_sort_long_rows_packed(const uint32_t* __restrict__ rows, uint32_t nrows, const
     __syncthreads();
 #pragma unroll
     for (int c = 0; c < kPackedPerThread; c++) {
-      const uint32_t i = threadIdx.x + c * kPackedSortThreads;
+      const uint32_t i = threadIdx.x + c * blockDim.x;
       if (i < len) {
         adj[rs + i] = e[c];
         eid[rs + i] = d[c];
@@ -388,6 +428,25 @@ k_sort_long_rows_packed(const uint32_t* __restrict__ rows, uint32_t nrows, const
     }
     __syncthreads();
   }
+}
+
+// the block sorts of every row of the list (lengths warp_max + 1 .. smem_max),
+// by class: (128, 256] with 128 threads, (256, 512] with 256, longer with 512
+ubt_status launch_block_sorts(const uint32_t* rows, uint32_t nrows, const uint32_t* row_ptr, uint64_t* adj, uint32_t* eid,
+                        uint32_t* ekey, int fixed, unsigned long long* err, uint32_t warp_max, uint32_t smem_max,
+                        int sms, cudaStream_t s) {
+  const uint32_t bounds[4] = {128, 256, 512, kPackedMax};
+  for (int c = 0; c < 3; c++) {
+    const uint32_t lo = bounds[c], hi = c == 2 ? std::max(smem_max, 512u) : bounds[c + 1];
+    if (hi <= warp_max || lo >= smem_max) continue;
+    const int threads = (int)std::min<uint32_t>(hi / 2, kPackedSortThreads);
+    const size_t smem = (size_t)hi * 8;
+    UBT_CUDA(cudaFuncSetAttribute(k_sort_long_rows_packed, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+    const int per_sm = std::max(1, std::min(2048 / threads, (int)(200 * 1024 / smem)));
+    const int g = (int)std::min<unsigned long long>(nrows, (unsigned long long)sms * per_sm);
+    k_sort_long_rows_packed<<<g, threads, smem, s>>>(rows, nrows, row_ptr, adj, eid, ekey, fixed, err, lo, hi);
+  }
+  return UBT_OK;
 }
 
 // Longer lists: one block per list, bitonic network in a per-block global
@@ -457,15 +516,17 @@ __global__ void k_sort_long_rows(const uint32_t* __restrict__ rows, uint32_t nro
   }
 }
 
-// Rows longer than 32: counts[2] of 33..128 (warp sort, listed from the end of
-// `mid`), counts[0] of 129..smem_max (block sort in shared memory, from the
-// start of `mid`), counts[1] longer (block sort in global memory, `huge`).
-__global__ void k_collect_long(int64_t n, const uint32_t* __restrict__ row_ptr, uint32_t smem_max, uint32_t* mid,
-                               uint32_t* huge, unsigned long long* counts) {
+// Rows longer than 32: counts[2] of 33..128, or up to warp_max and at most
+// smem_max (warp sort, listed from the end of `mid`), counts[0] of the others
+// up to smem_max (block sort in shared memory, from the start of `mid`),
+// counts[1] longer (block sort in global memory, `huge`).
+__global__ void k_collect_long(int64_t n, const uint32_t* __restrict__ row_ptr, uint32_t smem_max, uint32_t warp_max,
+                               uint32_t* mid, uint32_t* huge, unsigned long long* counts) {
   for (int64_t u = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; u < n; u += (int64_t)gridDim.x * blockDim.x) {
     const uint32_t len = row_ptr[u + 1] - row_ptr[u];
     if (len <= 32) continue;
-    if (len <= 128) mid[n - 1 - (int64_t)atomicAdd(&counts[2], 1ull)] = (uint32_t)u;
+    if (len <= 128 || (len <= warp_max && len <= smem_max))
+      mid[n - 1 - (int64_t)atomicAdd(&counts[2], 1ull)] = (uint32_t)u;
     else if (len <= smem_max) mid[atomicAdd(&counts[0], 1ull)] = (uint32_t)u;
     else huge[atomicAdd(&counts[1], 1ull)] = (uint32_t)u;
   }
@@ -487,25 +548,55 @@ __global__ void k_row_ids(int64_t n, const uint32_t* __restrict__ row_ptr, uint3
     for (uint32_t p = row_ptr[u]; p < row_ptr[u + 1]; p++) rowid[p] = (uint32_t)u;
 }
 
-// pairs per owner, one thread per forward entry (rowid: the row of every
-// CSR position); also the oriented wedges sum_u sum_{v in N>(u)} |N>(v)|
-// (Alg. 1's probes), one atomic per block
+// pairs per owner, one lane per forward entry (rowid: the row of every CSR
+// position; adjacent entries of one row that keep their owner share one
+// atomic); also the oriented wedges sum_u sum_{v in N>(u)} |N>(v)| (Alg. 1's
+// probes), one atomic per block
 __global__ void k_pair_count(int64_t m, const uint32_t* __restrict__ row_ptr, const uint64_t* __restrict__ adj,
                              const uint32_t* __restrict__ rowid, int pull, uint32_t* __restrict__ pcount,
                              unsigned long long* wedges) {
   __shared__ unsigned long long s_w;
   if (threadIdx.x == 0) s_w = 0;
   __syncthreads();
+  const uint32_t lane = lane_id();
   unsigned long long wsum = 0;
-  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < m; i += (int64_t)gridDim.x * blockDim.x) {
-    const uint32_t u = rowid[i], v = adj_col(adj[i]);
-    const uint32_t du = row_ptr[u + 1] - row_ptr[u], dv = row_ptr[v + 1] - row_ptr[v];
-    wsum += dv;
-    atomicAdd(&pcount[pair_owner(u, v, du, dv, pull)], 1u);
+  UBT_FOR_EDGE_WARPS(base, m) {
+    const int64_t i = base + lane;
+    const bool on = i < m;
+    uint32_t x = 0;
+    if (on) {
+      const uint32_t u = rowid[i], v = adj_col(adj[i]);
+      const uint32_t du = row_ptr[u + 1] - row_ptr[u], dv = row_ptr[v + 1] - row_ptr[v];
+      wsum += dv;
+      x = pair_owner(u, v, du, dv, pull);
+    }
+    add_by_runs(pcount, x, on);
   }
   atomicAdd(&s_w, wsum);
   __syncthreads();
   if (threadIdx.x == 0 && s_w) atomicAdd(wedges, s_w);
+}
+
+// ctr[key] += val over the active lanes, one atomic per run of adjacent
+// active lanes with equal keys (the run's sum from a warp prefix sum)
+__device__ __forceinline__ void sum_by_runs(unsigned long long* ctr, uint32_t key, unsigned long long val, bool on) {
+  const uint32_t lane = lane_id();
+  const unsigned act = __ballot_sync(kFull, on);
+  const uint32_t prev = __shfl_up_sync(kFull, key, 1);
+  const bool head = on && !(lane > 0 && ((act >> (lane - 1)) & 1u) && prev == key);
+  const unsigned heads = __ballot_sync(kFull, head);
+  const unsigned upto = (2u << lane) - 1u;
+  const unsigned after = (heads | ~act) & ~upto;
+  const uint32_t next = after ? (uint32_t)__ffs(after) - 1u : 32u;  // > lane
+  unsigned long long x = on ? val : 0ull;
+#pragma unroll
+  for (int d = 1; d < 32; d <<= 1) {
+    const unsigned long long y = __shfl_up_sync(kFull, x, d);
+    if (lane >= (uint32_t)d) x += y;
+  }
+  const unsigned long long end = __shfl_sync(kFull, x, (int)(next - 1u));
+  const unsigned long long before = __shfl_sync(kFull, x, (int)((lane + 31u) & 31u));
+  if (head) atomicAdd(&ctr[key], end - (lane > 0 ? before : 0ull));
 }
 
 // pair words grouped by owner: the streamed vertex and the edge's CSR
@@ -514,13 +605,21 @@ __global__ void k_pair_fill(int64_t m, const uint32_t* __restrict__ row_ptr, con
                             const uint32_t* __restrict__ rowid, int pull, const uint32_t* __restrict__ pair_ptr,
                             uint32_t* __restrict__ pfill, uint64_t* __restrict__ pairs,
                             unsigned long long* __restrict__ work) {
-  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < m; i += (int64_t)gridDim.x * blockDim.x) {
-    const uint32_t u = rowid[i], v = adj_col(adj[i]);
-    const uint32_t du = row_ptr[u + 1] - row_ptr[u], dv = row_ptr[v + 1] - row_ptr[v];
-    const uint32_t x = pair_owner(u, v, du, dv, pull);
-    const uint32_t streamed = x == u ? v : u;
-    pairs[pair_ptr[x] + atomicAdd(&pfill[x], 1u)] = ((uint64_t)i << 32) | streamed;
-    atomicAdd(&work[x], (unsigned long long)(x == u ? dv : du));
+  const uint32_t lane = lane_id();
+  UBT_FOR_EDGE_WARPS(base, m) {
+    const int64_t i = base + lane;
+    const bool on = i < m;
+    uint32_t x = 0, streamed = 0, slen = 0;
+    if (on) {
+      const uint32_t u = rowid[i], v = adj_col(adj[i]);
+      const uint32_t du = row_ptr[u + 1] - row_ptr[u], dv = row_ptr[v + 1] - row_ptr[v];
+      x = pair_owner(u, v, du, dv, pull);
+      streamed = x == u ? v : u;
+      slen = x == u ? dv : du;
+    }
+    const uint32_t slot = add_by_runs(pfill, x, on);
+    if (on) pairs[pair_ptr[x] + slot] = ((uint64_t)i << 32) | streamed;
+    sum_by_runs(work, x, slen, on);
   }
 }
 
@@ -987,21 +1086,18 @@ extern "C" ubt_status ubt_create_graph(int64_t n, int64_t m, const uint32_t* d_s
   if (n > 0) {
     k_sort_short_rows<<<grid_w, thr, 0, s>>>(n, L.row_ptr, L.adj, L.eid, L.ekey, fixed, &L.scratch->err);
     const uint32_t sort_smem = (uint32_t)tuning().sort_smem_max;
-    k_collect_long<<<grid_v, thr, 0, s>>>(n, L.row_ptr, sort_smem, L.mid_rows, L.huge_rows, lcount);
+    const uint32_t warp_max = (uint32_t)tuning().warp_sort_max;
+    k_collect_long<<<grid_v, thr, 0, s>>>(n, L.row_ptr, sort_smem, warp_max, L.mid_rows, L.huge_rows, lcount);
     unsigned long long lc[3] = {0, 0, 0};
     UBT_CUDA(cudaMemcpyAsync(lc, lcount, sizeof(lc), cudaMemcpyDeviceToHost, s));
     UBT_CUDA(cudaStreamSynchronize(s));
-    if (lc[2]) {
-      const int g = (int)std::min<unsigned long long>((lc[2] + 7) / 8, (unsigned long long)sms * 32);
-      k_sort_mid_rows<<<g, thr, 0, s>>>(L.mid_rows + (n - (int64_t)lc[2]), (uint32_t)lc[2], L.row_ptr, L.adj, L.eid,
-                                        L.ekey, fixed, &L.scratch->err);
-    }
+    if (lc[2])
+      launch_mid_sorts(L.mid_rows + (n - (int64_t)lc[2]), (uint32_t)lc[2], L.row_ptr, L.adj, L.eid, L.ekey, fixed,
+                       &L.scratch->err, warp_max, sms, thr, s);
     if (lc[0]) {
-      const size_t smem = (size_t)std::max<uint32_t>(sort_smem, 64) * 8;
-      UBT_CUDA(cudaFuncSetAttribute(k_sort_long_rows_packed, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
-      const int g = (int)std::min<unsigned long long>(lc[0], (unsigned long long)sms * 4);
-      k_sort_long_rows_packed<<<g, kPackedSortThreads, smem, s>>>(L.mid_rows, (uint32_t)lc[0], L.row_ptr, L.adj,
-                                                                  L.eid, L.ekey, fixed, &L.scratch->err);
+      st = launch_block_sorts(L.mid_rows, (uint32_t)lc[0], L.row_ptr, L.adj, L.eid, L.ekey, fixed, &L.scratch->err,
+                              warp_max, sort_smem, sms, s);
+      if (st != UBT_OK) return st;
     }
     if (lc[1]) {
       const int64_t cap = pow2_at_least(list_bound(n, m));
@@ -1073,21 +1169,18 @@ extern "C" ubt_status ubt_create_graph(int64_t n, int64_t m, const uint32_t* d_s
     k_sort_short_rows<<<grid_w, thr, 0, s>>>(n, L.uptr, L.uadj, L.ueid, nullptr, 1, &L.scratch->err);
     const uint32_t sort_smem = (uint32_t)tuning().sort_smem_max;
     UBT_CUDA(cudaMemsetAsync(lcount, 0, 3 * sizeof(unsigned long long), s));
-    k_collect_long<<<grid_v, thr, 0, s>>>(n, L.uptr, sort_smem, L.mid_rows, L.huge_rows, lcount);
+    const uint32_t warp_max = (uint32_t)tuning().warp_sort_max;
+    k_collect_long<<<grid_v, thr, 0, s>>>(n, L.uptr, sort_smem, warp_max, L.mid_rows, L.huge_rows, lcount);
     unsigned long long lc[3] = {0, 0, 0};
     UBT_CUDA(cudaMemcpyAsync(lc, lcount, sizeof(lc), cudaMemcpyDeviceToHost, s));
     UBT_CUDA(cudaStreamSynchronize(s));
-    if (lc[2]) {
-      const int g2 = (int)std::min<unsigned long long>((lc[2] + 7) / 8, (unsigned long long)sms * 32);
-      k_sort_mid_rows<<<g2, thr, 0, s>>>(L.mid_rows + (n - (int64_t)lc[2]), (uint32_t)lc[2], L.uptr, L.uadj, L.ueid,
-                                         nullptr, 1, &L.scratch->err);
-    }
+    if (lc[2])
+      launch_mid_sorts(L.mid_rows + (n - (int64_t)lc[2]), (uint32_t)lc[2], L.uptr, L.uadj, L.ueid, nullptr, 1,
+                       &L.scratch->err, warp_max, sms, thr, s);
     if (lc[0]) {
-      const size_t smem = (size_t)std::max<uint32_t>(sort_smem, 64) * 8;
-      UBT_CUDA(cudaFuncSetAttribute(k_sort_long_rows_packed, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
-      const int g2 = (int)std::min<unsigned long long>(lc[0], (unsigned long long)sms * 4);
-      k_sort_long_rows_packed<<<g2, kPackedSortThreads, smem, s>>>(L.mid_rows, (uint32_t)lc[0], L.uptr, L.uadj,
-                                                                   L.ueid, nullptr, 1, &L.scratch->err);
+      st = launch_block_sorts(L.mid_rows, (uint32_t)lc[0], L.uptr, L.uadj, L.ueid, nullptr, 1, &L.scratch->err,
+                              warp_max, sort_smem, sms, s);
+      if (st != UBT_OK) return st;
     }
     if (lc[1]) {
       const int g2 = (int)std::min<unsigned long long>(lc[1], (unsigned long long)sms * 2);

@@ -184,6 +184,7 @@ struct Tuning {
   int64_t edge_index = 1;         // vertex queries: 0 never look pairs up in the edge index, 1 when cheaper, 2 always
   int64_t vertex_split = 64;      // vertex samples with longer pruned rows are spread over all blocks (edge index)
   int64_t sort_smem_max = 4096;
+  int64_t warp_sort_max = 256;
 };
 Tuning& tuning();
 

@@ -635,7 +635,7 @@ __global__ void k_trav_stats(int64_t n, const uint32_t* __restrict__ row_ptr, co
       if (L > 0 && qe * (1ll << 30) < L) continue;
       const uint32_t vs = row_ptr[sv];
       uint32_t dv = row_ptr[sv + 1] - vs;
-      if (L > 0) dv = light ? stream_prefix(adj + vs, dv, qe * qmax, L) : prune_prefix(adj + vs, dv, qe * qmax, L);
+      if (L > 0 && !light) dv = prune_prefix(adj + vs, dv, qe * qmax, L);
       npairs += 1;
       str += dv;
     }

@@ -84,11 +84,13 @@ struct TravArgs {
   uint32_t long_min;        // streamed lists at least this long take the whole-warp path
   uint32_t long_tail;       // 1: a long list's last < 64 entries join the concatenated short lists
   int64_t L;                // prune level, 0 = none
-  uint32_t light_prune;     // 1: streamed lists pruned only where a sixteenth or more goes (stream_prefix)
+  uint32_t light_prune;     // 1: streamed lists kept whole (owner tables and pairs still pruned)
 };
 
 // At a low prune level (2t - 1 < 1/10) a streamed list rarely loses more than
-// a few entries, and checking two of them beats the binary search.
+// a few entries, and streaming them costs less than the load of the list's
+// last entry that decides whether any go.  The kept entries form no triangle
+// with |P| >= L, so every query answers the same.
 inline uint32_t light_prune_for(int64_t L) { return L > 0 && L < (1ll << 45) / 10 ? 1u : 0u; }
 
 __device__ __forceinline__ uint32_t hash_slot(uint32_t w, int shift) { return (w * 0x9E3779B1u) >> shift; }
@@ -118,18 +120,6 @@ __device__ __forceinline__ uint32_t prune_prefix(const uint64_t* __restrict__ ro
     if (qabs(adj_valbits(row[mid])) * c >= L) lo = mid; else hi = mid;
   }
   return hi;
-}
-
-// prune_prefix for a streamed list at a low prune level: when at most 1/16
-// of the list would go (its entry 1/16 from the end passes), the whole list
-// is kept -- two loads instead of a binary search; the kept entries form no
-// triangle with |P| >= L, so every query answers the same.
-__device__ __forceinline__ uint32_t stream_prefix(const uint64_t* __restrict__ row, uint32_t len, int64_t c, int64_t L) {
-  if (len == 0) return 0;
-  if (qabs(adj_valbits(row[len - 1])) * c >= L) return len;
-  const uint32_t probe = len - 1 - (len >> 4);
-  if (probe < len - 1 && qabs(adj_valbits(row[probe])) * c >= L) return len;
-  return prune_prefix(row, len, c, L);
 }
 
 // Hash table: key = neighbour id, val = edge value bits, pos = CSR position,
@@ -332,9 +322,7 @@ __device__ __forceinline__ void probe_pairs(const TravArgs& a, V& vis, const Tab
       const uint32_t ve = a.row_ptr[pr.s + 1];
       if (ve >= vs && ve <= a.m) {
         dv = ve - vs;
-        if (a.L > 0)
-          dv = a.light_prune ? stream_prefix(a.adj + vs, dv, qabs(pr.qe) * pr.qmax, a.L)
-                             : prune_prefix(a.adj + vs, dv, qabs(pr.qe) * pr.qmax, a.L);
+        if (a.L > 0 && !a.light_prune) dv = prune_prefix(a.adj + vs, dv, qabs(pr.qe) * pr.qmax, a.L);
       } else {
         guard_fail(a.sc, kGuardList, pr.s);
       }

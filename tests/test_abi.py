@@ -80,7 +80,8 @@ def test_workspace_size_argument_checks(L):
 def test_traversal_and_index_knobs(L):
     import paper_2602_14084_gb300 as ubt
     knobs = {"long_min": (1, 1 << 20, [0, (1 << 20) + 1]), "long_tail": (0, 1, [-1, 2]),
-             "edge_index": (0, 2, [-1, 3]), "vertex_split": (1, 1 << 32, [0, (1 << 32) + 1])}
+             "edge_index": (0, 2, [-1, 3]), "vertex_split": (1, 1 << 32, [0, (1 << 32) + 1]),
+             "warp_sort_max": (128, 512, [64, 384, 1024])}
     for name, (lo, hi, bad) in knobs.items():
         old = ubt.get_tuning(name)
         try:

@@ -115,6 +115,41 @@ def test_long_lists_sorted_in_global_memory(ubt):
         ubt.set_tuning("sort_smem_max", old)
 
 
+def core_graph(n, m, core, seed):
+    """Random graph plus a clique on `core` seeded vertices (deduplicated,
+    randomly oriented)."""
+    s, d = synth.er_graph(n, m, seed)
+    c = np.sort(synth.rng(seed + 3).choice(n, size=core, replace=False)).astype(np.int64)
+    iu = np.triu_indices(core, 1)
+    a = np.concatenate([s.astype(np.int64), c[iu[0]]])
+    b = np.concatenate([d.astype(np.int64), c[iu[1]]])
+    key = np.unique(np.minimum(a, b) * n + np.maximum(a, b))
+    return synth.random_orientation((key // n).astype(np.uint32), (key % n).astype(np.uint32), seed + 5)
+
+
+@pytest.mark.parametrize("knobs", [{"warp_sort_max": 128}, {"warp_sort_max": 256},
+                                   {"warp_sort_max": 512, "sort_smem_max": 256},
+                                   {"warp_sort_max": 128, "sort_smem_max": 512}])
+def test_layout_under_other_row_sorts(ubt, knobs):
+    """Rows of 129..512 entries sorted by one warp or by one block (and, past
+    sort_smem_max, in global memory) give the same layout.  The graph plants
+    a 600-clique, so its forward rows reach every length class up to 599."""
+    old = {k: ubt.get_tuning(k) for k in knobs}
+    try:
+        for k, v in knobs.items():
+            ubt.set_tuning(k, v)
+        s, d = core_graph(3000, 20000, 600, 15)
+        k = synth.k_uniform(s.size, 16)
+        G = ubt.Graph(3000, s, d, k=k)
+        assert G.info()["max_out_degree"] > 512
+        check_export(ubt, G, 3000, s, d, k=k)
+        p = synth.p_uniform_f32(s.size, 17)
+        check_export(ubt, ubt.Graph(3000, s, d, p=p), 3000, s, d, p=p)
+    finally:
+        for k, v in old.items():
+            ubt.set_tuning(k, v)
+
+
 @pytest.mark.parametrize("knobs", [{"pull": 0}, {"block_work": 1}, {"hub_threshold": 2, "block_work": 1 << 30}])
 def test_layout_under_other_partitions(ubt, knobs):
     old = {k: ubt.get_tuning(k) for k in knobs}

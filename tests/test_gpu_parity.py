@@ -192,7 +192,7 @@ def test_gradient_fixed_graph_exact(ubt, er2k):
     assert np.allclose(grad.cpu().numpy(), og, rtol=1e-6, atol=1e-6)
 
 
-@pytest.mark.parametrize("W", [64, 256])
+@pytest.mark.parametrize("W", [64, 256, 4096])
 def test_worlds_bit_exact(ubt, er2k, W):
     g = er2k
     G = ubt.Graph(g.n, g.src, g.dst, k=g.k)
@@ -203,6 +203,24 @@ def test_worlds_bit_exact(ubt, er2k, W):
         assert np.array_equal(got, want), wpp
         assert tot == int(want.sum())
     ubt.set_tuning("world_words_per_pass", 8)
+
+
+def test_worlds_64_words_per_pass_with_long_lists(ubt):
+    """One pass of 64 words (two words per lane, rows staged in shared
+    memory) on a graph with block tasks (a planted clique and star)."""
+    s, d = mixed_graph(3000, 30000, 5)
+    k = synth.k_uniform(s.size, 6)
+    G = ubt.Graph(3000, s, d, k=k)
+    old = ubt.get_tuning("world_words_per_pass")
+    try:
+        ubt.set_tuning("world_words_per_pass", 64)
+        got, tot = G.sample_worlds(seed=4321, W=4096)
+    finally:
+        ubt.set_tuning("world_words_per_pass", old)
+    want = oracle.world_counts(3000, s, d, k, 4321, list(range(64)))
+    assert np.array_equal(got, want)
+    assert tot == int(want.sum())
+    assert G.guard() == 0
 
 
 def test_worlds_with_edge_keys(ubt):

@@ -149,6 +149,33 @@ __device__ inline uint64_t key_by_absq(uint64_t e) {
   return ((uint64_t)(32768u - aq) << 32) | adj_col(e);
 }
 
+// How a row is sorted: REAL forward rows by neighbour id (a duplicate edge
+// shows as two equal neighbouring keys); FIXED forward rows by (|q|
+// descending, id) with duplicates found by a hash set or a lane match before
+// the one sort; undirected rows like FIXED ones but unchecked (the forward
+// rows of the same edges were checked first).
+enum : int { kSortById = 0, kSortByAbsqChecked = 1, kSortByAbsq = 2 };
+
+constexpr unsigned long long kSetEmpty = ~0ull;
+
+// Inserts (col, input edge id) into an open-addressing set of mask + 1
+// 64-bit slots (at least twice the row); a second entry with the same
+// neighbour is a duplicate edge, reported with the larger of the two ids.
+__device__ __forceinline__ void dedupe_insert(unsigned long long* set, uint32_t mask, uint32_t col, uint32_t id,
+                                              unsigned long long* err) {
+  const unsigned long long mine = ((unsigned long long)col << 32) | id;
+  uint32_t h = ((col * 0x9E3779B1u) >> 8) & mask;
+  for (uint32_t it = 0; it <= mask; it++) {
+    const unsigned long long cur = atomicCAS(&set[h], kSetEmpty, mine);
+    if (cur == kSetEmpty) return;
+    if ((uint32_t)(cur >> 32) == col) {
+      report(err, max(id, (uint32_t)cur), -UBT_ERR_DUPLICATE_EDGE);
+      return;
+    }
+    h = (h + 1) & mask;
+  }
+}
+
 // Lists of <= 32 entries: one warp per list, bitonic network over the lanes.
 // Bitonic sort of the values held by each aligned group of W lanes (W = 8,
 // 16 or 32), ascending by key within every group.
@@ -173,22 +200,29 @@ __device__ __forceinline__ void group_bitonic(uint64_t& key, uint64_t& e, uint32
 }
 
 // Sorts the rows of one group of W lanes (row rs..rs+len, len <= W; groups
-// without a row pass in = false everywhere): by neighbour id, reporting
-// duplicates, then (FIXED) by |q| descending.
+// without a row pass in = false everywhere), as `mode` says.
 template <int W>
 __device__ __forceinline__ void sort_group_row(uint64_t* adj, uint32_t* eid, uint32_t* ekey, uint32_t rs, uint32_t len,
-                                               bool row, int fixed, unsigned long long* err, int lane) {
+                                               bool row, int mode, unsigned long long* err, int lane) {
   const int li = lane & (W - 1);
   const bool in = row && (uint32_t)li < len;
   uint64_t e = in ? adj[rs + li] : ~0ull;
   uint32_t id = in ? eid[rs + li] : 0u;
   uint32_t ky = (in && ekey) ? ekey[rs + li] : 0u;
-  uint64_t key = in ? key_by_col(e) : ~0ull;
-  group_bitonic<W>(key, e, id, ky, lane);
-  const uint64_t prev = __shfl_up_sync(kFull, key, 1);
-  if (in && li > 0 && prev == key) report(err, rs + li, -UBT_ERR_DUPLICATE_EDGE);
-  if (fixed) {
-    key = in ? key_by_absq(e) : ~0ull;
+  if (mode == kSortById) {
+    uint64_t key = in ? key_by_col(e) : ~0ull;
+    group_bitonic<W>(key, e, id, ky, lane);
+    const uint64_t prev = __shfl_up_sync(kFull, key, 1);
+    if (in && li > 0 && prev == key) report(err, rs + li, -UBT_ERR_DUPLICATE_EDGE);
+  } else {
+    if (mode == kSortByAbsqChecked) {  // lanes of one group holding the same neighbour
+      const unsigned long long v = in ? (((unsigned long long)(lane / W) << 32) | adj_col(e))
+                                      : ((0xFFFFFFFFull << 32) | (unsigned long long)lane);
+      const unsigned others = __match_any_sync(kFull, v) & ~(1u << lane);
+      const uint32_t oid = __shfl_sync(kFull, id, others ? __ffs(others) - 1 : lane);
+      if (in && others) report(err, max(id, oid), -UBT_ERR_DUPLICATE_EDGE);
+    }
+    uint64_t key = in ? key_by_absq(e) : ~0ull;
     group_bitonic<W>(key, e, id, ky, lane);
   }
   if (in) {
@@ -202,7 +236,7 @@ __device__ __forceinline__ void sort_group_row(uint64_t* adj, uint32_t* eid, uin
 // most 8 entries are sorted together, one per 8-lane group, the others one
 // after another by the whole warp.
 __global__ void k_sort_short_rows(int64_t n, const uint32_t* __restrict__ row_ptr, uint64_t* adj, uint32_t* eid,
-                                  uint32_t* ekey, int fixed, unsigned long long* err) {
+                                  uint32_t* ekey, int mode, unsigned long long* err) {
   const int lane = threadIdx.x & 31;
   const int64_t warps = (int64_t)gridDim.x * (blockDim.x >> 5);
   for (int64_t u0 = 4 * (blockIdx.x * (int64_t)(blockDim.x >> 5) + (threadIdx.x >> 5)); u0 < n; u0 += 4 * warps) {
@@ -212,13 +246,13 @@ __global__ void k_sort_short_rows(int64_t n, const uint32_t* __restrict__ row_pt
       rs = row_ptr[u];
       len = row_ptr[u + 1] - rs;
     }
-    sort_group_row<8>(adj, eid, ekey, rs, len, len >= 2 && len <= 8, fixed, err, lane);
+    sort_group_row<8>(adj, eid, ekey, rs, len, len >= 2 && len <= 8, mode, err, lane);
     unsigned big = __ballot_sync(kFull, (lane & 7) == 0 && len > 8 && len <= 32);
     while (big) {
       const int g = __ffs(big) - 1;
       big &= big - 1;
       const uint32_t rsg = __shfl_sync(kFull, rs, g), leng = __shfl_sync(kFull, len, g);
-      sort_group_row<32>(adj, eid, ekey, rsg, leng, true, fixed, err, lane);
+      sort_group_row<32>(adj, eid, ekey, rsg, leng, true, mode, err, lane);
     }
   }
 }
@@ -260,28 +294,38 @@ __device__ __forceinline__ void warp_bitonic(unsigned long long (&k)[R], int lan
 
 template <int R>
 __device__ __forceinline__ void sort_row_warp(uint64_t* adj, uint32_t* eid, uint32_t* ekey, uint32_t rs, uint32_t len,
-                                              int fixed, unsigned long long* err, int lane) {
+                                              int mode, unsigned long long* set, unsigned long long* err, int lane) {
   unsigned long long k[R];
-#pragma unroll
-  for (int r = 0; r < R; r++) {
-    const uint32_t i = (uint32_t)(r * 32 + lane);
-    k[r] = i < len ? (key_by_col(adj[rs + i]) << 12) | i : ~0ull;
-  }
-  warp_bitonic<R>(k, lane);
-#pragma unroll
-  for (int r = 0; r < R; r++) {  // duplicates: equal neighbours at adjacent sorted positions
-    const unsigned long long up1 = __shfl_up_sync(kFull, k[r], 1);
-    const unsigned long long last = __shfl_sync(kFull, k[r > 0 ? r - 1 : 0], 31);
-    const unsigned long long prev = lane > 0 ? up1 : last;
-    const uint32_t i = (uint32_t)(r * 32 + lane);
-    if (i < len && i > 0 && (prev >> 12) == (k[r] >> 12)) report(err, rs + i, -UBT_ERR_DUPLICATE_EDGE);
-  }
-  if (fixed) {
+  if (mode == kSortById) {
 #pragma unroll
     for (int r = 0; r < R; r++) {
       const uint32_t i = (uint32_t)(r * 32 + lane);
-      const uint32_t w = (uint32_t)(k[r] & 0xFFFu);
-      k[r] = i < len ? (key_by_absq(adj[rs + w]) << 12) | w : ~0ull;
+      k[r] = i < len ? (key_by_col(adj[rs + i]) << 12) | i : ~0ull;
+    }
+    warp_bitonic<R>(k, lane);
+#pragma unroll
+    for (int r = 0; r < R; r++) {  // duplicates: equal neighbours at adjacent sorted positions
+      const unsigned long long up1 = __shfl_up_sync(kFull, k[r], 1);
+      const unsigned long long last = __shfl_sync(kFull, k[r > 0 ? r - 1 : 0], 31);
+      const unsigned long long prev = lane > 0 ? up1 : last;
+      const uint32_t i = (uint32_t)(r * 32 + lane);
+      if (i < len && i > 0 && (prev >> 12) == (k[r] >> 12)) report(err, rs + i, -UBT_ERR_DUPLICATE_EDGE);
+    }
+  } else {
+    if (mode == kSortByAbsqChecked) {  // this warp's set: 64 R slots for at most 32 R entries
+      for (int i = lane; i < 64 * R; i += 32) set[i] = kSetEmpty;
+      __syncwarp();
+#pragma unroll
+      for (int r = 0; r < R; r++) {
+        const uint32_t i = (uint32_t)(r * 32 + lane);
+        if (i < len) dedupe_insert(set, 64 * R - 1, adj_col(adj[rs + i]), eid[rs + i], err);
+      }
+      __syncwarp();
+    }
+#pragma unroll
+    for (int r = 0; r < R; r++) {
+      const uint32_t i = (uint32_t)(r * 32 + lane);
+      k[r] = i < len ? (key_by_absq(adj[rs + i]) << 12) | i : ~0ull;
     }
     warp_bitonic<R>(k, lane);
   }
@@ -323,25 +367,38 @@ __device__ __forceinline__ void sort_row_warp(uint64_t* adj, uint32_t* eid, uint
 // every row up to 128 entries) and leaves the others to the other launches.
 template <int R>
 __global__ void k_sort_mid_rows(const uint32_t* __restrict__ rows, uint32_t nrows, const uint32_t* __restrict__ row_ptr,
-                                uint64_t* adj, uint32_t* eid, uint32_t* ekey, int fixed, unsigned long long* err) {
+                                uint64_t* adj, uint32_t* eid, uint32_t* ekey, int mode, unsigned long long* err) {
+  extern __shared__ __align__(16) unsigned long long sets[];  // one set of 64 R slots per warp (checked mode)
+  unsigned long long* set = sets + (threadIdx.x >> 5) * (64 * R);
   const int lane = threadIdx.x & 31;
   const int64_t warps = (int64_t)gridDim.x * (blockDim.x >> 5);
   for (int64_t r0 = blockIdx.x * (int64_t)(blockDim.x >> 5) + (threadIdx.x >> 5); r0 < nrows; r0 += warps) {
     const uint32_t u = rows[r0];
     const uint32_t rs = row_ptr[u], len = row_ptr[u + 1] - rs;
     if (len > 32u * R || (R > 4 && len <= 16u * R)) continue;
-    sort_row_warp<R>(adj, eid, ekey, rs, len, fixed, err, lane);
+    sort_row_warp<R>(adj, eid, ekey, rs, len, mode, set, err, lane);
   }
 }
 
 // the warp sorts of every row of the list (lengths 33..warp_max)
-void launch_mid_sorts(const uint32_t* rows, uint32_t nrows, const uint32_t* row_ptr, uint64_t* adj, uint32_t* eid,
-                      uint32_t* ekey, int fixed, unsigned long long* err, uint32_t warp_max, int sms, int thr,
-                      cudaStream_t s) {
+template <int R>
+ubt_status launch_mid_sort(const uint32_t* rows, uint32_t nrows, const uint32_t* row_ptr, uint64_t* adj, uint32_t* eid,
+                           uint32_t* ekey, int mode, unsigned long long* err, int g, int thr, cudaStream_t s) {
+  const size_t smem = mode == kSortByAbsqChecked ? (size_t)(thr / 32) * 64 * R * 8 : 0;
+  UBT_CUDA(cudaFuncSetAttribute(k_sort_mid_rows<R>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+  k_sort_mid_rows<R><<<g, thr, smem, s>>>(rows, nrows, row_ptr, adj, eid, ekey, mode, err);
+  return UBT_OK;
+}
+
+ubt_status launch_mid_sorts(const uint32_t* rows, uint32_t nrows, const uint32_t* row_ptr, uint64_t* adj,
+                            uint32_t* eid, uint32_t* ekey, int mode, unsigned long long* err, uint32_t warp_max,
+                            int sms, int thr, cudaStream_t s) {
   const int g = (int)std::min<unsigned long long>((nrows + 7) / 8, (unsigned long long)sms * 32);
-  k_sort_mid_rows<4><<<g, thr, 0, s>>>(rows, nrows, row_ptr, adj, eid, ekey, fixed, err);
-  if (warp_max >= 256) k_sort_mid_rows<8><<<g, thr, 0, s>>>(rows, nrows, row_ptr, adj, eid, ekey, fixed, err);
-  if (warp_max >= 512) k_sort_mid_rows<16><<<g, thr, 0, s>>>(rows, nrows, row_ptr, adj, eid, ekey, fixed, err);
+  ubt_status st = launch_mid_sort<4>(rows, nrows, row_ptr, adj, eid, ekey, mode, err, g, thr, s);
+  if (st == UBT_OK && warp_max >= 256) st = launch_mid_sort<8>(rows, nrows, row_ptr, adj, eid, ekey, mode, err, g, thr, s);
+  if (st == UBT_OK && warp_max >= 512)
+    st = launch_mid_sort<16>(rows, nrows, row_ptr, adj, eid, ekey, mode, err, g, thr, s);
+  return st;
 }
 
 // Lists of 513..4096 entries (at most the "sort_smem_max" tuning): one block
@@ -375,9 +432,10 @@ __device__ __forceinline__ void bitonic_packed(unsigned long long* pk, uint32_t 
 // hi / 2 threads (at most 512): every thread has a comparator at every stage.
 __global__ void __launch_bounds__(kPackedSortThreads)
 k_sort_long_rows_packed(const uint32_t* __restrict__ rows, uint32_t nrows, const uint32_t* __restrict__ row_ptr,
-                        uint64_t* adj, uint32_t* eid, uint32_t* ekey, int fixed, unsigned long long* err,
+                        uint64_t* adj, uint32_t* eid, uint32_t* ekey, int mode, unsigned long long* err,
                         uint32_t lo, uint32_t hi) {
-  extern __shared__ __align__(16) unsigned long long pk[];
+  extern __shared__ __align__(16) unsigned long long pk[];  // hi words, then (checked mode) a set of 2 hi slots
+  unsigned long long* set = pk + hi;
   for (uint32_t r = blockIdx.x; r < nrows; r += gridDim.x) {
     const uint32_t u = rows[r];
     const uint32_t rs = row_ptr[u], len = row_ptr[u + 1] - rs;
@@ -388,18 +446,22 @@ k_sort_long_rows_packed(const uint32_t* __restrict__ rows, uint32_t nrows, const
     }
     uint32_t cap = 64;
     while (cap < len) cap <<= 1;
-    for (uint32_t i = threadIdx.x; i < cap; i += blockDim.x)
-      pk[i] = i < len ? (key_by_col(adj[rs + i]) << 12) | i : ~0ull;
-    __syncthreads();
-    bitonic_packed(pk, cap);
-    for (uint32_t i = threadIdx.x + 1; i < len; i += blockDim.x)
-      if ((pk[i] >> 12) == (pk[i - 1] >> 12)) report(err, rs + i, -UBT_ERR_DUPLICATE_EDGE);
-    if (fixed) {
+    if (mode == kSortById) {
+      for (uint32_t i = threadIdx.x; i < cap; i += blockDim.x)
+        pk[i] = i < len ? (key_by_col(adj[rs + i]) << 12) | i : ~0ull;
       __syncthreads();
-      for (uint32_t i = threadIdx.x; i < len; i += blockDim.x) {
-        const uint32_t w = (uint32_t)(pk[i] & 0xFFFu);
-        pk[i] = (key_by_absq(adj[rs + w]) << 12) | w;
+      bitonic_packed(pk, cap);
+      for (uint32_t i = threadIdx.x + 1; i < len; i += blockDim.x)
+        if ((pk[i] >> 12) == (pk[i - 1] >> 12)) report(err, rs + i, -UBT_ERR_DUPLICATE_EDGE);
+    } else {
+      if (mode == kSortByAbsqChecked) {  // 2 cap <= 2 hi slots
+        for (uint32_t i = threadIdx.x; i < 2 * cap; i += blockDim.x) set[i] = kSetEmpty;
+        __syncthreads();
+        for (uint32_t i = threadIdx.x; i < len; i += blockDim.x)
+          dedupe_insert(set, 2 * cap - 1, adj_col(adj[rs + i]), eid[rs + i], err);
       }
+      for (uint32_t i = threadIdx.x; i < cap; i += blockDim.x)
+        pk[i] = i < len ? (key_by_absq(adj[rs + i]) << 12) | i : ~0ull;
       __syncthreads();
       bitonic_packed(pk, cap);
     }
@@ -433,18 +495,18 @@ k_sort_long_rows_packed(const uint32_t* __restrict__ rows, uint32_t nrows, const
 // the block sorts of every row of the list (lengths warp_max + 1 .. smem_max),
 // by class: (128, 256] with 128 threads, (256, 512] with 256, longer with 512
 ubt_status launch_block_sorts(const uint32_t* rows, uint32_t nrows, const uint32_t* row_ptr, uint64_t* adj, uint32_t* eid,
-                        uint32_t* ekey, int fixed, unsigned long long* err, uint32_t warp_max, uint32_t smem_max,
+                        uint32_t* ekey, int mode, unsigned long long* err, uint32_t warp_max, uint32_t smem_max,
                         int sms, cudaStream_t s) {
   const uint32_t bounds[4] = {128, 256, 512, kPackedMax};
   for (int c = 0; c < 3; c++) {
     const uint32_t lo = bounds[c], hi = c == 2 ? std::max(smem_max, 512u) : bounds[c + 1];
     if (hi <= warp_max || lo >= smem_max) continue;
     const int threads = (int)std::min<uint32_t>(hi / 2, kPackedSortThreads);
-    const size_t smem = (size_t)hi * 8;
+    const size_t smem = (size_t)hi * 8 * (mode == kSortByAbsqChecked ? 3 : 1);
     UBT_CUDA(cudaFuncSetAttribute(k_sort_long_rows_packed, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
     const int per_sm = std::max(1, std::min(2048 / threads, (int)(200 * 1024 / smem)));
     const int g = (int)std::min<unsigned long long>(nrows, (unsigned long long)sms * per_sm);
-    k_sort_long_rows_packed<<<g, threads, smem, s>>>(rows, nrows, row_ptr, adj, eid, ekey, fixed, err, lo, hi);
+    k_sort_long_rows_packed<<<g, threads, smem, s>>>(rows, nrows, row_ptr, adj, eid, ekey, mode, err, lo, hi);
   }
   return UBT_OK;
 }
@@ -1082,20 +1144,23 @@ extern "C" ubt_status ubt_create_graph(int64_t n, int64_t m, const uint32_t* d_s
                                      opts ? opts->d_edge_key : nullptr, L.ekey);
   // 3. sort every forward list
   const int fixed = flags == UBT_GRAPH_FIXED;
+  const int mode = fixed ? kSortByAbsqChecked : kSortById;
   unsigned long long* lcount = L.stats + 2 * kStats;
   if (n > 0) {
-    k_sort_short_rows<<<grid_w, thr, 0, s>>>(n, L.row_ptr, L.adj, L.eid, L.ekey, fixed, &L.scratch->err);
+    k_sort_short_rows<<<grid_w, thr, 0, s>>>(n, L.row_ptr, L.adj, L.eid, L.ekey, mode, &L.scratch->err);
     const uint32_t sort_smem = (uint32_t)tuning().sort_smem_max;
     const uint32_t warp_max = (uint32_t)tuning().warp_sort_max;
     k_collect_long<<<grid_v, thr, 0, s>>>(n, L.row_ptr, sort_smem, warp_max, L.mid_rows, L.huge_rows, lcount);
     unsigned long long lc[3] = {0, 0, 0};
     UBT_CUDA(cudaMemcpyAsync(lc, lcount, sizeof(lc), cudaMemcpyDeviceToHost, s));
     UBT_CUDA(cudaStreamSynchronize(s));
-    if (lc[2])
-      launch_mid_sorts(L.mid_rows + (n - (int64_t)lc[2]), (uint32_t)lc[2], L.row_ptr, L.adj, L.eid, L.ekey, fixed,
-                       &L.scratch->err, warp_max, sms, thr, s);
+    if (lc[2]) {
+      st = launch_mid_sorts(L.mid_rows + (n - (int64_t)lc[2]), (uint32_t)lc[2], L.row_ptr, L.adj, L.eid, L.ekey, mode,
+                            &L.scratch->err, warp_max, sms, thr, s);
+      if (st != UBT_OK) return st;
+    }
     if (lc[0]) {
-      st = launch_block_sorts(L.mid_rows, (uint32_t)lc[0], L.row_ptr, L.adj, L.eid, L.ekey, fixed, &L.scratch->err,
+      st = launch_block_sorts(L.mid_rows, (uint32_t)lc[0], L.row_ptr, L.adj, L.eid, L.ekey, mode, &L.scratch->err,
                               warp_max, sort_smem, sms, s);
       if (st != UBT_OK) return st;
     }
@@ -1166,7 +1231,7 @@ extern "C" ubt_status ubt_create_graph(int64_t n, int64_t m, const uint32_t* d_s
     UBT_CUDA(exclusive_scan_u32(L.deg, L.uptr, n, L.scan_tmp, s));
     UBT_CUDA(cudaMemsetAsync(L.fill, 0, sizeof(uint32_t) * (n + 1), s));
     if (m > 0) k_uscatter<<<grid_e, thr, 0, s>>>(m, d_src, d_dst, d_k, L.uptr, L.fill, L.uadj, L.ueid);
-    k_sort_short_rows<<<grid_w, thr, 0, s>>>(n, L.uptr, L.uadj, L.ueid, nullptr, 1, &L.scratch->err);
+    k_sort_short_rows<<<grid_w, thr, 0, s>>>(n, L.uptr, L.uadj, L.ueid, nullptr, kSortByAbsq, &L.scratch->err);
     const uint32_t sort_smem = (uint32_t)tuning().sort_smem_max;
     UBT_CUDA(cudaMemsetAsync(lcount, 0, 3 * sizeof(unsigned long long), s));
     const uint32_t warp_max = (uint32_t)tuning().warp_sort_max;
@@ -1174,12 +1239,14 @@ extern "C" ubt_status ubt_create_graph(int64_t n, int64_t m, const uint32_t* d_s
     unsigned long long lc[3] = {0, 0, 0};
     UBT_CUDA(cudaMemcpyAsync(lc, lcount, sizeof(lc), cudaMemcpyDeviceToHost, s));
     UBT_CUDA(cudaStreamSynchronize(s));
-    if (lc[2])
-      launch_mid_sorts(L.mid_rows + (n - (int64_t)lc[2]), (uint32_t)lc[2], L.uptr, L.uadj, L.ueid, nullptr, 1,
-                       &L.scratch->err, warp_max, sms, thr, s);
+    if (lc[2]) {
+      st = launch_mid_sorts(L.mid_rows + (n - (int64_t)lc[2]), (uint32_t)lc[2], L.uptr, L.uadj, L.ueid, nullptr,
+                            kSortByAbsq, &L.scratch->err, warp_max, sms, thr, s);
+      if (st != UBT_OK) return st;
+    }
     if (lc[0]) {
-      st = launch_block_sorts(L.mid_rows, (uint32_t)lc[0], L.uptr, L.uadj, L.ueid, nullptr, 1, &L.scratch->err,
-                              warp_max, sort_smem, sms, s);
+      st = launch_block_sorts(L.mid_rows, (uint32_t)lc[0], L.uptr, L.uadj, L.ueid, nullptr, kSortByAbsq,
+                              &L.scratch->err, warp_max, sort_smem, sms, s);
       if (st != UBT_OK) return st;
     }
     if (lc[1]) {

@@ -150,6 +150,45 @@ def test_layout_under_other_row_sorts(ubt, knobs):
             ubt.set_tuning(k, v)
 
 
+def forward_rows(n, s, d):
+    """Owner of every edge under Node Order (the endpoint with the smaller
+    (degree, id)) and the length of each vertex's forward list."""
+    deg = np.bincount(s, minlength=n) + np.bincount(d, minlength=n)
+    a, b = s.astype(np.int64), d.astype(np.int64)
+    ab = (deg[a] < deg[b]) | ((deg[a] == deg[b]) & (a < b))
+    lo = np.where(ab, a, b)
+    return lo, np.bincount(lo, minlength=n)
+
+
+@pytest.mark.parametrize("lo,hi", [(2, 7), (10, 30), (40, 120), (140, 250), (270, 500), (520, 590)])
+@pytest.mark.parametrize("kind", ["fixed", "real"])
+def test_duplicate_edge_in_every_row_class(ubt, lo, hi, kind):
+    """A repeated edge (reversed, another probability) in a forward row of
+    each length class is refused with UBT_ERR_DUPLICATE_EDGE: lane groups,
+    warp sorts, block sorts; FIXED rows check with a set before their one
+    sort, REAL rows compare neighbours after theirs."""
+    n = 3000
+    s, d = core_graph(n, 20000, 600, 15)
+    owner, length = forward_rows(n, s, d)
+    cand = np.nonzero((length[owner] >= lo) & (length[owner] <= hi))[0]
+    assert cand.size > 0
+    e = int(cand[len(cand) // 2])
+    s2 = np.concatenate([s, d[e:e + 1]])
+    d2 = np.concatenate([d, s[e:e + 1]])
+    if kind == "fixed":
+        k = synth.k_uniform(s2.size, 18)
+        k[-1] = (int(k[e]) + 12345) % 65537
+        with pytest.raises(ubt.UbtError) as err:
+            ubt.Graph(n, s2, d2, k=k)
+    else:
+        p = synth.p_uniform_f32(s2.size, 19)
+        with pytest.raises(ubt.UbtError) as err:
+            ubt.Graph(n, s2, d2, p=p)
+    assert err.value.status == -3
+    k0 = synth.k_uniform(s.size, 18)
+    assert ubt.Graph(n, s, d, k=k0).guard() == 0  # the same graph without the copy builds
+
+
 @pytest.mark.parametrize("knobs", [{"pull": 0}, {"block_work": 1}, {"hub_threshold": 2, "block_work": 1 << 30}])
 def test_layout_under_other_partitions(ubt, knobs):
     old = {k: ubt.get_tuning(k) for k in knobs}

@@ -480,6 +480,8 @@ def main():
         assert stv == 0, stv
 
     e2e_times = []
+    e2e_clocks = Clocks(dev if ws == 1 else local)
+    e2e_clocks.start()
     for i in range(args.warmup + max(5, args.steps // 2)):
         torch.cuda.synchronize()
         t1 = time.perf_counter()
@@ -487,6 +489,7 @@ def main():
         t2 = time.perf_counter()
         if i >= args.warmup:
             e2e_times.append(t2 - t1)
+    e2e_clk = e2e_clocks.stop()
     assert np.array_equal(hout.numpy()[:len(TAUS)], cb)
     e2e_t = max_over_ranks(float(np.mean(e2e_times)), ws)
     # the copy part alone: the same three pinned arrays to device buffers
@@ -508,7 +511,8 @@ def main():
         "roofline": roofline,
         "e2e": {"value": job_throughput(T, e2e_t, ws), "unit": UNIT, "h2d_bytes_per_step": 12 * g.m,
                 "d2h_bytes_per_step": 16 * len(TAUS), "ms_per_step": 1e3 * e2e_t,
-                "ms_per_step_min": 1e3 * float(np.min(e2e_times)), "h2d_ms": h2d_ms,
+                "ms_per_step_min": 1e3 * float(np.min(e2e_times)),
+                "ms_per_step_all": [round(1e3 * x, 2) for x in e2e_times], "h2d_ms": h2d_ms, "clocks": e2e_clk,
                 "includes": "H2D of src/dst/k, graph build (validate, orient, CSR, sort), query, D2H"},
         # per query: the block-task traversal (giant / hub owners), the
         # warp-task traversal (medium owners; this workload has both) and the

@@ -242,9 +242,29 @@ def cpu_sample_desc(tri, mod=CPU_SAMPLE_MOD):
             % (tri, mod))
 
 
+class no_gc:
+    """Python's garbage collector off inside a timed loop (as timeit does), so
+    that a collection pause between two launches is not timed as GPU work."""
+
+    def __enter__(self):
+        import gc
+        self.was = gc.isenabled()
+        gc.disable()
+
+    def __exit__(self, *exc):
+        import gc
+        if self.was:
+            gc.enable()
+
+
 def time_steps(fn, steps, warmup, flush=None):
     """W untimed warm-up calls, then `steps` calls each bracketed by CUDA
     events on the current stream, with an L2 flush before each (untimed)."""
+    with no_gc():
+        return _time_steps(fn, steps, warmup, flush)
+
+
+def _time_steps(fn, steps, warmup, flush=None):
     import torch
     for _ in range(warmup):
         fn()
@@ -482,13 +502,14 @@ def main():
     e2e_times = []
     e2e_clocks = Clocks(dev if ws == 1 else local)
     e2e_clocks.start()
-    for i in range(args.warmup + max(5, args.steps // 2)):
-        torch.cuda.synchronize()
-        t1 = time.perf_counter()
-        e2e_step()
-        t2 = time.perf_counter()
-        if i >= args.warmup:
-            e2e_times.append(t2 - t1)
+    with no_gc():
+        for i in range(args.warmup + max(5, args.steps // 2)):
+            torch.cuda.synchronize()
+            t1 = time.perf_counter()
+            e2e_step()
+            t2 = time.perf_counter()
+            if i >= args.warmup:
+                e2e_times.append(t2 - t1)
     e2e_clk = e2e_clocks.stop()
     assert np.array_equal(hout.numpy()[:len(TAUS)], cb)
     e2e_t = max_over_ranks(float(np.mean(e2e_times)), ws)
@@ -699,12 +720,13 @@ def extra_cl1m(ubt, args, flush):
     del G
     _release()
     e2e_ms = []
-    for i in range(4):
-        torch.cuda.synchronize()
-        t1 = time.perf_counter()
-        ubt.count_host(g.n, g.src, g.dst, g.k, CL1M_TAUS)
-        if i:
-            e2e_ms.append(1e3 * (time.perf_counter() - t1))
+    with no_gc():
+        for i in range(4):
+            torch.cuda.synchronize()
+            t1 = time.perf_counter()
+            ubt.count_host(g.n, g.src, g.dst, g.k, CL1M_TAUS)
+            if i:
+                e2e_ms.append(1e3 * (time.perf_counter() - t1))
     res = {"workload": "Chung-Lu n=1,000,000 gamma=2.1 mean-deg 20 cap 50,000, P+ ~ Beta(0.5,0.5) -> k/65536, "
                        "4 thresholds in one traversal",
            "n": g.n, "m": g.m, "triangles": T, "ms": ms, "triangles_per_s": T / (ms / 1e3), "unpruned_ms": ms0,

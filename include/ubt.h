@@ -176,8 +176,10 @@ ubt_status ubt_graph_get_info(const ubt_graph* g, ubt_graph_info* h_info);
  *   h_tau     host double[n_tau], each in [0.5, 1], any order, 1 <= n_tau <= 64.
  *   prune     0: visit every triangle (Alg. 1).  1: skip edges and triangles
  *             that cannot reach the smallest threshold (Lemma 2 per edge;
- *             the order-free form of Lemma 3 per pair of edges); results are
- *             identical either way.
+ *             the order-free form of Lemma 3 per pair of edges, applied to
+ *             the streamed lists only when 2t - 1 >= 1/10 for the smallest
+ *             t: below that it removes too few entries to pay for itself);
+ *             results are identical either way.
  *   d_counts  device int64[2 * n_tau]: [0, n_tau) balanced counts,
  *             [n_tau, 2 n_tau) unbalanced counts, in the order of h_tau.
  * Graph kind: FIXED only (UBT_ERR_UNSUPPORTED otherwise).
@@ -333,7 +335,8 @@ ubt_status ubt_count_host(int64_t n, int64_t m, const uint32_t* h_src, const uin
  *             |N>(u)|, Lemma 2)
  *   h_out[1]  forward pairs (u, v) visited (same as h_out[0])
  *   h_out[2]  entries of N>(v) streamed and probed, summed over the pairs
- *             (pruned by Lemma 2 / the order-free Lemma 3 form when prune = 1)
+ *             (pruned by Lemma 2 / the order-free Lemma 3 form when prune = 1,
+ *             under the same rule as the query)
  *   h_out[3]  vertices with >= 2 forward entries (tasks)
  */
 ubt_status ubt_traversal_stats(ubt_graph* g, const double* h_tau, int32_t n_tau, int32_t prune,

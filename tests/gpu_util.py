@@ -37,6 +37,19 @@ def mixed_graph(n, m, seed):
     return synth.random_orientation(src, dst, seed + 9)
 
 
+def core_graph(n, m, core, seed):
+    """Random graph plus a clique on `core` seeded vertices (deduplicated,
+    randomly oriented)."""
+    import synth
+    s, d = synth.er_graph(n, m, seed)
+    c = np.sort(synth.rng(seed + 3).choice(n, size=core, replace=False)).astype(np.int64)
+    iu = np.triu_indices(core, 1)
+    a = np.concatenate([s.astype(np.int64), c[iu[0]]])
+    b = np.concatenate([d.astype(np.int64), c[iu[1]]])
+    key = np.unique(np.minimum(a, b) * n + np.maximum(a, b))
+    return synth.random_orientation((key // n).astype(np.uint32), (key % n).astype(np.uint32), seed + 5)
+
+
 def grad_report(got, want, gabs):
     """(ok mask, plain relative error per edge, edges where the floor applied)."""
     floor = 1e-3 * gabs

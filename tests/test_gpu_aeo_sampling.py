@@ -7,7 +7,7 @@ import pytest
 
 import oracle
 import synth
-from gpu_util import mixed_graph, require_gpu, sort_records
+from gpu_util import core_graph, mixed_graph, require_gpu, sort_records
 
 pytestmark = pytest.mark.gpu
 
@@ -84,6 +84,21 @@ def test_undirected_layout(ubt, case):
     assert np.array_equal(row[pos], owner) and np.array_equal(col[pos], other)
     du, dv = deg[owner], deg[other]
     assert np.all((du > dv) | ((du == dv) & (owner > other)))
+
+
+@pytest.mark.parametrize("knobs", [{"warp_sort_max": 128}, {"warp_sort_max": 512}, {"sort_smem_max": 256}])
+def test_undirected_layout_under_other_row_sorts(ubt, knobs):
+    """Undirected rows of every length up to ~620 (a planted 600-clique)
+    sorted by warps, by blocks of each class and in global memory give the
+    same layout, and Alg. 2 still counts as the oracle does."""
+    s, d = core_graph(3000, 20000, 600, 25)
+    k = synth.k_uniform(s.size, 26)
+    with with_knobs(ubt, knobs):
+        test_undirected_layout(ubt, ("core600", 3000, s, d, k))
+        G = ubt.Graph(3000, s, d, k=k, undirected=True)
+        ob, ou = oracle.count_threshold(3000, s, d, k, [0.6, 0.9])
+        gb, gu = G.count_aeo([0.6, 0.9])
+        assert np.array_equal(gb, ob) and np.array_equal(gu, ou)
 
 
 @pytest.mark.parametrize("case", CASES, ids=[c[0] for c in CASES])

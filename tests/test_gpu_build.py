@@ -5,7 +5,7 @@ import numpy as np
 import pytest
 
 import synth
-from gpu_util import mixed_graph, require_gpu
+from gpu_util import core_graph, mixed_graph, require_gpu
 
 pytestmark = pytest.mark.gpu
 
@@ -113,18 +113,6 @@ def test_long_lists_sorted_in_global_memory(ubt):
         check_export(ubt, ubt.Graph(3000, s, d, p=p), 3000, s, d, p=p)
     finally:
         ubt.set_tuning("sort_smem_max", old)
-
-
-def core_graph(n, m, core, seed):
-    """Random graph plus a clique on `core` seeded vertices (deduplicated,
-    randomly oriented)."""
-    s, d = synth.er_graph(n, m, seed)
-    c = np.sort(synth.rng(seed + 3).choice(n, size=core, replace=False)).astype(np.int64)
-    iu = np.triu_indices(core, 1)
-    a = np.concatenate([s.astype(np.int64), c[iu[0]]])
-    b = np.concatenate([d.astype(np.int64), c[iu[1]]])
-    key = np.unique(np.minimum(a, b) * n + np.maximum(a, b))
-    return synth.random_orientation((key // n).astype(np.uint32), (key % n).astype(np.uint32), seed + 5)
 
 
 @pytest.mark.parametrize("knobs", [{"warp_sort_max": 128}, {"warp_sort_max": 256},

@@ -503,7 +503,7 @@ def main():
     e2e_clocks = Clocks(dev if ws == 1 else local)
     e2e_clocks.start()
     with no_gc():
-        for i in range(args.warmup + max(5, args.steps // 2)):
+        for i in range(args.warmup + max(10, args.steps)):
             torch.cuda.synchronize()
             t1 = time.perf_counter()
             e2e_step()

@@ -5,9 +5,11 @@
 //   orient     each edge from its earlier endpoint in Node Order (degree,
 //              then id) to the later one                (Def. Node Order, Sec. 4)
 //   CSR        forward lists N>(u) as offsets + packed (neighbour, value)
-//   sort       each list by neighbour id (duplicate check), then -- FIXED
-//              graphs -- by |q| descending so that pruned entries (Lemma 2)
-//              form a suffix of every list
+//   sort       REAL graphs' lists by neighbour id (duplicates are equal
+//              neighbours); FIXED graphs' lists by |q| descending, then id,
+//              so that pruned entries (Lemma 2) form a suffix of every list,
+//              after a duplicate check (a lane match or a hash set per list;
+//              lists past the shared-memory limit are sorted by id first)
 //   pairs      every forward edge x-s is a pair owned by one endpoint: the
 //              one whose list becomes the hash table while the other
 //              endpoint's list is streamed through it (the shorter list is
@@ -141,7 +143,7 @@ __global__ void k_scatter(int64_t m, const uint32_t* __restrict__ src, const uin
   }
 }
 
-// sort keys: by neighbour id; FIXED graphs then by (32768 - |q|, id)
+// sort keys: by neighbour id (REAL rows); by (32768 - |q|, id) (FIXED and undirected rows)
 __device__ inline uint64_t key_by_col(uint64_t e) { return (uint64_t)adj_col(e); }
 __device__ inline uint64_t key_by_absq(uint64_t e) {
   const int32_t q = adj_q(e);

@@ -791,19 +791,31 @@ def extra_ego(ubt, args, flush):
     gen_s = time.perf_counter() - t0
     kp = torch.from_numpy(g.k.view(np.int32)).cuda()
     kb = kp[eg["eid"].long()]
+    nv = int(eg["v_off"][-1].item())
+
+    def make():
+        return ubt.Graph(nv, eg["src"], eg["dst"], k=kb, edge_key=eg["eid"], vertex_offsets=eg["v_off"])
+
+    from paper_2602_14084_gb300 import autotune as at
+    saved = at.current()
+    ng = int(eg["v_off"].numel()) - 1
+    counts = torch.empty(ng * 2 * len(EGO_TAUS), dtype=torch.int64, device="cuda")
+    expect = torch.empty(ng * 2, dtype=torch.float64, device="cuda")
+    worlds = torch.empty(ng * 64, dtype=torch.int64, device="cuda")
+    def run(G_):  # returns the outputs, which the tuner compares across configurations
+        G_.batch_query_(EGO_TAUS, 11, counts, expect, worlds)
+        return counts, expect, worlds
+
+    tuning = tuned(ubt, "batch", "ego10k", make, run, args)
     t0 = time.perf_counter()
-    G = ubt.Graph(int(eg["v_off"][-1].item()), eg["src"], eg["dst"], k=kb, edge_key=eg["eid"],
-                  vertex_offsets=eg["v_off"])
+    G = make()
     torch.cuda.synchronize()
     build_s = time.perf_counter() - t0
-    ng = G.n_graphs
+    assert G.n_graphs == ng
     m_total = G.m
     del kb, kp
     eg = {k: v for k, v in eg.items() if k in ("v_off",)}
     _release()
-    counts = torch.empty(ng * 2 * len(EGO_TAUS), dtype=torch.int64, device="cuda")
-    expect = torch.empty(ng * 2, dtype=torch.float64, device="cuda")
-    worlds = torch.empty(ng * 64, dtype=torch.int64, device="cuda")
     side = torch.cuda.Stream()
     side.wait_stream(torch.cuda.current_stream())
     with torch.cuda.stream(side):
@@ -822,9 +834,11 @@ def extra_ego(ubt, args, flush):
            "graphs": ng, "vertices": G.n, "edges": m_total, "triangles": int(round(tri)),
            "generate_s": gen_s, "build_s": build_s, "direct_ms": direct_ms, "graph_replay_ms": replay_ms,
            "replay_equals_direct": same, "triangles_per_s": tri / (replay_ms / 1e3),
-           "outputs": "per graph: counts at %s, E_bal/E_unbal, 64 world counts" % EGO_TAUS}
+           "outputs": "per graph: counts at %s, E_bal/E_unbal, 64 world counts" % EGO_TAUS,
+           "tuning": {k: tuning[k] for k in ("source", "config") if k in tuning}}
     del G, graph, counts, expect, worlds
     _release()
+    at.apply(saved)  # the later extras run with the knobs they had before
     return res
 
 

@@ -64,7 +64,8 @@ QUERY_KNOBS: Dict[str, List[str]] = {
                  "warp_threads", "smem_table_max", "pull"],
     "worlds": ["world_words_per_pass", "hub_threshold", "block_work", "block_unit", "small_batch",
                "blocks_per_sm", "long_tail", "long_min"],
-    "batch": ["block_work", "small_batch", "warp_threads", "blocks_per_sm"],
+    "batch": ["block_threads", "hub_threshold", "block_work", "block_unit", "small_batch", "warp_threads",
+              "blocks_per_sm", "long_tail", "long_min"],
 }
 ALL_KNOBS = {**BUILD_KNOBS, **RUN_KNOBS}
 

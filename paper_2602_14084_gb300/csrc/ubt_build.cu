@@ -403,11 +403,11 @@ ubt_status launch_mid_sorts(const uint32_t* rows, uint32_t nrows, const uint32_t
   return st;
 }
 
-// Lists of 513..4096 entries (at most the "sort_smem_max" tuning): one block
-// per list sorts 64-bit words (sort key << 12 | position in the list) in
-// shared memory; the keys are distinct by construction, so the network only
-// moves one word per comparator, and the entries are gathered by position
-// once at the end.
+// Lists longer than the "warp_sort_max" tuning (256) and at most
+// "sort_smem_max" (4096): one block per list sorts 64-bit words (sort key <<
+// 12 | position in the list) in shared memory; the keys are distinct by
+// construction, so the network only moves one word per comparator, and the
+// entries are gathered by position once at the end.
 constexpr int kPackedSortThreads = 512;
 constexpr int kPackedPerThread = 8;                  // 4096 entries / 512 threads
 constexpr uint32_t kPackedMax = kPackedSortThreads * kPackedPerThread;

@@ -183,8 +183,8 @@ struct Tuning {
   int64_t long_tail = 1;          // 1: the last < 64 entries of such a list join the short lists
   int64_t edge_index = 1;         // vertex queries: 0 never look pairs up in the edge index, 1 when cheaper, 2 always
   int64_t vertex_split = 64;      // vertex samples with longer pruned rows are spread over all blocks (edge index)
-  int64_t sort_smem_max = 4096;
-  int64_t warp_sort_max = 256;
+  int64_t sort_smem_max = 4096;   // longer forward lists are sorted in global memory
+  int64_t warp_sort_max = 256;    // lists up to this long are sorted by one warp in registers
 };
 Tuning& tuning();
 

@@ -328,9 +328,32 @@ struct CountMulti {
 // it, so r = b0 + #{S_j < P, b0 <= j < b0 + c} (c is 0 or 1 unless two
 // thresholds lie within 2^35 / 2^45 = 2^-10 of each other).  Bins 0 and 2 nt
 // (P classified at every threshold, the common case for confident edges)
-// are per-lane register counters; the others are shared 32-bit counters
-// with a carry word.
+// are per-lane register counters; the others are 32-bit counters in shared
+// memory, one set per warp, incremented without reading the old value.
+//
+// Overflow bound: a warp adds at most one per probed entry, and the bins are
+// moved to the global bins (an atomic exchange with 0, then a 64-bit add;
+// the exchange keeps adds made meanwhile) before a bin can reach 2^32:
+//   * degree-ordered traversal (CountBins): the warp counts the entries
+//     of each batch of pairs (probed(n); forward lists are shorter than
+//     sqrt(2m) < 2^17, so a batch of 32 lists counts at most 2^23), and lane
+//     0 moves the bins once the count reaches kWarpFlush = 2^31;
+//   * Alg. 2 kernels (CountBinsAeo, rows of any length): every lane counts
+//     the entries it was handed and moves the bins itself once its count
+//     reaches kBinFlush, so a bin holds fewer than 32 x 2^27 adds.
 constexpr int kSlices = 2049;
+// moves bins [1, top) to the global bins: an atomic exchange with 0 keeps the
+// adds other lanes make meanwhile (out of line: it runs at most once per
+// kBinFlush entries of a lane or kWarpFlush entries of a warp)
+static __device__ __noinline__ void count_bins_flush(uint32_t* bins, unsigned long long* out, int top) {
+  for (int i = 1; i < top; i++) {
+    const uint32_t v = atomicExch(&bins[i], 0u);
+    if (v) atomicAdd(&out[i], (unsigned long long)v);
+  }
+}
+constexpr int kBinStride = 144;                  // 32-bit words per warp's bins (>= 2 kMaxTau + 1)
+constexpr uint32_t kBinFlush = (1u << 27) - 64;  // entries per lane between flushes (Alg. 2 kernels)
+constexpr uint32_t kWarpFlush = 1u << 31;         // entries per warp between flushes (batch counts)
 struct CountBinsP {
   int nt;
   int64_t S[2 * kMaxTau];   // the 2 nt levels, ascending
@@ -342,13 +365,16 @@ struct CountBins {
   static constexpr bool kBatched = true;
   static constexpr int kRegCap = UBT_COUNT_REGCAP;
   static constexpr int kTabBytes = ((kSlices * 2 + 15) / 16) * 16;
-  static __host__ __device__ int smem_bytes(int) { return kTabBytes + 2 * kMaxTau * 8 + 2 * 2 * 144 * 4; }
+  static __host__ __device__ int smem_bytes(int threads) {
+    return kTabBytes + 2 * kMaxTau * 8 + (threads / 32) * kBinStride * 4;
+  }
   const uint16_t* tab;  // shared: slice table, b0 | c << 8
   const long long* S;   // shared: levels
-  uint32_t* lo;         // shared: bins, low words
-  uint32_t* hi;         // shared: bins, carries
+  uint32_t* bins;       // shared: this warp's bins
+  uint32_t* all;        // shared: every warp's bins, kBinStride words each
   unsigned long long* out;
   unsigned long long first = 0, last = 0;  // bins 0 and 2 nt of this lane
+  uint32_t since = 0;                       // entries since the last flush (this lane's or the warp's)
   int top;                                  // 2 nt
   __device__ CountBins(const P& p, char* smem) : out(p.out), top(2 * p.nt) {
     uint16_t* t = (uint16_t*)smem;
@@ -356,10 +382,10 @@ struct CountBins {
     uint32_t* b = (uint32_t*)(smem + kTabBytes + 2 * kMaxTau * 8);
     tab = t;
     S = sv;
-    lo = b;
-    hi = b + 144;
+    all = b;
+    bins = b + (threadIdx.x >> 5) * kBinStride;
     for (int i = threadIdx.x; i < 2 * p.nt; i += blockDim.x) sv[i] = p.S[i];
-    for (int i = threadIdx.x; i < 2 * 144; i += blockDim.x) b[i] = 0;
+    for (int i = threadIdx.x; i < (int)(blockDim.x >> 5) * kBinStride; i += blockDim.x) b[i] = 0;
     for (int i = threadIdx.x; i < kSlices; i += blockDim.x) {
       const long long start = (long long)i * (1ll << 35) - (1ll << 45);
       const long long end = start + (1ll << 35);
@@ -385,8 +411,7 @@ struct CountBins {
     } else if (r == top) {
       last++;
     } else {
-      const uint32_t old = atomicAdd(&lo[r], 1u);
-      if (old == 0xFFFFFFFFu) atomicAdd(&hi[r], 1u);
+      atomicAdd(&bins[r], 1u);
     }
   }
   __device__ __forceinline__ void step(bool hit, uint32_t, uint32_t, uint32_t, uint32_t quv, uint32_t quw,
@@ -400,6 +425,14 @@ struct CountBins {
     for (int s = 0; s < U; s++)
       if (hit[s]) count(tri_product(quv, quw[s], qvw[s]));
   }
+  // the degree-ordered traversal's batch count (all lanes, the same n)
+  __device__ __forceinline__ void probed(uint32_t n) {
+    since += n;
+    if (since >= kWarpFlush) {
+      if (lane_id() == 0) count_bins_flush(bins, out, top);
+      since = 0;
+    }
+  }
   __device__ void task_begin(uint32_t) {}
   __device__ void task_end(uint32_t) {}
   __device__ void block_end() {
@@ -409,9 +442,25 @@ struct CountBins {
       if (l) atomicAdd(&out[top], l);
     }
     __syncthreads();
+    const int nw = (int)(blockDim.x >> 5);
     for (int i = threadIdx.x + 1; i < top; i += blockDim.x) {
-      const unsigned long long v = ((unsigned long long)hi[i] << 32) | lo[i];
+      unsigned long long v = 0;
+      for (int w = 0; w < nw; w++) v += all[w * kBinStride + i];
       if (v) atomicAdd(&out[i], v);
+    }
+  }
+};
+
+// CountBins for the Alg. 2 kernels, whose rows have any length: every lane
+// counts the entries it was handed and moves its warp's bins itself
+struct CountBinsAeo : CountBins {
+  using CountBins::CountBins;
+  __device__ __forceinline__ void step(bool hit, uint32_t u, uint32_t v, uint32_t w, uint32_t quv, uint32_t quw,
+                                       uint32_t qvw, uint32_t puv, uint32_t puw, uint32_t pvw) {
+    CountBins::step(hit, u, v, w, quv, quw, qvw, puv, puw, pvw);
+    if (++since >= kBinFlush) {
+      count_bins_flush(bins, out, top);
+      since = 0;
     }
   }
 };
@@ -778,7 +827,7 @@ ubt_status count_impl(ubt_graph* g, const double* h_tau, int32_t n_tau, int32_t 
     }
     p.out = g->scratch->hist;
     UBT_CUDA(cudaMemsetAsync(g->scratch->hist, 0, sizeof(g->scratch->hist), s));
-    st = launch_count<CountBins>(g, p, L, aeo, s);
+    st = aeo ? launch_aeo<CountBinsAeo>(g, L, p, s) : launch_traverse<CountBins>(g, p, L, s);
     if (st != UBT_OK) return st;
     FinishMulti f;
     f.nt = n_tau;

@@ -41,10 +41,15 @@
 // (steps<U>: hit flags and the two streamed-edge values; the pair's is common).
 // A visitor sees a triangle as (x, s, w): the pair edge x-s, the table edge
 // x-w and the streamed edge s-w; under pull x is the later vertex of the pair,
-// so visitors treat the three edges symmetrically (they all do).
+// so visitors treat the three edges symmetrically (they all do).  A visitor
+// may also define probed(n): after each batch of at most 32 pairs the whole
+// warp calls it with n >= the number of entries the batch probed (the same n
+// in every lane).
 #pragma once
 
 #include <algorithm>
+#include <type_traits>
+#include <utility>
 
 #include "ubt_internal.cuh"
 
@@ -94,6 +99,12 @@ struct TravArgs {
 inline uint32_t light_prune_for(int64_t L) { return L > 0 && L < (1ll << 45) / 10 ? 1u : 0u; }
 
 __device__ __forceinline__ uint32_t hash_slot(uint32_t w, int shift) { return (w * 0x9E3779B1u) >> shift; }
+
+// visitors with a probed(n) member are told how many entries each batch probed
+template <class V, class = void>
+struct HasProbed : std::false_type {};
+template <class V>
+struct HasProbed<V, std::void_t<decltype(std::declval<V&>().probed(0u))>> : std::true_type {};
 
 // Self-checks record the first violated invariant in Scratch::guard and skip
 // the offending access: 1 probe limit (find), 2 probe limit (insert),
@@ -335,6 +346,7 @@ __device__ __forceinline__ void probe_pairs(const TravArgs& a, V& vis, const Tab
   const bool tail_short = a.long_tail != 0;
   const bool was_long = dv >= kLong;
   unsigned longm = __ballot_sync(kFull, was_long);
+  uint32_t probed = 0;  // entries of the long lists (the same in every lane)
   while (longm) {
     const int j = __ffs(longm) - 1;
     longm &= longm - 1;
@@ -342,6 +354,7 @@ __device__ __forceinline__ void probe_pairs(const TravArgs& a, V& vis, const Tab
     const uint32_t vj = __shfl_sync(kFull, pr.s, j);
     const uint32_t vsj = __shfl_sync(kFull, vs, j);
     const uint32_t dvj = __shfl_sync(kFull, dv, j);
+    if constexpr (HasProbed<V>::value) probed += dvj;
     const uint32_t qj = __shfl_sync(kFull, pr.qe, j);
     const uint32_t pj = __shfl_sync(kFull, pr.pe, j);
     uint32_t off = 0;
@@ -415,6 +428,8 @@ __device__ __forceinline__ void probe_pairs(const TravArgs& a, V& vis, const Tab
         vis.step(hit, uj, vj, adj_col(e[s]), qj, quw, adj_valbits(e[s]), pj, puw, f[s]);
     }
   }
+  // a long list's tail streamed with the short lists is counted twice: an upper bound
+  if constexpr (HasProbed<V>::value) vis.probed(probed + total);
 }
 
 // This lane's pair among the pairs [ps, ps + cnt) of owner x.  A pair whose

@@ -153,6 +153,19 @@ def tuned(ubt, query, variant, make, run, args, budget_s=None):
 
 
 
+def merge_model_bytes(n, src, dst):
+    """Bytes of Alg. 1 under the merge model of its analysis (Sec. 4): every
+    forward edge u -> v reads both forward lists once, 8 B per entry, i.e.
+    8 * sum over forward edges of (d+(u) + d+(v)).  Forward = from the earlier
+    endpoint in Node Order (degree, then id)."""
+    a, b = np.asarray(src, dtype=np.int64), np.asarray(dst, dtype=np.int64)
+    deg = np.bincount(a, minlength=n) + np.bincount(b, minlength=n)
+    a_first = (deg[a] < deg[b]) | ((deg[a] == deg[b]) & (a < b))
+    u, v = np.where(a_first, a, b), np.where(a_first, b, a)
+    dplus = np.bincount(u, minlength=n)
+    return 8 * int(dplus[u].sum() + dplus[v].sum())
+
+
 def alg_bytes_of(st):
     """Algorithmic bytes of one traversal (ubt_traversal_stats sizes): 8 B per
     table entry, 24 B per pair (its pair word, its edge's CSR entry and the
@@ -458,7 +471,8 @@ def main():
                 "kernel": kname, "peak_kind": pk_kind,
                 "alg_bytes_per_launch": alg_bytes, "streamed_entries": st["streamed"],
                 "table_entries": st["table_entries"], "pairs": st["pairs"],
-                "alg1_probes": info["wedges"]}
+                "alg1_probes": info["wedges"],
+                "merge_model_bytes": merge_model_bytes(g.n, g.src, g.dst)}
     st0 = G.traversal_stats(TAUS, prune=False)
     golden = golden_sweep(g)
     if golden is not None:
